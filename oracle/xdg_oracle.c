@@ -1,0 +1,572 @@
+/*
+ * xdg_oracle.c -- plain, slow, FP64 CPU oracle of the XDG multigrid solve.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the tests, the smoke check and the CPU-baseline leg of the
+ * benchmark load this library. The CUDA library never links, calls or includes it, and it
+ * includes nothing of the CUDA library.
+ *
+ * Kummer, Smuda, Weber, "BoSSS: a package for multigrid extended discontinuous Galerkin
+ * methods", arXiv 2003.02431. What each function follows:
+ *   or_bsr_spmv      the matrix form M^lambda U = b^lambda of the agglomerated system,
+ *                    Eq. (GenericMatrixSystem), sec. 3.2 "Agglomeration Algebra"
+ *   or_galerkin      M^{lambda+1} = (R^{X,lambda})^T M^lambda R^{X,lambda}, Eq. (XDGsysRestriction)
+ *   or_restrict      r_c := (R^{X,lambda})^T r, restriction step of Algorithm 4 (OrthoMG)
+ *   or_prolong       z := R^{X,lambda} z_c, prolongation step of Algorithm 4
+ *   block Jacobi     per-cell dense direct solves of the blocks M_{I_j,I_j} (the cell-local
+ *                    dense solves of Algorithm 1, used as a damped point-block smoother,
+ *                    i.e. the one-cell, no-overlap case of the Schwarz blocks of Algorithm 2)
+ *   coarse solve     direct solve on the coarsest level (sec. 3.3: sparse direct solver with a
+ *                    stored factorisation); here a dense Cholesky factorisation
+ *   or_vcycle        the level recursion of Algorithm 4 (pre-smoother, restrict, coarse
+ *                    correction, prolong, post-smoother) without the residual-minimisation
+ *                    steps: a symmetric V-cycle used as a preconditioner
+ *   or_pcg           conjugate gradients preconditioned by the V-cycle (the paper pairs its
+ *                    multigrid preconditioners with a Krylov method, sec. 3.3)
+ *   lambda_max       Lanczos estimate of the largest eigenvalue of D^{-1} M, used to set the
+ *                    smoother damping omega = 4/(3 lambda_max); the paper gives no damping rule.
+ *
+ * Plain loops only; OpenMP parallelises independent rows, nothing is blocked or fused.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MAXL 24
+
+/* ---------------- operator apply ---------------- */
+
+/* y = A x for a BSR matrix with Np x Np row-major blocks */
+void or_bsr_spmv(int64_t nb, int Np, const int64_t* rp, const int32_t* col, const double* val,
+                 const double* x, double* y) {
+  const int64_t Np2 = (int64_t)Np * Np;
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < nb; ++i) {
+    for (int r = 0; r < Np; ++r) {
+      double s = 0.0;
+      for (int64_t z = rp[i]; z < rp[i + 1]; ++z) {
+        const double* blk = val + z * Np2;
+        const double* xj = x + (int64_t)col[z] * Np;
+        for (int c = 0; c < Np; ++c) s += blk[r * Np + c] * xj[c];
+      }
+      y[i * Np + r] = s;
+    }
+  }
+}
+
+/* r = b - A x */
+void or_residual(int64_t nb, int Np, const int64_t* rp, const int32_t* col, const double* val,
+                 const double* b, const double* x, double* r) {
+  or_bsr_spmv(nb, Np, rp, col, val, x, r);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < nb * Np; ++i) r[i] = b[i] - r[i];
+}
+
+/* ---------------- transfers ---------------- */
+
+/* rc = R^T r : rc[agg[f]] += R_f^T r_f */
+void or_restrict(int64_t nbf, int64_t nbc, int Np, const int32_t* agg, const double* R,
+                 const double* r, double* rc) {
+  const int64_t Np2 = (int64_t)Np * Np;
+  memset(rc, 0, sizeof(double) * nbc * Np);
+  for (int64_t f = 0; f < nbf; ++f) {
+    const double* Rf = R + f * Np2;
+    double* o = rc + (int64_t)agg[f] * Np;
+    for (int n = 0; n < Np; ++n) {
+      double s = 0.0;
+      for (int m = 0; m < Np; ++m) s += Rf[m * Np + n] * r[f * Np + m];
+      o[n] += s;
+    }
+  }
+}
+
+/* x += R zc : x_f += R_f zc[agg[f]] */
+void or_prolong(int64_t nbf, int Np, const int32_t* agg, const double* R, const double* zc,
+                double* x) {
+  const int64_t Np2 = (int64_t)Np * Np;
+#pragma omp parallel for schedule(static)
+  for (int64_t f = 0; f < nbf; ++f) {
+    const double* Rf = R + f * Np2;
+    const double* z = zc + (int64_t)agg[f] * Np;
+    for (int m = 0; m < Np; ++m) {
+      double s = 0.0;
+      for (int n = 0; n < Np; ++n) s += Rf[m * Np + n] * z[n];
+      x[f * Np + m] += s;
+    }
+  }
+}
+
+/* ---------------- Galerkin product ---------------- */
+
+static int cmp_i32(const void* a, const void* b) {
+  int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+  return (x > y) - (x < y);
+}
+
+/* Mc = R^T M R. Output arrays are malloc'ed (release with or_free). Returns 0 on success. */
+int or_galerkin(int64_t nbf, int64_t nbc, int Np, const int64_t* rp, const int32_t* col,
+                const double* val, const int32_t* agg, const double* R, int64_t** rp_c,
+                int32_t** col_c, double** val_c, int64_t* nnz_c) {
+  const int64_t Np2 = (int64_t)Np * Np;
+  /* children of every coarse block */
+  int64_t* cp = (int64_t*)calloc(nbc + 1, sizeof(int64_t));
+  int64_t* ch = (int64_t*)malloc(sizeof(int64_t) * (nbf > 0 ? nbf : 1));
+  if (!cp || !ch) return -1;
+  for (int64_t f = 0; f < nbf; ++f) cp[agg[f] + 1]++;
+  for (int64_t I = 0; I < nbc; ++I) cp[I + 1] += cp[I];
+  {
+    int64_t* pos = (int64_t*)malloc(sizeof(int64_t) * (nbc > 0 ? nbc : 1));
+    for (int64_t I = 0; I < nbc; ++I) pos[I] = cp[I];
+    for (int64_t f = 0; f < nbf; ++f) ch[pos[agg[f]]++] = f;
+    free(pos);
+  }
+  /* symbolic: coarse columns of every coarse row */
+  int64_t* rc = (int64_t*)calloc(nbc + 1, sizeof(int64_t));
+  int32_t** cols = (int32_t**)malloc(sizeof(int32_t*) * (nbc > 0 ? nbc : 1));
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t I = 0; I < nbc; ++I) {
+    int64_t cnt = 0;
+    for (int64_t t = cp[I]; t < cp[I + 1]; ++t) cnt += rp[ch[t] + 1] - rp[ch[t]];
+    int32_t* lst = (int32_t*)malloc(sizeof(int32_t) * (cnt > 0 ? cnt : 1));
+    int64_t n = 0;
+    for (int64_t t = cp[I]; t < cp[I + 1]; ++t)
+      for (int64_t z = rp[ch[t]]; z < rp[ch[t] + 1]; ++z) lst[n++] = agg[col[z]];
+    qsort(lst, n, sizeof(int32_t), cmp_i32);
+    int64_t u = 0;
+    for (int64_t q = 0; q < n; ++q)
+      if (u == 0 || lst[q] != lst[u - 1]) lst[u++] = lst[q];
+    cols[I] = lst;
+    rc[I + 1] = u;
+  }
+  for (int64_t I = 0; I < nbc; ++I) rc[I + 1] += rc[I];
+  int64_t nnz = rc[nbc];
+  int32_t* cc = (int32_t*)malloc(sizeof(int32_t) * (nnz > 0 ? nnz : 1));
+  double* vc = (double*)calloc((size_t)(nnz > 0 ? nnz : 1) * Np2, sizeof(double));
+  if (!cc || !vc) return -1;
+  /* numeric: block (I, J) += R_i^T M_ij R_j */
+#pragma omp parallel
+  {
+    double* tmp = (double*)malloc(sizeof(double) * Np2);
+#pragma omp for schedule(dynamic, 64)
+    for (int64_t I = 0; I < nbc; ++I) {
+      int64_t len = rc[I + 1] - rc[I];
+      memcpy(cc + rc[I], cols[I], sizeof(int32_t) * len);
+      for (int64_t t = cp[I]; t < cp[I + 1]; ++t) {
+        int64_t i = ch[t];
+        const double* Ri = R + i * Np2;
+        for (int64_t z = rp[i]; z < rp[i + 1]; ++z) {
+          int64_t j = col[z];
+          const double* Mij = val + z * Np2;
+          const double* Rj = R + j * Np2;
+          int32_t J = agg[j];
+          /* position of J in the row */
+          int64_t lo = rc[I], hi = rc[I + 1] - 1;
+          while (lo < hi) {
+            int64_t mid = (lo + hi) / 2;
+            if (cc[mid] < J) lo = mid + 1;
+            else hi = mid;
+          }
+          double* dst = vc + lo * Np2;
+          /* tmp = M_ij R_j */
+          for (int a = 0; a < Np; ++a)
+            for (int n = 0; n < Np; ++n) {
+              double s = 0.0;
+              for (int b = 0; b < Np; ++b) s += Mij[a * Np + b] * Rj[b * Np + n];
+              tmp[a * Np + n] = s;
+            }
+          /* dst += R_i^T tmp */
+          for (int m = 0; m < Np; ++m)
+            for (int n = 0; n < Np; ++n) {
+              double s = 0.0;
+              for (int a = 0; a < Np; ++a) s += Ri[a * Np + m] * tmp[a * Np + n];
+              dst[m * Np + n] += s;
+            }
+        }
+      }
+    }
+    free(tmp);
+  }
+  for (int64_t I = 0; I < nbc; ++I) free(cols[I]);
+  free(cols);
+  free(cp);
+  free(ch);
+  *rp_c = rc;
+  *col_c = cc;
+  *val_c = vc;
+  *nnz_c = nnz;
+  return 0;
+}
+
+void or_free(void* p) { free(p); }
+
+/* ---------------- dense helpers ---------------- */
+
+/* in-place Cholesky (lower) of an n x n row-major matrix; returns 0 if SPD */
+static int chol(int64_t n, double* A) {
+  for (int64_t j = 0; j < n; ++j) {
+    double s = A[j * n + j];
+    for (int64_t p = 0; p < j; ++p) s -= A[j * n + p] * A[j * n + p];
+    if (!(s > 0.0)) return -1;
+    double d = sqrt(s);
+    A[j * n + j] = d;
+    for (int64_t i = j + 1; i < n; ++i) {
+      double t = A[i * n + j];
+      for (int64_t p = 0; p < j; ++p) t -= A[i * n + p] * A[j * n + p];
+      A[i * n + j] = t / d;
+    }
+  }
+  return 0;
+}
+
+/* x = (L L^T)^{-1} b */
+static void chol_solve(int64_t n, const double* L, const double* b, double* x) {
+  for (int64_t i = 0; i < n; ++i) {
+    double s = b[i];
+    for (int64_t p = 0; p < i; ++p) s -= L[i * n + p] * x[p];
+    x[i] = s / L[i * n + i];
+  }
+  for (int64_t i = n - 1; i >= 0; --i) {
+    double s = x[i];
+    for (int64_t p = i + 1; p < n; ++p) s -= L[p * n + i] * x[p];
+    x[i] = s / L[i * n + i];
+  }
+}
+
+/* ---------------- hierarchy ---------------- */
+
+typedef struct {
+  int64_t nb;
+  int64_t* rp;
+  int32_t* col;
+  double* val;
+  int owns;          /* rp/col/val allocated here (coarse levels) */
+  double* Dchol;     /* Cholesky factors of the diagonal blocks */
+  double lmax, omega;
+  const int32_t* agg; /* to the next level */
+  const double* R;
+  double* w[4];      /* work vectors */
+} or_level;
+
+typedef struct {
+  int Np, nlev, nu, gamma;
+  or_level L[OR_MAXL];
+  double* cchol; /* dense Cholesky factor of the coarsest operator */
+  int64_t nc;
+  double* pv[5]; /* PCG vectors */
+} or_hier;
+
+static double dot(int64_t n, const double* a, const double* b) {
+  double s = 0.0;
+#pragma omp parallel for reduction(+ : s) schedule(static)
+  for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+  return s;
+}
+
+/* z_b = D_b^{-1} r_b for every block */
+static void bj_apply(const or_level* L, int Np, const double* r, double* z) {
+  const int64_t Np2 = (int64_t)Np * Np;
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < L->nb; ++i) chol_solve(Np, L->Dchol + i * Np2, r + i * Np, z + i * Np);
+}
+
+/* Counter-based start vector for the Lanczos estimate (Knuth multiplicative hash):
+ * v_i = (((i+1) * 2654435761) mod 2^32) / 2^32 - 0.5 */
+static double start_entry(int64_t i) {
+  uint32_t h = (uint32_t)((uint64_t)(i + 1) * 2654435761ull);
+  return (double)h / 4294967296.0 - 0.5;
+}
+
+/* largest eigenvalue of a symmetric tridiagonal matrix (bisection on Sturm counts) */
+static double tridiag_max(int m, const double* a, const double* b) {
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < m; ++i) {
+    double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < m - 1 ? fabs(b[i]) : 0.0);
+    if (a[i] - r < lo) lo = a[i] - r;
+    if (a[i] + r > hi) hi = a[i] + r;
+  }
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    /* number of eigenvalues < mid */
+    int cnt = 0;
+    double q = a[0] - mid;
+    if (q < 0) cnt++;
+    for (int i = 1; i < m; ++i) {
+      if (q == 0.0) q = 1e-300;
+      q = a[i] - mid - b[i - 1] * b[i - 1] / q;
+      if (q < 0) cnt++;
+    }
+    if (cnt >= m) hi = mid;
+    else lo = mid;
+    if (hi - lo <= 1e-15 * fabs(hi)) break;
+  }
+  return hi;
+}
+
+/* m-step Lanczos in the D inner product for the pencil (M, D) */
+static double lambda_max(or_level* L, int Np, int m) {
+  const int64_t n = L->nb * Np, Np2 = (int64_t)Np * Np;
+  double* q = (double*)calloc(n, sizeof(double));
+  double* qp = (double*)calloc(n, sizeof(double));
+  double* u = (double*)malloc(sizeof(double) * n);
+  double* w = (double*)malloc(sizeof(double) * n);
+  double* Dw = (double*)malloc(sizeof(double) * n);
+  double al[64], be[64];
+  for (int64_t i = 0; i < n; ++i) q[i] = start_entry(i);
+  /* D q: D_b = L_b L_b^T */
+  for (int64_t b = 0; b < L->nb; ++b) {
+    const double* Lc = L->Dchol + b * Np2;
+    for (int r = 0; r < Np; ++r) {
+      double s = 0.0;
+      for (int c = 0; c < Np; ++c) {
+        double d = 0.0; /* (L L^T)_{rc} */
+        for (int p = 0; p <= (r < c ? r : c); ++p) d += Lc[r * Np + p] * Lc[c * Np + p];
+        s += d * q[b * Np + c];
+      }
+      Dw[b * Np + r] = s;
+    }
+  }
+  double nrm = sqrt(dot(n, q, Dw));
+  for (int64_t i = 0; i < n; ++i) q[i] /= nrm;
+  double bprev = 0.0;
+  int steps = 0;
+  for (int j = 0; j < m; ++j) {
+    or_bsr_spmv(L->nb, Np, L->rp, L->col, L->val, q, u);
+    al[j] = dot(n, q, u);
+    bj_apply(L, Np, u, w);
+    for (int64_t i = 0; i < n; ++i) w[i] -= al[j] * q[i] + bprev * qp[i];
+    for (int64_t b = 0; b < L->nb; ++b) {
+      const double* Lc = L->Dchol + b * Np2;
+      for (int r = 0; r < Np; ++r) {
+        double s = 0.0;
+        for (int c = 0; c < Np; ++c) {
+          double d = 0.0;
+          for (int p = 0; p <= (r < c ? r : c); ++p) d += Lc[r * Np + p] * Lc[c * Np + p];
+          s += d * w[b * Np + c];
+        }
+        Dw[b * Np + r] = s;
+      }
+    }
+    steps = j + 1;
+    double bj = sqrt(dot(n, w, Dw));
+    be[j] = bj;
+    if (!(bj > 1e-300)) break;
+    for (int64_t i = 0; i < n; ++i) {
+      qp[i] = q[i];
+      q[i] = w[i] / bj;
+    }
+    bprev = bj;
+  }
+  double lm = tridiag_max(steps, al, be);
+  free(q);
+  free(qp);
+  free(u);
+  free(w);
+  free(Dw);
+  return lm;
+}
+
+/* Build the hierarchy: level-1 operator plus per-level (agg, R). All input arrays must stay
+ * alive while the hierarchy exists. omega > 0 fixes the damping on every level; otherwise
+ * omega_l = 4/(3 lambda_max(D^{-1} M^l)) from lanczos_steps Lanczos steps.
+ * Returns NULL on failure (not SPD). */
+void* or_hier_create(int nlev, int Np, int64_t nb1, const int64_t* rp, const int32_t* col,
+                     const double* val, const int64_t* nbs, const int32_t* const* aggs,
+                     const double* const* Rs, double omega, int lanczos_steps, int nu,
+                     int gamma) {
+  if (nlev < 1 || nlev > OR_MAXL) return NULL;
+  or_hier* H = (or_hier*)calloc(1, sizeof(or_hier));
+  H->Np = Np;
+  H->nlev = nlev;
+  H->nu = nu < 1 ? 1 : nu;
+  H->gamma = gamma < 1 ? 1 : gamma;
+  const int64_t Np2 = (int64_t)Np * Np;
+  H->L[0].nb = nb1;
+  H->L[0].rp = (int64_t*)rp;
+  H->L[0].col = (int32_t*)col;
+  H->L[0].val = (double*)val;
+  for (int l = 0; l < nlev; ++l) {
+    or_level* L = &H->L[l];
+    if (l > 0) {
+      int64_t nnz;
+      if (or_galerkin(H->L[l - 1].nb, nbs[l], Np, H->L[l - 1].rp, H->L[l - 1].col,
+                      H->L[l - 1].val, aggs[l - 1], Rs[l - 1], &L->rp, &L->col, &L->val, &nnz))
+        return NULL;
+      L->nb = nbs[l];
+      L->owns = 1;
+    }
+    if (l + 1 < nlev) {
+      L->agg = aggs[l];
+      L->R = Rs[l];
+    }
+    for (int t = 0; t < 4; ++t) L->w[t] = (double*)calloc(L->nb * Np, sizeof(double));
+    if (l + 1 < nlev) {
+      L->Dchol = (double*)malloc(sizeof(double) * L->nb * Np2);
+      int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+      for (int64_t i = 0; i < L->nb; ++i) {
+        double* Dc = L->Dchol + i * Np2;
+        int64_t z = L->rp[i];
+        while (z < L->rp[i + 1] && L->col[z] != i) ++z;
+        if (z == L->rp[i + 1]) {
+          bad |= 1;
+          continue;
+        }
+        memcpy(Dc, L->val + z * Np2, sizeof(double) * Np2);
+        if (chol(Np, Dc)) bad |= 1;
+      }
+      if (bad) return NULL;
+      L->lmax = lambda_max(L, Np, lanczos_steps);
+      L->omega = omega > 0 ? omega : 4.0 / (3.0 * L->lmax);
+    }
+  }
+  /* coarsest level: dense Cholesky */
+  or_level* C = &H->L[nlev - 1];
+  H->nc = C->nb * Np;
+  H->cchol = (double*)calloc((size_t)H->nc * H->nc, sizeof(double));
+  for (int64_t i = 0; i < C->nb; ++i)
+    for (int64_t z = C->rp[i]; z < C->rp[i + 1]; ++z)
+      for (int r = 0; r < Np; ++r)
+        for (int c = 0; c < Np; ++c)
+          H->cchol[(i * Np + r) * H->nc + (int64_t)C->col[z] * Np + c] = C->val[z * Np2 + r * Np + c];
+  if (chol(H->nc, H->cchol)) return NULL;
+  for (int t = 0; t < 5; ++t) H->pv[t] = (double*)calloc(nb1 * Np, sizeof(double));
+  return H;
+}
+
+void or_hier_free(void* h) {
+  or_hier* H = (or_hier*)h;
+  if (!H) return;
+  for (int l = 0; l < H->nlev; ++l) {
+    or_level* L = &H->L[l];
+    if (L->owns) {
+      free(L->rp);
+      free(L->col);
+      free(L->val);
+    }
+    free(L->Dchol);
+    for (int t = 0; t < 4; ++t) free(L->w[t]);
+  }
+  free(H->cchol);
+  for (int t = 0; t < 5; ++t) free(H->pv[t]);
+  free(H);
+}
+
+/* level information: nb, nnzb, omega, lambda_max; pointers to the level's BSR arrays */
+int or_hier_level(void* h, int l, int64_t* nb, int64_t* nnzb, double* omega, double* lmax,
+                  const int64_t** rp, const int32_t** col, const double** val) {
+  or_hier* H = (or_hier*)h;
+  if (l < 0 || l >= H->nlev) return -1;
+  or_level* L = &H->L[l];
+  *nb = L->nb;
+  *nnzb = L->rp[L->nb];
+  *omega = L->omega;
+  *lmax = L->lmax;
+  *rp = L->rp;
+  *col = L->col;
+  *val = L->val;
+  return 0;
+}
+
+/* one damped block-Jacobi step on level l: x += omega D^{-1} (b - M x) */
+void or_smooth(void* h, int l, const double* b, double* x) {
+  or_hier* H = (or_hier*)h;
+  or_level* L = &H->L[l];
+  const int Np = H->Np;
+  const int64_t n = L->nb * Np;
+  or_residual(L->nb, Np, L->rp, L->col, L->val, b, x, L->w[2]);
+  bj_apply(L, Np, L->w[2], L->w[3]);
+  for (int64_t i = 0; i < n; ++i) x[i] += L->omega * L->w[3][i];
+}
+
+/* z = M_coarsest^{-1} r */
+void or_coarse_solve(void* h, const double* r, double* z) {
+  or_hier* H = (or_hier*)h;
+  chol_solve(H->nc, H->cchol, r, z);
+}
+
+static void vcycle_rec(or_hier* H, int l, const double* b, double* x) {
+  const int Np = H->Np;
+  or_level* L = &H->L[l];
+  const int64_t n = L->nb * Np;
+  if (l == H->nlev - 1) {
+    chol_solve(H->nc, H->cchol, b, x);
+    return;
+  }
+  /* pre-smoothing from x = 0 */
+  bj_apply(L, Np, b, x);
+  for (int64_t i = 0; i < n; ++i) x[i] *= L->omega;
+  for (int s = 1; s < H->nu; ++s) or_smooth(H, l, b, x);
+  /* restrict the residual */
+  double* r = L->w[0];
+  or_residual(L->nb, Np, L->rp, L->col, L->val, b, x, r);
+  or_level* Lc = &H->L[l + 1];
+  double* bc = (double*)malloc(sizeof(double) * Lc->nb * Np);
+  double* zc = (double*)malloc(sizeof(double) * Lc->nb * Np);
+  or_restrict(L->nb, Lc->nb, Np, L->agg, L->R, r, bc);
+  /* coarse-grid correction: gamma steps of the coarse cycle from zero (gamma = 1: V-cycle,
+   * gamma = 2: W-cycle); each step z_c += B_c (r_c - M_c z_c) keeps the cycle symmetric */
+  vcycle_rec(H, l + 1, bc, zc);
+  if (H->gamma > 1 && l + 2 < H->nlev) {
+    double* rc2 = (double*)malloc(sizeof(double) * Lc->nb * Np);
+    double* dz = (double*)malloc(sizeof(double) * Lc->nb * Np);
+    for (int g = 1; g < H->gamma; ++g) {
+      or_residual(Lc->nb, Np, Lc->rp, Lc->col, Lc->val, bc, zc, rc2);
+      vcycle_rec(H, l + 1, rc2, dz);
+      for (int64_t i = 0; i < Lc->nb * Np; ++i) zc[i] += dz[i];
+    }
+    free(rc2);
+    free(dz);
+  }
+  or_prolong(L->nb, Np, L->agg, L->R, zc, x);
+  free(zc);
+  free(bc);
+  /* post-smoothing */
+  for (int s = 0; s < H->nu; ++s) or_smooth(H, l, b, x);
+}
+
+/* x = B b, one symmetric V-cycle from a zero initial guess */
+void or_vcycle(void* h, const double* b, double* x) { vcycle_rec((or_hier*)h, 0, b, x); }
+
+/* PCG on level 1 with the V-cycle preconditioner. x holds the initial guess on entry.
+ * Stops when ||r||_2 <= tol ||b||_2 (recursive residual) or after maxit iterations.
+ * hist (optional, maxit+1 entries) receives ||r||/||b|| per iteration.
+ * Returns the number of iterations; *relres is the true final relative residual. */
+int or_pcg(void* h, const double* b, double* x, double tol, int maxit, double* relres,
+           double* hist) {
+  or_hier* H = (or_hier*)h;
+  or_level* L = &H->L[0];
+  const int Np = H->Np;
+  const int64_t n = L->nb * Np;
+  double *r = H->pv[0], *z = H->pv[1], *p = H->pv[2], *q = H->pv[3];
+  or_residual(L->nb, Np, L->rp, L->col, L->val, b, x, r);
+  double bn = sqrt(dot(n, b, b));
+  if (bn == 0.0) bn = 1.0;
+  double rn = sqrt(dot(n, r, r));
+  if (hist) hist[0] = rn / bn;
+  int it = 0;
+  if (rn / bn > tol) {
+    or_vcycle(H, r, z);
+    memcpy(p, z, sizeof(double) * n);
+    double rho = dot(n, r, z);
+    for (it = 1; it <= maxit; ++it) {
+      or_bsr_spmv(L->nb, Np, L->rp, L->col, L->val, p, q);
+      double alpha = rho / dot(n, p, q);
+      for (int64_t i = 0; i < n; ++i) {
+        x[i] += alpha * p[i];
+        r[i] -= alpha * q[i];
+      }
+      rn = sqrt(dot(n, r, r));
+      if (hist) hist[it] = rn / bn;
+      if (rn / bn <= tol) break;
+      or_vcycle(H, r, z);
+      double rho2 = dot(n, r, z);
+      double beta = rho2 / rho;
+      rho = rho2;
+      for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+    }
+    if (it > maxit) it = maxit;
+  }
+  or_residual(L->nb, Np, L->rp, L->col, L->val, b, x, r);
+  *relres = sqrt(dot(n, r, r)) / bn;
+  return it;
+}
