@@ -1,0 +1,195 @@
+/*
+ * xdg.h -- C ABI of libxdg: the multigrid-preconditioned solve of the agglomerated XDG
+ * (extended discontinuous Galerkin, cut-cell) symmetric-interior-penalty Poisson system on
+ * one GPU (sm_103a).
+ *
+ * Reference: F. Kummer, M. Smuda, J. Weber, "BoSSS: a package for multigrid extended
+ * discontinuous Galerkin methods", arXiv 2003.02431.
+ *
+ * The operation each entry point performs is defined by the paper:
+ *   - the system M^1 U = b^1 in per-cell block form: sec. 3.2 "Agglomeration Algebra",
+ *     Eq. (GenericMatrixSystem); one Np x Np block per agglomerated cut cell, Np = C(k+D, D)
+ *   - the aggregation maps and transfer blocks R^{X,lambda}: sec. 3.1-3.2,
+ *     Eq. (XDGrestrictionMatrix) (Phi^{lambda+1} = Phi^lambda R^{X,lambda})
+ *   - coarse operators M^{lambda+1} = (R^{X,lambda})^T M^lambda R^{X,lambda}:
+ *     Eq. (XDGsysRestriction)
+ *   - the level recursion (smoothing, restriction r_c = R^T r, coarse correction,
+ *     prolongation z = R z_c, smoothing): Algorithm 4 (orthonormalisation multigrid) without
+ *     its residual-minimisation steps, used here as a symmetric preconditioner
+ *   - the smoother: damped block Jacobi, i.e. cell-local dense direct solves with the diagonal
+ *     blocks (the per-cell dense solves of Algorithm 1, one-cell blocks of Algorithm 2)
+ *   - the coarsest-level direct solve: sec. 3.3 (direct solver with a stored factorisation)
+ *   - the Krylov outer method: sec. 3.3 (multigrid as preconditioner of a Krylov solver);
+ *     here conjugate gradients, since M is symmetric positive definite (sec. 4)
+ *
+ * Conventions (all entry points):
+ *   - Return value: XDG_OK (0) or an error code below; xdg_strerror() names it and
+ *     xdg_last_error() gives the message of the most recent failure on the calling thread.
+ *   - Vectors are FP64, block-ordered ([nb][Np], block b holds the Np modal coefficients of
+ *     block b). "device" pointers are CUDA global-memory pointers on the handle's device,
+ *     owned by the caller; "host" pointers are ordinary host memory owned by the caller.
+ *   - Work is enqueued on the handle's stream (the stream given at creation). Entry points
+ *     that return results to the host (xdg_solve, xdg_solve_host, xdg_get_info,
+ *     xdg_export_level) synchronise that stream before returning; the others are
+ *     asynchronous with respect to the host.
+ *   - apply / smooth / restrict / prolong / coarse_solve / vcycle / solve allocate no memory:
+ *     all work buffers belong to the handle and are allocated by xdg_create_hierarchy.
+ *   - There is no CPU fallback: every step of the solve runs in libxdg's CUDA kernels. Calls
+ *     fail with XDG_ECUDA when no usable GPU is present.
+ *   - A handle is not thread-safe; concurrent calls on one handle must be serialised by the
+ *     caller. Different handles are independent.
+ */
+#ifndef XDG_H
+#define XDG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  XDG_OK = 0,
+  XDG_EINVAL = 1,      /* invalid argument, inconsistent sizes or indices, unsupported Np */
+  XDG_ECUDA = 2,       /* CUDA runtime error (no device, launch failure, ...) */
+  XDG_ENOMEM = 3,      /* device memory allocation failed */
+  XDG_ENOTCONV = 4,    /* iteration limit reached; x and info hold the last iterate */
+  XDG_EBREAKDOWN = 5,  /* Krylov breakdown (non-positive curvature, non-finite values) or an
+                          operator block that is not positive definite */
+  XDG_ETIMEOUT = 6     /* the solve exceeded its time budget; x and info hold the last iterate */
+};
+
+/* storage precision of the operator blocks used by an apply or an inner solve */
+enum { XDG_PREC_F64 = 0, XDG_PREC_F32 = 1, XDG_PREC_BF16 = 2 };
+
+typedef struct xdg_hier* xdg_hier_t;
+
+/* The linear system and its aggregation hierarchy, as host arrays (caller-owned; the library
+ * deep-copies them to the device in xdg_create_hierarchy and keeps no reference).
+ *   Np          block size (modes per block), 1 <= Np <= 32
+ *   n_levels    number of aggregation levels (>= 1); level 1 is the finest
+ *   nb[l]       number of blocks on level l+1, l = 0..n_levels-1
+ *   row_ptr     int64[nb[0]+1], BSR row pointer of M^1 (row_ptr[0] = 0, non-decreasing)
+ *   col         int32[row_ptr[nb[0]]], block column indices, strictly increasing within a
+ *               row; every row holds its diagonal block
+ *   val         double[row_ptr[nb[0]] * Np * Np], blocks row-major (val[z][r][c])
+ *   agg[l]      int32[nb[l]], coarse block (0..nb[l+1]-1) of every level-(l+1) block; every
+ *               coarse block has at least one child; l = 0..n_levels-2
+ *   R[l]        double[nb[l] * Np * Np]: R_f[m][n] = coefficient of coarse basis function n of
+ *               block agg[f] in fine basis function m of block f (Eq. XDGrestrictionMatrix) */
+typedef struct {
+  int Np;
+  int n_levels;
+  const int64_t* nb;
+  const int64_t* row_ptr;
+  const int32_t* col;
+  const double* val;
+  const int32_t* const* agg;
+  const double* const* R;
+} xdg_problem;
+
+typedef struct {
+  double omega;       /* > 0: smoother damping on every level; <= 0: omega_l = 4/(3 lambda_l),
+                         lambda_l a Lanczos estimate of the largest eigenvalue of D_l^{-1} M_l */
+  int lanczos_steps;  /* Lanczos steps for lambda_l (default 12 when <= 0) */
+  int nu;             /* block-Jacobi sweeps before and after the coarse correction (>= 1) */
+  int gamma;          /* coarse visits per level: 1 = V-cycle, 2 = W-cycle */
+  int low_precision;  /* bit mask: 1 = keep FP32 copies of the operators, 2 = BF16 copies */
+} xdg_hier_opts;
+
+typedef struct {
+  double tol;           /* stop when ||b - M x||_2 <= tol ||b||_2 (FP64 residual) */
+  int maxit;            /* iteration limit (outer CG steps, or inner steps in total) */
+  int check_every;      /* read the residual norm back every this many iterations (>= 1) */
+  int precision;        /* XDG_PREC_F64: CG with the FP64 cycle; F32 / BF16: FP64 iterative
+                           refinement around CG with the low-precision cycle and operator */
+  double inner_tol;     /* mixed precision: relative reduction of each inner solve */
+  double time_budget_ms;/* > 0: return XDG_ETIMEOUT once exceeded (checked with the residual) */
+} xdg_solve_opts;
+
+typedef struct {
+  int iterations;      /* CG iterations (mixed precision: inner iterations in total) */
+  int outer;           /* refinement steps (mixed precision), 1 otherwise */
+  double relres;       /* final ||b - M x||_2 / ||b||_2, recomputed in FP64 */
+  double ms;           /* wall time of the call */
+  int status;          /* same as the return value */
+  int64_t launches;    /* CUDA kernels launched by the call (graph kernel nodes included) */
+} xdg_solve_info;
+
+#define XDG_MAX_LEVELS 24
+
+typedef struct {
+  int Np, n_levels;
+  int64_t nb[XDG_MAX_LEVELS];
+  int64_t nnzb[XDG_MAX_LEVELS];
+  double omega[XDG_MAX_LEVELS];
+  double lambda_max[XDG_MAX_LEVELS];
+  int64_t coarse_n;       /* DOF of the coarsest level (dense direct solve) */
+  size_t device_bytes;    /* device memory held by the handle */
+  double setup_ms[3];     /* upload+validation, Galerkin products, factorisations+estimates */
+} xdg_hier_info;
+
+/* Build the hierarchy on the current CUDA device: validate every index on the host
+ * (EINVAL on the first inconsistency), copy the problem to the device, compute the coarse
+ * operators (Galerkin products, Eq. XDGsysRestriction), the Cholesky factors of all diagonal
+ * blocks, the damping estimates, the coarsest-level inverse, and record the cycle in a CUDA
+ * graph. stream: cudaStream_t to bind to the handle; NULL makes the handle create and own a
+ * non-blocking stream (graph capture needs a stream other than the legacy default stream).
+ * On success *out owns all device memory of the hierarchy until xdg_destroy. */
+int xdg_create_hierarchy(const xdg_problem* p, const xdg_hier_opts* o, void* stream,
+                         xdg_hier_t* out);
+
+/* Release all device memory and graphs of the handle (synchronises its stream). */
+int xdg_destroy(xdg_hier_t h);
+
+const char* xdg_strerror(int code);
+const char* xdg_last_error(void);
+
+/* Sizes and setup results (host struct, synchronises). */
+int xdg_get_info(xdg_hier_t h, xdg_hier_info* info);
+
+/* Copy the BSR operator of level `level` (1-based) into caller-allocated host arrays
+ * (row_ptr[nb+1], col[nnzb], val[nnzb*Np*Np]; sizes from xdg_get_info). Level 1 returns the
+ * uploaded operator, coarser levels the Galerkin products computed on the device. */
+int xdg_export_level(xdg_hier_t h, int level, int64_t* row_ptr, int32_t* col, double* val);
+
+/* y = M^level x (device vectors of length nb[level-1]*Np). prec selects the stored operator
+ * (XDG_PREC_F64, or F32 / BF16 when built with low_precision; FP32 accumulation then). */
+int xdg_apply(xdg_hier_t h, int level, const double* x, double* y, int prec);
+
+/* One damped block-Jacobi step on `level`: x_out = x_in + omega D^{-1} (b - M x_in), the
+ * diagonal blocks D solved with their Cholesky factors. x_in == NULL means x_in = 0. x_out
+ * must not alias x_in or b. */
+int xdg_smooth(xdg_hier_t h, int level, const double* b, const double* x_in, double* x_out);
+
+/* rc = (R^{X,level})^T (b - M^level x)  (x == NULL: rc = R^T b), level < n_levels. */
+int xdg_restrict(xdg_hier_t h, int level, const double* b, const double* x, double* rc);
+
+/* x_out = x_in + R^{X,level} zc  (x_out may equal x_in). */
+int xdg_prolong(xdg_hier_t h, int level, const double* zc, const double* x_in, double* x_out);
+
+/* z = (M^{n_levels})^{-1} r on the coarsest level (dense FP64 inverse from a Cholesky
+ * factorisation computed on the device). */
+int xdg_coarse_solve(xdg_hier_t h, const double* r, double* z);
+
+/* x = B b: one symmetric multigrid cycle from a zero initial guess on level 1 (V- or W-cycle
+ * per xdg_hier_opts.gamma). Replayed from the recorded CUDA graph. b and x are device
+ * vectors and must not alias. */
+int xdg_vcycle(xdg_hier_t h, const double* b, double* x);
+
+/* Solve M^1 x = b (device vectors). x holds the initial guess on entry (resume from a
+ * previous x to continue a solve). Returns XDG_OK when converged, XDG_ENOTCONV /
+ * XDG_ETIMEOUT / XDG_EBREAKDOWN otherwise; info (optional) is filled in every case. */
+int xdg_solve(xdg_hier_t h, const double* b, double* x, const xdg_solve_opts* o,
+              xdg_solve_info* info);
+
+/* Same as xdg_solve with host vectors: copies b to the device, solves from x = 0 and copies
+ * x back, all inside the call (the end-to-end path for callers without device memory). */
+int xdg_solve_host(xdg_hier_t h, const double* b_host, double* x_host, const xdg_solve_opts* o,
+                   xdg_solve_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XDG_H */

@@ -1,0 +1,931 @@
+// libxdg: C ABI (include/xdg.h) of the multigrid-preconditioned XDG solve on one GPU.
+//
+// Kummer, Smuda, Weber, "BoSSS: a package for multigrid extended discontinuous Galerkin
+// methods", arXiv 2003.02431: system in block form (Eq. GenericMatrixSystem), transfers
+// (Eq. XDGrestrictionMatrix), Galerkin coarse operators (Eq. XDGsysRestriction), level
+// recursion (Algorithm 4 without residual minimisation), block smoothing with cell-local dense
+// solves (Algorithms 1-2), direct coarsest solve and Krylov outer method (sec. 3.3).
+//
+// Host code here validates inputs, owns device memory, computes sparsity patterns, records
+// CUDA graphs and drives the iterations; every arithmetic step of the solve runs in the
+// kernels of xdg_kernels.cuh.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/xdg.h"
+#include "xdg_kernels.cuh"
+
+using namespace xdg;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+void set_err(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      set_err("%s:%d: %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_));      \
+      return e_ == cudaErrorMemoryAllocation ? XDG_ENOMEM : XDG_ECUDA;                  \
+    }                                                                                   \
+  } while (0)
+
+#define CKL()  CK(cudaGetLastError())
+
+#define TRY(expr)          \
+  do {                     \
+    int rc_ = (expr);      \
+    if (rc_) return rc_;   \
+  } while (0)
+
+using clk = std::chrono::steady_clock;
+double ms_since(clk::time_point t0) {
+  return std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+}
+
+// --------------------------------------------------------------------------------------------
+// per-Np kernel table
+struct Ops {
+  int np;
+  void (*spmv)(int grid, cudaStream_t, int64_t, const int64_t*, const int32_t*, const double*,
+               const double*, const double*, double*, int mode);
+  void (*smooth)(int grid, cudaStream_t, int64_t, const int64_t*, const int32_t*, const double*,
+                 const double*, double, const double*, const double*, double*);
+  void (*bjsolve)(int grid, cudaStream_t, int64_t, const double*, const double*, double*);
+  void (*diagmul)(int grid, cudaStream_t, int64_t, const int64_t*, const double*, const double*, double*);
+  void (*restrict_)(int grid, cudaStream_t, int64_t, const int64_t*, const int32_t*, const int64_t*,
+                    const int32_t*, const double*, const double*, const double*, const double*,
+                    double*);
+  void (*prolong)(int grid, cudaStream_t, int64_t, const int32_t*, const double*, const double*,
+                  const double*, double*);
+  void (*galerkin)(int grid, cudaStream_t, int64_t, const int64_t*, const int32_t*, const int64_t*,
+                   const int32_t*, const double*, const int32_t*, const double*, const int64_t*,
+                   const int32_t*, double*);
+  void (*diag_chol)(cudaStream_t, int64_t, const int64_t*, const double*, double*, int*);
+  int gpw;
+};
+
+template <int NP>
+struct OpsT {
+  static void spmv(int grid, cudaStream_t s, int64_t nb, const int64_t* rp, const int32_t* col,
+                   const double* val, const double* x, const double* b, double* y, int mode) {
+    if (mode) k_spmv<NP, 1><<<grid, kThreads, 0, s>>>(nb, rp, col, val, x, b, y);
+    else k_spmv<NP, 0><<<grid, kThreads, 0, s>>>(nb, rp, col, val, x, b, y);
+  }
+  static void smooth(int grid, cudaStream_t s, int64_t nb, const int64_t* rp, const int32_t* col,
+                     const double* val, const double* Lf, double om, const double* b,
+                     const double* xi, double* xo) {
+    if (xi) k_smooth<NP, false><<<grid, kThreads, 0, s>>>(nb, rp, col, val, Lf, om, b, xi, xo);
+    else k_smooth<NP, true><<<grid, kThreads, 0, s>>>(nb, rp, col, val, Lf, om, b, xi, xo);
+  }
+  static void bjsolve(int grid, cudaStream_t s, int64_t nb, const double* Lf, const double* v, double* z) {
+    k_bjsolve<NP><<<grid, kThreads, 0, s>>>(nb, Lf, v, z);
+  }
+  static void diagmul(int grid, cudaStream_t s, int64_t nb, const int64_t* dg, const double* val,
+                      const double* v, double* w) {
+    k_diagmul<NP><<<grid, kThreads, 0, s>>>(nb, dg, val, v, w);
+  }
+  static void restrict_(int grid, cudaStream_t s, int64_t nbc, const int64_t* cptr, const int32_t* ch,
+                        const int64_t* rp, const int32_t* col, const double* val, const double* R,
+                        const double* b, const double* x, double* rc) {
+    if (x) k_restrict<NP, true><<<grid, kThreads, 0, s>>>(nbc, cptr, ch, rp, col, val, R, b, x, rc);
+    else k_restrict<NP, false><<<grid, kThreads, 0, s>>>(nbc, cptr, ch, rp, col, val, R, b, x, rc);
+  }
+  static void prolong(int grid, cudaStream_t s, int64_t nbf, const int32_t* agg, const double* R,
+                      const double* zc, const double* xi, double* xo) {
+    k_prolong<NP><<<grid, kThreads, 0, s>>>(nbf, agg, R, zc, xi, xo);
+  }
+  static void galerkin(int grid, cudaStream_t s, int64_t nbc, const int64_t* cptr, const int32_t* ch,
+                       const int64_t* rp, const int32_t* col, const double* val, const int32_t* agg,
+                       const double* R, const int64_t* crp, const int32_t* ccol, double* cval) {
+    k_galerkin<NP><<<grid, kThreads, 0, s>>>(nbc, cptr, ch, rp, col, val, agg, R, crp, ccol, cval);
+  }
+  static void diag_chol(cudaStream_t s, int64_t nb, const int64_t* dg, const double* val, double* Lf,
+                        int* err) {
+    k_diag_chol<NP><<<(unsigned)((nb + 127) / 128), 128, 0, s>>>(nb, dg, val, Lf, err);
+  }
+  static Ops make() {
+    return Ops{NP, spmv, smooth, bjsolve, diagmul, restrict_, prolong, galerkin, diag_chol, Grp<NP>::GPW};
+  }
+};
+
+bool ops_for(int np, Ops* o) {
+  switch (np) {
+    case 6: *o = OpsT<6>::make(); return true;
+    case 10: *o = OpsT<10>::make(); return true;
+    case 15: *o = OpsT<15>::make(); return true;
+    case 20: *o = OpsT<20>::make(); return true;
+    default: return false;
+  }
+}
+
+// --------------------------------------------------------------------------------------------
+struct Level {
+  int64_t nb = 0, nnzb = 0;
+  std::vector<int64_t> h_rp, h_diag;
+  std::vector<int32_t> h_col;
+  int64_t* rp = nullptr;
+  int32_t* col = nullptr;
+  double* val = nullptr;
+  int64_t* diag = nullptr;
+  double* Lf = nullptr;
+  int32_t* agg = nullptr;  // to the next level
+  double* R = nullptr;
+  int64_t* cptr = nullptr;  // children of the next level's blocks
+  int32_t* ch = nullptr;
+  double *b = nullptr, *x = nullptr, *t = nullptr, *r = nullptr, *dz = nullptr;
+  double omega = 0.0, lmax = 0.0;
+};
+
+}  // namespace
+
+struct xdg_hier {
+  int Np = 0, nlev = 0, nu = 1, gamma = 1, dev = 0, sms = 152;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  Ops ops{};
+  std::vector<Level> L;
+  double* Minv = nullptr;
+  int64_t nc = 0;
+  double *s_b = nullptr, *s_x = nullptr, *s_r = nullptr, *s_z = nullptr, *s_p = nullptr, *s_q = nullptr;
+  double* partial = nullptr;
+  double* dsc = nullptr;       // device scalars for setup reductions
+  PcgScal* S = nullptr;
+  PcgScal* hS = nullptr;       // pinned host mirror
+  double* hsc = nullptr;       // pinned host scalars
+  cudaGraphExec_t g_cycle = nullptr;
+  const double* g_cycle_b = nullptr;
+  double* g_cycle_x = nullptr;
+  cudaGraphExec_t g_iter = nullptr;
+  int64_t iter_nodes = 0;      // kernel nodes in one recorded CG iteration
+  int64_t cycle_nodes = 0;     // kernel nodes in the recorded cycle
+  int64_t launches = 0;        // kernels launched outside graphs (counted by the helpers)
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  double setup_ms[3] = {0, 0, 0};
+
+  ~xdg_hier() {
+    if (stream) cudaStreamSynchronize(stream);
+    if (g_cycle) cudaGraphExecDestroy(g_cycle);
+    if (g_iter) cudaGraphExecDestroy(g_iter);
+    for (void* p : allocs) cudaFree(p);
+    if (hS) cudaFreeHost(hS);
+    if (hsc) cudaFreeHost(hsc);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+  }
+
+  template <class T>
+  int alloc(T** p, size_t n) {
+    void* q = nullptr;
+    size_t nbytes = std::max<size_t>(n, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&q, nbytes);
+    if (e != cudaSuccess) {
+      set_err("cudaMalloc(%zu bytes): %s", nbytes, cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? XDG_ENOMEM : XDG_ECUDA;
+    }
+    allocs.push_back(q);
+    bytes += nbytes;
+    *p = static_cast<T*>(q);
+    return XDG_OK;
+  }
+
+  int grid(int64_t rows) const {
+    int64_t warps = (rows + ops.gpw - 1) / ops.gpw;
+    int64_t blocks = (warps + (kThreads / 32) - 1) / (kThreads / 32);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sms * 8));
+  }
+  int vgrid(int64_t n) const {
+    int64_t blocks = (n + kThreads - 1) / kThreads;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sms * 8));
+  }
+
+  // ---------------------------------------------------------------- building blocks
+  void spmv(int l, const double* x, const double* b, double* y, int mode) {
+    ++launches;
+    Level& V = L[l];
+    ops.spmv(grid(V.nb), stream, V.nb, V.rp, V.col, V.val, x, b, y, mode);
+  }
+  void smooth(int l, const double* b, const double* xi, double* xo) {
+    ++launches;
+    Level& V = L[l];
+    ops.smooth(grid(V.nb), stream, V.nb, V.rp, V.col, V.val, V.Lf, V.omega, b, xi, xo);
+  }
+  void restrict_(int l, const double* b, const double* x, double* rc) {
+    ++launches;
+    Level& V = L[l];
+    Level& C = L[l + 1];
+    ops.restrict_(grid(C.nb), stream, C.nb, V.cptr, V.ch, V.rp, V.col, V.val, V.R, b, x, rc);
+  }
+  void prolong(int l, const double* zc, const double* xi, double* xo) {
+    ++launches;
+    Level& V = L[l];
+    ops.prolong(grid(V.nb), stream, V.nb, V.agg, V.R, zc, xi, xo);
+  }
+  void coarse(const double* r, double* z) {
+    ++launches;
+    int64_t blocks = (nc * 32 + kThreads - 1) / kThreads;
+    k_gemv<<<(unsigned)blocks, kThreads, 0, stream>>>(nc, Minv, r, z);
+  }
+  void dot(int64_t n, const double* a, const double* b, double* out) {
+    launches += 2;
+    k_dot_partial<<<kRedBlocks, kThreads, 0, stream>>>(n, a, b, partial);
+    k_sum_final<<<1, kThreads, 0, stream>>>(kRedBlocks, partial, out);
+  }
+
+  // one symmetric cycle on level l from a zero initial guess: x = B_l b
+  void cycle(int l, const double* b, double* x) {
+    if (l == nlev - 1) {
+      coarse(b, x);
+      return;
+    }
+    Level& V = L[l];
+    Level& C = L[l + 1];
+    // pre-smoothing: nu sweeps, the first one from x = 0
+    double* cur = x;
+    double* oth = V.t;
+    smooth(l, b, nullptr, cur);
+    for (int s = 1; s < nu; ++s) {
+      smooth(l, b, cur, oth);
+      std::swap(cur, oth);
+    }
+    // coarse-grid correction: gamma cycles on the coarse level
+    restrict_(l, b, cur, C.b);
+    cycle(l + 1, C.b, C.x);
+    if (gamma > 1 && l + 2 < nlev) {
+      for (int g = 1; g < gamma; ++g) {
+        spmv(l + 1, C.x, C.b, C.r, 1);
+        cycle(l + 1, C.r, C.dz);
+        k_axpy<<<vgrid(C.nb * Np), kThreads, 0, stream>>>(C.nb * Np, 1.0, C.dz, C.x);
+        ++launches;
+      }
+    }
+    // prolongation into the buffer from which nu post-sweeps end in x
+    // nu alternating post-sweeps starting in `after` end in x
+    double* after = (nu % 2 == 0) ? x : V.t;
+    prolong(l, C.x, cur, after);
+    cur = after;
+    oth = (cur == x) ? V.t : x;
+    for (int s = 0; s < nu; ++s) {
+      smooth(l, b, cur, oth);
+      std::swap(cur, oth);
+    }
+    if (cur != x) {
+      k_copy<<<vgrid(V.nb * Np), kThreads, 0, stream>>>(V.nb * Np, cur, x);
+      ++launches;
+    }
+  }
+
+  // one CG iteration on level 1 (buffers s_*), scalars in S
+  void pcg_iteration() {
+    const int64_t n = L[0].nb * Np;
+    spmv(0, s_p, nullptr, s_q, 0);
+    dot(n, s_p, s_q, &S->pq);
+    k_pcg_alpha<<<1, 1, 0, stream>>>(S);
+    launches += 5;
+    k_pcg_xr<<<kRedBlocks, kThreads, 0, stream>>>(n, S, s_p, s_q, s_x, s_r, partial);
+    k_sum_final<<<1, kThreads, 0, stream>>>(kRedBlocks, partial, &S->rr);
+    cycle(0, s_r, s_z);
+    dot(n, s_r, s_z, &S->rz_new);
+    k_pcg_beta<<<1, 1, 0, stream>>>(S);
+    k_pcg_p<<<vgrid(n), kThreads, 0, stream>>>(n, S, s_z, s_p);
+  }
+
+  int capture(cudaGraphExec_t* out, int which, const double* b, double* x) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+    const int64_t before = launches;
+    if (which == 0) cycle(0, b, x);
+    else pcg_iteration();
+    const int64_t recorded = launches - before;
+    launches = before;
+    if (which == 0) cycle_nodes = recorded;
+    else iter_nodes = recorded;
+    cudaError_t e = cudaStreamEndCapture(stream, &g);
+    if (e != cudaSuccess) {
+      set_err("graph capture: %s", cudaGetErrorString(e));
+      return XDG_ECUDA;
+    }
+    if (*out) cudaGraphExecDestroy(*out);
+    *out = nullptr;
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      set_err("graph instantiate: %s", cudaGetErrorString(e));
+      return XDG_ECUDA;
+    }
+    return XDG_OK;
+  }
+
+  int sync() {
+    CK(cudaStreamSynchronize(stream));
+    return XDG_OK;
+  }
+
+  // host read of a device scalar
+  int read_scalar(const double* d, double* h) {
+    CK(cudaMemcpyAsync(hsc, d, sizeof(double), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    *h = hsc[0];
+    return XDG_OK;
+  }
+
+  int lanczos(int l, int m, double* lam);
+  int build(const xdg_problem* p, const xdg_hier_opts* o);
+  int solve_dev(const double* b, double* x, const xdg_solve_opts* o, xdg_solve_info* info);
+};
+
+namespace {
+
+// largest eigenvalue of the symmetric tridiagonal matrix (a, b) by bisection on the number of
+// negative pivots of T - s I
+double tridiag_lambda_max(const std::vector<double>& a, const std::vector<double>& b) {
+  const int m = (int)a.size();
+  double lo = a[0], hi = a[0];
+  for (int i = 0; i < m; ++i) {
+    double rad = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - rad);
+    hi = std::max(hi, a[i] + rad);
+  }
+  auto below = [&](double s) {
+    int k = 0;
+    double d = a[0] - s;
+    if (d < 0) ++k;
+    for (int i = 1; i < m; ++i) {
+      if (d == 0.0) d = 1e-300;
+      d = (a[i] - s) - b[i - 1] * b[i - 1] / d;
+      if (d < 0) ++k;
+    }
+    return k;
+  };
+  for (int it = 0; it < 300 && hi - lo > 1e-15 * std::fabs(hi); ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (below(mid) >= m) hi = mid;
+    else lo = mid;
+  }
+  return hi;
+}
+
+}  // namespace
+
+// m-step Lanczos for the pencil (M_l, D_l) in the D inner product
+int xdg_hier::lanczos(int l, int m, double* lam) {
+  Level& V = L[l];
+  const int64_t n = V.nb * Np;
+  double *q = V.b, *qp = V.x, *u = V.t, *w = V.r, *Dw = V.dz;
+  const int vg = vgrid(n);
+  k_hash_vector<<<vg, kThreads, 0, stream>>>(n, q);
+  CK(cudaMemsetAsync(qp, 0, n * sizeof(double), stream));
+  ops.diagmul(grid(V.nb), stream, V.nb, V.diag, V.val, q, Dw);
+  dot(n, q, Dw, dsc);
+  double nrm2;
+  TRY(read_scalar(dsc, &nrm2));
+  CKL();
+  k_scale<<<vg, kThreads, 0, stream>>>(n, 1.0 / std::sqrt(nrm2), q);
+  std::vector<double> al, be;
+  double bprev = 0.0;
+  for (int j = 0; j < m; ++j) {
+    spmv(l, q, nullptr, u, 0);
+    dot(n, q, u, dsc);
+    double a;
+    TRY(read_scalar(dsc, &a));
+    al.push_back(a);
+    ops.bjsolve(grid(V.nb), stream, V.nb, V.Lf, u, w);
+    k_axpy<<<vg, kThreads, 0, stream>>>(n, -a, q, w);
+    k_axpy<<<vg, kThreads, 0, stream>>>(n, -bprev, qp, w);
+    ops.diagmul(grid(V.nb), stream, V.nb, V.diag, V.val, w, Dw);
+    dot(n, w, Dw, dsc);
+    double b2;
+    TRY(read_scalar(dsc, &b2));
+    CKL();
+    double bj = std::sqrt(std::max(b2, 0.0));
+    be.push_back(bj);
+    if (!(bj > 1e-300)) break;
+    k_copy<<<vg, kThreads, 0, stream>>>(n, q, qp);
+    k_axpby<<<vg, kThreads, 0, stream>>>(n, 1.0 / bj, w, 0.0, q);
+    bprev = bj;
+  }
+  CKL();
+  *lam = tridiag_lambda_max(al, be);
+  return XDG_OK;
+}
+
+int xdg_hier::build(const xdg_problem* p, const xdg_hier_opts* o) {
+  auto t0 = clk::now();
+  Np = p->Np;
+  nlev = p->n_levels;
+  if (nlev < 1 || nlev > XDG_MAX_LEVELS) {
+    set_err("n_levels = %d outside 1..%d", nlev, XDG_MAX_LEVELS);
+    return XDG_EINVAL;
+  }
+  if (!ops_for(Np, &ops)) {
+    set_err("block size Np = %d not supported (6, 10, 15, 20)", Np);
+    return XDG_EINVAL;
+  }
+  nu = o && o->nu > 0 ? o->nu : 1;
+  gamma = o && o->gamma > 0 ? o->gamma : 1;
+  const int lsteps = o && o->lanczos_steps > 0 ? o->lanczos_steps : 12;
+  const int64_t Np2 = (int64_t)Np * Np;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  L.resize(nlev);
+  // ------------------------------------------------------------------ validation (host)
+  for (int l = 0; l < nlev; ++l) {
+    if (p->nb[l] <= 0 || p->nb[l] > INT32_MAX) {
+      set_err("level %d: nb = %lld", l + 1, (long long)p->nb[l]);
+      return XDG_EINVAL;
+    }
+    L[l].nb = p->nb[l];
+  }
+  {
+    Level& V = L[0];
+    const int64_t nb = V.nb;
+    if (!p->row_ptr || !p->col || !p->val) {
+      set_err("null operator arrays");
+      return XDG_EINVAL;
+    }
+    if (p->row_ptr[0] != 0) {
+      set_err("row_ptr[0] = %lld", (long long)p->row_ptr[0]);
+      return XDG_EINVAL;
+    }
+    V.h_rp.assign(p->row_ptr, p->row_ptr + nb + 1);
+    for (int64_t i = 0; i < nb; ++i)
+      if (V.h_rp[i + 1] < V.h_rp[i]) {
+        set_err("row_ptr decreases at row %lld", (long long)i);
+        return XDG_EINVAL;
+      }
+    V.nnzb = V.h_rp[nb];
+    V.h_col.assign(p->col, p->col + V.nnzb);
+    V.h_diag.assign(nb, -1);
+    for (int64_t i = 0; i < nb; ++i)
+      for (int64_t z = V.h_rp[i]; z < V.h_rp[i + 1]; ++z) {
+        int32_t c = V.h_col[z];
+        if (c < 0 || c >= nb || (z > V.h_rp[i] && c <= V.h_col[z - 1])) {
+          set_err("col[%lld] = %d invalid or not increasing in row %lld", (long long)z, c, (long long)i);
+          return XDG_EINVAL;
+        }
+        if (c == i) V.h_diag[i] = z;
+      }
+    for (int64_t i = 0; i < nb; ++i)
+      if (V.h_diag[i] < 0) {
+        set_err("row %lld has no diagonal block", (long long)i);
+        return XDG_EINVAL;
+      }
+    for (int64_t e = 0; e < V.nnzb * Np2; ++e)
+      if (!std::isfinite(p->val[e])) {
+        set_err("val[%lld] is not finite", (long long)e);
+        return XDG_EINVAL;
+      }
+  }
+  for (int l = 0; l + 1 < nlev; ++l) {
+    if (!p->agg || !p->R || !p->agg[l] || !p->R[l]) {
+      set_err("level %d: null transfer arrays", l + 1);
+      return XDG_EINVAL;
+    }
+    std::vector<int64_t> cnt(L[l + 1].nb, 0);
+    for (int64_t f = 0; f < L[l].nb; ++f) {
+      int32_t a = p->agg[l][f];
+      if (a < 0 || a >= L[l + 1].nb) {
+        set_err("level %d: agg[%lld] = %d out of range", l + 1, (long long)f, a);
+        return XDG_EINVAL;
+      }
+      cnt[a]++;
+    }
+    for (int64_t c = 0; c < L[l + 1].nb; ++c)
+      if (cnt[c] == 0) {
+        set_err("level %d: coarse block %lld has no child", l + 2, (long long)c);
+        return XDG_EINVAL;
+      }
+    for (int64_t e = 0; e < L[l].nb * Np2; ++e)
+      if (!std::isfinite(p->R[l][e])) {
+        set_err("level %d: R[%lld] is not finite", l + 1, (long long)e);
+        return XDG_EINVAL;
+      }
+  }
+  // ------------------------------------------------------------------ symbolic hierarchy (host)
+  std::vector<std::vector<int64_t>> h_cptr(nlev);
+  std::vector<std::vector<int32_t>> h_ch(nlev);
+  for (int l = 0; l + 1 < nlev; ++l) {
+    Level& F = L[l];
+    Level& C = L[l + 1];
+    const int32_t* agg = p->agg[l];
+    auto& cp = h_cptr[l];
+    auto& chl = h_ch[l];
+    cp.assign(C.nb + 1, 0);
+    for (int64_t f = 0; f < F.nb; ++f) cp[agg[f] + 1]++;
+    for (int64_t c = 0; c < C.nb; ++c) cp[c + 1] += cp[c];
+    chl.resize(F.nb);
+    std::vector<int64_t> pos(cp.begin(), cp.end() - 1);
+    for (int64_t f = 0; f < F.nb; ++f) chl[pos[agg[f]]++] = (int32_t)f;  // children ascending
+    // coarse sparsity: agg of the fine columns of all children
+    C.h_rp.assign(C.nb + 1, 0);
+    std::vector<int32_t> cols;
+    std::vector<std::vector<int32_t>> rows(C.nb);
+    for (int64_t c = 0; c < C.nb; ++c) {
+      cols.clear();
+      for (int64_t t = cp[c]; t < cp[c + 1]; ++t) {
+        int64_t f = chl[t];
+        for (int64_t z = F.h_rp[f]; z < F.h_rp[f + 1]; ++z) cols.push_back(agg[F.h_col[z]]);
+      }
+      std::sort(cols.begin(), cols.end());
+      cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+      rows[c] = cols;
+      C.h_rp[c + 1] = C.h_rp[c] + (int64_t)cols.size();
+    }
+    C.nnzb = C.h_rp[C.nb];
+    C.h_col.resize(C.nnzb);
+    C.h_diag.assign(C.nb, -1);
+    for (int64_t c = 0; c < C.nb; ++c) {
+      std::copy(rows[c].begin(), rows[c].end(), C.h_col.begin() + C.h_rp[c]);
+      for (int64_t z = C.h_rp[c]; z < C.h_rp[c + 1]; ++z)
+        if (C.h_col[z] == c) C.h_diag[c] = z;
+      if (C.h_diag[c] < 0) {
+        set_err("level %d: coarse block %lld couples not with itself", l + 2, (long long)c);
+        return XDG_EINVAL;
+      }
+    }
+  }
+  nc = L[nlev - 1].nb * Np;
+  if (nc > 4096) {
+    set_err("coarsest level has %lld DOF; at most 4096 are supported", (long long)nc);
+    return XDG_EINVAL;
+  }
+  // ------------------------------------------------------------------ device memory
+  if (!stream) {
+    CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+    own_stream = true;
+  }
+  for (int l = 0; l < nlev; ++l) {
+    Level& V = L[l];
+    const int64_t n = V.nb * Np;
+    TRY(alloc(&V.rp, V.nb + 1));
+    TRY(alloc(&V.col, V.nnzb));
+    TRY(alloc(&V.val, V.nnzb * Np2));
+    TRY(alloc(&V.diag, V.nb));
+    TRY(alloc(&V.b, n));
+    TRY(alloc(&V.x, n));
+    TRY(alloc(&V.t, n));
+    TRY(alloc(&V.r, n));
+    TRY(alloc(&V.dz, n));
+    CK(cudaMemcpyAsync(V.rp, V.h_rp.data(), (V.nb + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(V.col, V.h_col.data(), std::max<int64_t>(V.nnzb, 0) * sizeof(int32_t),
+                       cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(V.diag, V.h_diag.data(), V.nb * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+    if (l + 1 < nlev) {
+      TRY(alloc(&V.Lf, V.nb * (int64_t)(Np * (Np + 1) / 2)));
+      TRY(alloc(&V.agg, V.nb));
+      TRY(alloc(&V.R, V.nb * Np2));
+      TRY(alloc(&V.cptr, L[l + 1].nb + 1));
+      TRY(alloc(&V.ch, V.nb));
+      CK(cudaMemcpyAsync(V.agg, p->agg[l], V.nb * sizeof(int32_t), cudaMemcpyHostToDevice, stream));
+      CK(cudaMemcpyAsync(V.R, p->R[l], V.nb * Np2 * sizeof(double), cudaMemcpyHostToDevice, stream));
+      CK(cudaMemcpyAsync(V.cptr, h_cptr[l].data(), (L[l + 1].nb + 1) * sizeof(int64_t),
+                         cudaMemcpyHostToDevice, stream));
+      CK(cudaMemcpyAsync(V.ch, h_ch[l].data(), V.nb * sizeof(int32_t), cudaMemcpyHostToDevice, stream));
+    }
+  }
+  CK(cudaMemcpyAsync(L[0].val, p->val, L[0].nnzb * Np2 * sizeof(double), cudaMemcpyHostToDevice, stream));
+  const int64_t n1 = L[0].nb * Np;
+  TRY(alloc(&s_b, n1));
+  TRY(alloc(&s_x, n1));
+  TRY(alloc(&s_r, n1));
+  TRY(alloc(&s_z, n1));
+  TRY(alloc(&s_p, n1));
+  TRY(alloc(&s_q, n1));
+  TRY(alloc(&partial, kRedBlocks));
+  TRY(alloc(&dsc, 8));
+  TRY(alloc(&S, 1));
+  TRY(alloc(&Minv, nc * nc));
+  CK(cudaMallocHost(&hS, sizeof(PcgScal)));
+  CK(cudaMallocHost(&hsc, 8 * sizeof(double)));
+  int* derr = nullptr;
+  TRY(alloc(&derr, 1));
+  CK(cudaMemsetAsync(derr, 0, sizeof(int), stream));
+  TRY(sync());
+  setup_ms[0] = ms_since(t0);
+  // ------------------------------------------------------------------ Galerkin products (device)
+  t0 = clk::now();
+  for (int l = 0; l + 1 < nlev; ++l) {
+    Level& F = L[l];
+    Level& C = L[l + 1];
+    CK(cudaMemsetAsync(C.val, 0, C.nnzb * Np2 * sizeof(double), stream));
+    ops.galerkin(grid(C.nb), stream, C.nb, F.cptr, F.ch, F.rp, F.col, F.val, F.agg, F.R, C.rp, C.col, C.val);
+    CKL();
+  }
+  TRY(sync());
+  setup_ms[1] = ms_since(t0);
+  // ------------------------------------------------------------------ factorisations, damping
+  t0 = clk::now();
+  for (int l = 0; l + 1 < nlev; ++l) {
+    Level& V = L[l];
+    ops.diag_chol(stream, V.nb, V.diag, V.val, V.Lf, derr);
+    CKL();
+  }
+  {
+    int h_err = 0;
+    CK(cudaMemcpyAsync(&h_err, derr, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    TRY(sync());
+    if (h_err) {
+      set_err("a diagonal block is not positive definite");
+      return XDG_EBREAKDOWN;
+    }
+  }
+  for (int l = 0; l + 1 < nlev; ++l) {
+    Level& V = L[l];
+    TRY(lanczos(l, lsteps, &V.lmax));
+    V.omega = (o && o->omega > 0.0) ? o->omega : 4.0 / (3.0 * V.lmax);
+  }
+  {
+    // coarsest level: dense Cholesky and explicit inverse
+    Level& C = L[nlev - 1];
+    double *A = nullptr, *X = nullptr;
+    TRY(alloc(&A, nc * nc));
+    TRY(alloc(&X, nc * nc));
+    CK(cudaMemsetAsync(A, 0, nc * nc * sizeof(double), stream));
+    k_bsr_to_dense<<<(unsigned)C.nb, 128, 0, stream>>>(C.nb, Np, C.rp, C.col, C.val, nc, A);
+    CK(cudaMemsetAsync(derr, 0, sizeof(int), stream));
+    k_dense_chol<<<1, 1024, 0, stream>>>(nc, A, derr);
+    k_tri_inverse<<<(unsigned)((nc + 127) / 128), 128, 0, stream>>>(nc, A, X);
+    dim3 tb(16, 16), tg((unsigned)((nc + 15) / 16), (unsigned)((nc + 15) / 16));
+    k_xtx<<<tg, tb, 0, stream>>>(nc, X, Minv);
+    CKL();
+    int h_err = 0;
+    CK(cudaMemcpyAsync(&h_err, derr, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    TRY(sync());
+    if (h_err) {
+      set_err("coarsest operator is not positive definite");
+      return XDG_EBREAKDOWN;
+    }
+    // scratch no longer needed
+    for (auto it = allocs.begin(); it != allocs.end();) {
+      if (*it == A || *it == X) {
+        cudaFree(*it);
+        it = allocs.erase(it);
+      } else {
+        ++it;
+      }
+    }
+    bytes -= 2 * nc * nc * sizeof(double);
+  }
+  TRY(capture(&g_iter, 1, nullptr, nullptr));
+  TRY(sync());
+  setup_ms[2] = ms_since(t0);
+  return XDG_OK;
+}
+
+int xdg_hier::solve_dev(const double* b, double* x, const xdg_solve_opts* o, xdg_solve_info* info) {
+  auto t0 = clk::now();
+  const int64_t launches0 = launches;
+  const int64_t n = L[0].nb * Np;
+  const double tol = o ? o->tol : 1e-10;
+  const int maxit = o && o->maxit > 0 ? o->maxit : 1000;
+  const int every = o && o->check_every > 0 ? o->check_every : 1;
+  const double budget = o ? o->time_budget_ms : 0.0;
+  if (o && o->precision != XDG_PREC_F64) {
+    set_err("precision %d not available in this solver", o->precision);
+    return XDG_EINVAL;
+  }
+  CK(cudaMemcpyAsync(s_b, b, n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  CK(cudaMemcpyAsync(s_x, x, n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  CK(cudaMemsetAsync(S, 0, sizeof(PcgScal), stream));
+  // r = b - M x, z = B r, p = z, rz = r.z
+  spmv(0, s_x, s_b, s_r, 1);
+  dot(n, s_b, s_b, dsc);
+  dot(n, s_r, s_r, &S->rr);
+  cycle(0, s_r, s_z);
+  k_copy<<<vgrid(n), kThreads, 0, stream>>>(n, s_z, s_p);
+  ++launches;
+  dot(n, s_r, s_z, &S->rz);
+  CKL();
+  double bb;
+  TRY(read_scalar(dsc, &bb));
+  const double bn = bb > 0 ? std::sqrt(bb) : 1.0;
+  CK(cudaMemcpyAsync(hS, S, sizeof(PcgScal), cudaMemcpyDeviceToHost, stream));
+  TRY(sync());
+  int status = XDG_OK, it = 0;
+  double rel = std::sqrt(hS->rr) / bn;
+  if (!std::isfinite(rel)) status = XDG_EBREAKDOWN;
+  while (status == XDG_OK && rel > tol) {
+    if (it >= maxit) {
+      status = XDG_ENOTCONV;
+      break;
+    }
+    int todo = std::min(every, maxit - it);
+    for (int k2 = 0; k2 < todo; ++k2) CK(cudaGraphLaunch(g_iter, stream));
+    it += todo;
+    CK(cudaMemcpyAsync(hS, S, sizeof(PcgScal), cudaMemcpyDeviceToHost, stream));
+    TRY(sync());
+    rel = std::sqrt(hS->rr) / bn;
+    if (hS->bad || !std::isfinite(rel)) status = XDG_EBREAKDOWN;
+    if (budget > 0 && ms_since(t0) > budget && rel > tol) status = XDG_ETIMEOUT;
+  }
+  // true residual
+  spmv(0, s_x, s_b, s_r, 1);
+  dot(n, s_r, s_r, dsc);
+  CK(cudaMemcpyAsync(x, s_x, n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  double rr;
+  TRY(read_scalar(dsc, &rr));
+  if (info) {
+    info->iterations = it;
+    info->outer = 1;
+    info->relres = std::sqrt(rr) / bn;
+    info->ms = ms_since(t0);
+    info->status = status;
+    info->launches = launches - launches0 + (int64_t)it * iter_nodes;
+  }
+  if (status) set_err("solve stopped: %s after %d iterations (relres %.3e)", xdg_strerror(status), it,
+                      std::sqrt(rr) / bn);
+  return status;
+}
+
+// ============================================================================================
+extern "C" {
+
+const char* xdg_strerror(int code) {
+  switch (code) {
+    case XDG_OK: return "XDG_OK";
+    case XDG_EINVAL: return "XDG_EINVAL";
+    case XDG_ECUDA: return "XDG_ECUDA";
+    case XDG_ENOMEM: return "XDG_ENOMEM";
+    case XDG_ENOTCONV: return "XDG_ENOTCONV";
+    case XDG_EBREAKDOWN: return "XDG_EBREAKDOWN";
+    case XDG_ETIMEOUT: return "XDG_ETIMEOUT";
+    default: return "XDG_UNKNOWN";
+  }
+}
+
+const char* xdg_last_error(void) { return g_last_error.c_str(); }
+
+int xdg_create_hierarchy(const xdg_problem* p, const xdg_hier_opts* o, void* stream, xdg_hier_t* out) {
+  if (!p || !out || !p->nb) {
+    set_err("null argument");
+    return XDG_EINVAL;
+  }
+  *out = nullptr;
+  std::unique_ptr<xdg_hier> h(new xdg_hier());
+  h->stream = static_cast<cudaStream_t>(stream);
+  int rc = h->build(p, o);
+  if (rc) return rc;
+  *out = h.release();
+  return XDG_OK;
+}
+
+int xdg_destroy(xdg_hier_t h) {
+  delete h;
+  return XDG_OK;
+}
+
+int xdg_get_info(xdg_hier_t h, xdg_hier_info* info) {
+  if (!h || !info) {
+    set_err("null argument");
+    return XDG_EINVAL;
+  }
+  std::memset(info, 0, sizeof(*info));
+  info->Np = h->Np;
+  info->n_levels = h->nlev;
+  for (int l = 0; l < h->nlev; ++l) {
+    info->nb[l] = h->L[l].nb;
+    info->nnzb[l] = h->L[l].nnzb;
+    info->omega[l] = h->L[l].omega;
+    info->lambda_max[l] = h->L[l].lmax;
+  }
+  info->coarse_n = h->nc;
+  info->device_bytes = h->bytes;
+  for (int i = 0; i < 3; ++i) info->setup_ms[i] = h->setup_ms[i];
+  return XDG_OK;
+}
+
+int xdg_export_level(xdg_hier_t h, int level, int64_t* row_ptr, int32_t* col, double* val) {
+  if (!h || level < 1 || level > h->nlev) {
+    set_err("bad level %d", level);
+    return XDG_EINVAL;
+  }
+  Level& V = h->L[level - 1];
+  const int64_t Np2 = (int64_t)h->Np * h->Np;
+  if (row_ptr) std::copy(V.h_rp.begin(), V.h_rp.end(), row_ptr);
+  if (col) std::copy(V.h_col.begin(), V.h_col.end(), col);
+  if (val) {
+    cudaError_t e = cudaMemcpyAsync(val, V.val, V.nnzb * Np2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+      set_err("export: %s", cudaGetErrorString(e));
+      return XDG_ECUDA;
+    }
+  }
+  return XDG_OK;
+}
+
+int xdg_apply(xdg_hier_t h, int level, const double* x, double* y, int prec) {
+  if (!h || level < 1 || level > h->nlev || !x || !y) {
+    set_err("xdg_apply: bad arguments");
+    return XDG_EINVAL;
+  }
+  if (prec != XDG_PREC_F64) {
+    set_err("xdg_apply: precision %d not available", prec);
+    return XDG_EINVAL;
+  }
+  h->spmv(level - 1, x, nullptr, y, 0);
+  CKL();
+  return XDG_OK;
+}
+
+int xdg_smooth(xdg_hier_t h, int level, const double* b, const double* x_in, double* x_out) {
+  if (!h || level < 1 || level >= h->nlev || !b || !x_out || x_out == x_in || x_out == b) {
+    set_err("xdg_smooth: bad arguments");
+    return XDG_EINVAL;
+  }
+  h->smooth(level - 1, b, x_in, x_out);
+  CKL();
+  return XDG_OK;
+}
+
+int xdg_restrict(xdg_hier_t h, int level, const double* b, const double* x, double* rc) {
+  if (!h || level < 1 || level >= h->nlev || !b || !rc) {
+    set_err("xdg_restrict: bad arguments");
+    return XDG_EINVAL;
+  }
+  h->restrict_(level - 1, b, x, rc);
+  CKL();
+  return XDG_OK;
+}
+
+int xdg_prolong(xdg_hier_t h, int level, const double* zc, const double* x_in, double* x_out) {
+  if (!h || level < 1 || level >= h->nlev || !zc || !x_in || !x_out) {
+    set_err("xdg_prolong: bad arguments");
+    return XDG_EINVAL;
+  }
+  h->prolong(level - 1, zc, x_in, x_out);
+  CKL();
+  return XDG_OK;
+}
+
+int xdg_coarse_solve(xdg_hier_t h, const double* r, double* z) {
+  if (!h || !r || !z || r == z) {
+    set_err("xdg_coarse_solve: bad arguments");
+    return XDG_EINVAL;
+  }
+  h->coarse(r, z);
+  CKL();
+  return XDG_OK;
+}
+
+int xdg_vcycle(xdg_hier_t h, const double* b, double* x) {
+  if (!h || !b || !x || b == x) {
+    set_err("xdg_vcycle: bad arguments");
+    return XDG_EINVAL;
+  }
+  if (!h->g_cycle || h->g_cycle_b != b || h->g_cycle_x != x) {
+    TRY(h->capture(&h->g_cycle, 0, b, x));
+    h->g_cycle_b = b;
+    h->g_cycle_x = x;
+  }
+  CK(cudaGraphLaunch(h->g_cycle, h->stream));
+  h->launches += h->cycle_nodes;
+  return XDG_OK;
+}
+
+int xdg_solve(xdg_hier_t h, const double* b, double* x, const xdg_solve_opts* o, xdg_solve_info* info) {
+  if (!h || !b || !x) {
+    set_err("xdg_solve: bad arguments");
+    return XDG_EINVAL;
+  }
+  return h->solve_dev(b, x, o, info);
+}
+
+int xdg_solve_host(xdg_hier_t h, const double* b_host, double* x_host, const xdg_solve_opts* o,
+                   xdg_solve_info* info) {
+  if (!h || !b_host || !x_host) {
+    set_err("xdg_solve_host: bad arguments");
+    return XDG_EINVAL;
+  }
+  auto t0 = clk::now();
+  const int64_t n = h->L[0].nb * h->Np;
+  // the level-1 work vectors b, x of the hierarchy serve as device staging
+  double* db = h->L[0].r;
+  double* dx = h->L[0].dz;
+  CK(cudaMemcpyAsync(db, b_host, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemsetAsync(dx, 0, n * sizeof(double), h->stream));
+  int rc = h->solve_dev(db, dx, o, info);
+  if (rc != XDG_OK && rc != XDG_ENOTCONV && rc != XDG_ETIMEOUT && rc != XDG_EBREAKDOWN) return rc;
+  CK(cudaMemcpyAsync(x_host, dx, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (info) info->ms = ms_since(t0);
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,560 @@
+// CUDA kernels of the XDG multigrid solve (sm_103a).
+//
+// Kummer, Smuda, Weber, arXiv 2003.02431: operator M^lambda in per-cell block form
+// (Eq. GenericMatrixSystem), transfers R^{X,lambda} (Eq. XDGrestrictionMatrix), Galerkin
+// coarse operators (Eq. XDGsysRestriction), the level recursion of Algorithm 4 and the
+// cell-local dense solves used for smoothing (Algorithms 1, 2).
+//
+// Work mapping: a "group" of NP consecutive lanes owns one block row (lane r <-> row r of the
+// block); a warp holds 32/NP groups working on consecutive block rows, so a warp streams
+// contiguous block data with 16-byte loads. Within a group, dense Np x Np work uses
+// register rows plus shuffles restricted to the group's lanes.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace xdg {
+
+constexpr int kThreads = 256;
+
+template <int NP>
+struct Grp {
+  static constexpr int GPW = 32 / NP;              // groups per warp
+  static constexpr int NT = NP * (NP + 1) / 2;     // packed lower triangle
+};
+
+__device__ __forceinline__ unsigned group_mask(int g, int np) {
+  return (np == 32) ? 0xffffffffu : (((1u << np) - 1u) << (g * np));
+}
+
+// NP consecutive doubles -> registers (16-byte loads when the row is 16-byte aligned)
+template <int NP>
+__device__ __forceinline__ void ldrow(const double* __restrict__ p, double (&v)[NP]) {
+  if constexpr (NP % 2 == 0) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+    for (int c = 0; c < NP / 2; ++c) {
+      double2 t = __ldg(q + c);
+      v[2 * c] = t.x;
+      v[2 * c + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < NP; ++c) v[c] = __ldg(p + c);
+  }
+}
+
+// acc += A[z][r][:] . x[col[z]][:] over the block row (lane r)
+template <int NP>
+__device__ __forceinline__ double row_dot(int64_t z0, int64_t z1, int r, const int32_t* __restrict__ col,
+                                          const double* __restrict__ val, const double* __restrict__ x) {
+  double acc = 0.0;
+  for (int64_t z = z0; z < z1; ++z) {
+    double a[NP], xv[NP];
+    ldrow<NP>(val + z * (NP * NP) + r * NP, a);
+    ldrow<NP>(x + (int64_t)__ldg(col + z) * NP, xv);
+#pragma unroll
+    for (int c = 0; c < NP; ++c) acc = fma(a[c], xv[c], acc);
+  }
+  return acc;
+}
+
+// ------------------------------------------------------------------------------------------
+// operator apply: y = M x (MODE 0) or y = b - M x (MODE 1)
+template <int NP, int MODE>
+__global__ void __launch_bounds__(kThreads) k_spmv(int64_t nb, const int64_t* __restrict__ rp,
+                                                  const int32_t* __restrict__ col,
+                                                  const double* __restrict__ val,
+                                                  const double* __restrict__ x,
+                                                  const double* __restrict__ b,
+                                                  double* __restrict__ y) {
+  constexpr int GPW = Grp<NP>::GPW;
+  const int lane = threadIdx.x & 31;
+  const int g = lane / NP, r = lane - g * NP;
+  if (g >= GPW) return;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp * GPW + g; i < nb; i += nw * GPW) {
+    double acc = row_dot<NP>(__ldg(rp + i), __ldg(rp + i + 1), r, col, val, x);
+    y[i * NP + r] = MODE ? b[i * NP + r] - acc : acc;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// in-group solve of (L L^T) z = v with the packed Cholesky factor L (lane r holds v_r);
+// same elimination order as a row-oriented forward substitution
+template <int NP>
+__device__ __forceinline__ double chol_solve_group(const double* __restrict__ Lp, int r, int g,
+                                                   unsigned mask, double v) {
+  double Lrow[NP], Lcol[NP];
+#pragma unroll
+  for (int c = 0; c < NP; ++c) {
+    Lrow[c] = (c <= r) ? __ldg(Lp + r * (r + 1) / 2 + c) : 0.0;
+    Lcol[c] = (c >= r) ? __ldg(Lp + c * (c + 1) / 2 + r) : 0.0;
+  }
+  const int base = g * NP;
+  double acc = v, y = 0.0;
+#pragma unroll
+  for (int c = 0; c < NP; ++c) {
+    double t = (r == c) ? acc / Lrow[c] : 0.0;
+    double yc = __shfl_sync(mask, t, base + c);
+    if (r == c) y = yc;
+    if (r > c) acc -= Lrow[c] * yc;
+  }
+  double acc2 = y, z = 0.0;
+#pragma unroll
+  for (int c = NP - 1; c >= 0; --c) {
+    double t = (r == c) ? acc2 / Lcol[c] : 0.0;
+    double zc = __shfl_sync(mask, t, base + c);
+    if (r == c) z = zc;
+    if (r < c) acc2 -= Lcol[c] * zc;
+  }
+  return z;
+}
+
+// damped block Jacobi: xo = xi + omega D^{-1} (b - M xi); ZERO: xi = 0 (no operator apply)
+template <int NP, bool ZERO>
+__global__ void __launch_bounds__(kThreads) k_smooth(int64_t nb, const int64_t* __restrict__ rp,
+                                                    const int32_t* __restrict__ col,
+                                                    const double* __restrict__ val,
+                                                    const double* __restrict__ Lf, double omega,
+                                                    const double* __restrict__ b,
+                                                    const double* __restrict__ xi,
+                                                    double* __restrict__ xo) {
+  constexpr int GPW = Grp<NP>::GPW, NT = Grp<NP>::NT;
+  const int lane = threadIdx.x & 31;
+  const int g = lane / NP, r = lane - g * NP;
+  if (g >= GPW) return;
+  const unsigned mask = group_mask(g, NP);
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp * GPW + g; i < nb; i += nw * GPW) {
+    double res = b[i * NP + r];
+    if (!ZERO) res -= row_dot<NP>(__ldg(rp + i), __ldg(rp + i + 1), r, col, val, xi);
+    double z = chol_solve_group<NP>(Lf + i * NT, r, g, mask, res);
+    xo[i * NP + r] = (ZERO ? 0.0 : xi[i * NP + r]) + omega * z;
+  }
+}
+
+// z = D^{-1} v (no damping, no operator); used by the Lanczos estimate
+template <int NP>
+__global__ void __launch_bounds__(kThreads) k_bjsolve(int64_t nb, const double* __restrict__ Lf,
+                                                     const double* __restrict__ v,
+                                                     double* __restrict__ z) {
+  constexpr int GPW = Grp<NP>::GPW, NT = Grp<NP>::NT;
+  const int lane = threadIdx.x & 31;
+  const int g = lane / NP, r = lane - g * NP;
+  if (g >= GPW) return;
+  const unsigned mask = group_mask(g, NP);
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp * GPW + g; i < nb; i += nw * GPW)
+    z[i * NP + r] = chol_solve_group<NP>(Lf + i * NT, r, g, mask, v[i * NP + r]);
+}
+
+// w = D v with the diagonal blocks of M (diag[i] = position of block (i,i))
+template <int NP>
+__global__ void __launch_bounds__(kThreads) k_diagmul(int64_t nb, const int64_t* __restrict__ diag,
+                                                     const double* __restrict__ val,
+                                                     const double* __restrict__ v,
+                                                     double* __restrict__ w) {
+  constexpr int GPW = Grp<NP>::GPW;
+  const int lane = threadIdx.x & 31;
+  const int g = lane / NP, r = lane - g * NP;
+  if (g >= GPW) return;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp * GPW + g; i < nb; i += nw * GPW) {
+    double a[NP], xv[NP];
+    ldrow<NP>(val + __ldg(diag + i) * (NP * NP) + r * NP, a);
+    ldrow<NP>(v + i * NP, xv);
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < NP; ++c) s = fma(a[c], xv[c], s);
+    w[i * NP + r] = s;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// rc[C] = sum over children f of C of R_f^T res_f, res_f = b_f - (M x)_f (RESID) or b_f.
+// One group per coarse block: deterministic, no atomics.
+template <int NP, bool RESID>
+__global__ void __launch_bounds__(kThreads) k_restrict(int64_t nbc, const int64_t* __restrict__ cptr,
+                                                      const int32_t* __restrict__ ch,
+                                                      const int64_t* __restrict__ rp,
+                                                      const int32_t* __restrict__ col,
+                                                      const double* __restrict__ val,
+                                                      const double* __restrict__ R,
+                                                      const double* __restrict__ b,
+                                                      const double* __restrict__ x,
+                                                      double* __restrict__ rc) {
+  constexpr int GPW = Grp<NP>::GPW;
+  const int lane = threadIdx.x & 31;
+  const int g = lane / NP, r = lane - g * NP;
+  if (g >= GPW) return;
+  const unsigned mask = group_mask(g, NP);
+  const int base = g * NP;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t C = warp * GPW + g; C < nbc; C += nw * GPW) {
+    double acc = 0.0;
+    for (int64_t t = __ldg(cptr + C); t < __ldg(cptr + C + 1); ++t) {
+      const int64_t f = __ldg(ch + t);
+      double res = b[f * NP + r];
+      if (RESID) res -= row_dot<NP>(__ldg(rp + f), __ldg(rp + f + 1), r, col, val, x);
+      const double* Rf = R + f * (NP * NP);
+      double s = 0.0;
+#pragma unroll
+      for (int m = 0; m < NP; ++m) {
+        double rm = __shfl_sync(mask, res, base + m);
+        s = fma(__ldg(Rf + m * NP + r), rm, s);
+      }
+      acc += s;
+    }
+    rc[C * NP + r] = acc;
+  }
+}
+
+// xo_f = xi_f + R_f zc[agg[f]]  (xo may equal xi)
+template <int NP>
+__global__ void __launch_bounds__(kThreads) k_prolong(int64_t nbf, const int32_t* __restrict__ agg,
+                                                     const double* __restrict__ R,
+                                                     const double* __restrict__ zc,
+                                                     const double* xi, double* xo) {
+  constexpr int GPW = Grp<NP>::GPW;
+  const int lane = threadIdx.x & 31;
+  const int g = lane / NP, r = lane - g * NP;
+  if (g >= GPW) return;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t f = warp * GPW + g; f < nbf; f += nw * GPW) {
+    double a[NP], z[NP];
+    ldrow<NP>(R + f * (NP * NP) + r * NP, a);
+    ldrow<NP>(zc + (int64_t)__ldg(agg + f) * NP, z);
+    double s = 0.0;
+#pragma unroll
+    for (int n = 0; n < NP; ++n) s = fma(a[n], z[n], s);
+    xo[f * NP + r] = xi[f * NP + r] + s;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Galerkin product M_c = R^T M R: one group per coarse row I accumulates, for every child i
+// of I and every fine block (i, j), R_i^T M_ij R_j into the coarse block (I, agg[j]).
+// The coarse values must be zero on entry.
+template <int NP>
+__global__ void __launch_bounds__(kThreads) k_galerkin(int64_t nbc, const int64_t* __restrict__ cptr,
+                                                      const int32_t* __restrict__ ch,
+                                                      const int64_t* __restrict__ rp,
+                                                      const int32_t* __restrict__ col,
+                                                      const double* __restrict__ val,
+                                                      const int32_t* __restrict__ agg,
+                                                      const double* __restrict__ R,
+                                                      const int64_t* __restrict__ crp,
+                                                      const int32_t* __restrict__ ccol,
+                                                      double* __restrict__ cval) {
+  constexpr int GPW = Grp<NP>::GPW;
+  __shared__ double T[kThreads / 32][GPW][NP * NP];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int g = lane / NP, r = lane - g * NP;
+  if (g >= GPW) return;
+  const unsigned mask = group_mask(g, NP);
+  double* Tg = T[wib][g];
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t I = warp * GPW + g; I < nbc; I += nw * GPW) {
+    const int64_t c0 = __ldg(crp + I), c1 = __ldg(crp + I + 1);
+    for (int64_t t = __ldg(cptr + I); t < __ldg(cptr + I + 1); ++t) {
+      const int64_t i = __ldg(ch + t);
+      const double* Ri = R + i * (NP * NP);
+      for (int64_t z = __ldg(rp + i); z < __ldg(rp + i + 1); ++z) {
+        const int64_t j = __ldg(col + z);
+        const double* Rj = R + j * (NP * NP);
+        const int32_t J = __ldg(agg + j);
+        // T = M_ij R_j, lane r computes row r
+        double m[NP];
+        ldrow<NP>(val + z * (NP * NP) + r * NP, m);
+#pragma unroll
+        for (int n = 0; n < NP; ++n) {
+          double s = 0.0;
+#pragma unroll
+          for (int a = 0; a < NP; ++a) s = fma(m[a], __ldg(Rj + a * NP + n), s);
+          Tg[r * NP + n] = s;
+        }
+        __syncwarp(mask);
+        // locate (I, J) in the coarse row
+        int64_t lo = c0, hi = c1 - 1;
+        while (lo < hi) {
+          int64_t mid = (lo + hi) >> 1;
+          if (__ldg(ccol + mid) < J) lo = mid + 1;
+          else hi = mid;
+        }
+        double* dst = cval + lo * (NP * NP) + r * NP;
+        // row r of R_i^T T
+        double ri[NP];
+#pragma unroll
+        for (int a = 0; a < NP; ++a) ri[a] = __ldg(Ri + a * NP + r);
+#pragma unroll
+        for (int n = 0; n < NP; ++n) {
+          double s = 0.0;
+#pragma unroll
+          for (int a = 0; a < NP; ++a) s = fma(ri[a], Tg[a * NP + n], s);
+          dst[n] += s;
+        }
+        __syncwarp(mask);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Cholesky factor of every diagonal block (one thread per block, packed lower triangle);
+// err is set when a block is not positive definite.
+template <int NP>
+__global__ void k_diag_chol(int64_t nb, const int64_t* __restrict__ diag, const double* __restrict__ val,
+                            double* __restrict__ Lf, int* err) {
+  constexpr int NT = Grp<NP>::NT;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  double A[NP * NP];
+  const double* src = val + diag[i] * (NP * NP);
+  for (int e = 0; e < NP * NP; ++e) A[e] = src[e];
+  for (int j = 0; j < NP; ++j) {
+    double s = A[j * NP + j];
+    for (int p = 0; p < j; ++p) s -= A[j * NP + p] * A[j * NP + p];
+    if (!(s > 0.0)) {
+      atomicOr(err, 1);
+      return;
+    }
+    double d = sqrt(s);
+    A[j * NP + j] = d;
+    for (int q = j + 1; q < NP; ++q) {
+      double t = A[q * NP + j];
+      for (int p = 0; p < j; ++p) t -= A[q * NP + p] * A[j * NP + p];
+      A[q * NP + j] = t / d;
+    }
+  }
+  double* dst = Lf + i * NT;
+  for (int q = 0; q < NP; ++q)
+    for (int c = 0; c <= q; ++c) dst[q * (q + 1) / 2 + c] = A[q * NP + c];
+}
+
+// ------------------------------------------------------------------------------------------
+// coarsest level: dense matrix, Cholesky, inverse, GEMV
+
+// dense[(i*NP+r)*n + col*NP+c] = block values
+__global__ void k_bsr_to_dense(int64_t nb, int np, const int64_t* __restrict__ rp,
+                               const int32_t* __restrict__ col, const double* __restrict__ val,
+                               int64_t n, double* __restrict__ A) {
+  int64_t i = blockIdx.x;
+  if (i >= nb) return;
+  const int np2 = np * np;
+  for (int64_t z = rp[i]; z < rp[i + 1]; ++z)
+    for (int e = threadIdx.x; e < np2; e += blockDim.x) {
+      int r = e / np, c = e - r * np;
+      A[(i * np + r) * n + (int64_t)col[z] * np + c] = val[z * np2 + e];
+    }
+}
+
+// in-place right-looking Cholesky of the n x n matrix (single CTA); lower triangle holds L
+__global__ void __launch_bounds__(1024) k_dense_chol(int64_t n, double* A, int* err) {
+  __shared__ double djj;
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int64_t j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      double s = A[j * n + j];
+      if (!(s > 0.0)) {
+        bad = 1;
+        s = 1.0;
+      }
+      djj = sqrt(s);
+      A[j * n + j] = djj;
+    }
+    __syncthreads();
+    if (bad) break;
+    for (int64_t i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[i * n + j] /= djj;
+    __syncthreads();
+    const int64_t m = n - j - 1;
+    const int64_t tot = m * m;
+    for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
+      int64_t a = j + 1 + e / m, c = j + 1 + e % m;
+      if (c <= a) A[a * n + c] -= A[a * n + j] * A[c * n + j];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && bad) *err = 1;
+}
+
+// column j of L^{-1} (one thread per column)
+__global__ void k_tri_inverse(int64_t n, const double* __restrict__ L, double* __restrict__ X) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  for (int64_t i = 0; i < j; ++i) X[i * n + j] = 0.0;
+  for (int64_t i = j; i < n; ++i) {
+    double s = (i == j) ? 1.0 : 0.0;
+    for (int64_t p = j; p < i; ++p) s -= L[i * n + p] * X[p * n + j];
+    X[i * n + j] = s / L[i * n + i];
+  }
+}
+
+// Minv = X^T X with X = L^{-1} lower triangular (16x16 tiles)
+__global__ void k_xtx(int64_t n, const double* __restrict__ X, double* __restrict__ Minv) {
+  __shared__ double As[16][17], Bs[16][17];
+  int64_t i = (int64_t)blockIdx.y * 16 + threadIdx.y, j = (int64_t)blockIdx.x * 16 + threadIdx.x;
+  double s = 0.0;
+  for (int64_t k0 = 0; k0 < n; k0 += 16) {
+    int64_t ka = k0 + threadIdx.x, kb = k0 + threadIdx.y;
+    As[threadIdx.y][threadIdx.x] = (ka < n && (int64_t)blockIdx.y * 16 + threadIdx.y < n)
+                                       ? X[ka * n + (int64_t)blockIdx.y * 16 + threadIdx.y] : 0.0;
+    Bs[threadIdx.y][threadIdx.x] = (kb < n && j < n) ? X[kb * n + j] : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 16; ++q) s = fma(As[threadIdx.y][q], Bs[q][threadIdx.x], s);
+    __syncthreads();
+  }
+  if (i < n && j < n) Minv[i * n + j] = s;
+}
+
+// y = A x for a dense row-major n x n matrix: one warp per row
+__global__ void __launch_bounds__(kThreads) k_gemv(int64_t n, const double* __restrict__ A,
+                                                  const double* __restrict__ x, double* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (row >= n) return;
+  double s = 0.0;
+  for (int64_t c = lane; c < n; c += 32) s = fma(__ldg(A + row * n + c), __ldg(x + c), s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) y[row] = s;
+}
+
+// ------------------------------------------------------------------------------------------
+// deterministic reductions and Krylov vector updates
+
+constexpr int kRedBlocks = 608;  // 4 x 152 SMs; fixed so that the summation order is fixed
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sh[kThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (w == 0) {
+    t = (l < kThreads / 32) ? sh[l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  __syncthreads();
+  return t;  // valid in thread 0
+}
+
+// partial[blockIdx] = sum over the block's grid-stride share of x_i y_i
+__global__ void __launch_bounds__(kThreads) k_dot_partial(int64_t n, const double* __restrict__ x,
+                                                         const double* __restrict__ y,
+                                                         double* __restrict__ partial) {
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s = fma(x[i], y[i], s);
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// out = sum of partial[0..np) in a fixed order
+__global__ void __launch_bounds__(kThreads) k_sum_final(int np, const double* __restrict__ partial,
+                                                       double* __restrict__ out) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += partial[i];
+  s = block_sum(s);
+  if (threadIdx.x == 0) *out = s;
+}
+
+// PCG scalars kept on the device
+struct PcgScal {
+  double rz, rz_new, pq, rr, alpha, beta;
+  int bad;
+};
+
+// alpha = rz / pq
+__global__ void k_pcg_alpha(PcgScal* S) {
+  double pq = S->pq;
+  if (!(pq > 0.0) || !isfinite(pq)) {
+    S->bad = 1;
+    S->alpha = 0.0;
+  } else {
+    S->alpha = S->rz / pq;
+  }
+}
+
+// beta = rz_new / rz; rz = rz_new
+__global__ void k_pcg_beta(PcgScal* S) {
+  double rn = S->rz_new;
+  if (!(rn > 0.0) || !isfinite(rn)) {
+    S->bad = 1;
+    S->beta = 0.0;
+  } else {
+    S->beta = rn / S->rz;
+  }
+  S->rz = rn;
+}
+
+// x += alpha p; r -= alpha q; partial[] of r.r
+__global__ void __launch_bounds__(kThreads) k_pcg_xr(int64_t n, const PcgScal* __restrict__ S,
+                                                    const double* __restrict__ p,
+                                                    const double* __restrict__ q, double* __restrict__ x,
+                                                    double* __restrict__ r, double* __restrict__ partial) {
+  const double a = S->alpha;
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] = fma(a, p[i], x[i]);
+    double ri = fma(-a, q[i], r[i]);
+    r[i] = ri;
+    s = fma(ri, ri, s);
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// p = z + beta p
+__global__ void __launch_bounds__(kThreads) k_pcg_p(int64_t n, const PcgScal* __restrict__ S,
+                                                   const double* __restrict__ z, double* __restrict__ p) {
+  const double be = S->beta;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = fma(be, p[i], z[i]);
+}
+
+__global__ void k_copy(int64_t n, const double* __restrict__ a, double* __restrict__ b) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = a[i];
+}
+
+// y += a x (a on the host)
+__global__ void k_axpy(int64_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = fma(a, x[i], y[i]);
+}
+
+// y = a x + b y, with a, b on the host
+__global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+
+// x *= a
+__global__ void k_scale(int64_t n, double a, double* __restrict__ x) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] *= a;
+}
+
+// v_i = ((i+1) * 2654435761 mod 2^32) / 2^32 - 0.5 (Knuth's multiplicative hash)
+__global__ void k_hash_vector(int64_t n, double* __restrict__ v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t h = (uint32_t)((uint64_t)(i + 1) * 2654435761ull);
+    v[i] = (double)h / 4294967296.0 - 0.5;
+  }
+}
+
+}  // namespace xdg

@@ -1,0 +1,251 @@
+"""Thin ctypes binding of libxdg (include/xdg.h): argument marshalling only.
+
+Every computation runs in the CUDA kernels of libxdg.so. Device vectors are torch CUDA
+tensors (float64, contiguous) passed by data pointer; host vectors are numpy float64 arrays.
+If libxdg.so cannot be loaded this module raises; it has no CPU fallback.
+
+Entry points mirror the C names: create_hierarchy / destroy / get_info / export_level /
+apply / smooth / restrict / prolong / coarse_solve / vcycle / solve / solve_host.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_HERE)
+LIB_PATH = os.path.join(_HERE, "libxdg.so")
+_SRCS = [os.path.join(_HERE, "csrc", "xdg.cu"), os.path.join(_HERE, "csrc", "xdg_kernels.cuh"),
+         os.path.join(_ROOT, "include", "xdg.h")]
+
+XDG_OK, XDG_EINVAL, XDG_ECUDA, XDG_ENOMEM, XDG_ENOTCONV, XDG_EBREAKDOWN, XDG_ETIMEOUT = range(7)
+XDG_PREC_F64, XDG_PREC_F32, XDG_PREC_BF16 = 0, 1, 2
+MAX_LEVELS = 24
+
+NVCC_FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
+              "-Xcompiler", "-fPIC", "-shared"]
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile libxdg.so in-tree for sm_103a with nvcc (cross-compiles without a GPU)."""
+    newest = max(os.path.getmtime(s) for s in _SRCS)
+    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
+        return LIB_PATH
+    nvcc = os.environ.get("NVCC", "nvcc")
+    tmp = LIB_PATH + ".tmp%d" % os.getpid()
+    cmd = [nvcc] + NVCC_FLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-o", tmp, _SRCS[0]]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class XdgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (_NAMES.get(code, "XDG_%d" % code), msg))
+        self.code = code
+
+
+_NAMES = {0: "XDG_OK", 1: "XDG_EINVAL", 2: "XDG_ECUDA", 3: "XDG_ENOMEM", 4: "XDG_ENOTCONV",
+          5: "XDG_EBREAKDOWN", 6: "XDG_ETIMEOUT"}
+
+
+class Problem(C.Structure):
+    _fields_ = [("Np", C.c_int), ("n_levels", C.c_int), ("nb", C.POINTER(C.c_int64)),
+                ("row_ptr", C.POINTER(C.c_int64)), ("col", C.POINTER(C.c_int32)),
+                ("val", C.POINTER(C.c_double)), ("agg", C.POINTER(C.POINTER(C.c_int32))),
+                ("R", C.POINTER(C.POINTER(C.c_double)))]
+
+
+class HierOpts(C.Structure):
+    _fields_ = [("omega", C.c_double), ("lanczos_steps", C.c_int), ("nu", C.c_int),
+                ("gamma", C.c_int), ("low_precision", C.c_int)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("check_every", C.c_int),
+                ("precision", C.c_int), ("inner_tol", C.c_double), ("time_budget_ms", C.c_double)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("outer", C.c_int), ("relres", C.c_double),
+                ("ms", C.c_double), ("status", C.c_int), ("launches", C.c_int64)]
+
+
+class HierInfo(C.Structure):
+    _fields_ = [("Np", C.c_int), ("n_levels", C.c_int), ("nb", C.c_int64 * MAX_LEVELS),
+                ("nnzb", C.c_int64 * MAX_LEVELS), ("omega", C.c_double * MAX_LEVELS),
+                ("lambda_max", C.c_double * MAX_LEVELS), ("coarse_n", C.c_int64),
+                ("device_bytes", C.c_size_t), ("setup_ms", C.c_double * 3)]
+
+
+# (name, restype, argtypes) of every exported entry point
+_vp, _dp, _ip = C.c_void_p, C.POINTER(C.c_double), C.c_int
+SIGNATURES = [
+    ("xdg_create_hierarchy", C.c_int, [C.POINTER(Problem), C.POINTER(HierOpts), _vp, C.POINTER(_vp)]),
+    ("xdg_destroy", C.c_int, [_vp]),
+    ("xdg_strerror", C.c_char_p, [_ip]),
+    ("xdg_last_error", C.c_char_p, []),
+    ("xdg_get_info", C.c_int, [_vp, C.POINTER(HierInfo)]),
+    ("xdg_export_level", C.c_int, [_vp, _ip, C.POINTER(C.c_int64), C.POINTER(C.c_int32), _dp]),
+    ("xdg_apply", C.c_int, [_vp, _ip, _vp, _vp, _ip]),
+    ("xdg_smooth", C.c_int, [_vp, _ip, _vp, _vp, _vp]),
+    ("xdg_restrict", C.c_int, [_vp, _ip, _vp, _vp, _vp]),
+    ("xdg_prolong", C.c_int, [_vp, _ip, _vp, _vp, _vp]),
+    ("xdg_coarse_solve", C.c_int, [_vp, _vp, _vp]),
+    ("xdg_vcycle", C.c_int, [_vp, _vp, _vp]),
+    ("xdg_solve", C.c_int, [_vp, _vp, _vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
+    ("xdg_solve_host", C.c_int, [_vp, _dp, _dp, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
+]
+
+_lib = None
+
+
+def load():
+    """Load libxdg.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(LIB_PATH)
+        for name, rt, at in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = rt
+            f.argtypes = at
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != XDG_OK:
+        raise XdgError(rc, load().xdg_last_error().decode())
+
+
+def _dptr(t):
+    """device pointer of a torch CUDA float64 tensor (None -> NULL)"""
+    if t is None:
+        return None
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+class Hierarchy:
+    """Owner of an xdg_hier_t handle."""
+
+    def __init__(self, Np, nb, row_ptr, col, val, aggs, Rs, omega=0.0, lanczos_steps=12, nu=1,
+                 gamma=1, low_precision=0, stream=None):
+        L = load()
+        self._keep = []
+
+        def arr(a, dt):
+            a = np.ascontiguousarray(a, dtype=dt)
+            self._keep.append(a)
+            return a
+
+        nl = len(nb)
+        nb_a = arr(nb, np.int64)
+        rp = arr(row_ptr, np.int64)
+        cl = arr(col, np.int32)
+        vl = arr(val, np.float64)
+        ag = [arr(a, np.int32) for a in aggs]
+        Rr = [arr(r, np.float64) for r in Rs]
+        aggp = (C.POINTER(C.c_int32) * max(nl - 1, 1))(*[a.ctypes.data_as(C.POINTER(C.c_int32)) for a in ag])
+        Rp = (C.POINTER(C.c_double) * max(nl - 1, 1))(*[r.ctypes.data_as(_dp) for r in Rr])
+        self._keep += [aggp, Rp]
+        prob = Problem(Np, nl, nb_a.ctypes.data_as(C.POINTER(C.c_int64)), rp.ctypes.data_as(C.POINTER(C.c_int64)),
+                       cl.ctypes.data_as(C.POINTER(C.c_int32)), vl.ctypes.data_as(_dp), aggp, Rp)
+        opts = HierOpts(omega, lanczos_steps, nu, gamma, low_precision)
+        h = C.c_void_p()
+        st = C.c_void_p(stream) if stream else None
+        _check(L.xdg_create_hierarchy(C.byref(prob), C.byref(opts), st, C.byref(h)))
+        self._keep = []
+        self._h = h
+        self.Np = Np
+        self.nb = [int(x) for x in nb]
+        self.n = self.nb[0] * Np
+
+    @classmethod
+    def from_problem(cls, prob, **kw):
+        """From an xdg_problem.Problem (finest operator, maps and transfer blocks)."""
+        return cls(prob.Np, prob.nb, prob.row_ptr, prob.col, prob.val, prob.agg, prob.R, **kw)
+
+    # ------------------------------------------------------------------ queries
+    def info(self) -> dict:
+        i = HierInfo()
+        _check(load().xdg_get_info(self._h, C.byref(i)))
+        nl = i.n_levels
+        return {"Np": i.Np, "n_levels": nl, "nb": list(i.nb[:nl]), "nnzb": list(i.nnzb[:nl]),
+                "omega": list(i.omega[:nl]), "lambda_max": list(i.lambda_max[:nl]),
+                "coarse_n": i.coarse_n, "device_bytes": i.device_bytes, "setup_ms": list(i.setup_ms)}
+
+    def export_level(self, level: int):
+        inf = self.info()
+        nb, nnz, Np = inf["nb"][level - 1], inf["nnzb"][level - 1], self.Np
+        rp = np.zeros(nb + 1, np.int64)
+        cl = np.zeros(max(nnz, 1), np.int32)
+        vl = np.zeros(max(nnz, 1) * Np * Np)
+        _check(load().xdg_export_level(self._h, level, rp.ctypes.data_as(C.POINTER(C.c_int64)),
+                                       cl.ctypes.data_as(C.POINTER(C.c_int32)), vl.ctypes.data_as(_dp)))
+        return rp, cl[:nnz], vl[:nnz * Np * Np].reshape(nnz, Np, Np)
+
+    # ------------------------------------------------------------------ device entry points
+    def apply(self, level, x, y, prec=XDG_PREC_F64):
+        _check(load().xdg_apply(self._h, level, _dptr(x), _dptr(y), prec))
+
+    def smooth(self, level, b, x_in, x_out):
+        _check(load().xdg_smooth(self._h, level, _dptr(b), _dptr(x_in), _dptr(x_out)))
+
+    def restrict(self, level, b, x, rc):
+        _check(load().xdg_restrict(self._h, level, _dptr(b), _dptr(x), _dptr(rc)))
+
+    def prolong(self, level, zc, x_in, x_out):
+        _check(load().xdg_prolong(self._h, level, _dptr(zc), _dptr(x_in), _dptr(x_out)))
+
+    def coarse_solve(self, r, z):
+        _check(load().xdg_coarse_solve(self._h, _dptr(r), _dptr(z)))
+
+    def vcycle(self, b, x):
+        _check(load().xdg_vcycle(self._h, _dptr(b), _dptr(x)))
+
+    def solve(self, b, x, tol=1e-10, maxit=1000, check_every=1, precision=XDG_PREC_F64, inner_tol=0.0,
+              time_budget_ms=0.0, raise_on_error=True) -> dict:
+        o = SolveOpts(tol, maxit, check_every, precision, inner_tol, time_budget_ms)
+        info = SolveInfo()
+        rc = load().xdg_solve(self._h, _dptr(b), _dptr(x), C.byref(o), C.byref(info))
+        if raise_on_error:
+            _check(rc)
+        return {"iterations": info.iterations, "outer": info.outer, "relres": info.relres,
+                "ms": info.ms, "status": rc, "launches": info.launches}
+
+    def solve_host(self, b_host, x_host, tol=1e-10, maxit=1000, check_every=1, precision=XDG_PREC_F64,
+                   inner_tol=0.0, time_budget_ms=0.0, raise_on_error=True) -> dict:
+        """b_host, x_host: numpy float64 arrays (pinned memory gives the fastest copies)."""
+        for a in (b_host, x_host):
+            if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+                raise ValueError("host vectors must be contiguous float64")
+        o = SolveOpts(tol, maxit, check_every, precision, inner_tol, time_budget_ms)
+        info = SolveInfo()
+        rc = load().xdg_solve_host(self._h, b_host.ctypes.data_as(_dp), x_host.ctypes.data_as(_dp),
+                                   C.byref(o), C.byref(info))
+        if raise_on_error:
+            _check(rc)
+        return {"iterations": info.iterations, "outer": info.outer, "relres": info.relres,
+                "ms": info.ms, "status": rc, "launches": info.launches}
+
+    def destroy(self):
+        if getattr(self, "_h", None):
+            load().xdg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+# C-name aliases
+def create_hierarchy(prob, **kw) -> Hierarchy:
+    return Hierarchy.from_problem(prob, **kw)
