@@ -176,12 +176,12 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
+    stream = torch.cuda.Stream(device=dev)   # the handle's stream; events are recorded on it
 
     P = make_problem()
     n = P.dof
     t = time.perf_counter()
-    H = xdg.Hierarchy.from_problem(P, gamma=2, stream=stream.cuda_stream)
+    H = xdg.Hierarchy.from_problem(P, gamma=2, stream=stream)
     setup_s = time.perf_counter() - t
     hinfo = H.info()
     b = torch.from_numpy(P.b.reshape(-1).copy()).to(dev)

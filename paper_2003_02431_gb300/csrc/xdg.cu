@@ -69,15 +69,15 @@ struct Ops {
                  const double*, double, const double*, const double*, double*);
   void (*bjsolve)(int grid, cudaStream_t, int64_t, const double*, const double*, double*);
   void (*diagmul)(int grid, cudaStream_t, int64_t, const int64_t*, const double*, const double*, double*);
-  void (*restrict_)(int grid, cudaStream_t, int64_t, const int64_t*, const int32_t*, const int64_t*,
-                    const int32_t*, const double*, const double*, const double*, const double*,
-                    double*);
+  void (*resid_rt)(int grid, cudaStream_t, int64_t, const int64_t*, const int32_t*, const double*,
+                   const double*, const double*, const double*, double*);
+  void (*gather)(int grid, cudaStream_t, int64_t, const int64_t*, const int32_t*, const double*, double*);
   void (*prolong)(int grid, cudaStream_t, int64_t, const int32_t*, const double*, const double*,
                   const double*, double*);
   void (*galerkin)(int grid, cudaStream_t, int64_t, const int64_t*, const int32_t*, const int64_t*,
                    const int32_t*, const double*, const int32_t*, const double*, const int64_t*,
                    const int32_t*, double*);
-  void (*diag_chol)(cudaStream_t, int64_t, const int64_t*, const double*, double*, int*);
+  void (*diag_inv)(cudaStream_t, int64_t, const int64_t*, const double*, double*, int*);
   int gpw;
 };
 
@@ -89,23 +89,26 @@ struct OpsT {
     else k_spmv<NP, 0><<<grid, kThreads, 0, s>>>(nb, rp, col, val, x, b, y);
   }
   static void smooth(int grid, cudaStream_t s, int64_t nb, const int64_t* rp, const int32_t* col,
-                     const double* val, const double* Lf, double om, const double* b,
+                     const double* val, const double* Dinv, double om, const double* b,
                      const double* xi, double* xo) {
-    if (xi) k_smooth<NP, false><<<grid, kThreads, 0, s>>>(nb, rp, col, val, Lf, om, b, xi, xo);
-    else k_smooth<NP, true><<<grid, kThreads, 0, s>>>(nb, rp, col, val, Lf, om, b, xi, xo);
+    if (xi) k_smooth<NP, false><<<grid, kThreads, 0, s>>>(nb, rp, col, val, Dinv, om, b, xi, xo);
+    else k_smooth<NP, true><<<grid, kThreads, 0, s>>>(nb, rp, col, val, Dinv, om, b, xi, xo);
   }
-  static void bjsolve(int grid, cudaStream_t s, int64_t nb, const double* Lf, const double* v, double* z) {
-    k_bjsolve<NP><<<grid, kThreads, 0, s>>>(nb, Lf, v, z);
+  static void bjsolve(int grid, cudaStream_t s, int64_t nb, const double* Dinv, const double* v, double* z) {
+    k_bjsolve<NP><<<grid, kThreads, 0, s>>>(nb, Dinv, v, z);
   }
   static void diagmul(int grid, cudaStream_t s, int64_t nb, const int64_t* dg, const double* val,
                       const double* v, double* w) {
     k_diagmul<NP><<<grid, kThreads, 0, s>>>(nb, dg, val, v, w);
   }
-  static void restrict_(int grid, cudaStream_t s, int64_t nbc, const int64_t* cptr, const int32_t* ch,
-                        const int64_t* rp, const int32_t* col, const double* val, const double* R,
-                        const double* b, const double* x, double* rc) {
-    if (x) k_restrict<NP, true><<<grid, kThreads, 0, s>>>(nbc, cptr, ch, rp, col, val, R, b, x, rc);
-    else k_restrict<NP, false><<<grid, kThreads, 0, s>>>(nbc, cptr, ch, rp, col, val, R, b, x, rc);
+  static void resid_rt(int grid, cudaStream_t s, int64_t nbf, const int64_t* rp, const int32_t* col,
+                       const double* val, const double* R, const double* b, const double* x, double* t) {
+    if (x) k_resid_rt<NP, true><<<grid, kThreads, 0, s>>>(nbf, rp, col, val, R, b, x, t);
+    else k_resid_rt<NP, false><<<grid, kThreads, 0, s>>>(nbf, rp, col, val, R, b, x, t);
+  }
+  static void gather(int grid, cudaStream_t s, int64_t nbc, const int64_t* cptr, const int32_t* ch,
+                     const double* t, double* rc) {
+    k_gather<NP><<<grid, kThreads, 0, s>>>(nbc, cptr, ch, t, rc);
   }
   static void prolong(int grid, cudaStream_t s, int64_t nbf, const int32_t* agg, const double* R,
                       const double* zc, const double* xi, double* xo) {
@@ -116,12 +119,12 @@ struct OpsT {
                        const double* R, const int64_t* crp, const int32_t* ccol, double* cval) {
     k_galerkin<NP><<<grid, kThreads, 0, s>>>(nbc, cptr, ch, rp, col, val, agg, R, crp, ccol, cval);
   }
-  static void diag_chol(cudaStream_t s, int64_t nb, const int64_t* dg, const double* val, double* Lf,
-                        int* err) {
-    k_diag_chol<NP><<<(unsigned)((nb + 127) / 128), 128, 0, s>>>(nb, dg, val, Lf, err);
+  static void diag_inv(cudaStream_t s, int64_t nb, const int64_t* dg, const double* val, double* Dinv,
+                       int* err) {
+    k_diag_inv<NP><<<(unsigned)((nb + 63) / 64), 64, 0, s>>>(nb, dg, val, Dinv, err);
   }
   static Ops make() {
-    return Ops{NP, spmv, smooth, bjsolve, diagmul, restrict_, prolong, galerkin, diag_chol, Grp<NP>::GPW};
+    return Ops{NP, spmv, smooth, bjsolve, diagmul, resid_rt, gather, prolong, galerkin, diag_inv, Grp<NP>::GPW};
   }
 };
 
@@ -144,12 +147,13 @@ struct Level {
   int32_t* col = nullptr;
   double* val = nullptr;
   int64_t* diag = nullptr;
-  double* Lf = nullptr;
+  double* Dinv = nullptr;   // inverses of the diagonal blocks (levels above the coarsest)
   int32_t* agg = nullptr;  // to the next level
   double* R = nullptr;
   int64_t* cptr = nullptr;  // children of the next level's blocks
   int32_t* ch = nullptr;
   double *b = nullptr, *x = nullptr, *t = nullptr, *r = nullptr, *dz = nullptr;
+  double* s = nullptr;       // restriction scratch R_f^T res_f (levels above the coarsest)
   double omega = 0.0, lmax = 0.0;
 };
 
@@ -224,13 +228,14 @@ struct xdg_hier {
   void smooth(int l, const double* b, const double* xi, double* xo) {
     ++launches;
     Level& V = L[l];
-    ops.smooth(grid(V.nb), stream, V.nb, V.rp, V.col, V.val, V.Lf, V.omega, b, xi, xo);
+    ops.smooth(grid(V.nb), stream, V.nb, V.rp, V.col, V.val, V.Dinv, V.omega, b, xi, xo);
   }
   void restrict_(int l, const double* b, const double* x, double* rc) {
-    ++launches;
+    launches += 2;
     Level& V = L[l];
     Level& C = L[l + 1];
-    ops.restrict_(grid(C.nb), stream, C.nb, V.cptr, V.ch, V.rp, V.col, V.val, V.R, b, x, rc);
+    ops.resid_rt(grid(V.nb), stream, V.nb, V.rp, V.col, V.val, V.R, b, x, V.s);
+    ops.gather(vgrid(C.nb * Np), stream, C.nb, V.cptr, V.ch, V.s, rc);
   }
   void prolong(int l, const double* zc, const double* xi, double* xo) {
     ++launches;
@@ -405,7 +410,7 @@ int xdg_hier::lanczos(int l, int m, double* lam) {
     double a;
     TRY(read_scalar(dsc, &a));
     al.push_back(a);
-    ops.bjsolve(grid(V.nb), stream, V.nb, V.Lf, u, w);
+    ops.bjsolve(grid(V.nb), stream, V.nb, V.Dinv, u, w);
     k_axpy<<<vg, kThreads, 0, stream>>>(n, -a, q, w);
     k_axpy<<<vg, kThreads, 0, stream>>>(n, -bprev, qp, w);
     ops.diagmul(grid(V.nb), stream, V.nb, V.diag, V.val, w, Dw);
@@ -587,7 +592,8 @@ int xdg_hier::build(const xdg_problem* p, const xdg_hier_opts* o) {
                        cudaMemcpyHostToDevice, stream));
     CK(cudaMemcpyAsync(V.diag, V.h_diag.data(), V.nb * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
     if (l + 1 < nlev) {
-      TRY(alloc(&V.Lf, V.nb * (int64_t)(Np * (Np + 1) / 2)));
+      TRY(alloc(&V.Dinv, V.nb * Np2));
+      TRY(alloc(&V.s, n));
       TRY(alloc(&V.agg, V.nb));
       TRY(alloc(&V.R, V.nb * Np2));
       TRY(alloc(&V.cptr, L[l + 1].nb + 1));
@@ -633,7 +639,7 @@ int xdg_hier::build(const xdg_problem* p, const xdg_hier_opts* o) {
   t0 = clk::now();
   for (int l = 0; l + 1 < nlev; ++l) {
     Level& V = L[l];
-    ops.diag_chol(stream, V.nb, V.diag, V.val, V.Lf, derr);
+    ops.diag_inv(stream, V.nb, V.diag, V.val, V.Dinv, derr);
     CKL();
   }
   {

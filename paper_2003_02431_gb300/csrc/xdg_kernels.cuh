@@ -81,47 +81,29 @@ __global__ void __launch_bounds__(kThreads) k_spmv(int64_t nb, const int64_t* __
 }
 
 // ------------------------------------------------------------------------------------------
-// in-group solve of (L L^T) z = v with the packed Cholesky factor L (lane r holds v_r);
-// same elimination order as a row-oriented forward substitution
+// (W v)_r for an Np x Np row-major block W (lane r; v_c held by lane c of the group)
 template <int NP>
-__device__ __forceinline__ double chol_solve_group(const double* __restrict__ Lp, int r, int g,
-                                                   unsigned mask, double v) {
-  double Lrow[NP], Lcol[NP];
+__device__ __forceinline__ double block_gemv(const double* __restrict__ W, int r, int base, unsigned mask,
+                                             double v) {
+  double w[NP];
+  ldrow<NP>(W + r * NP, w);
+  double s = 0.0;
 #pragma unroll
-  for (int c = 0; c < NP; ++c) {
-    Lrow[c] = (c <= r) ? __ldg(Lp + r * (r + 1) / 2 + c) : 0.0;
-    Lcol[c] = (c >= r) ? __ldg(Lp + c * (c + 1) / 2 + r) : 0.0;
-  }
-  const int base = g * NP;
-  double acc = v, y = 0.0;
-#pragma unroll
-  for (int c = 0; c < NP; ++c) {
-    double t = (r == c) ? acc / Lrow[c] : 0.0;
-    double yc = __shfl_sync(mask, t, base + c);
-    if (r == c) y = yc;
-    if (r > c) acc -= Lrow[c] * yc;
-  }
-  double acc2 = y, z = 0.0;
-#pragma unroll
-  for (int c = NP - 1; c >= 0; --c) {
-    double t = (r == c) ? acc2 / Lcol[c] : 0.0;
-    double zc = __shfl_sync(mask, t, base + c);
-    if (r == c) z = zc;
-    if (r < c) acc2 -= Lcol[c] * zc;
-  }
-  return z;
+  for (int c = 0; c < NP; ++c) s = fma(w[c], __shfl_sync(mask, v, base + c), s);
+  return s;
 }
 
-// damped block Jacobi: xo = xi + omega D^{-1} (b - M xi); ZERO: xi = 0 (no operator apply)
+// damped block Jacobi: xo = xi + omega D^{-1} (b - M xi); ZERO: xi = 0 (no operator apply).
+// Dinv holds the inverse of every diagonal block (from its Cholesky factor).
 template <int NP, bool ZERO>
 __global__ void __launch_bounds__(kThreads) k_smooth(int64_t nb, const int64_t* __restrict__ rp,
                                                     const int32_t* __restrict__ col,
                                                     const double* __restrict__ val,
-                                                    const double* __restrict__ Lf, double omega,
+                                                    const double* __restrict__ Dinv, double omega,
                                                     const double* __restrict__ b,
                                                     const double* __restrict__ xi,
                                                     double* __restrict__ xo) {
-  constexpr int GPW = Grp<NP>::GPW, NT = Grp<NP>::NT;
+  constexpr int GPW = Grp<NP>::GPW;
   const int lane = threadIdx.x & 31;
   const int g = lane / NP, r = lane - g * NP;
   if (g >= GPW) return;
@@ -131,17 +113,17 @@ __global__ void __launch_bounds__(kThreads) k_smooth(int64_t nb, const int64_t* 
   for (int64_t i = warp * GPW + g; i < nb; i += nw * GPW) {
     double res = b[i * NP + r];
     if (!ZERO) res -= row_dot<NP>(__ldg(rp + i), __ldg(rp + i + 1), r, col, val, xi);
-    double z = chol_solve_group<NP>(Lf + i * NT, r, g, mask, res);
-    xo[i * NP + r] = (ZERO ? 0.0 : xi[i * NP + r]) + omega * z;
+    double z = block_gemv<NP>(Dinv + i * (NP * NP), r, g * NP, mask, res);
+    xo[i * NP + r] = ZERO ? omega * z : fma(omega, z, xi[i * NP + r]);
   }
 }
 
 // z = D^{-1} v (no damping, no operator); used by the Lanczos estimate
 template <int NP>
-__global__ void __launch_bounds__(kThreads) k_bjsolve(int64_t nb, const double* __restrict__ Lf,
+__global__ void __launch_bounds__(kThreads) k_bjsolve(int64_t nb, const double* __restrict__ Dinv,
                                                      const double* __restrict__ v,
                                                      double* __restrict__ z) {
-  constexpr int GPW = Grp<NP>::GPW, NT = Grp<NP>::NT;
+  constexpr int GPW = Grp<NP>::GPW;
   const int lane = threadIdx.x & 31;
   const int g = lane / NP, r = lane - g * NP;
   if (g >= GPW) return;
@@ -149,7 +131,7 @@ __global__ void __launch_bounds__(kThreads) k_bjsolve(int64_t nb, const double* 
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = warp * GPW + g; i < nb; i += nw * GPW)
-    z[i * NP + r] = chol_solve_group<NP>(Lf + i * NT, r, g, mask, v[i * NP + r]);
+    z[i * NP + r] = block_gemv<NP>(Dinv + i * (NP * NP), r, g * NP, mask, v[i * NP + r]);
 }
 
 // w = D v with the diagonal blocks of M (diag[i] = position of block (i,i))
@@ -176,18 +158,15 @@ __global__ void __launch_bounds__(kThreads) k_diagmul(int64_t nb, const int64_t*
 }
 
 // ------------------------------------------------------------------------------------------
-// rc[C] = sum over children f of C of R_f^T res_f, res_f = b_f - (M x)_f (RESID) or b_f.
-// One group per coarse block: deterministic, no atomics.
+// restriction, phase 1 (row-parallel): t_f = R_f^T res_f, res_f = b_f - (M x)_f (RESID) or b_f
 template <int NP, bool RESID>
-__global__ void __launch_bounds__(kThreads) k_restrict(int64_t nbc, const int64_t* __restrict__ cptr,
-                                                      const int32_t* __restrict__ ch,
-                                                      const int64_t* __restrict__ rp,
+__global__ void __launch_bounds__(kThreads) k_resid_rt(int64_t nbf, const int64_t* __restrict__ rp,
                                                       const int32_t* __restrict__ col,
                                                       const double* __restrict__ val,
                                                       const double* __restrict__ R,
                                                       const double* __restrict__ b,
                                                       const double* __restrict__ x,
-                                                      double* __restrict__ rc) {
+                                                      double* __restrict__ t) {
   constexpr int GPW = Grp<NP>::GPW;
   const int lane = threadIdx.x & 31;
   const int g = lane / NP, r = lane - g * NP;
@@ -196,22 +175,31 @@ __global__ void __launch_bounds__(kThreads) k_restrict(int64_t nbc, const int64_
   const int base = g * NP;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t C = warp * GPW + g; C < nbc; C += nw * GPW) {
-    double acc = 0.0;
-    for (int64_t t = __ldg(cptr + C); t < __ldg(cptr + C + 1); ++t) {
-      const int64_t f = __ldg(ch + t);
-      double res = b[f * NP + r];
-      if (RESID) res -= row_dot<NP>(__ldg(rp + f), __ldg(rp + f + 1), r, col, val, x);
-      const double* Rf = R + f * (NP * NP);
-      double s = 0.0;
+  for (int64_t f = warp * GPW + g; f < nbf; f += nw * GPW) {
+    double res = b[f * NP + r];
+    if (RESID) res -= row_dot<NP>(__ldg(rp + f), __ldg(rp + f + 1), r, col, val, x);
+    const double* Rf = R + f * (NP * NP);
+    double s = 0.0;
 #pragma unroll
-      for (int m = 0; m < NP; ++m) {
-        double rm = __shfl_sync(mask, res, base + m);
-        s = fma(__ldg(Rf + m * NP + r), rm, s);
-      }
-      acc += s;
-    }
-    rc[C * NP + r] = acc;
+    for (int m = 0; m < NP; ++m) s = fma(__ldg(Rf + m * NP + r), __shfl_sync(mask, res, base + m), s);
+    t[f * NP + r] = s;
+  }
+}
+
+// restriction, phase 2: rc[C] = sum of t_f over the children f of C, in increasing f
+// (deterministic; one thread per coarse entry)
+template <int NP>
+__global__ void __launch_bounds__(kThreads) k_gather(int64_t nbc, const int64_t* __restrict__ cptr,
+                                                    const int32_t* __restrict__ ch,
+                                                    const double* __restrict__ t,
+                                                    double* __restrict__ rc) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nbc * NP;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t C = e / NP;
+    const int r = (int)(e - C * NP);
+    double s = 0.0;
+    for (int64_t q = __ldg(cptr + C); q < __ldg(cptr + C + 1); ++q) s += t[(int64_t)__ldg(ch + q) * NP + r];
+    rc[e] = s;
   }
 }
 
@@ -308,12 +296,12 @@ __global__ void __launch_bounds__(kThreads) k_galerkin(int64_t nbc, const int64_
 }
 
 // ------------------------------------------------------------------------------------------
-// Cholesky factor of every diagonal block (one thread per block, packed lower triangle);
+// inverse of every diagonal block D = L L^T (one thread per block): Cholesky factor L, then
+// X = L^{-1} by forward substitution, then D^{-1} = X^T X (row-major, symmetric).
 // err is set when a block is not positive definite.
 template <int NP>
-__global__ void k_diag_chol(int64_t nb, const int64_t* __restrict__ diag, const double* __restrict__ val,
-                            double* __restrict__ Lf, int* err) {
-  constexpr int NT = Grp<NP>::NT;
+__global__ void k_diag_inv(int64_t nb, const int64_t* __restrict__ diag, const double* __restrict__ val,
+                           double* __restrict__ Dinv, int* err) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nb) return;
   double A[NP * NP];
@@ -334,9 +322,24 @@ __global__ void k_diag_chol(int64_t nb, const int64_t* __restrict__ diag, const 
       A[q * NP + j] = t / d;
     }
   }
-  double* dst = Lf + i * NT;
-  for (int q = 0; q < NP; ++q)
-    for (int c = 0; c <= q; ++c) dst[q * (q + 1) / 2 + c] = A[q * NP + c];
+  // X = L^{-1}, column by column (lower triangular)
+  double X[NP * NP];
+  for (int e = 0; e < NP * NP; ++e) X[e] = 0.0;
+  for (int c = 0; c < NP; ++c)
+    for (int q = c; q < NP; ++q) {
+      double s = (q == c) ? 1.0 : 0.0;
+      for (int p = c; p < q; ++p) s -= A[q * NP + p] * X[p * NP + c];
+      X[q * NP + c] = s / A[q * NP + q];
+    }
+  // D^{-1} = X^T X: entry (r, c) = sum over q >= max(r, c) of X[q][r] X[q][c]
+  double* dst = Dinv + i * (NP * NP);
+  for (int r = 0; r < NP; ++r)
+    for (int c = r; c < NP; ++c) {
+      double s = 0.0;
+      for (int q = c; q < NP; ++q) s += X[q * NP + r] * X[q * NP + c];
+      dst[r * NP + c] = s;
+      dst[c * NP + r] = s;
+    }
 }
 
 // ------------------------------------------------------------------------------------------

@@ -126,17 +126,45 @@ def _dptr(t):
     """device pointer of a torch CUDA float64 tensor (None -> NULL)"""
     if t is None:
         return None
-    if not (t.is_cuda and t.is_contiguous()):
-        raise ValueError("expected a contiguous CUDA tensor")
+    if not (t.is_cuda and t.is_contiguous() and t.dtype == _torch().float64):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
     return C.c_void_p(t.data_ptr())
 
 
+def _torch():
+    import torch
+    return torch
+
+
+class _Ordered:
+    """Orders a library call after the work already queued on torch's current stream, and the
+    work queued after it on torch's current stream after the call (event waits only)."""
+
+    def __init__(self, h):
+        self.h = h
+
+    def __enter__(self):
+        if self.h.stream is not None:
+            self.h.stream.wait_stream(_torch().cuda.current_stream(self.h.stream.device))
+
+    def __exit__(self, *a):
+        if self.h.stream is not None:
+            _torch().cuda.current_stream(self.h.stream.device).wait_stream(self.h.stream)
+
+
 class Hierarchy:
-    """Owner of an xdg_hier_t handle."""
+    """Owner of an xdg_hier_t handle.
+
+    The handle works on its own CUDA stream (`self.stream`, a torch.cuda.Stream created here
+    unless one is given); every call is ordered with torch's current stream by event waits."""
 
     def __init__(self, Np, nb, row_ptr, col, val, aggs, Rs, omega=0.0, lanczos_steps=12, nu=1,
                  gamma=1, low_precision=0, stream=None):
         L = load()
+        torch = _torch()
+        if stream is None:
+            stream = torch.cuda.Stream()
+        self.stream = stream
         self._keep = []
 
         def arr(a, dt):
@@ -158,8 +186,10 @@ class Hierarchy:
                        cl.ctypes.data_as(C.POINTER(C.c_int32)), vl.ctypes.data_as(_dp), aggp, Rp)
         opts = HierOpts(omega, lanczos_steps, nu, gamma, low_precision)
         h = C.c_void_p()
-        st = C.c_void_p(stream) if stream else None
-        _check(L.xdg_create_hierarchy(C.byref(prob), C.byref(opts), st, C.byref(h)))
+        st = C.c_void_p(stream.cuda_stream)
+        self._h = None
+        with _Ordered(self):
+            _check(L.xdg_create_hierarchy(C.byref(prob), C.byref(opts), st, C.byref(h)))
         self._keep = []
         self._h = h
         self.Np = Np
@@ -181,6 +211,7 @@ class Hierarchy:
                 "coarse_n": i.coarse_n, "device_bytes": i.device_bytes, "setup_ms": list(i.setup_ms)}
 
     def export_level(self, level: int):
+        _torch().cuda.synchronize(self.stream.device)
         inf = self.info()
         nb, nnz, Np = inf["nb"][level - 1], inf["nnzb"][level - 1], self.Np
         rp = np.zeros(nb + 1, np.int64)
@@ -192,28 +223,35 @@ class Hierarchy:
 
     # ------------------------------------------------------------------ device entry points
     def apply(self, level, x, y, prec=XDG_PREC_F64):
-        _check(load().xdg_apply(self._h, level, _dptr(x), _dptr(y), prec))
+        with _Ordered(self):
+            _check(load().xdg_apply(self._h, level, _dptr(x), _dptr(y), prec))
 
     def smooth(self, level, b, x_in, x_out):
-        _check(load().xdg_smooth(self._h, level, _dptr(b), _dptr(x_in), _dptr(x_out)))
+        with _Ordered(self):
+            _check(load().xdg_smooth(self._h, level, _dptr(b), _dptr(x_in), _dptr(x_out)))
 
     def restrict(self, level, b, x, rc):
-        _check(load().xdg_restrict(self._h, level, _dptr(b), _dptr(x), _dptr(rc)))
+        with _Ordered(self):
+            _check(load().xdg_restrict(self._h, level, _dptr(b), _dptr(x), _dptr(rc)))
 
     def prolong(self, level, zc, x_in, x_out):
-        _check(load().xdg_prolong(self._h, level, _dptr(zc), _dptr(x_in), _dptr(x_out)))
+        with _Ordered(self):
+            _check(load().xdg_prolong(self._h, level, _dptr(zc), _dptr(x_in), _dptr(x_out)))
 
     def coarse_solve(self, r, z):
-        _check(load().xdg_coarse_solve(self._h, _dptr(r), _dptr(z)))
+        with _Ordered(self):
+            _check(load().xdg_coarse_solve(self._h, _dptr(r), _dptr(z)))
 
     def vcycle(self, b, x):
-        _check(load().xdg_vcycle(self._h, _dptr(b), _dptr(x)))
+        with _Ordered(self):
+            _check(load().xdg_vcycle(self._h, _dptr(b), _dptr(x)))
 
     def solve(self, b, x, tol=1e-10, maxit=1000, check_every=1, precision=XDG_PREC_F64, inner_tol=0.0,
               time_budget_ms=0.0, raise_on_error=True) -> dict:
         o = SolveOpts(tol, maxit, check_every, precision, inner_tol, time_budget_ms)
         info = SolveInfo()
-        rc = load().xdg_solve(self._h, _dptr(b), _dptr(x), C.byref(o), C.byref(info))
+        with _Ordered(self):
+            rc = load().xdg_solve(self._h, _dptr(b), _dptr(x), C.byref(o), C.byref(info))
         if raise_on_error:
             _check(rc)
         return {"iterations": info.iterations, "outer": info.outer, "relres": info.relres,
@@ -227,8 +265,9 @@ class Hierarchy:
                 raise ValueError("host vectors must be contiguous float64")
         o = SolveOpts(tol, maxit, check_every, precision, inner_tol, time_budget_ms)
         info = SolveInfo()
-        rc = load().xdg_solve_host(self._h, b_host.ctypes.data_as(_dp), x_host.ctypes.data_as(_dp),
-                                   C.byref(o), C.byref(info))
+        with _Ordered(self):
+            rc = load().xdg_solve_host(self._h, b_host.ctypes.data_as(_dp), x_host.ctypes.data_as(_dp),
+                                       C.byref(o), C.byref(info))
         if raise_on_error:
             _check(rc)
         return {"iterations": info.iterations, "outer": info.outer, "relres": info.relres,
