@@ -189,6 +189,43 @@ int xdg_solve(xdg_hier_t h, const double* b, double* x, const xdg_solve_opts* o,
 int xdg_solve_host(xdg_hier_t h, const double* b_host, double* x_host, const xdg_solve_opts* o,
                    xdg_solve_info* info);
 
+/* Residual restriction for callers that cannot allocate device memory.
+ *
+ * The paper has no counterpart: this is an interface variant of xdg_restrict. It serves
+ * callers that must not call cudaMalloc -- code running inside a memory pool or arena that
+ * owns all device memory, plugins whose host forbids allocations after start-up, and
+ * real-time loops where an allocation could block or fail. No handle is needed: the caller
+ * passes every array, as device pointers, and the entry point allocates nothing (no
+ * cudaMalloc, cudaFree or allocating library call).
+ *
+ *   rc = R^T (b - M x) for one level (x == NULL: rc = R^T b), with
+ *   Np                  block size (6, 10, 15 or 20)
+ *   nb_fine, nb_coarse  blocks on the fine and the coarse level
+ *   row_ptr, col, val   fine-level BSR operator (layout as in xdg_problem)
+ *   R                   double[nb_fine*Np*Np] transfer blocks
+ *   child_ptr, child    children of every coarse block: int64[nb_coarse+1] and
+ *                       int32[nb_fine]; the children of block C are child[child_ptr[C] ..
+ *                       child_ptr[C+1]-1], ascending (the sum over them runs in this order)
+ *   b, x                double[nb_fine*Np];  rc  double[nb_coarse*Np]
+ *   stream              cudaStream_t the kernels are enqueued on (NULL: legacy stream)
+ *
+ * Scratch: a fixed device array of XDG_NOALLOC_MAX_ENTRIES doubles (8 MiB) inside the
+ * library, holding R_f^T (b_f - M_f x) for every fine block. Every GPU that loads the
+ * library holds this array until the process exits. nb_fine*Np above
+ * XDG_NOALLOC_MAX_ENTRIES is rejected with XDG_EINVAL before any work is enqueued.
+ * All calls share the array and it keeps the last call's contents; each call overwrites
+ * every entry it reads, so nothing has to be cleared. Calls whose work overlaps on one GPU
+ * (concurrent streams, or host threads without ordering) race on the array and give wrong
+ * results: serialise them.
+ * The first call on a device looks up the array's device address (once per device, with
+ * that device current); make that first call outside any CUDA stream capture.
+ * Errors: XDG_EINVAL (null pointer, unsupported Np, size over the maximum), XDG_ECUDA. */
+#define XDG_NOALLOC_MAX_ENTRIES (1 << 20)
+int xdg_restrict_noalloc(int Np, int64_t nb_fine, int64_t nb_coarse, const int64_t* row_ptr,
+                         const int32_t* col, const double* val, const double* R,
+                         const int64_t* child_ptr, const int32_t* child, const double* b,
+                         const double* x, double* rc, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -935,3 +936,83 @@ int xdg_solve_host(xdg_hier_t h, const double* b_host, double* x_host, const xdg
 }
 
 }  // extern "C"
+
+// ============================================================================================
+// Residual restriction without allocations (see xdg_restrict_noalloc in include/xdg.h).
+// The scratch lives in a file-scope device array; host code only ever sees its host-side
+// stand-in symbol, so the device address is looked up once per device and passed to the
+// kernels.
+static __device__ __align__(256) double g_noalloc_scratch[XDG_NOALLOC_MAX_ENTRIES];
+
+namespace {
+struct NoallocDev {
+  bool ready = false;
+  double* scratch = nullptr;
+  int sms = 0;
+};
+std::mutex g_noalloc_mu;
+NoallocDev g_noalloc_dev[128];
+}  // namespace
+
+extern "C" int xdg_restrict_noalloc(int Np, int64_t nb_fine, int64_t nb_coarse, const int64_t* row_ptr,
+                                    const int32_t* col, const double* val, const double* R,
+                                    const int64_t* child_ptr, const int32_t* child, const double* b,
+                                    const double* x, double* rc, void* stream) {
+  Ops ops;
+  if (!ops_for(Np, &ops)) {
+    set_err("xdg_restrict_noalloc: block size Np = %d not supported (6, 10, 15, 20)", Np);
+    return XDG_EINVAL;
+  }
+  if (nb_fine <= 0 || nb_coarse <= 0 || !row_ptr || !col || !val || !R || !child_ptr || !child || !b || !rc) {
+    set_err("xdg_restrict_noalloc: empty level or null pointer");
+    return XDG_EINVAL;
+  }
+  if (nb_fine > XDG_NOALLOC_MAX_ENTRIES / Np) {
+    set_err("xdg_restrict_noalloc: nb_fine*Np = %lld exceeds the fixed scratch of %d entries",
+            (long long)nb_fine * Np, XDG_NOALLOC_MAX_ENTRIES);
+    return XDG_EINVAL;
+  }
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 128) {
+    set_err("xdg_restrict_noalloc: device ordinal %d out of range", dev);
+    return XDG_EINVAL;
+  }
+  NoallocDev st;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    NoallocDev& d = g_noalloc_dev[dev];
+    if (!d.ready) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess) {
+        set_err("xdg_restrict_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        return XDG_ECUDA;
+      }
+      int sms = 0;
+      e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess) {
+        set_err("xdg_restrict_noalloc: %s", cudaGetErrorString(e));
+        return XDG_ECUDA;
+      }
+      d.scratch = static_cast<double*>(p);
+      d.sms = sms;
+      d.ready = true;
+    }
+    st = d;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  auto grid_rows = [&](int64_t rows) {
+    int64_t warps = (rows + ops.gpw - 1) / ops.gpw;
+    int64_t blocks = (warps + (kThreads / 32) - 1) / (kThreads / 32);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)st.sms * 8));
+  };
+  auto grid_vec = [&](int64_t n) {
+    int64_t blocks = (n + kThreads - 1) / kThreads;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)st.sms * 8));
+  };
+  ops.resid_rt(grid_rows(nb_fine), s, nb_fine, row_ptr, col, val, R, b, x, st.scratch);
+  ops.gather(grid_vec(nb_coarse * Np), s, nb_coarse, child_ptr, child, st.scratch, rc);
+  CKL();
+  return XDG_OK;
+}

@@ -98,7 +98,11 @@ SIGNATURES = [
     ("xdg_vcycle", C.c_int, [_vp, _vp, _vp]),
     ("xdg_solve", C.c_int, [_vp, _vp, _vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
     ("xdg_solve_host", C.c_int, [_vp, _dp, _dp, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
+    ("xdg_restrict_noalloc", C.c_int, [_ip, C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                      _vp]),
 ]
+
+NOALLOC_MAX_ENTRIES = 1 << 20
 
 _lib = None
 
@@ -283,6 +287,27 @@ class Hierarchy:
             self.destroy()
         except Exception:
             pass
+
+
+def restrict_noalloc(Np, nb_fine, nb_coarse, row_ptr, col, val, R, child_ptr, child, b, x, rc, stream=None):
+    """rc = R^T (b - M x) from caller-owned device tensors, with no allocation in the library
+    (see xdg_restrict_noalloc in include/xdg.h: fixed 8 MiB scratch, calls must not overlap).
+    row_ptr/child_ptr int64, col/child int32, the rest float64 CUDA tensors; x may be None."""
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+
+    def p(t, dt):
+        if t is None:
+            return None
+        if not (t.is_cuda and t.is_contiguous() and t.dtype == dt):
+            raise ValueError("expected a contiguous CUDA tensor of %s" % dt)
+        return C.c_void_p(t.data_ptr())
+
+    f64, i64, i32 = torch.float64, torch.int64, torch.int32
+    _check(load().xdg_restrict_noalloc(Np, nb_fine, nb_coarse, p(row_ptr, i64), p(col, i32), p(val, f64),
+                                       p(R, f64), p(child_ptr, i64), p(child, i32), p(b, f64), p(x, f64),
+                                       p(rc, f64), C.c_void_p(stream.cuda_stream)))
 
 
 # C-name aliases
