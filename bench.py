@@ -4,12 +4,14 @@
 Workload (synthetic, generated in-process): 3D XDG Poisson problem on the unit cube, 64^3
 Cartesian cells, spherical interface (centre (0.5,0.5,0.5), radius 0.31), diffusivity 1 inside /
 1000 outside, SIP, DG degree k=2 (Np=10), agglomeration threshold 0.1, manufactured smooth
-solution: 266,232 blocks, 2,662,320 DOF, 1,849,256 non-zero 10x10 blocks.
+solution: 266,232 blocks, 2,662,320 DOF, 1,849,256 non-zero 10x10 blocks, 5 levels.
 
-A step is one complete solve from x = 0: conjugate gradients preconditioned by the symmetric
-W-cycle (block-Jacobi smoothing, fused residual-restriction, prolongation, dense coarsest
-solve), stopped at ||b - M x|| <= 1e-10 ||b|| (the parity tests show the solution then lies
-within 1e-8 relative L2 of the FP64 oracle's solution). value = DOF solved per second.
+A step is one complete solve from x = 0 to ||b - M x|| <= 1e-10 ||b|| (the parity tests show
+the solution then lies within 1e-8 relative L2 of the FP64 oracle's solution). The headline
+path is flexible CG in FP64 (operator apply, residuals, updates) preconditioned by an FP32
+W-cycle (block-Jacobi smoothing, fused residual-restriction, prolongation, FP64 coarsest
+solve); the plain FP64 path (CG with the FP64 W-cycle) is timed next to it. value = DOF
+solved per second of the headline path.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl xdg|reference]
 """
@@ -28,13 +30,13 @@ sys.path.insert(0, ROOT)
 METRIC = "XDG solve time to 1e-8 rel. L2 & V-cycle MDOF/s vs plain FP64 path, 1 GB300"
 WORKLOAD = "xdg-poisson-3d-64^3-k2-sphere-R0.31-mu1:1000"
 TOL = 1e-10
+GAMMA, W_LEVELS = 2, 2   # W-cycle on the two finest levels, V-cycle below
 
 
-def peaks():
+def hbm_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
     except Exception:
         return 6800.0, "fallback"
 
@@ -47,17 +49,14 @@ class ClockSampler:
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
-        self.index = index
-        self.proc = None
-        self.lines = []
+        self.index, self.proc, self.lines = index, None, []
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
+            threading.Thread(target=self._read, daemon=True).start()
         except Exception:
             self.proc = None
         return self
@@ -93,18 +92,27 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+SIZE = 64  # cells per direction (--size; the benchmark workload is 64)
+
+
 def make_problem():
     import xdg_problem as xp
-    return xp.Problem(xp.config_3d_64(max_coarse_dof=1000))
+    return xp.Problem(xp.config_3d_64(N=SIZE, max_coarse_dof=1000))
+
+
+def oracle_hierarchy(P):
+    import oracle
+    O = oracle.Hierarchy(P, gamma=GAMMA)
+    oracle.set_w_levels(O, W_LEVELS)
+    return O
 
 
 def oracle_sample(P, iters_needed, budget_s=12.0):
     """Time the oracle's PCG iterations on this problem (bounded sample) and extrapolate."""
-    import oracle
     t = time.perf_counter()
-    O = oracle.Hierarchy(P, gamma=2)
+    O = oracle_hierarchy(P)
     setup = time.perf_counter() - t
-    m, spent, per = 4, 0.0, None
+    m, spent = 2, 0.0
     while True:
         t = time.perf_counter()
         O.pcg(P.b, tol=0.0, maxit=m)
@@ -114,39 +122,34 @@ def oracle_sample(P, iters_needed, budget_s=12.0):
         if dt >= budget_s / 3 or spent >= budget_s:
             break
         m *= 2
-    est = per * iters_needed
-    return {"per_iteration_s": per, "sample_iterations": m, "setup_s": setup, "est_solve_s": est,
-            "cores": os.cpu_count()}
+    return {"per_iteration_s": per, "sample_iterations": m, "setup_s": setup,
+            "est_solve_s": per * iters_needed, "cores": os.cpu_count()}
 
 
 def reference_arm(args):
-    """The oracle (plain FP64 CPU) on the same workload: each step a bounded sample of PCG
-    iterations; the metric extrapolates with the iteration count the oracle needs."""
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    """The oracle (plain FP64 CPU code) on the same workload: each step is a bounded sample of
+    5 PCG iterations, extrapolated with the iteration count of the oracle's full solve."""
+    if int(os.environ.get("RANK", "0")) != 0:
         return
-    import oracle
     P = make_problem()
-    O = oracle.Hierarchy(P, gamma=2)
-    _, iters, _, _ = O.pcg(P.b, tol=TOL, maxit=1000)  # warm-up: a full solve gives the count
+    O = oracle_hierarchy(P)
+    _, iters, _, _ = O.pcg(P.b, tol=TOL, maxit=1000)  # warm-up: the full solve gives the count
     per = []
     for s in range(args.warmup + args.steps):
         t = time.perf_counter()
         O.pcg(P.b, tol=0.0, maxit=5)
         if s >= args.warmup:
             per.append((time.perf_counter() - t) / 5)
-    t_iter = statistics.mean(per)
-    t_solve = t_iter * iters
+    t_solve = statistics.mean(per) * iters
     value = P.dof / t_solve / 1e6
     line = {"metric": METRIC, "value": value, "unit": "MDOF/s", "n_gpus": 0, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "impl": "reference",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "dof": P.dof, "tol": TOL, "iterations": iters,
-                       "l2": "inputs larger than L2"},
+                       "cycle": "W(1,1) on 2 levels, block Jacobi", "l2": "inputs larger than L2"},
             "cpu_baseline": {"value": value, "unit": "MDOF/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": "5 PCG+W-cycle iterations per step, extrapolated to the %d "
-                                       "iterations of the full solve" % iters},
+                             "sample": "5 PCG iterations per step, extrapolated to the %d iterations "
+                                       "of the oracle's full solve" % iters},
             "e2e": {"value": value, "unit": "MDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -158,11 +161,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="xdg", choices=["xdg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--size", type=int, default=64,
+                    help="cells per direction; 64 is the benchmark workload, smaller sizes serve profiling")
     args = ap.parse_args()
+    global SIZE, WORKLOAD
+    SIZE = args.size
+    if SIZE != 64:
+        WORKLOAD = WORKLOAD.replace("64^3", "%d^3" % SIZE)
     if args.impl == "reference":
         return reference_arm(args)
 
-    import numpy as np
     import torch
 
     from paper_2003_02431_gb300 import xdg
@@ -176,67 +184,60 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    stream = torch.cuda.Stream(device=dev)   # the handle's stream; events are recorded on it
+    stream = torch.cuda.Stream(device=dev)   # the handle's stream: events are recorded on it
+    warmup = max(args.warmup, 3)
 
     P = make_problem()
-    n = P.dof
+    n, Np, nb, nnzb = P.dof, P.Np, P.nb[0], int(P.row_ptr[-1])
     t = time.perf_counter()
-    H = xdg.Hierarchy.from_problem(P, gamma=2, stream=stream)
+    H = xdg.Hierarchy.from_problem(P, gamma=GAMMA, w_levels=W_LEVELS, low_precision=3, stream=stream)
     setup_s = time.perf_counter() - t
     hinfo = H.info()
     b = torch.from_numpy(P.b.reshape(-1).copy()).to(dev)
     x = torch.zeros(n, dtype=torch.float64, device=dev)
-
-    def solve():
-        x.zero_()
-        return H.solve(b, x, tol=TOL, maxit=1000)
-
-    for _ in range(max(args.warmup, 3)):
-        info = solve()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    launches, iters = 0, []
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clocks:
+
+    def timed_solves(prec, steps, prof=False):
+        for _ in range(warmup):
+            x.zero_()
+            H.solve(b, x, tol=TOL, maxit=1000, precision=prec)
+        launches, iters = 0, []
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if prof:
+            torch.cuda.profiler.start()
         ev0.record(stream)
-        for _ in range(args.steps):
-            info = solve()
+        for _ in range(steps):
+            x.zero_()
+            info = H.solve(b, x, tol=TOL, maxit=1000, precision=prec)
             launches += info["launches"]
             iters.append(info["iterations"])
         ev1.record(stream)
         torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    t_ms = ev0.elapsed_time(ev1)
-    if dist:
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
+        if prof:
+            torch.cuda.profiler.stop()
+        if dist:
+            dist.barrier()
+        ms = ev0.elapsed_time(ev1)
+        if dist:
+            tt = torch.tensor([ms], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms = float(tt.item())
+        return ms, launches, iters
+
+    # XDG_BENCH_PROFILE_RANGE=1 marks the headline timed region for `ncu --profile-from-start off`
+    prof = os.environ.get("XDG_BENCH_PROFILE_RANGE") == "1"
+    with ClockSampler(local) as clocks:
+        t_ms, launches, iters = timed_solves(xdg.XDG_PREC_F32, args.steps, prof=prof)
     value = world * n * args.steps / (t_ms / 1e3) / 1e6
+    t64_ms, _, iters64 = timed_solves(xdg.XDG_PREC_F64, args.steps)
+    tbf_ms, _, itersbf = timed_solves(xdg.XDG_PREC_BF16, args.steps)
 
-    # one cycle alone (graph replay), CUDA events on the same stream
-    z = torch.empty_like(x)
-    for _ in range(3):
-        H.vcycle(b, z)
-    nv = 20
-    ev0.record(stream)
-    for _ in range(nv):
-        H.vcycle(b, z)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    cycle_ms = ev0.elapsed_time(ev1) / nv
-
-    # dominant kernels on level 1, CUDA events on the launching stream
-    Np, nb, nnzb = P.Np, P.nb[0], int(P.row_ptr[-1])
-    bytes_apply = nnzb * (Np * Np * 8 + 4) + (nb + 1) * 8 + 2 * n * 8
-    bytes_smooth = bytes_apply + nb * (Np * (Np + 1) // 2) * 8 + 2 * n * 8
-    bytes_restrict = bytes_apply - n * 8 + nb * (Np * Np * 8 + 8) + n * 8 + P.nb[1] * Np * 8 + (P.nb[1] + 1) * 8
-    y = torch.empty_like(x)
-
-    def time_kernel(fn, reps=20):
+    def time_call(fn, reps=20):
         for _ in range(3):
             fn()
+        torch.cuda.synchronize()
         ev0.record(stream)
         for _ in range(reps):
             fn()
@@ -244,24 +245,29 @@ def main():
         torch.cuda.synchronize()
         return ev0.elapsed_time(ev1) / reps
 
-    rc = torch.empty(P.nb[1] * Np, dtype=torch.float64, device=dev)
-    k_ms = {"apply": time_kernel(lambda: H.apply(1, b, y)),
-            "smooth": time_kernel(lambda: H.smooth(1, b, z, y)),
-            "restrict": time_kernel(lambda: H.restrict(1, b, z, rc))}
-    k_bytes = {"apply": bytes_apply, "smooth": bytes_smooth, "restrict": bytes_restrict}
-    peak, peak_kind = peaks()
-    dom = "restrict"
-    achieved = k_bytes[dom] / (k_ms[dom] / 1e3) / 1e9
+    z = torch.empty_like(x)
+    cyc_ms = {p: time_call(lambda: H.cycle(p, b, z)) for p in (0, 1, 2)}
+
+    # dominant kernels, level 1, CUDA events on the launching stream
+    y = torch.empty_like(x)
+    ms_apply64 = time_call(lambda: H.apply(1, b, y))
+    ms_apply32 = time_call(lambda: H.apply(1, b, y, prec=xdg.XDG_PREC_F32))
+    flops_apply = 2.0 * nnzb * Np * Np
+    bytes_apply32 = nnzb * (4 * Np * Np + 4 + 4) + (nb + 1) * 8 + 2 * n * 8
+    fp64_peak = xdg.fma_peak(xdg.XDG_PREC_F64)
+    hbm, hbm_kind = hbm_peak()
+    ach64 = flops_apply / (ms_apply64 / 1e3) / 1e12
+    ach32 = bytes_apply32 / (ms_apply32 / 1e3) / 1e9
 
     # end to end through the host-buffer entry point (pinned host memory)
     bh = torch.from_numpy(P.b.reshape(-1).copy()).pin_memory().numpy()
     xh = torch.zeros(n, dtype=torch.float64).pin_memory().numpy()
-    H.solve_host(bh, xh, tol=TOL, maxit=1000)
+    H.solve_host(bh, xh, tol=TOL, maxit=1000, precision=xdg.XDG_PREC_F32)
     if dist:
         dist.barrier()
     t = time.perf_counter()
     for _ in range(args.steps):
-        H.solve_host(bh, xh, tol=TOL, maxit=1000)
+        H.solve_host(bh, xh, tol=TOL, maxit=1000, precision=xdg.XDG_PREC_F32)
     e2e_s = time.perf_counter() - t
     if dist:
         tt = torch.tensor([e2e_s], device=dev)
@@ -271,28 +277,41 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        s = oracle_sample(P, int(statistics.median(iters)))
+        it64 = int(statistics.median(iters64))
+        s = oracle_sample(P, it64)
         cpu = {"value": n / s["est_solve_s"] / 1e6, "unit": "MDOF/s", "cores": s["cores"], "kind": "oracle",
-               "sample": "%d PCG+W-cycle iterations of the same 64^3 problem (%.2f s/iteration), "
-                         "extrapolated to the %d iterations of the GPU solve"
-                         % (s["sample_iterations"], s["per_iteration_s"], int(statistics.median(iters)))}
+               "sample": "%d FP64 PCG iterations of the same 64^3 problem (%.3f s each), extrapolated to the "
+                         "%d iterations of the FP64 solve" % (s["sample_iterations"], s["per_iteration_s"], it64)}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "MDOF/s", "n_gpus": world, "steps": args.steps,
-            "warmup": max(args.warmup, 3), "ms_per_step": t_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "warmup": warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 outer / f32 cycle", "data": "synthetic",
             "config": {"workload": WORKLOAD, "dof": n, "blocks": nb, "nnz_blocks": nnzb, "Np": Np,
-                       "levels": hinfo["nb"], "cycle": "W(1,1) block-Jacobi", "tol": TOL,
-                       "iterations": iters, "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "inputs larger than L2 (operator 1.49 GB)"},
-            "vcycle_mdofs": n / (cycle_ms / 1e3) / 1e6, "vcycle_ms": cycle_ms,
+                       "levels": hinfo["nb"], "cycle": "W(1,1) on the 2 finest levels, V below; block Jacobi",
+                       "outer": "flexible CG, FP64 apply/residual/update", "tol": TOL, "iterations": iters,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (operator 1.49 GB FP64 + 0.74 GB FP32)"},
+            "paths": {
+                "mixed_f32": {"solve_ms": t_ms / args.steps, "iterations": iters, "mdofs": value / world},
+                "plain_f64": {"solve_ms": t64_ms / args.steps, "iterations": iters64,
+                              "mdofs": n * args.steps / (t64_ms / 1e3) / 1e6},
+                "mixed_bf16_transfers": {"solve_ms": tbf_ms / args.steps, "iterations": itersbf,
+                                         "mdofs": n * args.steps / (tbf_ms / 1e3) / 1e6},
+                "speedup_mixed_vs_f64": t64_ms / t_ms,
+            },
+            "vcycle_mdofs": {"f64": n / cyc_ms[0] / 1e3, "f32": n / cyc_ms[1] / 1e3, "bf16": n / cyc_ms[2] / 1e3},
+            "vcycle_ms": cyc_ms,
             "setup_s": setup_s, "setup_ms_phases": hinfo["setup_ms"],
-            "kernels_ms": k_ms,
-            "kernels_gbs": {k: k_bytes[k] / (k_ms[k] / 1e3) / 1e9 for k in k_ms},
-            "roofline": {"bound": "hbm", "kernel": "k_restrict (fused residual + restriction, level 1)",
-                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "peak_kind": peak_kind, "traffic": None},
+            "roofline": {"bound": "alu", "kernel": "k_spmv<10> FP64 operator apply, level 1 (outer FP64 apply)",
+                         "achieved": ach64, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach64 / fp64_peak,
+                         "peak_kind": "measured live: FP64 FMA probe (xdg_fma_peak)",
+                         "work": "2*nnzb*Np^2 = %.1f MFLOP per launch" % (flops_apply / 1e6),
+                         "ms": ms_apply64, "traffic": None},
+            "roofline_fp32_apply": {"bound": "hbm", "kernel": "k_spmv_lp<10,float> FP32 operator apply, level 1",
+                                    "achieved": ach32, "peak": hbm, "unit": "GB/s", "frac": ach32 / hbm,
+                                    "peak_kind": hbm_kind, "bytes": bytes_apply32, "ms": ms_apply32},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": "MDOF/s", "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8},
             "gpu_launches": launches,

@@ -95,7 +95,11 @@ typedef struct {
   int lanczos_steps;  /* Lanczos steps for lambda_l (default 12 when <= 0) */
   int nu;             /* block-Jacobi sweeps before and after the coarse correction (>= 1) */
   int gamma;          /* coarse visits per level: 1 = V-cycle, 2 = W-cycle */
-  int low_precision;  /* bit mask: 1 = keep FP32 copies of the operators, 2 = BF16 copies */
+  int low_precision;  /* bit mask: 1 = FP32 copies of operators, block inverses and transfers;
+                         2 = BF16 copies of operators and transfers (the cycle then still reads
+                         FP32 operators and block inverses, see xdg_cycle) */
+  int w_levels;       /* > 0: only the w_levels finest levels repeat their coarse correction
+                         gamma times (V-cycle below); <= 0: all levels */
 } xdg_hier_opts;
 
 typedef struct {
@@ -178,6 +182,18 @@ int xdg_coarse_solve(xdg_hier_t h, const double* r, double* z);
  * vectors and must not alias. */
 int xdg_vcycle(xdg_hier_t h, const double* b, double* x);
 
+/* x = B_prec b: one cycle as xdg_vcycle in low precision (sec. 3.3: single-precision solves
+ * inside, double-precision residuals outside): FP32 vectors and FP32 accumulation; level
+ * operators and block inverses (computed in FP64) read from their FP32 copies (entries
+ * divided by one FP32 scale per block); transfer blocks read from the FP32
+ * (prec = XDG_PREC_F32) or BF16 (prec = XDG_PREC_BF16) copy; the coarsest level keeps its
+ * FP64 inverse. A BF16-rounded operator is not used inside the cycle: with 2^-9 relative
+ * rounding per entry it is indefinite on the smooth modes of these systems
+ * (2^-9 cond(M) >> 1). b and x are FP64 device vectors (rounded to FP32 on entry, widened
+ * on exit). prec = XDG_PREC_F64 is xdg_vcycle. Needs the copy requested in
+ * xdg_hier_opts.low_precision, else XDG_EINVAL. */
+int xdg_cycle(xdg_hier_t h, int prec, const double* b, double* x);
+
 /* Solve M^1 x = b (device vectors). x holds the initial guess on entry (resume from a
  * previous x to continue a solve). Returns XDG_OK when converged, XDG_ENOTCONV /
  * XDG_ETIMEOUT / XDG_EBREAKDOWN otherwise; info (optional) is filled in every case. */
@@ -188,6 +204,14 @@ int xdg_solve(xdg_hier_t h, const double* b, double* x, const xdg_solve_opts* o,
  * x back, all inside the call (the end-to-end path for callers without device memory). */
 int xdg_solve_host(xdg_hier_t h, const double* b_host, double* x_host, const xdg_solve_opts* o,
                    xdg_solve_info* info);
+
+/* Measured fused multiply-add throughput of the current GPU (a utility of the benchmark, no
+ * counterpart in the paper): runs 8 independent FMA chains per thread over 8 CTAs of 256
+ * threads per SM and stores 2 * FMAs / time in *tflops (FP64 for prec = XDG_PREC_F64, FP32
+ * for XDG_PREC_F32). Allocates and frees a small device buffer; synchronises the device.
+ * This is the denominator of the FP64 kernels' roofline: on GB300 an FP64 block-sparse
+ * apply (0.25 flop/byte) is bound by the FP64 pipe, not by HBM. */
+int xdg_fma_peak(int prec, double* tflops);
 
 /* Residual restriction for callers that cannot allocate device memory.
  *

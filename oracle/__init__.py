@@ -198,3 +198,25 @@ class Hierarchy:
             self.close()
         except Exception:
             pass
+
+
+def quantize_blocks(blocks, prec):
+    """Dequantised FP64 values of the low-precision block storage (prec 1 = FP32, 2 = BF16)
+    and the per-block scales."""
+    L = _load()
+    if not hasattr(L, "_q_set"):
+        L.or_quantize_blocks.argtypes = [C.c_int64, C.c_int, C.c_int, _dp, _dp, C.POINTER(C.c_float)]
+        L._q_set = True
+    a = _f64(blocks)
+    nblk, np2 = a.shape[0], a.shape[1] * a.shape[2]
+    out = np.empty_like(a)
+    sc = np.empty(nblk, dtype=np.float32)
+    L.or_quantize_blocks(nblk, np2, prec, _p(a, _dp), _p(out, _dp), sc.ctypes.data_as(C.POINTER(C.c_float)))
+    return out, sc
+
+
+def set_w_levels(h, wlev):
+    """Repeat the coarse correction (gamma times) only on the wlev finest levels."""
+    L = _load()
+    L.or_hier_set_wlev.argtypes = [C.c_void_p, C.c_int]
+    L.or_hier_set_wlev(h._h, wlev)

@@ -249,6 +249,7 @@ typedef struct {
 
 typedef struct {
   int Np, nlev, nu, gamma;
+  int wlev; /* levels l < wlev repeat their coarse correction gamma times */
   or_level L[OR_MAXL];
   double* cchol; /* dense Cholesky factor of the coarsest operator */
   int64_t nc;
@@ -379,6 +380,7 @@ void* or_hier_create(int nlev, int Np, int64_t nb1, const int64_t* rp, const int
   H->nlev = nlev;
   H->nu = nu < 1 ? 1 : nu;
   H->gamma = gamma < 1 ? 1 : gamma;
+  H->wlev = OR_MAXL;
   const int64_t Np2 = (int64_t)Np * Np;
   H->L[0].nb = nb1;
   H->L[0].rp = (int64_t*)rp;
@@ -506,7 +508,7 @@ static void vcycle_rec(or_hier* H, int l, const double* b, double* x) {
   /* coarse-grid correction: gamma steps of the coarse cycle from zero (gamma = 1: V-cycle,
    * gamma = 2: W-cycle); each step z_c += B_c (r_c - M_c z_c) keeps the cycle symmetric */
   vcycle_rec(H, l + 1, bc, zc);
-  if (H->gamma > 1 && l + 2 < H->nlev) {
+  if (H->gamma > 1 && l + 2 < H->nlev && l < H->wlev) {
     double* rc2 = (double*)malloc(sizeof(double) * Lc->nb * Np);
     double* dz = (double*)malloc(sizeof(double) * Lc->nb * Np);
     for (int g = 1; g < H->gamma; ++g) {
@@ -570,3 +572,39 @@ int or_pcg(void* h, const double* b, double* x, double tol, int maxit, double* r
   *relres = sqrt(dot(n, r, r)) / bn;
   return it;
 }
+
+/* ---------------- low-precision block storage ---------------- */
+
+/* Round a float to the nearest bfloat16 (ties to even) and widen it back: keep the upper 16
+ * bits of the IEEE-754 single after adding half an ulp of bfloat16 plus the tie bit. */
+static float bf16_round(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  u &= 0xFFFF0000u;
+  float r;
+  memcpy(&r, &u, 4);
+  return r;
+}
+
+/* Stored form of Np x Np blocks for the low-precision cycle: s = max |entry| rounded to float
+ * (1 for a zero block), stored entry = entry / s rounded to float (prec 1) or to bfloat16
+ * through float (prec 2). out receives s * stored in FP64, scales receives s. */
+void or_quantize_blocks(int64_t nblk, int np2, int prec, const double* in, double* out, float* scales) {
+#pragma omp parallel for schedule(static)
+  for (int64_t b = 0; b < nblk; ++b) {
+    const double* a = in + b * np2;
+    double m = 0.0;
+    for (int e = 0; e < np2; ++e) m = fabs(a[e]) > m ? fabs(a[e]) : m;
+    float s = m > 0.0 ? (float)m : 1.0f;
+    scales[b] = s;
+    for (int e = 0; e < np2; ++e) {
+      float q = (float)(a[e] / (double)s);
+      if (prec == 2) q = bf16_round(q);
+      out[b * np2 + e] = (double)s * (double)q;
+    }
+  }
+}
+
+/* restrict the repeated coarse corrections to levels l < wlev (V-cycle below) */
+void or_hier_set_wlev(void* h, int wlev) { ((or_hier*)h)->wlev = wlev; }

@@ -22,6 +22,7 @@
 
 #include "../../include/xdg.h"
 #include "xdg_kernels.cuh"
+#include "xdg_kernels_lp.cuh"
 
 using namespace xdg;
 
@@ -139,6 +140,102 @@ bool ops_for(int np, Ops* o) {
   }
 }
 
+// per-(Np, storage type) kernel table of the low-precision cycle (vectors in FP32)
+struct OpsLP {
+  void (*make)(cudaStream_t, int64_t nblk, int np2, const double*, void*, float*);
+  void (*spmv_f)(int, cudaStream_t, int64_t, const int64_t*, const int32_t*, const void*, const float*,
+                 const float*, const float*, float*, int mode);
+  void (*spmv_d)(int, cudaStream_t, int64_t, const int64_t*, const int32_t*, const void*, const float*,
+                 const double*, double*);
+  void (*smooth)(int, cudaStream_t, int64_t, const int64_t*, const int32_t*, const void*, const float*,
+                 const void*, const float*, float, const float*, const float*, float*);
+  void (*resid_rt)(int, cudaStream_t, int64_t, const int64_t*, const int32_t*, const void*, const float*,
+                   const void*, const float*, const float*, const float*, float*);
+  void (*gather)(int, cudaStream_t, int64_t, const int64_t*, const int32_t*, const float*, float*);
+  void (*prolong)(int, cudaStream_t, int64_t, const int32_t*, const void*, const float*, const float*,
+                  const float*, float*);
+  void (*resid32)(int, cudaStream_t, int64_t, const int64_t*, const int32_t*, const void*, const float*,
+                  const float*, const float*, float*);
+  size_t elem;
+};
+
+template <int NP, class TS>
+struct OpsLPT {
+  static void make(cudaStream_t s, int64_t nblk, int np2, const double* src, void* dst, float* sc) {
+    k_make_lp<TS><<<(unsigned)((nblk * 32 + 255) / 256), 256, 0, s>>>(nblk, np2, src, (TS*)dst, sc);
+  }
+  static void spmv_f(int grid, cudaStream_t s, int64_t nb, const int64_t* rp, const int32_t* col,
+                     const void* val, const float* sc, const float* x, const float* b, float* y, int mode) {
+    if (mode) k_spmv_lp<NP, TS, float, 1><<<grid, kThreads, 0, s>>>(nb, rp, col, (const TS*)val, sc, x, b, y);
+    else k_spmv_lp<NP, TS, float, 0><<<grid, kThreads, 0, s>>>(nb, rp, col, (const TS*)val, sc, x, b, y);
+  }
+  static void spmv_d(int grid, cudaStream_t s, int64_t nb, const int64_t* rp, const int32_t* col,
+                     const void* val, const float* sc, const double* x, double* y) {
+    k_spmv_lp<NP, TS, double, 0><<<grid, kThreads, 0, s>>>(nb, rp, col, (const TS*)val, sc, x, nullptr, y);
+  }
+  // val: the FP32 operator copy (a BF16 operator is not usable in the sweeps, see k_resid_rt_lp)
+  static void smooth(int grid, cudaStream_t s, int64_t nb, const int64_t* rp, const int32_t* col,
+                     const void* val, const float* sc, const void* Dinv, const float* dsc, float om,
+                     const float* b, const float* xi, float* xo) {
+    if (xi)
+      k_smooth_lp<NP, float, false><<<grid, kThreads, 0, s>>>(nb, rp, col, (const float*)val, sc,
+                                                              (const float*)Dinv, dsc, om, b, xi, xo);
+    else
+      k_smooth_lp<NP, float, true><<<grid, kThreads, 0, s>>>(nb, rp, col, (const float*)val, sc,
+                                                             (const float*)Dinv, dsc, om, b, xi, xo);
+  }
+  // val: the FP32 operator copy
+  static void resid_rt(int grid, cudaStream_t s, int64_t nbf, const int64_t* rp, const int32_t* col,
+                       const void* val, const float* sc, const void* R, const float* rsc, const float* b,
+                       const float* x, float* t) {
+    if (x)
+      k_resid_rt_lp<NP, float, TS, true><<<grid, kThreads, 0, s>>>(nbf, rp, col, (const float*)val, sc,
+                                                                   (const TS*)R, rsc, b, x, t);
+    else
+      k_resid_rt_lp<NP, float, TS, false><<<grid, kThreads, 0, s>>>(nbf, rp, col, (const float*)val, sc,
+                                                                    (const TS*)R, rsc, b, x, t);
+  }
+  // W-cycle coarse residual b - M x with the FP32 operator copy
+  static void resid32(int grid, cudaStream_t s, int64_t nb, const int64_t* rp, const int32_t* col,
+                      const void* val, const float* sc, const float* x, const float* b, float* y) {
+    k_spmv_lp<NP, float, float, 1><<<grid, kThreads, 0, s>>>(nb, rp, col, (const float*)val, sc, x, b, y);
+  }
+  static void gather(int grid, cudaStream_t s, int64_t nbc, const int64_t* cptr, const int32_t* ch,
+                     const float* t, float* rc) {
+    k_gather_lp<NP><<<grid, kThreads, 0, s>>>(nbc, cptr, ch, t, rc);
+  }
+  static void prolong(int grid, cudaStream_t s, int64_t nbf, const int32_t* agg, const void* R, const float* rsc,
+                      const float* zc, const float* xi, float* xo) {
+    k_prolong_lp<NP, TS><<<grid, kThreads, 0, s>>>(nbf, agg, (const TS*)R, rsc, zc, xi, xo);
+  }
+  static OpsLP get() { return OpsLP{make, spmv_f, spmv_d, smooth, resid_rt, gather, prolong, resid32, sizeof(TS)}; }
+};
+
+// prec: XDG_PREC_F32 or XDG_PREC_BF16
+bool ops_lp_for(int np, int prec, OpsLP* o) {
+  const bool bf = prec == XDG_PREC_BF16;
+  switch (np) {
+    case 6: *o = bf ? OpsLPT<6, __nv_bfloat16>::get() : OpsLPT<6, float>::get(); return true;
+    case 10: *o = bf ? OpsLPT<10, __nv_bfloat16>::get() : OpsLPT<10, float>::get(); return true;
+    case 15: *o = bf ? OpsLPT<15, __nv_bfloat16>::get() : OpsLPT<15, float>::get(); return true;
+    case 20: *o = bf ? OpsLPT<20, __nv_bfloat16>::get() : OpsLPT<20, float>::get(); return true;
+    default: return false;
+  }
+}
+
+// low-precision copy of one level
+struct LevelLP {
+  void* val = nullptr;       // operator in the storage precision (smoothing sweeps, apply)
+  float* sc = nullptr;
+  void* val32 = nullptr;     // FP32 operator (residuals that are restricted); == val in FP32 mode
+  float* sc32 = nullptr;
+  void* Dinv = nullptr;
+  float* dsc = nullptr;
+  void* R = nullptr;
+  float* rsc = nullptr;
+  float *b = nullptr, *x = nullptr, *t = nullptr, *r = nullptr, *dz = nullptr, *s = nullptr;
+};
+
 // --------------------------------------------------------------------------------------------
 struct Level {
   int64_t nb = 0, nnzb = 0;
@@ -161,7 +258,7 @@ struct Level {
 }  // namespace
 
 struct xdg_hier {
-  int Np = 0, nlev = 0, nu = 1, gamma = 1, dev = 0, sms = 152;
+  int Np = 0, nlev = 0, nu = 1, gamma = 1, wlev = 1 << 20, dev = 0, sms = 152;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   Ops ops{};
@@ -181,6 +278,16 @@ struct xdg_hier {
   int64_t iter_nodes = 0;      // kernel nodes in one recorded CG iteration
   int64_t cycle_nodes = 0;     // kernel nodes in the recorded cycle
   int64_t launches = 0;        // kernels launched outside graphs (counted by the helpers)
+  // low-precision cycles, indexed by XDG_PREC_F32 (1) and XDG_PREC_BF16 (2)
+  bool has_lp[3] = {false, false, false};
+  OpsLP opl[3]{};
+  std::vector<LevelLP> LP[3];
+  cudaGraphExec_t g_iter_lp[3] = {nullptr, nullptr, nullptr};
+  int64_t iter_lp_nodes[3] = {0, 0, 0};
+  cudaGraphExec_t g_cyc_lp[3] = {nullptr, nullptr, nullptr};
+  const double* g_cyc_lp_b[3] = {nullptr, nullptr, nullptr};
+  double* g_cyc_lp_x[3] = {nullptr, nullptr, nullptr};
+  int64_t cyc_lp_nodes[3] = {0, 0, 0};
   std::vector<void*> allocs;
   size_t bytes = 0;
   double setup_ms[3] = {0, 0, 0};
@@ -189,6 +296,10 @@ struct xdg_hier {
     if (stream) cudaStreamSynchronize(stream);
     if (g_cycle) cudaGraphExecDestroy(g_cycle);
     if (g_iter) cudaGraphExecDestroy(g_iter);
+    for (int p = 0; p < 3; ++p) {
+      if (g_iter_lp[p]) cudaGraphExecDestroy(g_iter_lp[p]);
+      if (g_cyc_lp[p]) cudaGraphExecDestroy(g_cyc_lp[p]);
+    }
     for (void* p : allocs) cudaFree(p);
     if (hS) cudaFreeHost(hS);
     if (hsc) cudaFreeHost(hsc);
@@ -273,7 +384,7 @@ struct xdg_hier {
     // coarse-grid correction: gamma cycles on the coarse level
     restrict_(l, b, cur, C.b);
     cycle(l + 1, C.b, C.x);
-    if (gamma > 1 && l + 2 < nlev) {
+    if (gamma > 1 && l + 2 < nlev && l < wlev) {
       for (int g = 1; g < gamma; ++g) {
         spmv(l + 1, C.x, C.b, C.r, 1);
         cycle(l + 1, C.r, C.dz);
@@ -312,16 +423,101 @@ struct xdg_hier {
     k_pcg_p<<<vgrid(n), kThreads, 0, stream>>>(n, S, s_z, s_p);
   }
 
-  int capture(cudaGraphExec_t* out, int which, const double* b, double* x) {
+  // ---------------------------------------------------------------- low-precision cycle
+  void cycle_lp(int p, int l, const float* b, float* x) {
+    const OpsLP& o = opl[p];
+    if (l == nlev - 1) {
+      ++launches;
+      int64_t blocks = (nc * 32 + kThreads - 1) / kThreads;
+      k_gemv_coarse_lp<<<(unsigned)blocks, kThreads, 0, stream>>>(nc, Minv, b, x);
+      return;
+    }
+    Level& V = L[l];
+    Level& C = L[l + 1];
+    LevelLP& W = LP[p][l];
+    LevelLP& WC = LP[p][l + 1];
+    const float om = (float)V.omega;
+    float* cur = x;
+    float* oth = W.t;
+    o.smooth(grid(V.nb), stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, b, nullptr, cur);
+    ++launches;
+    for (int s = 1; s < nu; ++s) {
+      o.smooth(grid(V.nb), stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, b, cur, oth);
+      ++launches;
+      std::swap(cur, oth);
+    }
+    o.resid_rt(grid(V.nb), stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.R, W.rsc, b, cur, W.s);
+    o.gather(vgrid(C.nb * Np), stream, C.nb, V.cptr, V.ch, W.s, WC.b);
+    launches += 2;
+    cycle_lp(p, l + 1, WC.b, WC.x);
+    if (gamma > 1 && l + 2 < nlev && l < wlev) {
+      for (int g = 1; g < gamma; ++g) {
+        o.resid32(grid(C.nb), stream, C.nb, C.rp, C.col, WC.val32, WC.sc32, WC.x, WC.b, WC.r);
+        cycle_lp(p, l + 1, WC.r, WC.dz);
+        k_axpy_f<<<vgrid(C.nb * Np), kThreads, 0, stream>>>(C.nb * Np, 1.0f, WC.dz, WC.x);
+        launches += 2;
+      }
+    }
+    float* after = (nu % 2 == 0) ? x : W.t;
+    o.prolong(grid(V.nb), stream, V.nb, V.agg, W.R, W.rsc, WC.x, cur, after);
+    ++launches;
+    cur = after;
+    oth = (cur == x) ? W.t : x;
+    for (int s = 0; s < nu; ++s) {
+      o.smooth(grid(V.nb), stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, b, cur, oth);
+      ++launches;
+      std::swap(cur, oth);
+    }
+    if (cur != x) {
+      k_copy_f<<<vgrid(V.nb * Np), kThreads, 0, stream>>>(V.nb * Np, cur, x);
+      ++launches;
+    }
+  }
+
+  // z = B_p r for FP64 vectors: round r to FP32, run the low-precision cycle, widen the result
+  void cycle_lp_d(int p, const double* r, double* z) {
+    const int64_t n = L[0].nb * Np;
+    LevelLP& W = LP[p][0];
+    k_d2f<<<vgrid(n), kThreads, 0, stream>>>(n, r, W.b);
+    cycle_lp(p, 0, W.b, W.x);
+    k_f2d<<<vgrid(n), kThreads, 0, stream>>>(n, W.x, z);
+    launches += 2;
+  }
+
+  // one flexible-CG iteration (FP64 operator, residual and updates; low-precision cycle)
+  void fcg_iteration(int p) {
+    const int64_t n = L[0].nb * Np;
+    spmv(0, s_p, nullptr, s_q, 0);
+    dot(n, s_p, s_q, &S->pq);
+    k_pcg_alpha<<<1, 1, 0, stream>>>(S);
+    k_pcg_xr<<<kRedBlocks, kThreads, 0, stream>>>(n, S, s_p, s_q, s_x, s_r, partial);
+    k_sum_final<<<1, kThreads, 0, stream>>>(kRedBlocks, partial, &S->rr);
+    launches += 3;
+    cycle_lp_d(p, s_r, s_z);
+    dot(n, s_r, s_z, &S->rz);
+    dot(n, s_z, s_q, &S->zq);
+    k_fcg_beta<<<1, 1, 0, stream>>>(S);
+    k_pcg_p<<<vgrid(n), kThreads, 0, stream>>>(n, S, s_z, s_p);
+    launches += 2;
+  }
+
+  int build_lp(int p);
+
+  // which: 0 FP64 cycle, 1 FP64 CG iteration, 2 low-precision cycle, 3 flexible-CG iteration
+  int capture(cudaGraphExec_t* out, int which, const double* b, double* x, int p = 0) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
     const int64_t before = launches;
     if (which == 0) cycle(0, b, x);
-    else pcg_iteration();
+    else if (which == 1) pcg_iteration();
+    else if (which == 2) cycle_lp_d(p, b, x);
+    else fcg_iteration(p);
     const int64_t recorded = launches - before;
     launches = before;
     if (which == 0) cycle_nodes = recorded;
-    else iter_nodes = recorded;
+    else if (which == 1) iter_nodes = recorded;
+    else if (which == 2) cyc_lp_nodes[p] = recorded;
+    else iter_lp_nodes[p] = recorded;
     cudaError_t e = cudaStreamEndCapture(stream, &g);
     if (e != cudaSuccess) {
       set_err("graph capture: %s", cudaGetErrorString(e));
@@ -445,6 +641,7 @@ int xdg_hier::build(const xdg_problem* p, const xdg_hier_opts* o) {
   }
   nu = o && o->nu > 0 ? o->nu : 1;
   gamma = o && o->gamma > 0 ? o->gamma : 1;
+  wlev = o && o->w_levels > 0 ? o->w_levels : (1 << 20);
   const int lsteps = o && o->lanczos_steps > 0 ? o->lanczos_steps : 12;
   const int64_t Np2 = (int64_t)Np * Np;
   CK(cudaGetDevice(&dev));
@@ -690,8 +887,68 @@ int xdg_hier::build(const xdg_problem* p, const xdg_hier_opts* o) {
     bytes -= 2 * nc * nc * sizeof(double);
   }
   TRY(capture(&g_iter, 1, nullptr, nullptr));
+  if (o && (o->low_precision & 1)) TRY(build_lp(XDG_PREC_F32));
+  if (o && (o->low_precision & 2)) TRY(build_lp(XDG_PREC_BF16));
   TRY(sync());
   setup_ms[2] = ms_since(t0);
+  return XDG_OK;
+}
+
+// low-precision copies of every level (operator, block inverses, transfers: entry / block scale,
+// rounded to FP32 or BF16) and FP32 work vectors; the FP64 originals stay resident
+int xdg_hier::build_lp(int p) {
+  if (!ops_lp_for(Np, p, &opl[p])) {
+    set_err("no low-precision kernels for Np = %d", Np);
+    return XDG_EINVAL;
+  }
+  const int np2 = Np * Np;
+  const size_t el = opl[p].elem;
+  LP[p].resize(nlev);
+  for (int l = 0; l < nlev; ++l) {
+    Level& V = L[l];
+    LevelLP& W = LP[p][l];
+    const int64_t n = V.nb * Np;
+    char* raw = nullptr;
+    TRY(alloc(&raw, V.nnzb * np2 * el));
+    W.val = raw;
+    TRY(alloc(&W.sc, V.nnzb));
+    opl[p].make(stream, V.nnzb, np2, V.val, W.val, W.sc);
+    if (p == XDG_PREC_F32) {
+      W.val32 = W.val;
+      W.sc32 = W.sc;
+    } else if (has_lp[XDG_PREC_F32]) {  // share the FP32 copy
+      W.val32 = LP[XDG_PREC_F32][l].val;
+      W.sc32 = LP[XDG_PREC_F32][l].sc;
+    } else {
+      float* v32 = nullptr;
+      TRY(alloc(&v32, V.nnzb * np2));
+      TRY(alloc(&W.sc32, V.nnzb));
+      k_make_lp<float><<<(unsigned)((V.nnzb * 32 + 255) / 256), 256, 0, stream>>>(V.nnzb, np2, V.val, v32,
+                                                                                   W.sc32);
+      W.val32 = v32;
+    }
+    TRY(alloc(&W.b, n));
+    TRY(alloc(&W.x, n));
+    TRY(alloc(&W.t, n));
+    TRY(alloc(&W.r, n));
+    TRY(alloc(&W.dz, n));
+    if (l + 1 < nlev) {
+      float* dinv = nullptr;  // FP32 in both modes
+      TRY(alloc(&dinv, V.nb * np2));
+      W.Dinv = dinv;
+      TRY(alloc(&W.dsc, V.nb));
+      k_make_lp<float><<<(unsigned)((V.nb * 32 + 255) / 256), 256, 0, stream>>>(V.nb, np2, V.Dinv, dinv, W.dsc);
+      TRY(alloc(&raw, V.nb * np2 * el));
+      W.R = raw;
+      TRY(alloc(&W.rsc, V.nb));
+      opl[p].make(stream, V.nb, np2, V.R, W.R, W.rsc);
+      TRY(alloc(&W.s, n));
+    }
+    CKL();
+  }
+  TRY(sync());
+  has_lp[p] = true;
+  TRY(capture(&g_iter_lp[p], 3, nullptr, nullptr, p));
   return XDG_OK;
 }
 
@@ -703,10 +960,16 @@ int xdg_hier::solve_dev(const double* b, double* x, const xdg_solve_opts* o, xdg
   const int maxit = o && o->maxit > 0 ? o->maxit : 1000;
   const int every = o && o->check_every > 0 ? o->check_every : 1;
   const double budget = o ? o->time_budget_ms : 0.0;
-  if (o && o->precision != XDG_PREC_F64) {
-    set_err("precision %d not available in this solver", o->precision);
+  const int prec = o ? o->precision : XDG_PREC_F64;
+  if (prec != XDG_PREC_F64 && (prec < 0 || prec > 2 || !has_lp[prec])) {
+    set_err("precision %d requested but the hierarchy holds no such copy (xdg_hier_opts.low_precision)",
+            prec);
     return XDG_EINVAL;
   }
+  // FP64: CG with the FP64 cycle. FP32/BF16: flexible CG (FP64 operator, residuals and
+  // updates) with the low-precision cycle as preconditioner.
+  cudaGraphExec_t gi = (prec == XDG_PREC_F64) ? g_iter : g_iter_lp[prec];
+  const int64_t gi_nodes = (prec == XDG_PREC_F64) ? iter_nodes : iter_lp_nodes[prec];
   CK(cudaMemcpyAsync(s_b, b, n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
   CK(cudaMemcpyAsync(s_x, x, n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
   CK(cudaMemsetAsync(S, 0, sizeof(PcgScal), stream));
@@ -714,7 +977,8 @@ int xdg_hier::solve_dev(const double* b, double* x, const xdg_solve_opts* o, xdg
   spmv(0, s_x, s_b, s_r, 1);
   dot(n, s_b, s_b, dsc);
   dot(n, s_r, s_r, &S->rr);
-  cycle(0, s_r, s_z);
+  if (prec == XDG_PREC_F64) cycle(0, s_r, s_z);
+  else cycle_lp_d(prec, s_r, s_z);
   k_copy<<<vgrid(n), kThreads, 0, stream>>>(n, s_z, s_p);
   ++launches;
   dot(n, s_r, s_z, &S->rz);
@@ -733,7 +997,7 @@ int xdg_hier::solve_dev(const double* b, double* x, const xdg_solve_opts* o, xdg
       break;
     }
     int todo = std::min(every, maxit - it);
-    for (int k2 = 0; k2 < todo; ++k2) CK(cudaGraphLaunch(g_iter, stream));
+    for (int k2 = 0; k2 < todo; ++k2) CK(cudaGraphLaunch(gi, stream));
     it += todo;
     CK(cudaMemcpyAsync(hS, S, sizeof(PcgScal), cudaMemcpyDeviceToHost, stream));
     TRY(sync());
@@ -753,7 +1017,7 @@ int xdg_hier::solve_dev(const double* b, double* x, const xdg_solve_opts* o, xdg
     info->relres = std::sqrt(rr) / bn;
     info->ms = ms_since(t0);
     info->status = status;
-    info->launches = launches - launches0 + (int64_t)it * iter_nodes;
+    info->launches = launches - launches0 + (int64_t)it * gi_nodes;
   }
   if (status) set_err("solve stopped: %s after %d iterations (relres %.3e)", xdg_strerror(status), it,
                       std::sqrt(rr) / bn);
@@ -842,11 +1106,23 @@ int xdg_apply(xdg_hier_t h, int level, const double* x, double* y, int prec) {
     set_err("xdg_apply: bad arguments");
     return XDG_EINVAL;
   }
-  if (prec != XDG_PREC_F64) {
-    set_err("xdg_apply: precision %d not available", prec);
-    return XDG_EINVAL;
+  if (prec == XDG_PREC_F64) {
+    h->spmv(level - 1, x, nullptr, y, 0);
+  } else {
+    if (prec < 0 || prec > 2 || !h->has_lp[prec]) {
+      set_err("xdg_apply: precision %d not stored (xdg_hier_opts.low_precision)", prec);
+      return XDG_EINVAL;
+    }
+    Level& V = h->L[level - 1];
+    LevelLP& W = h->LP[prec][level - 1];
+    // vectors rounded to FP32 once (a per-element FP64 -> FP32 conversion inside the product
+    // would run on the FP64 pipe); the level's FP32 work vectors r and dz hold x and y
+    const int64_t n = V.nb * h->Np;
+    k_d2f<<<h->vgrid(n), kThreads, 0, h->stream>>>(n, x, W.r);
+    h->opl[prec].spmv_f(h->grid(V.nb), h->stream, V.nb, V.rp, V.col, W.val, W.sc, W.r, nullptr, W.dz, 0);
+    k_f2d<<<h->vgrid(n), kThreads, 0, h->stream>>>(n, W.dz, y);
+    h->launches += 3;
   }
-  h->spmv(level - 1, x, nullptr, y, 0);
   CKL();
   return XDG_OK;
 }
@@ -903,6 +1179,22 @@ int xdg_vcycle(xdg_hier_t h, const double* b, double* x) {
   }
   CK(cudaGraphLaunch(h->g_cycle, h->stream));
   h->launches += h->cycle_nodes;
+  return XDG_OK;
+}
+
+int xdg_cycle(xdg_hier_t h, int prec, const double* b, double* x) {
+  if (prec == XDG_PREC_F64) return xdg_vcycle(h, b, x);
+  if (!h || !b || !x || b == x || prec < 0 || prec > 2 || !h->has_lp[prec]) {
+    set_err("xdg_cycle: bad arguments or precision %d not stored", prec);
+    return XDG_EINVAL;
+  }
+  if (!h->g_cyc_lp[prec] || h->g_cyc_lp_b[prec] != b || h->g_cyc_lp_x[prec] != x) {
+    TRY(h->capture(&h->g_cyc_lp[prec], 2, b, x, prec));
+    h->g_cyc_lp_b[prec] = b;
+    h->g_cyc_lp_x[prec] = x;
+  }
+  CK(cudaGraphLaunch(h->g_cyc_lp[prec], h->stream));
+  h->launches += h->cyc_lp_nodes[prec];
   return XDG_OK;
 }
 
@@ -1015,4 +1307,60 @@ extern "C" int xdg_restrict_noalloc(int Np, int64_t nb_fine, int64_t nb_coarse, 
   ops.gather(grid_vec(nb_coarse * Np), s, nb_coarse, child_ptr, child, st.scratch, rc);
   CKL();
   return XDG_OK;
+}
+
+// ============================================================================================
+// FMA throughput probe (benchmark utility)
+namespace {
+template <class T>
+__global__ void k_fma_probe(T* out, int iters) {
+  T a0 = threadIdx.x * (T)1e-3, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3, a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6,
+    a7 = a0 + 7;
+  const T m = (T)0.9999999, c = (T)1e-7;
+  for (int i = 0; i < iters; ++i) {
+    a0 = fma(a0, m, c); a1 = fma(a1, m, c); a2 = fma(a2, m, c); a3 = fma(a3, m, c);
+    a4 = fma(a4, m, c); a5 = fma(a5, m, c); a6 = fma(a6, m, c); a7 = fma(a7, m, c);
+  }
+  out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+}
+
+template <class T>
+int fma_probe(int iters, double* tflops) {
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = sms * 8, threads = 256;
+  T* d = nullptr;
+  CK(cudaMalloc(&d, sizeof(T) * (size_t)blocks * threads));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  k_fma_probe<T><<<blocks, threads>>>(d, 64);
+  cudaEventRecord(e0);
+  k_fma_probe<T><<<blocks, threads>>>(d, iters);
+  cudaEventRecord(e1);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(d);
+  if (e != cudaSuccess) {
+    set_err("fma probe: %s", cudaGetErrorString(e));
+    return XDG_ECUDA;
+  }
+  *tflops = 2.0 * 8.0 * blocks * threads * (double)iters / (ms * 1e-3) / 1e12;
+  return XDG_OK;
+}
+}  // namespace
+
+extern "C" int xdg_fma_peak(int prec, double* tflops) {
+  if (!tflops) {
+    set_err("xdg_fma_peak: null output");
+    return XDG_EINVAL;
+  }
+  if (prec == XDG_PREC_F64) return fma_probe<double>(4096, tflops);
+  if (prec == XDG_PREC_F32) return fma_probe<float>(65536, tflops);
+  set_err("xdg_fma_peak: precision %d not probed", prec);
+  return XDG_EINVAL;
 }

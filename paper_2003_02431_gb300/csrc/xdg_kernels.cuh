@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(kThreads) k_sum_final(int np, const double* __
 
 // PCG scalars kept on the device
 struct PcgScal {
-  double rz, rz_new, pq, rr, alpha, beta;
+  double rz, rz_new, pq, rr, alpha, beta, zq;
   int bad;
 };
 

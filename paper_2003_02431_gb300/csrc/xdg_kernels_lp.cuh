@@ -1,0 +1,261 @@
+// Low-precision variants of the cycle kernels: operator, block inverses and transfer blocks
+// stored in FP32 or BF16 with one FP32 scale per Np x Np block (stored value = entry / scale),
+// vectors in FP32, accumulation in FP32.
+//
+// Kummer, Smuda, Weber, arXiv 2003.02431, sec. 3.3: the low-order solves of the p-multigrid
+// preconditioner may run in single precision as long as residuals are computed in double
+// precision. Here the whole multigrid cycle (the preconditioner) runs in FP32/BF16 while the
+// flexible CG around it keeps FP64 residuals and updates.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "xdg_kernels.cuh"
+
+namespace xdg {
+
+template <class T>
+__device__ __forceinline__ float to_f(T v);
+template <>
+__device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float to_f<double>(double v) { return (float)v; }
+template <>
+__device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// NP consecutive stored values -> FP32 registers (paired loads for even NP)
+template <int NP, class T>
+__device__ __forceinline__ void ldrow_f(const T* __restrict__ p, float (&v)[NP]) {
+  if constexpr (std::is_same<T, float>::value && NP % 2 == 0) {
+    const float2* q = reinterpret_cast<const float2*>(p);
+#pragma unroll
+    for (int c = 0; c < NP / 2; ++c) {
+      float2 t = __ldg(q + c);
+      v[2 * c] = t.x;
+      v[2 * c + 1] = t.y;
+    }
+  } else if constexpr (std::is_same<T, __nv_bfloat16>::value && NP % 2 == 0) {
+    const __nv_bfloat162* q = reinterpret_cast<const __nv_bfloat162*>(p);
+#pragma unroll
+    for (int c = 0; c < NP / 2; ++c) {
+      float2 t = __bfloat1622float2(q[c]);
+      v[2 * c] = t.x;
+      v[2 * c + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < NP; ++c) v[c] = to_f<T>(p[c]);
+  }
+}
+
+// sum_z s_z (A_z[r][:] . x[col z][:]) in FP32
+template <int NP, class TS, class VT>
+__device__ __forceinline__ float row_dot_lp(int64_t z0, int64_t z1, int r, const int32_t* __restrict__ col,
+                                            const TS* __restrict__ val, const float* __restrict__ sc,
+                                            const VT* __restrict__ x) {
+  float acc = 0.0f;
+  for (int64_t z = z0; z < z1; ++z) {
+    float a[NP], xv[NP];
+    ldrow_f<NP, TS>(val + z * (NP * NP) + r * NP, a);
+    ldrow_f<NP, VT>(x + (int64_t)__ldg(col + z) * NP, xv);
+    float s = 0.0f;
+#pragma unroll
+    for (int c = 0; c < NP; ++c) s = fmaf(a[c], xv[c], s);
+    acc = fmaf(__ldg(sc + z), s, acc);
+  }
+  return acc;
+}
+
+// y = M x (MODE 0) or b - M x (MODE 1); VT = vector type of x, b and y (float or double)
+template <int NP, class TS, class VT, int MODE>
+__global__ void __launch_bounds__(kThreads) k_spmv_lp(int64_t nb, const int64_t* __restrict__ rp,
+                                                     const int32_t* __restrict__ col,
+                                                     const TS* __restrict__ val, const float* __restrict__ sc,
+                                                     const VT* __restrict__ x, const VT* __restrict__ b,
+                                                     VT* __restrict__ y) {
+  constexpr int GPW = Grp<NP>::GPW;
+  const int lane = threadIdx.x & 31;
+  const int g = lane / NP, r = lane - g * NP;
+  if (g >= GPW) return;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp * GPW + g; i < nb; i += nw * GPW) {
+    float acc = row_dot_lp<NP, TS, VT>(__ldg(rp + i), __ldg(rp + i + 1), r, col, val, sc, x);
+    y[i * NP + r] = MODE ? (VT)(to_f<VT>(b[i * NP + r]) - acc) : (VT)acc;
+  }
+}
+
+template <int NP, class TS>
+__device__ __forceinline__ float block_gemv_lp(const TS* __restrict__ W, float s, int r, int base,
+                                               unsigned mask, float v) {
+  float w[NP];
+  ldrow_f<NP, TS>(W + r * NP, w);
+  float acc = 0.0f;
+#pragma unroll
+  for (int c = 0; c < NP; ++c) acc = fmaf(w[c], __shfl_sync(mask, v, base + c), acc);
+  return s * acc;
+}
+
+// damped block Jacobi in FP32: xo = xi + omega D^{-1} (b - M xi). The block inverses are
+// computed in FP64 and stored in FP32 in both modes: rounding the inverse of an ill-conditioned
+// cut-cell block to BF16 loses it.
+template <int NP, class TS, bool ZERO>
+__global__ void __launch_bounds__(kThreads) k_smooth_lp(int64_t nb, const int64_t* __restrict__ rp,
+                                                       const int32_t* __restrict__ col,
+                                                       const TS* __restrict__ val, const float* __restrict__ sc,
+                                                       const float* __restrict__ Dinv, const float* __restrict__ dsc,
+                                                       float omega, const float* __restrict__ b,
+                                                       const float* __restrict__ xi, float* __restrict__ xo) {
+  constexpr int GPW = Grp<NP>::GPW;
+  const int lane = threadIdx.x & 31;
+  const int g = lane / NP, r = lane - g * NP;
+  if (g >= GPW) return;
+  const unsigned mask = group_mask(g, NP);
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp * GPW + g; i < nb; i += nw * GPW) {
+    float res = b[i * NP + r];
+    if (!ZERO) res -= row_dot_lp<NP, TS, float>(__ldg(rp + i), __ldg(rp + i + 1), r, col, val, sc, xi);
+    float z = block_gemv_lp<NP, float>(Dinv + i * (NP * NP), __ldg(dsc + i), r, g * NP, mask, res);
+    xo[i * NP + r] = ZERO ? omega * z : fmaf(omega, z, xi[i * NP + r]);
+  }
+}
+
+// restriction phase 1 in FP32: t_f = R_f^T (b_f - M_f x). The operator is read from its FP32
+// copy in both modes (TA = float): a BF16-rounded operator is not positive definite on the
+// smooth modes the coarse levels correct (2^-9 cond(M) >> 1); TR is the transfer storage.
+template <int NP, class TA, class TR, bool RESID>
+__global__ void __launch_bounds__(kThreads) k_resid_rt_lp(int64_t nbf, const int64_t* __restrict__ rp,
+                                                         const int32_t* __restrict__ col,
+                                                         const TA* __restrict__ val, const float* __restrict__ sc,
+                                                         const TR* __restrict__ R, const float* __restrict__ rsc,
+                                                         const float* __restrict__ b, const float* __restrict__ x,
+                                                         float* __restrict__ t) {
+  constexpr int GPW = Grp<NP>::GPW;
+  const int lane = threadIdx.x & 31;
+  const int g = lane / NP, r = lane - g * NP;
+  if (g >= GPW) return;
+  const unsigned mask = group_mask(g, NP);
+  const int base = g * NP;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t f = warp * GPW + g; f < nbf; f += nw * GPW) {
+    float res = b[f * NP + r];
+    if (RESID) res -= row_dot_lp<NP, TA, float>(__ldg(rp + f), __ldg(rp + f + 1), r, col, val, sc, x);
+    const TR* Rf = R + f * (NP * NP);
+    float s = 0.0f;
+#pragma unroll
+    for (int m = 0; m < NP; ++m) s = fmaf(to_f<TR>(Rf[m * NP + r]), __shfl_sync(mask, res, base + m), s);
+    t[f * NP + r] = __ldg(rsc + f) * s;
+  }
+}
+
+// restriction phase 2 in FP32 (children in ascending order)
+template <int NP>
+__global__ void __launch_bounds__(kThreads) k_gather_lp(int64_t nbc, const int64_t* __restrict__ cptr,
+                                                       const int32_t* __restrict__ ch,
+                                                       const float* __restrict__ t, float* __restrict__ rc) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nbc * NP;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t C = e / NP;
+    const int r = (int)(e - C * NP);
+    float s = 0.0f;
+    for (int64_t q = __ldg(cptr + C); q < __ldg(cptr + C + 1); ++q) s += t[(int64_t)__ldg(ch + q) * NP + r];
+    rc[e] = s;
+  }
+}
+
+// xo_f = xi_f + R_f zc[agg[f]] in FP32 (xo may equal xi)
+template <int NP, class TS>
+__global__ void __launch_bounds__(kThreads) k_prolong_lp(int64_t nbf, const int32_t* __restrict__ agg,
+                                                        const TS* __restrict__ R, const float* __restrict__ rsc,
+                                                        const float* __restrict__ zc, const float* xi, float* xo) {
+  constexpr int GPW = Grp<NP>::GPW;
+  const int lane = threadIdx.x & 31;
+  const int g = lane / NP, r = lane - g * NP;
+  if (g >= GPW) return;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t f = warp * GPW + g; f < nbf; f += nw * GPW) {
+    float a[NP], z[NP];
+    ldrow_f<NP, TS>(R + f * (NP * NP) + r * NP, a);
+    ldrow_f<NP, float>(zc + (int64_t)__ldg(agg + f) * NP, z);
+    float s = 0.0f;
+#pragma unroll
+    for (int n = 0; n < NP; ++n) s = fmaf(a[n], z[n], s);
+    xo[f * NP + r] = fmaf(__ldg(rsc + f), s, xi[f * NP + r]);
+  }
+}
+
+// coarsest level: z = Minv r with the FP64 inverse, FP32 vectors (one warp per row)
+__global__ void __launch_bounds__(kThreads) k_gemv_coarse_lp(int64_t n, const double* __restrict__ A,
+                                                            const float* __restrict__ x, float* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (row >= n) return;
+  double s = 0.0;
+  for (int64_t c = lane; c < n; c += 32) s = fma(__ldg(A + row * n + c), (double)__ldg(x + c), s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) y[row] = (float)s;
+}
+
+// stored copy of Np x Np blocks: scale s = max |entry| (as float, 1 for a zero block),
+// stored entry = round(entry / s) to TS (round to nearest even; BF16 through FP32)
+template <class TS>
+__device__ __forceinline__ TS store_lp(double v);
+template <>
+__device__ __forceinline__ float store_lp<float>(double v) { return (float)v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 store_lp<__nv_bfloat16>(double v) { return __float2bfloat16_rn((float)v); }
+
+template <class TS>
+__global__ void k_make_lp(int64_t nblk, int np2, const double* __restrict__ src, TS* __restrict__ dst,
+                          float* __restrict__ scale) {
+  const int lane = threadIdx.x & 31;
+  const int64_t blk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (blk >= nblk) return;
+  const double* s = src + blk * np2;
+  double m = 0.0;
+  for (int e = lane; e < np2; e += 32) m = fmax(m, fabs(s[e]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  float sf = (m > 0.0) ? (float)m : 1.0f;
+  const double sd = (double)sf;
+  for (int e = lane; e < np2; e += 32) dst[blk * np2 + e] = store_lp<TS>(s[e] / sd);
+  if (lane == 0) scale[blk] = sf;
+}
+
+__global__ void k_d2f(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+__global__ void k_f2d(int64_t n, const float* __restrict__ a, double* __restrict__ b) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+
+__global__ void k_axpy_f(int64_t n, float a, const float* __restrict__ x, float* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = fmaf(a, x[i], y[i]);
+}
+
+__global__ void k_copy_f(int64_t n, const float* __restrict__ a, float* __restrict__ b) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = a[i];
+}
+
+// flexible CG (one previous direction kept): beta = -(z_new . q) / (p . q), q = M p
+__global__ void k_fcg_beta(PcgScal* S) {
+  double pq = S->pq, zq = S->zq;
+  if (!(pq > 0.0) || !isfinite(zq)) {
+    S->bad = 1;
+    S->beta = 0.0;
+  } else {
+    S->beta = -zq / pq;
+  }
+}
+
+}  // namespace xdg

@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _ROOT = os.path.dirname(_HERE)
 LIB_PATH = os.path.join(_HERE, "libxdg.so")
 _SRCS = [os.path.join(_HERE, "csrc", "xdg.cu"), os.path.join(_HERE, "csrc", "xdg_kernels.cuh"),
-         os.path.join(_ROOT, "include", "xdg.h")]
+         os.path.join(_HERE, "csrc", "xdg_kernels_lp.cuh"), os.path.join(_ROOT, "include", "xdg.h")]
 
 XDG_OK, XDG_EINVAL, XDG_ECUDA, XDG_ENOMEM, XDG_ENOTCONV, XDG_EBREAKDOWN, XDG_ETIMEOUT = range(7)
 XDG_PREC_F64, XDG_PREC_F32, XDG_PREC_BF16 = 0, 1, 2
@@ -61,7 +61,7 @@ class Problem(C.Structure):
 
 class HierOpts(C.Structure):
     _fields_ = [("omega", C.c_double), ("lanczos_steps", C.c_int), ("nu", C.c_int),
-                ("gamma", C.c_int), ("low_precision", C.c_int)]
+                ("gamma", C.c_int), ("low_precision", C.c_int), ("w_levels", C.c_int)]
 
 
 class SolveOpts(C.Structure):
@@ -96,11 +96,20 @@ SIGNATURES = [
     ("xdg_prolong", C.c_int, [_vp, _ip, _vp, _vp, _vp]),
     ("xdg_coarse_solve", C.c_int, [_vp, _vp, _vp]),
     ("xdg_vcycle", C.c_int, [_vp, _vp, _vp]),
+    ("xdg_cycle", C.c_int, [_vp, _ip, _vp, _vp]),
     ("xdg_solve", C.c_int, [_vp, _vp, _vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
     ("xdg_solve_host", C.c_int, [_vp, _dp, _dp, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
     ("xdg_restrict_noalloc", C.c_int, [_ip, C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                       _vp]),
+    ("xdg_fma_peak", C.c_int, [_ip, _dp]),
 ]
+
+
+def fma_peak(prec=XDG_PREC_F64) -> float:
+    """Measured FMA throughput (TFLOP/s) of the current GPU in FP64 or FP32."""
+    out = C.c_double()
+    _check(load().xdg_fma_peak(prec, C.byref(out)))
+    return out.value
 
 NOALLOC_MAX_ENTRIES = 1 << 20
 
@@ -163,7 +172,7 @@ class Hierarchy:
     unless one is given); every call is ordered with torch's current stream by event waits."""
 
     def __init__(self, Np, nb, row_ptr, col, val, aggs, Rs, omega=0.0, lanczos_steps=12, nu=1,
-                 gamma=1, low_precision=0, stream=None):
+                 gamma=1, low_precision=0, stream=None, w_levels=0):
         L = load()
         torch = _torch()
         if stream is None:
@@ -188,7 +197,7 @@ class Hierarchy:
         self._keep += [aggp, Rp]
         prob = Problem(Np, nl, nb_a.ctypes.data_as(C.POINTER(C.c_int64)), rp.ctypes.data_as(C.POINTER(C.c_int64)),
                        cl.ctypes.data_as(C.POINTER(C.c_int32)), vl.ctypes.data_as(_dp), aggp, Rp)
-        opts = HierOpts(omega, lanczos_steps, nu, gamma, low_precision)
+        opts = HierOpts(omega, lanczos_steps, nu, gamma, low_precision, w_levels)
         h = C.c_void_p()
         st = C.c_void_p(stream.cuda_stream)
         self._h = None
@@ -249,6 +258,10 @@ class Hierarchy:
     def vcycle(self, b, x):
         with _Ordered(self):
             _check(load().xdg_vcycle(self._h, _dptr(b), _dptr(x)))
+
+    def cycle(self, prec, b, x):
+        with _Ordered(self):
+            _check(load().xdg_cycle(self._h, prec, _dptr(b), _dptr(x)))
 
     def solve(self, b, x, tol=1e-10, maxit=1000, check_every=1, precision=XDG_PREC_F64, inner_tol=0.0,
               time_budget_ms=0.0, raise_on_error=True) -> dict:

@@ -31,6 +31,8 @@ CASES = {
     "2d_k4": (xp.Config(D=2, N=13, k=4, c=(0.5, 0.5, 0), R=0.27, muA=1, muB=10, max_coarse_dof=120), 1),
     "3d_k2": (xp.Config(D=3, N=14, k=2, c=(0.5, 0.5, 0.5), R=0.31, muA=1, muB=1000, max_coarse_dof=300), 2),
     "3d_k3": (xp.Config(D=3, N=7, k=3, c=(0.48, 0.51, 0.5), R=0.3, muA=1, muB=1000, max_coarse_dof=200), 1),
+    # W-cycle on the finest level only, V-cycle below
+    "3d_k2_w1": (xp.Config(D=3, N=12, k=2, c=(0.47, 0.52, 0.5), R=0.3, muA=1, muB=1000, max_coarse_dof=100), 2, 1),
 }
 
 
@@ -49,11 +51,14 @@ def _rel(a, b):
 
 @pytest.fixture(scope="module", params=sorted(CASES))
 def case(request):
-    cfg, gamma = CASES[request.param]
+    cfg, gamma, *rest = CASES[request.param]
+    wlev = rest[0] if rest else 0
     P = xp.Problem(cfg)
     assert P.n_levels >= 2
     O = oracle.Hierarchy(P, gamma=gamma)
-    G = xdg.Hierarchy.from_problem(P, gamma=gamma)
+    if wlev:
+        oracle.set_w_levels(O, wlev)
+    G = xdg.Hierarchy.from_problem(P, gamma=gamma, w_levels=wlev)
     return request.param, P, O, G
 
 

@@ -170,3 +170,22 @@ def test_mesh_independent_iterations_2d():
         H = oracle.Hierarchy(P, gamma=2)
         its.append(H.pcg(P.b, tol=1e-10, maxit=400)[1])
     assert max(its) <= 1.25 * min(its), its
+
+
+def test_quantized_storage_rounding():
+    # FP32 storage: entry/scale rounded to float; BF16: further rounded to bfloat16 with ties to
+    # even -- checked against torch's float32 -> bfloat16 conversion
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(12)
+    a = rng.standard_normal((200, 6, 6)) * np.exp(rng.uniform(-20, 20, (200, 1, 1)))
+    a[3] = 0.0
+    for prec in (1, 2):
+        q, s = oracle.quantize_blocks(a, prec)
+        m = np.abs(a).reshape(200, -1).max(axis=1)
+        assert np.array_equal(s, np.where(m > 0, m, 1.0).astype(np.float32))
+        ratio = (a.reshape(200, -1) / s.astype(np.float64)[:, None]).astype(np.float32)
+        if prec == 2:
+            ratio = torch.from_numpy(ratio).to(torch.bfloat16).to(torch.float32).numpy()
+        expect = s.astype(np.float64)[:, None] * ratio.astype(np.float64)
+        assert np.array_equal(q.reshape(200, -1), expect)
+        assert np.all(q[3] == 0.0)
