@@ -74,6 +74,8 @@ struct Ops {
   void (*resid_rt)(int grid, cudaStream_t, int64_t, const int64_t*, const int32_t*, const double*,
                    const double*, const double*, const double*, double*);
   void (*gather)(int grid, cudaStream_t, int64_t, const int64_t*, const int32_t*, const double*, double*);
+  void (*gather_smooth0)(int grid, cudaStream_t, int64_t, const int64_t*, const int32_t*, const double*,
+                         const double*, double, double*, double*);
   void (*prolong)(int grid, cudaStream_t, int64_t, const int32_t*, const double*, const double*,
                   const double*, double*);
   void (*galerkin)(int grid, cudaStream_t, int64_t, const int64_t*, const int32_t*, const int64_t*,
@@ -112,6 +114,10 @@ struct OpsT {
                      const double* t, double* rc) {
     k_gather<NP><<<grid, kThreads, 0, s>>>(nbc, cptr, ch, t, rc);
   }
+  static void gather_smooth0(int grid, cudaStream_t s, int64_t nbc, const int64_t* cptr, const int32_t* ch,
+                             const double* t, const double* Dinv, double om, double* bc, double* xc) {
+    k_gather_smooth0<NP><<<grid, kThreads, 0, s>>>(nbc, cptr, ch, t, Dinv, om, bc, xc);
+  }
   static void prolong(int grid, cudaStream_t s, int64_t nbf, const int32_t* agg, const double* R,
                       const double* zc, const double* xi, double* xo) {
     k_prolong<NP><<<grid, kThreads, 0, s>>>(nbf, agg, R, zc, xi, xo);
@@ -126,7 +132,8 @@ struct OpsT {
     k_diag_inv<NP><<<(unsigned)((nb + 63) / 64), 64, 0, s>>>(nb, dg, val, Dinv, err);
   }
   static Ops make() {
-    return Ops{NP, spmv, smooth, bjsolve, diagmul, resid_rt, gather, prolong, galerkin, diag_inv, Grp<NP>::GPW};
+    return Ops{NP, spmv, smooth, bjsolve, diagmul, resid_rt, gather, gather_smooth0, prolong, galerkin, diag_inv,
+               Grp<NP>::GPW};
   }
 };
 
@@ -156,6 +163,8 @@ struct OpsLP {
                   const float*, float*);
   void (*resid32)(int, cudaStream_t, int64_t, const int64_t*, const int32_t*, const void*, const float*,
                   const float*, const float*, float*);
+  void (*gather_smooth0)(int, cudaStream_t, int64_t, const int64_t*, const int32_t*, const float*, const float*,
+                         const float*, float, float*, float*);
   size_t elem;
 };
 
@@ -208,7 +217,13 @@ struct OpsLPT {
                       const float* zc, const float* xi, float* xo) {
     k_prolong_lp<NP, TS><<<grid, kThreads, 0, s>>>(nbf, agg, (const TS*)R, rsc, zc, xi, xo);
   }
-  static OpsLP get() { return OpsLP{make, spmv_f, spmv_d, smooth, resid_rt, gather, prolong, resid32, sizeof(TS)}; }
+  static void gather_smooth0(int grid, cudaStream_t s, int64_t nbc, const int64_t* cptr, const int32_t* ch,
+                             const float* t, const float* Dinv, const float* dsc, float om, float* bc, float* xc) {
+    k_gather_smooth0_lp<NP><<<grid, kThreads, 0, s>>>(nbc, cptr, ch, t, Dinv, dsc, om, bc, xc);
+  }
+  static OpsLP get() {
+    return OpsLP{make, spmv_f, spmv_d, smooth, resid_rt, gather, prolong, resid32, gather_smooth0, sizeof(TS)};
+  }
 };
 
 // prec: XDG_PREC_F32 or XDG_PREC_BF16
@@ -365,8 +380,9 @@ struct xdg_hier {
     k_sum_final<<<1, kThreads, 0, stream>>>(kRedBlocks, partial, out);
   }
 
-  // one symmetric cycle on level l from a zero initial guess: x = B_l b
-  void cycle(int l, const double* b, double* x) {
+  // one symmetric cycle on level l from a zero initial guess: x = B_l b. pre0: x already
+  // holds the first sweep omega D^{-1} b (done by the fused restriction of the finer level)
+  void cycle(int l, const double* b, double* x, bool pre0 = false) {
     if (l == nlev - 1) {
       coarse(b, x);
       return;
@@ -376,14 +392,22 @@ struct xdg_hier {
     // pre-smoothing: nu sweeps, the first one from x = 0
     double* cur = x;
     double* oth = V.t;
-    smooth(l, b, nullptr, cur);
+    if (!pre0) smooth(l, b, nullptr, cur);
     for (int s = 1; s < nu; ++s) {
       smooth(l, b, cur, oth);
       std::swap(cur, oth);
     }
-    // coarse-grid correction: gamma cycles on the coarse level
-    restrict_(l, b, cur, C.b);
-    cycle(l + 1, C.b, C.x);
+    // coarse-grid correction: gamma cycles on the coarse level; above the coarsest level the
+    // restriction's gather also does the coarse level's first sweep
+    if (l + 2 < nlev) {
+      ops.resid_rt(grid(V.nb), stream, V.nb, V.rp, V.col, V.val, V.R, b, cur, V.s);
+      ops.gather_smooth0(grid(C.nb), stream, C.nb, V.cptr, V.ch, V.s, C.Dinv, C.omega, C.b, C.x);
+      launches += 2;
+      cycle(l + 1, C.b, C.x, true);
+    } else {
+      restrict_(l, b, cur, C.b);
+      cycle(l + 1, C.b, C.x);
+    }
     if (gamma > 1 && l + 2 < nlev && l < wlev) {
       for (int g = 1; g < gamma; ++g) {
         spmv(l + 1, C.x, C.b, C.r, 1);
@@ -424,7 +448,7 @@ struct xdg_hier {
   }
 
   // ---------------------------------------------------------------- low-precision cycle
-  void cycle_lp(int p, int l, const float* b, float* x) {
+  void cycle_lp(int p, int l, const float* b, float* x, bool pre0 = false) {
     const OpsLP& o = opl[p];
     if (l == nlev - 1) {
       ++launches;
@@ -439,17 +463,24 @@ struct xdg_hier {
     const float om = (float)V.omega;
     float* cur = x;
     float* oth = W.t;
-    o.smooth(grid(V.nb), stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, b, nullptr, cur);
-    ++launches;
+    if (!pre0) {
+      o.smooth(grid(V.nb), stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, b, nullptr, cur);
+      ++launches;
+    }
     for (int s = 1; s < nu; ++s) {
       o.smooth(grid(V.nb), stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, b, cur, oth);
       ++launches;
       std::swap(cur, oth);
     }
     o.resid_rt(grid(V.nb), stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.R, W.rsc, b, cur, W.s);
-    o.gather(vgrid(C.nb * Np), stream, C.nb, V.cptr, V.ch, W.s, WC.b);
     launches += 2;
-    cycle_lp(p, l + 1, WC.b, WC.x);
+    if (l + 2 < nlev) {
+      o.gather_smooth0(grid(C.nb), stream, C.nb, V.cptr, V.ch, W.s, (const float*)WC.Dinv, WC.dsc, (float)C.omega, WC.b, WC.x);
+      cycle_lp(p, l + 1, WC.b, WC.x, true);
+    } else {
+      o.gather(vgrid(C.nb * Np), stream, C.nb, V.cptr, V.ch, W.s, WC.b);
+      cycle_lp(p, l + 1, WC.b, WC.x);
+    }
     if (gamma > 1 && l + 2 < nlev && l < wlev) {
       for (int g = 1; g < gamma; ++g) {
         o.resid32(grid(C.nb), stream, C.nb, C.rp, C.col, WC.val32, WC.sc32, WC.x, WC.b, WC.r);

@@ -44,17 +44,34 @@ __device__ __forceinline__ void ldrow(const double* __restrict__ p, double (&v)[
   }
 }
 
-// acc += A[z][r][:] . x[col[z]][:] over the block row (lane r)
+// blocks of a row whose loads are put in flight together: the column indices of a chunk are
+// read first, so the dependent x-block loads of the chunk overlap (short rows of coarse levels
+// run with few warps, where a block-by-block dependent chain is not hidden)
+template <int NP>
+struct Chunk {
+  static constexpr int F64 = NP <= 10 ? 2 : 1;
+  static constexpr int F32 = NP <= 10 ? 4 : 2;
+};
+
+// acc += A[z][r][:] . x[col[z]][:] over the block row (lane r), blocks in increasing z
 template <int NP>
 __device__ __forceinline__ double row_dot(int64_t z0, int64_t z1, int r, const int32_t* __restrict__ col,
                                           const double* __restrict__ val, const double* __restrict__ x) {
+  constexpr int CH = Chunk<NP>::F64;
   double acc = 0.0;
-  for (int64_t z = z0; z < z1; ++z) {
-    double a[NP], xv[NP];
-    ldrow<NP>(val + z * (NP * NP) + r * NP, a);
-    ldrow<NP>(x + (int64_t)__ldg(col + z) * NP, xv);
+  for (int64_t z = z0; z < z1; z += CH) {
+    int32_t cc[CH];
 #pragma unroll
-    for (int c = 0; c < NP; ++c) acc = fma(a[c], xv[c], acc);
+    for (int u = 0; u < CH; ++u) cc[u] = (z + u < z1) ? __ldg(col + z + u) : -1;
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      if (cc[u] < 0) continue;
+      double a[NP], xv[NP];
+      ldrow<NP>(val + (z + u) * (NP * NP) + r * NP, a);
+      ldrow<NP>(x + (int64_t)cc[u] * NP, xv);
+#pragma unroll
+      for (int c = 0; c < NP; ++c) acc = fma(a[c], xv[c], acc);
+    }
   }
   return acc;
 }
@@ -186,6 +203,26 @@ __global__ void __launch_bounds__(kThreads) k_resid_rt(int64_t nbf, const int64_
   }
 }
 
+// sum of t[f][r] over the children f = ch[q0..q1) in increasing q (child indices read in chunks
+// of 8 so the value loads overlap)
+template <int NP, class T, class A>
+__device__ __forceinline__ A child_sum(int64_t q0, int64_t q1, int r, const int32_t* __restrict__ ch,
+                                       const T* __restrict__ t) {
+  A s = 0;
+  for (int64_t q = q0; q < q1; q += 8) {
+    int32_t f[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) f[u] = (q + u < q1) ? __ldg(ch + q + u) : -1;
+    T v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = (f[u] >= 0) ? t[(int64_t)f[u] * NP + r] : (T)0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (f[u] >= 0) s += v[u];
+  }
+  return s;
+}
+
 // restriction, phase 2: rc[C] = sum of t_f over the children f of C, in increasing f
 // (deterministic; one thread per coarse entry)
 template <int NP>
@@ -197,9 +234,34 @@ __global__ void __launch_bounds__(kThreads) k_gather(int64_t nbc, const int64_t*
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t C = e / NP;
     const int r = (int)(e - C * NP);
+    rc[e] = child_sum<NP, double, double>(__ldg(cptr + C), __ldg(cptr + C + 1), r, ch, t);
+  }
+}
+
+// phase 2 fused with the first sweep of the coarse level from a zero guess:
+// bc_C = sum over children of t_f; xc_C = omega D_C^{-1} bc_C (one group per coarse block)
+template <int NP>
+__global__ void __launch_bounds__(kThreads) k_gather_smooth0(int64_t nbc, const int64_t* __restrict__ cptr,
+                                                            const int32_t* __restrict__ ch,
+                                                            const double* __restrict__ t,
+                                                            const double* __restrict__ Dinv, double omega,
+                                                            double* __restrict__ bc, double* __restrict__ xc) {
+  constexpr int GPW = Grp<NP>::GPW;
+  const int lane = threadIdx.x & 31;
+  const int g = lane / NP, r = lane - g * NP;
+  if (g >= GPW) return;
+  const unsigned mask = group_mask(g, NP);
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t C = warp * GPW + g; C < nbc; C += nw * GPW) {
+    double bv = child_sum<NP, double, double>(__ldg(cptr + C), __ldg(cptr + C + 1), r, ch, t);
+    bc[C * NP + r] = bv;
+    double w[NP];
+    ldrow<NP>(Dinv + C * (NP * NP) + r * NP, w);
     double s = 0.0;
-    for (int64_t q = __ldg(cptr + C); q < __ldg(cptr + C + 1); ++q) s += t[(int64_t)__ldg(ch + q) * NP + r];
-    rc[e] = s;
+#pragma unroll
+    for (int c = 0; c < NP; ++c) s = fma(w[c], __shfl_sync(mask, bv, g * NP + c), s);
+    xc[C * NP + r] = omega * s;
   }
 }
 

@@ -54,15 +54,23 @@ template <int NP, class TS, class VT>
 __device__ __forceinline__ float row_dot_lp(int64_t z0, int64_t z1, int r, const int32_t* __restrict__ col,
                                             const TS* __restrict__ val, const float* __restrict__ sc,
                                             const VT* __restrict__ x) {
+  constexpr int CH = Chunk<NP>::F32;
   float acc = 0.0f;
-  for (int64_t z = z0; z < z1; ++z) {
-    float a[NP], xv[NP];
-    ldrow_f<NP, TS>(val + z * (NP * NP) + r * NP, a);
-    ldrow_f<NP, VT>(x + (int64_t)__ldg(col + z) * NP, xv);
-    float s = 0.0f;
+  for (int64_t z = z0; z < z1; z += CH) {
+    int32_t cc[CH];
 #pragma unroll
-    for (int c = 0; c < NP; ++c) s = fmaf(a[c], xv[c], s);
-    acc = fmaf(__ldg(sc + z), s, acc);
+    for (int u = 0; u < CH; ++u) cc[u] = (z + u < z1) ? __ldg(col + z + u) : -1;
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      if (cc[u] < 0) continue;
+      float a[NP], xv[NP];
+      ldrow_f<NP, TS>(val + (z + u) * (NP * NP) + r * NP, a);
+      ldrow_f<NP, VT>(x + (int64_t)cc[u] * NP, xv);
+      float s = 0.0f;
+#pragma unroll
+      for (int c = 0; c < NP; ++c) s = fmaf(a[c], xv[c], s);
+      acc = fmaf(__ldg(sc + z + u), s, acc);
+    }
   }
   return acc;
 }
@@ -160,9 +168,30 @@ __global__ void __launch_bounds__(kThreads) k_gather_lp(int64_t nbc, const int64
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t C = e / NP;
     const int r = (int)(e - C * NP);
-    float s = 0.0f;
-    for (int64_t q = __ldg(cptr + C); q < __ldg(cptr + C + 1); ++q) s += t[(int64_t)__ldg(ch + q) * NP + r];
-    rc[e] = s;
+    rc[e] = child_sum<NP, float, float>(__ldg(cptr + C), __ldg(cptr + C + 1), r, ch, t);
+  }
+}
+
+// phase 2 fused with the first sweep of the coarse level from a zero guess (FP32)
+template <int NP>
+__global__ void __launch_bounds__(kThreads) k_gather_smooth0_lp(int64_t nbc, const int64_t* __restrict__ cptr,
+                                                               const int32_t* __restrict__ ch,
+                                                               const float* __restrict__ t,
+                                                               const float* __restrict__ Dinv,
+                                                               const float* __restrict__ dsc, float omega,
+                                                               float* __restrict__ bc, float* __restrict__ xc) {
+  constexpr int GPW = Grp<NP>::GPW;
+  const int lane = threadIdx.x & 31;
+  const int g = lane / NP, r = lane - g * NP;
+  if (g >= GPW) return;
+  const unsigned mask = group_mask(g, NP);
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t C = warp * GPW + g; C < nbc; C += nw * GPW) {
+    float bv = child_sum<NP, float, float>(__ldg(cptr + C), __ldg(cptr + C + 1), r, ch, t);
+    bc[C * NP + r] = bv;
+    float z = block_gemv_lp<NP, float>(Dinv + C * (NP * NP), __ldg(dsc + C), r, g * NP, mask, bv);
+    xc[C * NP + r] = omega * z;
   }
 }
 
