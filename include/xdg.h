@@ -213,6 +213,72 @@ int xdg_solve_host(xdg_hier_t h, const double* b_host, double* x_host, const xdg
  * apply (0.25 flop/byte) is bound by the FP64 pipe, not by HBM. */
 int xdg_fma_peak(int prec, double* tflops);
 
+/* ---------------------------------------------------------------------------------------------
+ * Batches of independent problems.
+ *
+ * Each problem is solved exactly as by xdg_solve on its own hierarchy (sec. 3.3: Krylov method
+ * preconditioned by the multigrid cycle of Algorithm 4 without residual minimisation; damping,
+ * Lanczos estimate and coarsest inverse computed per problem), but all problems run in one
+ * CUDA graph launch. Problems with the same Np and the same number of levels form a group; a
+ * group is one block-diagonal union hierarchy (the problems' level operators, aggregation maps
+ * and transfers concatenated), so every kernel of a cycle covers all problems of the group.
+ * Krylov scalars (inner products, step lengths, convergence) are per problem; a problem that
+ * has converged takes no further steps while the others continue. The iteration loop of each
+ * group is a conditional (while) node of the graph, set on the device by the convergence check
+ * and bounded by maxit, so the whole batched solve needs no host round trip. */
+typedef struct xdg_batch* xdg_batch_t;
+
+typedef struct {
+  int iterations;  /* CG iterations of this problem */
+  int status;      /* XDG_OK, XDG_ENOTCONV (maxit reached) or XDG_EBREAKDOWN */
+  double relres;   /* ||b - M x||_2 / ||b||_2 of this problem, recomputed in FP64 */
+} xdg_batch_result;
+
+typedef struct {
+  int n_problems, n_groups;
+  int64_t total_dof;           /* length of the concatenated vectors */
+  size_t device_bytes;
+  double setup_ms;
+  int64_t nodes_fixed[3];          /* kernel nodes of a recorded solve outside its loops and */
+  int64_t nodes_per_iteration[3];  /* per loop iteration (all groups), by precision; 0 until
+                                      the first solve of that precision */
+} xdg_batch_info;
+
+/* Build the hierarchies of n problems (layout of each as in xdg_problem; host arrays, deep
+ * copied). Every index is validated against the problem's own sizes (EINVAL names the
+ * problem). Supported: Np in {6, 10, 15, 20}, at most 4096 DOF on each problem's coarsest
+ * level, at most 65535 problems per group. opts apply to every problem (omega <= 0 gives each
+ * problem its own Lanczos-based damping per level). stream: as in xdg_create_hierarchy (all
+ * work of the batch is ordered on it). */
+int xdg_create_batch(int n, const xdg_problem* probs, const xdg_hier_opts* o, void* stream,
+                     xdg_batch_t* out);
+int xdg_batch_destroy(xdg_batch_t b);
+int xdg_batch_get_info(xdg_batch_t b, xdg_batch_info* info);
+
+/* Group g (0-based, groups numbered by first appearance in the problem list): *h = its union
+ * hierarchy (owned by the batch; the single-problem entry points apply to it, on vectors of the
+ * group's problems concatenated in member order, and run on the batch's stream),
+ * *n_members = number of problems, members[] (optional, n_members entries) = their indices in
+ * the caller's list, in the order of the union. */
+int xdg_batch_group(xdg_batch_t b, int g, xdg_hier_t* h, int* n_members, int* members);
+
+/* Solve all problems: b and x are device vectors holding every problem's right-hand side and
+ * initial guess (solution on return) concatenated in the caller's order (problem i at offset
+ * sum_{j<i} nb_j[0] Np_j). o->precision: XDG_PREC_F64 gives CG with the FP64 cycle, F32 /
+ * BF16 flexible CG with the low-precision cycle (as xdg_solve). o->tol and o->maxit apply to
+ * every problem; check_every and time_budget_ms are not used (the loop runs on the device).
+ * The first solve of a precision records its graph (outside any stream capture). info
+ * (optional): iterations = largest per-problem count, relres = largest, status = worst,
+ * launches = kernel nodes executed. results (optional): n entries. Returns XDG_OK when every
+ * problem converged, else XDG_EBREAKDOWN if any broke down, else XDG_ENOTCONV. */
+int xdg_solve_batch(xdg_batch_t b, const double* bvec, double* x, const xdg_solve_opts* o,
+                    xdg_solve_info* info, xdg_batch_result* results);
+
+/* Same with host vectors: copies b in, solves from x = 0, copies x out, inside the call. */
+int xdg_solve_batch_host(xdg_batch_t b, const double* b_host, double* x_host,
+                         const xdg_solve_opts* o, xdg_solve_info* info,
+                         xdg_batch_result* results);
+
 /* Residual restriction for callers that cannot allocate device memory.
  *
  * The paper has no counterpart: this is an interface variant of xdg_restrict. It serves

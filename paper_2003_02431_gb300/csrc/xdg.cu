@@ -23,6 +23,7 @@
 #include "../../include/xdg.h"
 #include "xdg_kernels.cuh"
 #include "xdg_kernels_lp.cuh"
+#include "xdg_kernels_batch.cuh"
 
 using namespace xdg;
 
@@ -68,14 +69,14 @@ struct Ops {
   void (*spmv)(int grid, cudaStream_t, int64_t, const int64_t*, const int32_t*, const double*,
                const double*, const double*, double*, int mode);
   void (*smooth)(int grid, cudaStream_t, int64_t, const int64_t*, const int32_t*, const double*,
-                 const double*, double, const double*, const double*, double*);
+                 const double*, double, const double*, const double*, const double*, double*);
   void (*bjsolve)(int grid, cudaStream_t, int64_t, const double*, const double*, double*);
   void (*diagmul)(int grid, cudaStream_t, int64_t, const int64_t*, const double*, const double*, double*);
   void (*resid_rt)(int grid, cudaStream_t, int64_t, const int64_t*, const int32_t*, const double*,
                    const double*, const double*, const double*, double*);
   void (*gather)(int grid, cudaStream_t, int64_t, const int64_t*, const int32_t*, const double*, double*);
   void (*gather_smooth0)(int grid, cudaStream_t, int64_t, const int64_t*, const int32_t*, const double*,
-                         const double*, double, double*, double*);
+                         const double*, double, const double*, double*, double*);
   void (*prolong)(int grid, cudaStream_t, int64_t, const int32_t*, const double*, const double*,
                   const double*, double*);
   void (*galerkin)(int grid, cudaStream_t, int64_t, const int64_t*, const int32_t*, const int64_t*,
@@ -93,10 +94,10 @@ struct OpsT {
     else k_spmv<NP, 0><<<grid, kThreads, 0, s>>>(nb, rp, col, val, x, b, y);
   }
   static void smooth(int grid, cudaStream_t s, int64_t nb, const int64_t* rp, const int32_t* col,
-                     const double* val, const double* Dinv, double om, const double* b,
+                     const double* val, const double* Dinv, double om, const double* omr, const double* b,
                      const double* xi, double* xo) {
-    if (xi) k_smooth<NP, false><<<grid, kThreads, 0, s>>>(nb, rp, col, val, Dinv, om, b, xi, xo);
-    else k_smooth<NP, true><<<grid, kThreads, 0, s>>>(nb, rp, col, val, Dinv, om, b, xi, xo);
+    if (xi) k_smooth<NP, false><<<grid, kThreads, 0, s>>>(nb, rp, col, val, Dinv, om, omr, b, xi, xo);
+    else k_smooth<NP, true><<<grid, kThreads, 0, s>>>(nb, rp, col, val, Dinv, om, omr, b, xi, xo);
   }
   static void bjsolve(int grid, cudaStream_t s, int64_t nb, const double* Dinv, const double* v, double* z) {
     k_bjsolve<NP><<<grid, kThreads, 0, s>>>(nb, Dinv, v, z);
@@ -115,8 +116,9 @@ struct OpsT {
     k_gather<NP><<<grid, kThreads, 0, s>>>(nbc, cptr, ch, t, rc);
   }
   static void gather_smooth0(int grid, cudaStream_t s, int64_t nbc, const int64_t* cptr, const int32_t* ch,
-                             const double* t, const double* Dinv, double om, double* bc, double* xc) {
-    k_gather_smooth0<NP><<<grid, kThreads, 0, s>>>(nbc, cptr, ch, t, Dinv, om, bc, xc);
+                             const double* t, const double* Dinv, double om, const double* omr, double* bc,
+                             double* xc) {
+    k_gather_smooth0<NP><<<grid, kThreads, 0, s>>>(nbc, cptr, ch, t, Dinv, om, omr, bc, xc);
   }
   static void prolong(int grid, cudaStream_t s, int64_t nbf, const int32_t* agg, const double* R,
                       const double* zc, const double* xi, double* xo) {
@@ -155,7 +157,7 @@ struct OpsLP {
   void (*spmv_d)(int, cudaStream_t, int64_t, const int64_t*, const int32_t*, const void*, const float*,
                  const double*, double*);
   void (*smooth)(int, cudaStream_t, int64_t, const int64_t*, const int32_t*, const void*, const float*,
-                 const void*, const float*, float, const float*, const float*, float*);
+                 const void*, const float*, float, const float*, const float*, const float*, float*);
   void (*resid_rt)(int, cudaStream_t, int64_t, const int64_t*, const int32_t*, const void*, const float*,
                    const void*, const float*, const float*, const float*, float*);
   void (*gather)(int, cudaStream_t, int64_t, const int64_t*, const int32_t*, const float*, float*);
@@ -164,7 +166,7 @@ struct OpsLP {
   void (*resid32)(int, cudaStream_t, int64_t, const int64_t*, const int32_t*, const void*, const float*,
                   const float*, const float*, float*);
   void (*gather_smooth0)(int, cudaStream_t, int64_t, const int64_t*, const int32_t*, const float*, const float*,
-                         const float*, float, float*, float*);
+                         const float*, float, const float*, float*, float*);
   size_t elem;
 };
 
@@ -185,13 +187,13 @@ struct OpsLPT {
   // val: the FP32 operator copy (a BF16 operator is not usable in the sweeps, see k_resid_rt_lp)
   static void smooth(int grid, cudaStream_t s, int64_t nb, const int64_t* rp, const int32_t* col,
                      const void* val, const float* sc, const void* Dinv, const float* dsc, float om,
-                     const float* b, const float* xi, float* xo) {
+                     const float* omr, const float* b, const float* xi, float* xo) {
     if (xi)
       k_smooth_lp<NP, float, false><<<grid, kThreads, 0, s>>>(nb, rp, col, (const float*)val, sc,
-                                                              (const float*)Dinv, dsc, om, b, xi, xo);
+                                                              (const float*)Dinv, dsc, om, omr, b, xi, xo);
     else
       k_smooth_lp<NP, float, true><<<grid, kThreads, 0, s>>>(nb, rp, col, (const float*)val, sc,
-                                                             (const float*)Dinv, dsc, om, b, xi, xo);
+                                                             (const float*)Dinv, dsc, om, omr, b, xi, xo);
   }
   // val: the FP32 operator copy
   static void resid_rt(int grid, cudaStream_t s, int64_t nbf, const int64_t* rp, const int32_t* col,
@@ -218,8 +220,9 @@ struct OpsLPT {
     k_prolong_lp<NP, TS><<<grid, kThreads, 0, s>>>(nbf, agg, (const TS*)R, rsc, zc, xi, xo);
   }
   static void gather_smooth0(int grid, cudaStream_t s, int64_t nbc, const int64_t* cptr, const int32_t* ch,
-                             const float* t, const float* Dinv, const float* dsc, float om, float* bc, float* xc) {
-    k_gather_smooth0_lp<NP><<<grid, kThreads, 0, s>>>(nbc, cptr, ch, t, Dinv, dsc, om, bc, xc);
+                             const float* t, const float* Dinv, const float* dsc, float om, const float* omr,
+                             float* bc, float* xc) {
+    k_gather_smooth0_lp<NP><<<grid, kThreads, 0, s>>>(nbc, cptr, ch, t, Dinv, dsc, om, omr, bc, xc);
   }
   static OpsLP get() {
     return OpsLP{make, spmv_f, spmv_d, smooth, resid_rt, gather, prolong, resid32, gather_smooth0, sizeof(TS)};
@@ -268,6 +271,12 @@ struct Level {
   double *b = nullptr, *x = nullptr, *t = nullptr, *r = nullptr, *dz = nullptr;
   double* s = nullptr;       // restriction scratch R_f^T res_f (levels above the coarsest)
   double omega = 0.0, lmax = 0.0;
+  // batches: damping per block row (one value per problem), problem offsets on this level
+  double* omr = nullptr;
+  float* omr_f = nullptr;
+  std::vector<int64_t> hseg;   // block offsets of the problems (nprob + 1)
+  int64_t* sdof = nullptr;     // DOF offsets of the problems (device, nprob + 1)
+  std::vector<double> lmax_p, omega_p;
 };
 
 }  // namespace
@@ -278,8 +287,26 @@ struct xdg_hier {
   bool own_stream = false;
   Ops ops{};
   std::vector<Level> L;
-  double* Minv = nullptr;
-  int64_t nc = 0;
+  double* Minv = nullptr;       // dense inverses of the coarsest level, one per problem
+  int64_t nc = 0;               // DOF of the coarsest level (all problems)
+  int nprob = 1;                // problems in the hierarchy (a batch when > 1)
+  int64_t* cs_doff = nullptr;   // coarsest level: DOF offset of every problem (nprob + 1)
+  int64_t* cs_moff = nullptr;   // offset of every problem's inverse in Minv
+  BatchScal B{};                // per-problem Krylov scalars (batches)
+  double* h_bsc = nullptr;      // pinned host scalars (nprob; setup)
+  double* spart = nullptr;      // slice sums of the per-problem setup reductions (nprob * 64)
+  // level-1 chunks that never straddle two problems: cb boundaries (nchunk + 1), cseg problem
+  // of every chunk, cfirst first chunk of every problem (nprob + 1), cpart 2 partial sums each
+  int nchunk = 0;
+  int64_t* cb = nullptr;
+  int* cseg = nullptr;
+  int* cfirst = nullptr;
+  double* cpart = nullptr;
+  int64_t* ioff = nullptr;      // offset of every problem in the caller's concatenated vectors
+  int* gidx = nullptr;          // index of every problem in the caller's list
+  cudaStream_t body_stream = nullptr;
+  int64_t bnodes_fixed[3] = {0, 0, 0};  // kernel nodes of a recorded batched solve outside
+  int64_t bnodes_body[3] = {0, 0, 0};   // its loop, and inside one loop iteration
   double *s_b = nullptr, *s_x = nullptr, *s_r = nullptr, *s_z = nullptr, *s_p = nullptr, *s_q = nullptr;
   double* partial = nullptr;
   double* dsc = nullptr;       // device scalars for setup reductions
@@ -316,6 +343,8 @@ struct xdg_hier {
       if (g_cyc_lp[p]) cudaGraphExecDestroy(g_cyc_lp[p]);
     }
     for (void* p : allocs) cudaFree(p);
+    if (h_bsc) cudaFreeHost(h_bsc);
+    if (body_stream) cudaStreamDestroy(body_stream);
     if (hS) cudaFreeHost(hS);
     if (hsc) cudaFreeHost(hsc);
     if (own_stream && stream) cudaStreamDestroy(stream);
@@ -355,7 +384,7 @@ struct xdg_hier {
   void smooth(int l, const double* b, const double* xi, double* xo) {
     ++launches;
     Level& V = L[l];
-    ops.smooth(grid(V.nb), stream, V.nb, V.rp, V.col, V.val, V.Dinv, V.omega, b, xi, xo);
+    ops.smooth(grid(V.nb), stream, V.nb, V.rp, V.col, V.val, V.Dinv, V.omega, V.omr, b, xi, xo);
   }
   void restrict_(int l, const double* b, const double* x, double* rc) {
     launches += 2;
@@ -372,7 +401,7 @@ struct xdg_hier {
   void coarse(const double* r, double* z) {
     ++launches;
     int64_t blocks = (nc * 32 + kThreads - 1) / kThreads;
-    k_gemv<<<(unsigned)blocks, kThreads, 0, stream>>>(nc, Minv, r, z);
+    k_gemv_seg<double><<<(unsigned)blocks, kThreads, 0, stream>>>(nc, nprob, cs_doff, cs_moff, Minv, r, z);
   }
   void dot(int64_t n, const double* a, const double* b, double* out) {
     launches += 2;
@@ -401,7 +430,7 @@ struct xdg_hier {
     // restriction's gather also does the coarse level's first sweep
     if (l + 2 < nlev) {
       ops.resid_rt(grid(V.nb), stream, V.nb, V.rp, V.col, V.val, V.R, b, cur, V.s);
-      ops.gather_smooth0(grid(C.nb), stream, C.nb, V.cptr, V.ch, V.s, C.Dinv, C.omega, C.b, C.x);
+      ops.gather_smooth0(grid(C.nb), stream, C.nb, V.cptr, V.ch, V.s, C.Dinv, C.omega, C.omr, C.b, C.x);
       launches += 2;
       cycle(l + 1, C.b, C.x, true);
     } else {
@@ -453,7 +482,7 @@ struct xdg_hier {
     if (l == nlev - 1) {
       ++launches;
       int64_t blocks = (nc * 32 + kThreads - 1) / kThreads;
-      k_gemv_coarse_lp<<<(unsigned)blocks, kThreads, 0, stream>>>(nc, Minv, b, x);
+      k_gemv_seg<float><<<(unsigned)blocks, kThreads, 0, stream>>>(nc, nprob, cs_doff, cs_moff, Minv, b, x);
       return;
     }
     Level& V = L[l];
@@ -464,18 +493,19 @@ struct xdg_hier {
     float* cur = x;
     float* oth = W.t;
     if (!pre0) {
-      o.smooth(grid(V.nb), stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, b, nullptr, cur);
+      o.smooth(grid(V.nb), stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, V.omr_f, b, nullptr, cur);
       ++launches;
     }
     for (int s = 1; s < nu; ++s) {
-      o.smooth(grid(V.nb), stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, b, cur, oth);
+      o.smooth(grid(V.nb), stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, V.omr_f, b, cur, oth);
       ++launches;
       std::swap(cur, oth);
     }
     o.resid_rt(grid(V.nb), stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.R, W.rsc, b, cur, W.s);
     launches += 2;
     if (l + 2 < nlev) {
-      o.gather_smooth0(grid(C.nb), stream, C.nb, V.cptr, V.ch, W.s, (const float*)WC.Dinv, WC.dsc, (float)C.omega, WC.b, WC.x);
+      o.gather_smooth0(grid(C.nb), stream, C.nb, V.cptr, V.ch, W.s, (const float*)WC.Dinv, WC.dsc, (float)C.omega,
+                       C.omr_f, WC.b, WC.x);
       cycle_lp(p, l + 1, WC.b, WC.x, true);
     } else {
       o.gather(vgrid(C.nb * Np), stream, C.nb, V.cptr, V.ch, W.s, WC.b);
@@ -495,7 +525,7 @@ struct xdg_hier {
     cur = after;
     oth = (cur == x) ? W.t : x;
     for (int s = 0; s < nu; ++s) {
-      o.smooth(grid(V.nb), stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, b, cur, oth);
+      o.smooth(grid(V.nb), stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, V.omr_f, b, cur, oth);
       ++launches;
       std::swap(cur, oth);
     }
@@ -578,7 +608,25 @@ struct xdg_hier {
     return XDG_OK;
   }
 
-  int lanczos(int l, int m, double* lam);
+  // out[s] = (x, y) restricted to problem s on level l (fixed-order slice sums)
+  void seg_dot(int l, const double* x, const double* y, double* out) {
+    const int spl = std::max(1, std::min(64, 4 * sms / nprob));
+    k_seg_dot<<<dim3((unsigned)spl, (unsigned)nprob), kThreads, 0, stream>>>(nprob, L[l].sdof, x, y, spart);
+    k_seg_sum<<<(nprob + 255) / 256, 256, 0, stream>>>(nprob, spl, spart, out);
+  }
+  int sgrid() const { return (nprob + 255) / 256; }
+  // z = B r with the FP64 cycle (prec = F64) or the low-precision one
+  void precond(int prec, const double* r, double* z) {
+    if (prec == XDG_PREC_F64) cycle(0, r, z);
+    else cycle_lp_d(prec, r, z);
+  }
+
+  std::vector<std::vector<int64_t>> seg_in;  // problem block offsets per level (set before build)
+  int lanczos(int l, int m);
+  int read_scalars(const double* d, int n, double* h);
+  int build_batch(int n, const xdg_problem* probs, const xdg_hier_opts* o);
+  void batch_iteration(int prec, const BatchCtl* ctl, cudaGraphConditionalHandle cond);
+  int record_batch(int prec, const BatchCtl* ctl, double* res, int gslot);
   int build(const xdg_problem* p, const xdg_hier_opts* o);
   int solve_dev(const double* b, double* x, const xdg_solve_opts* o, xdg_solve_info* info);
 };
@@ -616,45 +664,75 @@ double tridiag_lambda_max(const std::vector<double>& a, const std::vector<double
 
 }  // namespace
 
-// m-step Lanczos for the pencil (M_l, D_l) in the D inner product
-int xdg_hier::lanczos(int l, int m, double* lam) {
+int xdg_hier::read_scalars(const double* d, int n, double* h) {
+  CK(cudaMemcpyAsync(h_bsc, d, n * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  CK(cudaStreamSynchronize(stream));
+  std::copy(h_bsc, h_bsc + n, h);
+  return XDG_OK;
+}
+
+// m-step Lanczos for the pencil (M_l, D_l) in the D inner product, run for every problem of
+// the level at once (segment-wise scalars); the start vector restarts the counter-based hash
+// at every problem. Result: V.lmax_p.
+int xdg_hier::lanczos(int l, int m) {
   Level& V = L[l];
   const int64_t n = V.nb * Np;
+  const int P = nprob;
   double *q = V.b, *qp = V.x, *u = V.t, *w = V.r, *Dw = V.dz;
   const int vg = vgrid(n);
-  k_hash_vector<<<vg, kThreads, 0, stream>>>(n, q);
+  double* dv = B.alpha;  // device scratch of nprob doubles (free during setup)
+  k_hash_vector_seg<<<vg, kThreads, 0, stream>>>(n, P, V.sdof, q);
   CK(cudaMemsetAsync(qp, 0, n * sizeof(double), stream));
   ops.diagmul(grid(V.nb), stream, V.nb, V.diag, V.val, q, Dw);
-  dot(n, q, Dw, dsc);
-  double nrm2;
-  TRY(read_scalar(dsc, &nrm2));
-  CKL();
-  k_scale<<<vg, kThreads, 0, stream>>>(n, 1.0 / std::sqrt(nrm2), q);
-  std::vector<double> al, be;
-  double bprev = 0.0;
+  seg_dot(l, q, Dw, dv);
+  std::vector<double> nrm2(P), fac(P), a(P), b2(P), bprev(P, 0.0), coef(P);
+  TRY(read_scalars(dv, P, nrm2.data()));
+  for (int s = 0; s < P; ++s) fac[s] = 1.0 / std::sqrt(nrm2[s]);
+  auto put = [&](const std::vector<double>& h) -> int {
+    std::copy(h.begin(), h.end(), h_bsc);
+    CK(cudaMemcpyAsync(dv, h_bsc, P * sizeof(double), cudaMemcpyHostToDevice, stream));
+    CK(cudaStreamSynchronize(stream));  // h_bsc is reused by the next transfer
+    return XDG_OK;
+  };
+  TRY(put(fac));
+  k_seg_scale<<<vg, kThreads, 0, stream>>>(n, P, V.sdof, dv, q);
+  std::vector<std::vector<double>> al(P), be(P);
+  std::vector<char> live(P, 1);
   for (int j = 0; j < m; ++j) {
     spmv(l, q, nullptr, u, 0);
-    dot(n, q, u, dsc);
-    double a;
-    TRY(read_scalar(dsc, &a));
-    al.push_back(a);
+    seg_dot(l, q, u, dv);
+    TRY(read_scalars(dv, P, a.data()));
+    for (int s = 0; s < P; ++s)
+      if (live[s]) al[s].push_back(a[s]);
     ops.bjsolve(grid(V.nb), stream, V.nb, V.Dinv, u, w);
-    k_axpy<<<vg, kThreads, 0, stream>>>(n, -a, q, w);
-    k_axpy<<<vg, kThreads, 0, stream>>>(n, -bprev, qp, w);
+    for (int s = 0; s < P; ++s) coef[s] = -a[s];
+    TRY(put(coef));
+    k_seg_axpy<<<vg, kThreads, 0, stream>>>(n, P, V.sdof, dv, q, w);
+    for (int s = 0; s < P; ++s) coef[s] = -bprev[s];
+    TRY(put(coef));
+    k_seg_axpy<<<vg, kThreads, 0, stream>>>(n, P, V.sdof, dv, qp, w);
     ops.diagmul(grid(V.nb), stream, V.nb, V.diag, V.val, w, Dw);
-    dot(n, w, Dw, dsc);
-    double b2;
-    TRY(read_scalar(dsc, &b2));
+    seg_dot(l, w, Dw, dv);
+    TRY(read_scalars(dv, P, b2.data()));
     CKL();
-    double bj = std::sqrt(std::max(b2, 0.0));
-    be.push_back(bj);
-    if (!(bj > 1e-300)) break;
+    bool any = false;
+    for (int s = 0; s < P; ++s) {
+      double bj = std::sqrt(std::max(b2[s], 0.0));
+      if (live[s]) be[s].push_back(bj);
+      if (!(bj > 1e-300)) live[s] = 0;
+      fac[s] = live[s] ? 1.0 / bj : 0.0;
+      bprev[s] = live[s] ? bj : 0.0;
+      any = any || live[s];
+    }
+    if (!any) break;
     k_copy<<<vg, kThreads, 0, stream>>>(n, q, qp);
-    k_axpby<<<vg, kThreads, 0, stream>>>(n, 1.0 / bj, w, 0.0, q);
-    bprev = bj;
+    k_copy<<<vg, kThreads, 0, stream>>>(n, w, q);
+    TRY(put(fac));
+    k_seg_scale<<<vg, kThreads, 0, stream>>>(n, P, V.sdof, dv, q);
   }
   CKL();
-  *lam = tridiag_lambda_max(al, be);
+  V.lmax_p.resize(P);
+  for (int s = 0; s < P; ++s) V.lmax_p[s] = tridiag_lambda_max(al[s], be[s]);
   return XDG_OK;
 }
 
@@ -795,10 +873,23 @@ int xdg_hier::build(const xdg_problem* p, const xdg_hier_opts* o) {
     }
   }
   nc = L[nlev - 1].nb * Np;
-  if (nc > 4096) {
-    set_err("coarsest level has %lld DOF; at most 4096 are supported", (long long)nc);
-    return XDG_EINVAL;
+  // problem segments per level (a single problem is one segment)
+  if ((int)seg_in.size() != nlev) {
+    seg_in.assign(nlev, std::vector<int64_t>());
+    for (int l = 0; l < nlev; ++l) seg_in[l] = {0, L[l].nb};
   }
+  nprob = (int)seg_in[0].size() - 1;
+  std::vector<int64_t> h_csd(nprob + 1, 0), h_csm(nprob + 1, 0);
+  for (int s = 0; s < nprob; ++s) {
+    const int64_t ns = (seg_in[nlev - 1][s + 1] - seg_in[nlev - 1][s]) * Np;
+    if (ns > 4096 || ns <= 0) {
+      set_err("problem %d: coarsest level has %lld DOF; 1..4096 are supported", s, (long long)ns);
+      return XDG_EINVAL;
+    }
+    h_csd[s + 1] = h_csd[s] + ns;
+    h_csm[s + 1] = h_csm[s] + ns * ns;
+  }
+  const int64_t minv_len = h_csm[nprob];
   // ------------------------------------------------------------------ device memory
   if (!stream) {
     CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
@@ -845,7 +936,63 @@ int xdg_hier::build(const xdg_problem* p, const xdg_hier_opts* o) {
   TRY(alloc(&partial, kRedBlocks));
   TRY(alloc(&dsc, 8));
   TRY(alloc(&S, 1));
-  TRY(alloc(&Minv, nc * nc));
+  TRY(alloc(&Minv, minv_len));
+  TRY(alloc(&cs_doff, nprob + 1));
+  TRY(alloc(&cs_moff, nprob + 1));
+  CK(cudaMemcpyAsync(cs_doff, h_csd.data(), (nprob + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(cs_moff, h_csm.data(), (nprob + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+  for (int l = 0; l < nlev; ++l) {
+    Level& V = L[l];
+    V.hseg = seg_in[l];
+    std::vector<int64_t> d(nprob + 1);
+    for (int s = 0; s <= nprob; ++s) d[s] = V.hseg[s] * Np;
+    TRY(alloc(&V.sdof, nprob + 1));
+    CK(cudaMemcpyAsync(V.sdof, d.data(), (nprob + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+  }
+  {
+    // per-problem Krylov scalars and the level-1 chunks of the batched reductions
+    double** f[] = {&B.rz, &B.rr, &B.bb, &B.pq, &B.zq, &B.alpha, &B.beta};
+    for (double** q : f) TRY(alloc(q, nprob));
+    TRY(alloc(&B.active, nprob));
+    TRY(alloc(&B.bad, nprob));
+    TRY(alloc(&B.iters, nprob));
+    TRY(alloc(&B.it, 1));
+    TRY(alloc(&spart, (size_t)nprob * 64));
+    CK(cudaMallocHost(&h_bsc, (nprob + 1) * sizeof(double)));
+    const int64_t target = std::max<int64_t>(1, n1 / (4 * (int64_t)sms));
+    const int64_t ch = std::min<int64_t>(65536, std::max<int64_t>(2048, (target + 1023) / 1024 * 1024));
+    std::vector<int64_t> hcb(1, 0);
+    std::vector<int> hcs, hcf(1, 0);
+    for (int s = 0; s < nprob; ++s) {
+      const int64_t lo = seg_in[0][s] * Np, len = (seg_in[0][s + 1] - seg_in[0][s]) * Np;
+      const int64_t m = std::max<int64_t>(1, (len + ch - 1) / ch);
+      for (int64_t j = 1; j <= m; ++j) {
+        hcb.push_back(lo + len * j / m);
+        hcs.push_back(s);
+      }
+      hcf.push_back((int)hcs.size());
+    }
+    nchunk = (int)hcs.size();
+    TRY(alloc(&cb, nchunk + 1));
+    TRY(alloc(&cseg, nchunk));
+    TRY(alloc(&cfirst, nprob + 1));
+    TRY(alloc(&cpart, 2 * (size_t)nchunk));
+    CK(cudaMemcpyAsync(cb, hcb.data(), (nchunk + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(cseg, hcs.data(), nchunk * sizeof(int), cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(cfirst, hcf.data(), (nprob + 1) * sizeof(int), cudaMemcpyHostToDevice, stream));
+    // caller layout: by default the problems in hierarchy order
+    std::vector<int64_t> hio(nprob);
+    std::vector<int> hgi(nprob);
+    for (int s = 0; s < nprob; ++s) {
+      hio[s] = seg_in[0][s] * Np;
+      hgi[s] = s;
+    }
+    TRY(alloc(&ioff, nprob));
+    TRY(alloc(&gidx, nprob));
+    CK(cudaMemcpyAsync(ioff, hio.data(), nprob * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(gidx, hgi.data(), nprob * sizeof(int), cudaMemcpyHostToDevice, stream));
+    TRY(sync());
+  }
   CK(cudaMallocHost(&hS, sizeof(PcgScal)));
   CK(cudaMallocHost(&hsc, 8 * sizeof(double)));
   int* derr = nullptr;
@@ -882,22 +1029,55 @@ int xdg_hier::build(const xdg_problem* p, const xdg_hier_opts* o) {
   }
   for (int l = 0; l + 1 < nlev; ++l) {
     Level& V = L[l];
-    TRY(lanczos(l, lsteps, &V.lmax));
-    V.omega = (o && o->omega > 0.0) ? o->omega : 4.0 / (3.0 * V.lmax);
+    TRY(lanczos(l, lsteps));
+    V.omega_p.resize(nprob);
+    for (int s = 0; s < nprob; ++s)
+      V.omega_p[s] = (o && o->omega > 0.0) ? o->omega : 4.0 / (3.0 * V.lmax_p[s]);
+    V.lmax = V.lmax_p[0];
+    V.omega = V.omega_p[0];
+    if (nprob > 1) {  // damping per block row
+      std::vector<double> om(V.nb);
+      std::vector<float> omf(V.nb);
+      for (int s = 0; s < nprob; ++s)
+        for (int64_t i = V.hseg[s]; i < V.hseg[s + 1]; ++i) {
+          om[i] = V.omega_p[s];
+          omf[i] = (float)V.omega_p[s];
+        }
+      TRY(alloc(&V.omr, V.nb));
+      TRY(alloc(&V.omr_f, V.nb));
+      CK(cudaMemcpyAsync(V.omr, om.data(), V.nb * sizeof(double), cudaMemcpyHostToDevice, stream));
+      CK(cudaMemcpyAsync(V.omr_f, omf.data(), V.nb * sizeof(float), cudaMemcpyHostToDevice, stream));
+      TRY(sync());
+    }
   }
   {
-    // coarsest level: dense Cholesky and explicit inverse
+    // coarsest level: dense Cholesky and explicit inverse of every problem's matrix
     Level& C = L[nlev - 1];
     double *A = nullptr, *X = nullptr;
-    TRY(alloc(&A, nc * nc));
-    TRY(alloc(&X, nc * nc));
-    CK(cudaMemsetAsync(A, 0, nc * nc * sizeof(double), stream));
-    k_bsr_to_dense<<<(unsigned)C.nb, 128, 0, stream>>>(C.nb, Np, C.rp, C.col, C.val, nc, A);
+    int64_t* cs_blk = nullptr;
+    TRY(alloc(&A, minv_len));
+    TRY(alloc(&X, minv_len));
+    TRY(alloc(&cs_blk, nprob + 1));
+    CK(cudaMemcpyAsync(cs_blk, C.hseg.data(), (nprob + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+    CK(cudaMemsetAsync(A, 0, minv_len * sizeof(double), stream));
+    k_bsr_to_dense_seg<<<(unsigned)C.nb, 128, 0, stream>>>(C.nb, Np, nprob, cs_blk, cs_moff, C.rp, C.col, C.val, A);
     CK(cudaMemsetAsync(derr, 0, sizeof(int), stream));
-    k_dense_chol<<<1, 1024, 0, stream>>>(nc, A, derr);
-    k_tri_inverse<<<(unsigned)((nc + 127) / 128), 128, 0, stream>>>(nc, A, X);
-    dim3 tb(16, 16), tg((unsigned)((nc + 15) / 16), (unsigned)((nc + 15) / 16));
-    k_xtx<<<tg, tb, 0, stream>>>(nc, X, Minv);
+    int64_t* cs_n = nullptr;
+    TRY(alloc(&cs_n, nprob));
+    int64_t nmax = 0;
+    {
+      std::vector<int64_t> hn(nprob);
+      for (int s = 0; s < nprob; ++s) {
+        hn[s] = h_csd[s + 1] - h_csd[s];
+        nmax = std::max(nmax, hn[s]);
+      }
+      CK(cudaMemcpyAsync(cs_n, hn.data(), nprob * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+    }
+    k_dense_chol_seg<<<(unsigned)nprob, 1024, 0, stream>>>(nprob, cs_n, cs_moff, A, derr);
+    k_tri_inverse_seg<<<dim3((unsigned)((nmax + 127) / 128), (unsigned)nprob), 128, 0, stream>>>(nprob, cs_n, cs_moff,
+                                                                                                A, X);
+    dim3 tb(16, 16), tg((unsigned)((nmax + 15) / 16), (unsigned)((nmax + 15) / 16), (unsigned)nprob);
+    k_xtx_seg<<<tg, tb, 0, stream>>>(nprob, cs_n, cs_moff, X, Minv);
     CKL();
     int h_err = 0;
     CK(cudaMemcpyAsync(&h_err, derr, sizeof(int), cudaMemcpyDeviceToHost, stream));
@@ -915,7 +1095,7 @@ int xdg_hier::build(const xdg_problem* p, const xdg_hier_opts* o) {
         ++it;
       }
     }
-    bytes -= 2 * nc * nc * sizeof(double);
+    bytes -= 2 * minv_len * sizeof(double);
   }
   TRY(capture(&g_iter, 1, nullptr, nullptr));
   if (o && (o->low_precision & 1)) TRY(build_lp(XDG_PREC_F32));
@@ -980,6 +1160,215 @@ int xdg_hier::build_lp(int p) {
   TRY(sync());
   has_lp[p] = true;
   TRY(capture(&g_iter_lp[p], 3, nullptr, nullptr, p));
+  return XDG_OK;
+}
+
+// Host validation of problem s of a batch against its own sizes (no CUDA call).
+static int validate_problem(const xdg_problem& q, int s) {
+  const int nl = q.n_levels;
+  if (!q.nb || !q.row_ptr || !q.col || !q.val || (nl > 1 && (!q.agg || !q.R))) {
+    set_err("problem %d: null arrays", s);
+    return XDG_EINVAL;
+  }
+  if (nl < 1 || nl > XDG_MAX_LEVELS) {
+    set_err("problem %d: n_levels = %d outside 1..%d", s, nl, XDG_MAX_LEVELS);
+    return XDG_EINVAL;
+  }
+  for (int l = 0; l < nl; ++l)
+    if (q.nb[l] <= 0 || q.nb[l] > INT32_MAX) {
+      set_err("problem %d: level %d: nb = %lld", s, l + 1, (long long)q.nb[l]);
+      return XDG_EINVAL;
+    }
+  if (q.row_ptr[0] != 0) {
+    set_err("problem %d: row_ptr[0] = %lld", s, (long long)q.row_ptr[0]);
+    return XDG_EINVAL;
+  }
+  for (int64_t i = 0; i < q.nb[0]; ++i) {
+    if (q.row_ptr[i + 1] < q.row_ptr[i]) {
+      set_err("problem %d: row_ptr decreases at row %lld", s, (long long)i);
+      return XDG_EINVAL;
+    }
+    bool diag = false;
+    for (int64_t z = q.row_ptr[i]; z < q.row_ptr[i + 1]; ++z) {
+      const int32_t c = q.col[z];
+      if (c < 0 || c >= q.nb[0] || (z > q.row_ptr[i] && c <= q.col[z - 1])) {
+        set_err("problem %d: col[%lld] = %d out of range or not increasing in row %lld", s, (long long)z, c,
+                (long long)i);
+        return XDG_EINVAL;
+      }
+      diag = diag || c == i;
+    }
+    if (!diag) {
+      set_err("problem %d: row %lld has no diagonal block", s, (long long)i);
+      return XDG_EINVAL;
+    }
+  }
+  for (int l = 0; l + 1 < nl; ++l) {
+    if (!q.agg[l] || !q.R[l]) {
+      set_err("problem %d: level %d: null transfer arrays", s, l + 1);
+      return XDG_EINVAL;
+    }
+    std::vector<char> hit(q.nb[l + 1], 0);
+    for (int64_t f = 0; f < q.nb[l]; ++f) {
+      const int32_t a = q.agg[l][f];
+      if (a < 0 || a >= q.nb[l + 1]) {
+        set_err("problem %d: level %d: agg[%lld] = %d out of range", s, l + 1, (long long)f, a);
+        return XDG_EINVAL;
+      }
+      hit[a] = 1;
+    }
+    for (int64_t c = 0; c < q.nb[l + 1]; ++c)
+      if (!hit[c]) {
+        set_err("problem %d: level %d: coarse block %lld has no child", s, l + 2, (long long)c);
+        return XDG_EINVAL;
+      }
+  }
+  return XDG_OK;
+}
+
+// Union of n problems with the same block size and depth: level operators, aggregation maps
+// and transfers concatenated block-diagonally (problem s's blocks follow problem s-1's on every
+// level). The problems must have passed validate_problem, so that the union couples no two
+// problems.
+int xdg_hier::build_batch(int n, const xdg_problem* probs, const xdg_hier_opts* o) {
+  if (n < 1 || n > 65535 || !probs) {
+    set_err("batch of %d problems (1..65535 per block size)", n);
+    return XDG_EINVAL;
+  }
+  const int np = probs[0].Np, nl = probs[0].n_levels;
+  const int64_t np2 = (int64_t)np * np;
+  seg_in.assign(nl, std::vector<int64_t>(1, 0));
+  for (int s = 0; s < n; ++s) {
+    if (probs[s].Np != np || probs[s].n_levels != nl) {
+      set_err("problem %d: Np = %d, n_levels = %d differ from the group's %d, %d", s, probs[s].Np,
+              probs[s].n_levels, np, nl);
+      return XDG_EINVAL;
+    }
+    for (int l = 0; l < nl; ++l) seg_in[l].push_back(seg_in[l].back() + probs[s].nb[l]);
+  }
+  if (seg_in[0].back() > INT32_MAX) {
+    set_err("batch exceeds 2^31 blocks on level 1");
+    return XDG_EINVAL;
+  }
+  // concatenation
+  std::vector<int64_t> nb(nl), rp(1, 0);
+  for (int l = 0; l < nl; ++l) nb[l] = seg_in[l][n];
+  int64_t nnz = 0;
+  for (int s = 0; s < n; ++s) nnz += probs[s].row_ptr[probs[s].nb[0]];
+  std::vector<int32_t> col;
+  std::vector<double> val;
+  col.reserve(nnz);
+  val.reserve(nnz * np2);
+  rp.reserve(nb[0] + 1);
+  std::vector<std::vector<int32_t>> agg(std::max(nl - 1, 0));
+  std::vector<std::vector<double>> R(std::max(nl - 1, 0));
+  for (int s = 0; s < n; ++s) {
+    const xdg_problem& q = probs[s];
+    const int64_t z0 = (int64_t)col.size(), b0 = seg_in[0][s], nz = q.row_ptr[q.nb[0]];
+    for (int64_t i = 1; i <= q.nb[0]; ++i) rp.push_back(z0 + q.row_ptr[i]);
+    for (int64_t z = 0; z < nz; ++z) col.push_back((int32_t)(b0 + q.col[z]));
+    val.insert(val.end(), q.val, q.val + nz * np2);
+    for (int l = 0; l + 1 < nl; ++l) {
+      const int64_t c0 = seg_in[l + 1][s];
+      for (int64_t f = 0; f < q.nb[l]; ++f) agg[l].push_back((int32_t)(c0 + q.agg[l][f]));
+      R[l].insert(R[l].end(), q.R[l], q.R[l] + q.nb[l] * np2);
+    }
+  }
+  std::vector<const int32_t*> aggp(std::max(nl - 1, 1), nullptr);
+  std::vector<const double*> Rp(std::max(nl - 1, 1), nullptr);
+  for (int l = 0; l + 1 < nl; ++l) {
+    aggp[l] = agg[l].data();
+    Rp[l] = R[l].data();
+  }
+  xdg_problem u{np, nl, nb.data(), rp.data(), col.data(), val.data(), aggp.data(), Rp.data()};
+  return build(&u, o);
+}
+
+// One batched CG / flexible-CG step of every problem still running (finished problems take
+// zero steps: alpha = 0). The loop condition is set by the convergence check.
+void xdg_hier::batch_iteration(int prec, const BatchCtl* ctl, cudaGraphConditionalHandle cond) {
+  const int flex = prec != XDG_PREC_F64;
+  spmv(0, s_p, nullptr, s_q, 0);
+  k_chunk_dot<1><<<nchunk, kThreads, 0, stream>>>(nchunk, cb, s_p, s_q, nullptr, nullptr, cpart);
+  k_bcg_alpha<<<sgrid(), 256, 0, stream>>>(nprob, cfirst, cpart, B);
+  k_bcg_xr<<<nchunk, kThreads, 0, stream>>>(nchunk, cb, cseg, B.alpha, s_p, s_q, s_x, s_r, cpart);
+  k_bcg_check<<<1, 1024, 0, stream>>>(nprob, cfirst, cpart, B, ctl, 1, cond, 1);
+  launches += 4;
+  precond(prec, s_r, s_z);
+  if (flex) k_chunk_dot<2><<<nchunk, kThreads, 0, stream>>>(nchunk, cb, s_r, s_z, s_z, s_q, cpart);
+  else k_chunk_dot<1><<<nchunk, kThreads, 0, stream>>>(nchunk, cb, s_r, s_z, nullptr, nullptr, cpart);
+  k_bcg_beta<<<sgrid(), 256, 0, stream>>>(nprob, nchunk, cfirst, cpart, flex, 0, B);
+  k_bcg_p<<<nchunk, kThreads, 0, stream>>>(nchunk, cb, cseg, B.beta, 0, s_z, s_p);
+  launches += 3;
+}
+
+// Records the whole batched solve into the capture running on `stream`: gather of b and x from
+// the caller's vectors, start (r = b - M x, z = B r, p = z), the iteration loop as a
+// conditional while node of the graph (its body one batch_iteration; the loop ends when no
+// problem is running or after maxit iterations), per-problem results, scatter of x.
+int xdg_hier::record_batch(int prec, const BatchCtl* ctl, double* res, int gslot) {
+  const int64_t n = L[0].nb * Np;
+  const int flex = prec != XDG_PREC_F64;
+  const int64_t l0 = launches;
+  k_batch_gather<<<vgrid(n), kThreads, 0, stream>>>(n, nprob, L[0].sdof, ioff, ctl, s_b, s_x);
+  spmv(0, s_x, s_b, s_r, 1);
+  k_chunk_dot<2><<<nchunk, kThreads, 0, stream>>>(nchunk, cb, s_r, s_r, s_b, s_b, cpart);
+  k_bcg_start<<<sgrid(), 256, 0, stream>>>(nprob, nchunk, cfirst, cpart, B);
+  launches += 3;
+  cudaStreamCaptureStatus st;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(stream, &st, nullptr, &cg, &deps, nullptr, &nd));
+  if (st != cudaStreamCaptureStatusActive) {
+    set_err("record_batch: stream is not capturing");
+    return XDG_ECUDA;
+  }
+  cudaGraphConditionalHandle cond;
+  CK(cudaGraphConditionalHandleCreate(&cond, cg, 0, cudaGraphCondAssignDefault));
+  k_bcg_check<<<1, 1024, 0, stream>>>(nprob, cfirst, nullptr, B, ctl, 0, cond, 1);
+  ++launches;
+  precond(prec, s_r, s_z);
+  k_chunk_dot<1><<<nchunk, kThreads, 0, stream>>>(nchunk, cb, s_r, s_z, nullptr, nullptr, cpart);
+  k_bcg_beta<<<sgrid(), 256, 0, stream>>>(nprob, nchunk, cfirst, cpart, flex, 1, B);
+  k_bcg_p<<<nchunk, kThreads, 0, stream>>>(nchunk, cb, cseg, B.beta, 1, s_z, s_p);
+  launches += 3;
+  CKL();
+  // the loop
+  CK(cudaStreamGetCaptureInfo(stream, &st, nullptr, &cg, &deps, nullptr, &nd));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  CK(cudaGraphAddNode(&wnode, cg, deps, nullptr, nd, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  CK(cudaStreamUpdateCaptureDependencies(stream, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+  if (!body_stream) CK(cudaStreamCreateWithFlags(&body_stream, cudaStreamNonBlocking));
+  CK(cudaStreamBeginCaptureToGraph(body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  cudaStream_t main_stream = stream;
+  stream = body_stream;
+  const int64_t lb = launches;
+  batch_iteration(prec, ctl, cond);
+  bnodes_body[prec] = launches - lb;
+  stream = main_stream;
+  cudaError_t e = cudaGetLastError();
+  cudaGraph_t bout = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(body_stream, &bout);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    set_err("record_batch: loop body: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    return XDG_ECUDA;
+  }
+  // results and scatter
+  spmv(0, s_x, s_b, s_r, 1);
+  k_chunk_dot<1><<<nchunk, kThreads, 0, stream>>>(nchunk, cb, s_r, s_r, nullptr, nullptr, cpart);
+  k_bcg_result<<<sgrid(), 256, 0, stream>>>(nprob, cfirst, cpart, gidx, B, res, gslot);
+  k_batch_scatter<<<vgrid(n), kThreads, 0, stream>>>(n, nprob, L[0].sdof, ioff, ctl, s_x);
+  launches += 3;
+  CKL();
+  bnodes_fixed[prec] = launches - l0 - bnodes_body[prec];
+  launches = l0;
   return XDG_OK;
 }
 
@@ -1054,6 +1443,149 @@ int xdg_hier::solve_dev(const double* b, double* x, const xdg_solve_opts* o, xdg
                       std::sqrt(rr) / bn);
   return status;
 }
+
+// ============================================================================================
+// Batches: problems grouped by (Np, depth); every group is one block-diagonal union hierarchy.
+// One solve is one CUDA graph: the groups' recorded solves run as parallel branches, each with
+// its iteration loop as a conditional node, so that the whole batch is a single launch.
+struct xdg_batch {
+  int n = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<std::unique_ptr<xdg_hier>> grp;
+  std::vector<std::vector<int>> members;  // caller indices of every group, in hierarchy order
+  std::vector<int64_t> off;               // DOF offset of every problem in the caller's vectors
+  BatchCtl* ctl = nullptr;                // device controls
+  BatchCtl* hctl = nullptr;               // pinned host mirror
+  double* res = nullptr;                  // device results (3 n + groups)
+  double* hres = nullptr;                 // pinned host mirror
+  double *stage_b = nullptr, *stage_x = nullptr;  // device staging of the host-vector solve
+  cudaGraphExec_t gx[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr;
+  std::vector<cudaEvent_t> ev_join;
+  std::vector<cudaStream_t> gstream;      // capture branch of every group
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  double setup_ms = 0.0;
+
+  ~xdg_batch() {
+    if (stream) cudaStreamSynchronize(stream);
+    for (auto& g : gx)
+      if (g) cudaGraphExecDestroy(g);
+    grp.clear();
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    for (auto e : ev_join) cudaEventDestroy(e);
+    for (auto q : gstream) cudaStreamDestroy(q);
+    for (void* p : allocs) cudaFree(p);
+    if (hctl) cudaFreeHost(hctl);
+    if (hres) cudaFreeHost(hres);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+  }
+  template <class T>
+  int alloc(T** p, size_t cnt) {
+    void* q = nullptr;
+    const size_t nbytes = std::max<size_t>(cnt, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&q, nbytes);
+    if (e != cudaSuccess) {
+      set_err("cudaMalloc(%zu bytes): %s", nbytes, cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? XDG_ENOMEM : XDG_ECUDA;
+    }
+    allocs.push_back(q);
+    bytes += nbytes;
+    *p = static_cast<T*>(q);
+    return XDG_OK;
+  }
+
+  // record the batched solve of precision prec (all groups) into gx[prec]
+  int capture(int prec) {
+    CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+    int rc = XDG_OK;
+    cudaError_t e = cudaEventRecord(ev_fork, stream);
+    for (size_t g = 0; g < grp.size() && rc == XDG_OK && e == cudaSuccess; ++g) {
+      xdg_hier& H = *grp[g];
+      e = cudaStreamWaitEvent(gstream[g], ev_fork, 0);
+      if (e != cudaSuccess) break;
+      cudaStream_t keep = H.stream;
+      H.stream = gstream[g];
+      rc = H.record_batch(prec, ctl, res, 3 * n + (int)g);
+      H.stream = keep;
+      if (rc) break;
+      e = cudaEventRecord(ev_join[g], gstream[g]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, ev_join[g], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(stream, &graph);
+    if (rc == XDG_OK && (e != cudaSuccess || e2 != cudaSuccess)) {
+      set_err("batch capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+      rc = XDG_ECUDA;
+    }
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return rc;
+    }
+    if (gx[prec]) cudaGraphExecDestroy(gx[prec]);
+    gx[prec] = nullptr;
+    e = cudaGraphInstantiate(&gx[prec], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      set_err("batch graph instantiate: %s", cudaGetErrorString(e));
+      return XDG_ECUDA;
+    }
+    return XDG_OK;
+  }
+
+  int solve(const double* b, double* x, const xdg_solve_opts* o, xdg_solve_info* info, xdg_batch_result* out) {
+    auto t0 = clk::now();
+    const int prec = o ? o->precision : XDG_PREC_F64;
+    if (prec < 0 || prec > 2) {
+      set_err("precision %d", prec);
+      return XDG_EINVAL;
+    }
+    for (auto& g : grp)
+      if (prec != XDG_PREC_F64 && !g->has_lp[prec]) {
+        set_err("precision %d requested but the batch holds no such copy (xdg_hier_opts.low_precision)", prec);
+        return XDG_EINVAL;
+      }
+    if (!gx[prec]) TRY(capture(prec));
+    const double tol = o ? o->tol : 1e-10;
+    hctl->b = b;
+    hctl->x = x;
+    hctl->tol2 = tol * tol;
+    hctl->maxit = o && o->maxit > 0 ? o->maxit : 1000;
+    CK(cudaMemcpyAsync(ctl, hctl, sizeof(BatchCtl), cudaMemcpyHostToDevice, stream));
+    CK(cudaGraphLaunch(gx[prec], stream));
+    CK(cudaMemcpyAsync(hres, res, (3 * (size_t)n + grp.size()) * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    int worst = XDG_OK, itmax = 0;
+    double rmax = 0.0;
+    int64_t nodes = 0;
+    for (int i = 0; i < n; ++i) {
+      const int it = (int)hres[3 * i], st = (int)hres[3 * i + 2];
+      const double rr = hres[3 * i + 1];
+      if (out) {
+        out[i].iterations = it;
+        out[i].relres = rr;
+        out[i].status = st;
+      }
+      itmax = std::max(itmax, it);
+      rmax = std::max(rmax, rr);
+      if (st == XDG_EBREAKDOWN || (st == XDG_ENOTCONV && worst == XDG_OK)) worst = st;
+    }
+    for (size_t g = 0; g < grp.size(); ++g)
+      nodes += grp[g]->bnodes_fixed[prec] + (int64_t)hres[3 * n + g] * grp[g]->bnodes_body[prec];
+    if (info) {
+      info->iterations = itmax;
+      info->outer = 1;
+      info->relres = rmax;
+      info->ms = ms_since(t0);
+      info->status = worst;
+      info->launches = nodes;
+    }
+    if (worst) set_err("batched solve: %s (largest relres %.3e)", xdg_strerror(worst), rmax);
+    return worst;
+  }
+};
 
 // ============================================================================================
 extern "C" {
@@ -1254,6 +1786,140 @@ int xdg_solve_host(xdg_hier_t h, const double* b_host, double* x_host, const xdg
   if (rc != XDG_OK && rc != XDG_ENOTCONV && rc != XDG_ETIMEOUT && rc != XDG_EBREAKDOWN) return rc;
   CK(cudaMemcpyAsync(x_host, dx, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if (info) info->ms = ms_since(t0);
+  return rc;
+}
+
+int xdg_create_batch(int n, const xdg_problem* probs, const xdg_hier_opts* o, void* stream, xdg_batch_t* out) {
+  if (!out || !probs || n < 1) {
+    set_err("xdg_create_batch: bad arguments (n = %d)", n);
+    return XDG_EINVAL;
+  }
+  *out = nullptr;
+  auto t0 = clk::now();
+  for (int i = 0; i < n; ++i) TRY(validate_problem(probs[i], i));  // host only, before any CUDA call
+  std::unique_ptr<xdg_batch> bt(new xdg_batch());
+  bt->n = n;
+  bt->stream = static_cast<cudaStream_t>(stream);
+  if (!bt->stream) {
+    CK(cudaStreamCreateWithFlags(&bt->stream, cudaStreamNonBlocking));
+    bt->own_stream = true;
+  }
+  // groups by (Np, depth), in order of first appearance
+  std::vector<std::pair<int, int>> key;
+  std::vector<int> gof(n);
+  bt->off.assign(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    std::pair<int, int> k{probs[i].Np, probs[i].n_levels};
+    int g = (int)(std::find(key.begin(), key.end(), k) - key.begin());
+    if (g == (int)key.size()) {
+      key.push_back(k);
+      bt->members.emplace_back();
+    }
+    gof[i] = g;
+    bt->members[g].push_back(i);
+    bt->off[i + 1] = bt->off[i] + probs[i].nb[0] * probs[i].Np;
+  }
+  for (size_t g = 0; g < key.size(); ++g) {
+    std::vector<xdg_problem> sub;
+    for (int i : bt->members[g]) sub.push_back(probs[i]);
+    std::unique_ptr<xdg_hier> h(new xdg_hier());
+    h->stream = bt->stream;  // the groups work on the batch's stream (capture branches aside)
+    int rc = h->build_batch((int)sub.size(), sub.data(), o);
+    if (rc) {
+      std::string m = g_last_error;
+      set_err("group of Np = %d, %d levels (problems from %d): %s", key[g].first, key[g].second,
+              bt->members[g][0], m.c_str());
+      return rc;
+    }
+    // the group's problems in the caller's vectors
+    const int P = (int)sub.size();
+    std::vector<int64_t> io(P);
+    for (int s = 0; s < P; ++s) io[s] = bt->off[bt->members[g][s]];
+    CK(cudaMemcpyAsync(h->ioff, io.data(), P * sizeof(int64_t), cudaMemcpyHostToDevice, bt->stream));
+    CK(cudaMemcpyAsync(h->gidx, bt->members[g].data(), P * sizeof(int), cudaMemcpyHostToDevice, bt->stream));
+    CK(cudaStreamSynchronize(bt->stream));
+    bt->bytes += h->bytes;
+    bt->grp.push_back(std::move(h));
+  }
+  TRY(bt->alloc(&bt->ctl, 1));
+  TRY(bt->alloc(&bt->res, 3 * (size_t)n + key.size()));
+  TRY(bt->alloc(&bt->stage_b, bt->off[n]));
+  TRY(bt->alloc(&bt->stage_x, bt->off[n]));
+  CK(cudaMallocHost(&bt->hctl, sizeof(BatchCtl)));
+  CK(cudaMallocHost(&bt->hres, (3 * (size_t)n + key.size()) * sizeof(double)));
+  CK(cudaEventCreateWithFlags(&bt->ev_fork, cudaEventDisableTiming));
+  for (size_t g = 0; g < key.size(); ++g) {
+    cudaEvent_t e;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    bt->ev_join.push_back(e);
+    cudaStream_t q;
+    CK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+    bt->gstream.push_back(q);
+  }
+  bt->setup_ms = ms_since(t0);
+  *out = bt.release();
+  return XDG_OK;
+}
+
+int xdg_batch_destroy(xdg_batch_t bt) {
+  delete bt;
+  return XDG_OK;
+}
+
+int xdg_batch_get_info(xdg_batch_t bt, xdg_batch_info* info) {
+  if (!bt || !info) {
+    set_err("null argument");
+    return XDG_EINVAL;
+  }
+  std::memset(info, 0, sizeof(*info));
+  info->n_problems = bt->n;
+  info->n_groups = (int)bt->grp.size();
+  info->total_dof = bt->off[bt->n];
+  info->device_bytes = bt->bytes;
+  info->setup_ms = bt->setup_ms;
+  for (int p = 0; p < 3; ++p)
+    for (auto& g : bt->grp) {
+      info->nodes_fixed[p] += g->bnodes_fixed[p];
+      info->nodes_per_iteration[p] += g->bnodes_body[p];
+    }
+  return XDG_OK;
+}
+
+int xdg_batch_group(xdg_batch_t bt, int g, xdg_hier_t* h, int* n_members, int* members) {
+  if (!bt || g < 0 || g >= (int)bt->grp.size()) {
+    set_err("xdg_batch_group: bad group %d", g);
+    return XDG_EINVAL;
+  }
+  if (h) *h = bt->grp[g].get();
+  if (n_members) *n_members = (int)bt->members[g].size();
+  if (members) std::copy(bt->members[g].begin(), bt->members[g].end(), members);
+  return XDG_OK;
+}
+
+int xdg_solve_batch(xdg_batch_t bt, const double* b, double* x, const xdg_solve_opts* o, xdg_solve_info* info,
+                    xdg_batch_result* results) {
+  if (!bt || !b || !x || b == x) {
+    set_err("xdg_solve_batch: bad arguments");
+    return XDG_EINVAL;
+  }
+  return bt->solve(b, x, o, info, results);
+}
+
+int xdg_solve_batch_host(xdg_batch_t bt, const double* b_host, double* x_host, const xdg_solve_opts* o,
+                         xdg_solve_info* info, xdg_batch_result* results) {
+  if (!bt || !b_host || !x_host) {
+    set_err("xdg_solve_batch_host: bad arguments");
+    return XDG_EINVAL;
+  }
+  auto t0 = clk::now();
+  const size_t nbytes = bt->off[bt->n] * sizeof(double);
+  CK(cudaMemcpyAsync(bt->stage_b, b_host, nbytes, cudaMemcpyHostToDevice, bt->stream));
+  CK(cudaMemsetAsync(bt->stage_x, 0, nbytes, bt->stream));
+  int rc = bt->solve(bt->stage_b, bt->stage_x, o, info, results);
+  if (rc != XDG_OK && rc != XDG_ENOTCONV && rc != XDG_EBREAKDOWN) return rc;
+  CK(cudaMemcpyAsync(x_host, bt->stage_x, nbytes, cudaMemcpyDeviceToHost, bt->stream));
+  CK(cudaStreamSynchronize(bt->stream));
   if (info) info->ms = ms_since(t0);
   return rc;
 }

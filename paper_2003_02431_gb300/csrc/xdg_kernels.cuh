@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(kThreads) k_smooth(int64_t nb, const int64_t* 
                                                     const int32_t* __restrict__ col,
                                                     const double* __restrict__ val,
                                                     const double* __restrict__ Dinv, double omega,
+                                                    const double* __restrict__ omr,
                                                     const double* __restrict__ b,
                                                     const double* __restrict__ xi,
                                                     double* __restrict__ xo) {
@@ -131,7 +132,8 @@ __global__ void __launch_bounds__(kThreads) k_smooth(int64_t nb, const int64_t* 
     double res = b[i * NP + r];
     if (!ZERO) res -= row_dot<NP>(__ldg(rp + i), __ldg(rp + i + 1), r, col, val, xi);
     double z = block_gemv<NP>(Dinv + i * (NP * NP), r, g * NP, mask, res);
-    xo[i * NP + r] = ZERO ? omega * z : fma(omega, z, xi[i * NP + r]);
+    const double om = omr ? __ldg(omr + i) : omega;  // per-row damping in batches
+    xo[i * NP + r] = ZERO ? om * z : fma(om, z, xi[i * NP + r]);
   }
 }
 
@@ -245,6 +247,7 @@ __global__ void __launch_bounds__(kThreads) k_gather_smooth0(int64_t nbc, const 
                                                             const int32_t* __restrict__ ch,
                                                             const double* __restrict__ t,
                                                             const double* __restrict__ Dinv, double omega,
+                                                            const double* __restrict__ omr,
                                                             double* __restrict__ bc, double* __restrict__ xc) {
   constexpr int GPW = Grp<NP>::GPW;
   const int lane = threadIdx.x & 31;
@@ -261,7 +264,7 @@ __global__ void __launch_bounds__(kThreads) k_gather_smooth0(int64_t nbc, const 
     double s = 0.0;
 #pragma unroll
     for (int c = 0; c < NP; ++c) s = fma(w[c], __shfl_sync(mask, bv, g * NP + c), s);
-    xc[C * NP + r] = omega * s;
+    xc[C * NP + r] = (omr ? __ldg(omr + C) : omega) * s;
   }
 }
 

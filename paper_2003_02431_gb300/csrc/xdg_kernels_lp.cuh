@@ -113,7 +113,8 @@ __global__ void __launch_bounds__(kThreads) k_smooth_lp(int64_t nb, const int64_
                                                        const int32_t* __restrict__ col,
                                                        const TS* __restrict__ val, const float* __restrict__ sc,
                                                        const float* __restrict__ Dinv, const float* __restrict__ dsc,
-                                                       float omega, const float* __restrict__ b,
+                                                       float omega, const float* __restrict__ omr,
+                                                       const float* __restrict__ b,
                                                        const float* __restrict__ xi, float* __restrict__ xo) {
   constexpr int GPW = Grp<NP>::GPW;
   const int lane = threadIdx.x & 31;
@@ -126,7 +127,8 @@ __global__ void __launch_bounds__(kThreads) k_smooth_lp(int64_t nb, const int64_
     float res = b[i * NP + r];
     if (!ZERO) res -= row_dot_lp<NP, TS, float>(__ldg(rp + i), __ldg(rp + i + 1), r, col, val, sc, xi);
     float z = block_gemv_lp<NP, float>(Dinv + i * (NP * NP), __ldg(dsc + i), r, g * NP, mask, res);
-    xo[i * NP + r] = ZERO ? omega * z : fmaf(omega, z, xi[i * NP + r]);
+    const float om = omr ? __ldg(omr + i) : omega;  // per-row damping in batches
+    xo[i * NP + r] = ZERO ? om * z : fmaf(om, z, xi[i * NP + r]);
   }
 }
 
@@ -179,6 +181,7 @@ __global__ void __launch_bounds__(kThreads) k_gather_smooth0_lp(int64_t nbc, con
                                                                const float* __restrict__ t,
                                                                const float* __restrict__ Dinv,
                                                                const float* __restrict__ dsc, float omega,
+                                                               const float* __restrict__ omr,
                                                                float* __restrict__ bc, float* __restrict__ xc) {
   constexpr int GPW = Grp<NP>::GPW;
   const int lane = threadIdx.x & 31;
@@ -191,7 +194,7 @@ __global__ void __launch_bounds__(kThreads) k_gather_smooth0_lp(int64_t nbc, con
     float bv = child_sum<NP, float, float>(__ldg(cptr + C), __ldg(cptr + C + 1), r, ch, t);
     bc[C * NP + r] = bv;
     float z = block_gemv_lp<NP, float>(Dinv + C * (NP * NP), __ldg(dsc + C), r, g * NP, mask, bv);
-    xc[C * NP + r] = omega * z;
+    xc[C * NP + r] = (omr ? __ldg(omr + C) : omega) * z;
   }
 }
 

@@ -19,7 +19,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _ROOT = os.path.dirname(_HERE)
 LIB_PATH = os.path.join(_HERE, "libxdg.so")
 _SRCS = [os.path.join(_HERE, "csrc", "xdg.cu"), os.path.join(_HERE, "csrc", "xdg_kernels.cuh"),
-         os.path.join(_HERE, "csrc", "xdg_kernels_lp.cuh"), os.path.join(_ROOT, "include", "xdg.h")]
+         os.path.join(_HERE, "csrc", "xdg_kernels_lp.cuh"), os.path.join(_HERE, "csrc", "xdg_kernels_batch.cuh"),
+         os.path.join(_ROOT, "include", "xdg.h")]
 
 XDG_OK, XDG_EINVAL, XDG_ECUDA, XDG_ENOMEM, XDG_ENOTCONV, XDG_EBREAKDOWN, XDG_ETIMEOUT = range(7)
 XDG_PREC_F64, XDG_PREC_F32, XDG_PREC_BF16 = 0, 1, 2
@@ -81,6 +82,16 @@ class HierInfo(C.Structure):
                 ("device_bytes", C.c_size_t), ("setup_ms", C.c_double * 3)]
 
 
+class BatchResult(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("status", C.c_int), ("relres", C.c_double)]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("n_problems", C.c_int), ("n_groups", C.c_int), ("total_dof", C.c_int64),
+                ("device_bytes", C.c_size_t), ("setup_ms", C.c_double),
+                ("nodes_fixed", C.c_int64 * 3), ("nodes_per_iteration", C.c_int64 * 3)]
+
+
 # (name, restype, argtypes) of every exported entry point
 _vp, _dp, _ip = C.c_void_p, C.POINTER(C.c_double), C.c_int
 SIGNATURES = [
@@ -102,6 +113,14 @@ SIGNATURES = [
     ("xdg_restrict_noalloc", C.c_int, [_ip, C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                       _vp]),
     ("xdg_fma_peak", C.c_int, [_ip, _dp]),
+    ("xdg_create_batch", C.c_int, [_ip, C.POINTER(Problem), C.POINTER(HierOpts), _vp, C.POINTER(_vp)]),
+    ("xdg_batch_destroy", C.c_int, [_vp]),
+    ("xdg_batch_get_info", C.c_int, [_vp, C.POINTER(BatchInfo)]),
+    ("xdg_batch_group", C.c_int, [_vp, _ip, C.POINTER(_vp), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    ("xdg_solve_batch", C.c_int, [_vp, _vp, _vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo),
+                                  C.POINTER(BatchResult)]),
+    ("xdg_solve_batch_host", C.c_int, [_vp, _dp, _dp, C.POINTER(SolveOpts), C.POINTER(SolveInfo),
+                                       C.POINTER(BatchResult)]),
 ]
 
 
@@ -165,6 +184,28 @@ class _Ordered:
             _torch().cuda.current_stream(self.h.stream.device).wait_stream(self.h.stream)
 
 
+def _marshal(Np, nb, row_ptr, col, val, aggs, Rs, keep):
+    """xdg_problem struct over contiguous copies of the arrays (kept alive in `keep`)."""
+
+    def arr(a, dt):
+        a = np.ascontiguousarray(a, dtype=dt)
+        keep.append(a)
+        return a
+
+    nl = len(nb)
+    nb_a = arr(nb, np.int64)
+    rp = arr(row_ptr, np.int64)
+    cl = arr(col, np.int32)
+    vl = arr(val, np.float64)
+    ag = [arr(a, np.int32) for a in aggs]
+    Rr = [arr(r, np.float64) for r in Rs]
+    aggp = (C.POINTER(C.c_int32) * max(nl - 1, 1))(*[a.ctypes.data_as(C.POINTER(C.c_int32)) for a in ag])
+    Rp = (C.POINTER(C.c_double) * max(nl - 1, 1))(*[r.ctypes.data_as(_dp) for r in Rr])
+    keep += [aggp, Rp]
+    return Problem(Np, nl, nb_a.ctypes.data_as(C.POINTER(C.c_int64)), rp.ctypes.data_as(C.POINTER(C.c_int64)),
+                   cl.ctypes.data_as(C.POINTER(C.c_int32)), vl.ctypes.data_as(_dp), aggp, Rp)
+
+
 class Hierarchy:
     """Owner of an xdg_hier_t handle.
 
@@ -180,23 +221,7 @@ class Hierarchy:
         self.stream = stream
         self._keep = []
 
-        def arr(a, dt):
-            a = np.ascontiguousarray(a, dtype=dt)
-            self._keep.append(a)
-            return a
-
-        nl = len(nb)
-        nb_a = arr(nb, np.int64)
-        rp = arr(row_ptr, np.int64)
-        cl = arr(col, np.int32)
-        vl = arr(val, np.float64)
-        ag = [arr(a, np.int32) for a in aggs]
-        Rr = [arr(r, np.float64) for r in Rs]
-        aggp = (C.POINTER(C.c_int32) * max(nl - 1, 1))(*[a.ctypes.data_as(C.POINTER(C.c_int32)) for a in ag])
-        Rp = (C.POINTER(C.c_double) * max(nl - 1, 1))(*[r.ctypes.data_as(_dp) for r in Rr])
-        self._keep += [aggp, Rp]
-        prob = Problem(Np, nl, nb_a.ctypes.data_as(C.POINTER(C.c_int64)), rp.ctypes.data_as(C.POINTER(C.c_int64)),
-                       cl.ctypes.data_as(C.POINTER(C.c_int32)), vl.ctypes.data_as(_dp), aggp, Rp)
+        prob = _marshal(Np, nb, row_ptr, col, val, aggs, Rs, self._keep)
         opts = HierOpts(omega, lanczos_steps, nu, gamma, low_precision, w_levels)
         h = C.c_void_p()
         st = C.c_void_p(stream.cuda_stream)
@@ -292,7 +317,101 @@ class Hierarchy:
 
     def destroy(self):
         if getattr(self, "_h", None):
-            load().xdg_destroy(self._h)
+            if not getattr(self, "_borrowed", None):
+                load().xdg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def _solve_result(rc, info, res):
+    return {"iterations": info.iterations, "relres": info.relres, "ms": info.ms, "status": rc,
+            "launches": info.launches,
+            "problems": [{"iterations": r.iterations, "status": r.status, "relres": r.relres} for r in res]}
+
+
+class Batch:
+    """Owner of an xdg_batch_t: n independent problems solved in one graph launch.
+
+    problems: list of xdg_problem.Problem (or objects with Np, nb, row_ptr, col, val, agg, R).
+    Vectors are the problems' level-1 vectors concatenated in list order (`offsets`)."""
+
+    def __init__(self, problems, omega=0.0, lanczos_steps=12, nu=1, gamma=1, low_precision=0,
+                 w_levels=0, stream=None):
+        L = load()
+        torch = _torch()
+        if stream is None:
+            stream = torch.cuda.Stream()
+        self.stream = stream
+        keep = []
+        arr = (Problem * len(problems))()
+        for i, p in enumerate(problems):
+            arr[i] = _marshal(p.Np, p.nb, p.row_ptr, p.col, p.val, p.agg, p.R, keep)
+        opts = HierOpts(omega, lanczos_steps, nu, gamma, low_precision, w_levels)
+        h = C.c_void_p()
+        self._h = None
+        with _Ordered(self):
+            _check(L.xdg_create_batch(len(problems), arr, C.byref(opts), C.c_void_p(stream.cuda_stream),
+                                      C.byref(h)))
+        self._h = h
+        self.n = len(problems)
+        sizes = [int(p.nb[0]) * int(p.Np) for p in problems]
+        self.offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        self.total_dof = int(self.offsets[-1])
+
+    def info(self) -> dict:
+        i = BatchInfo()
+        _check(load().xdg_batch_get_info(self._h, C.byref(i)))
+        return {"n_problems": i.n_problems, "n_groups": i.n_groups, "total_dof": i.total_dof,
+                "device_bytes": i.device_bytes, "setup_ms": i.setup_ms,
+                "nodes_fixed": list(i.nodes_fixed), "nodes_per_iteration": list(i.nodes_per_iteration)}
+
+    def group(self, g):
+        """(Hierarchy view of group g's union hierarchy, list of member indices)."""
+        h = C.c_void_p()
+        m = C.c_int()
+        _check(load().xdg_batch_group(self._h, g, C.byref(h), C.byref(m), None))
+        mem = (C.c_int * max(m.value, 1))()
+        _check(load().xdg_batch_group(self._h, g, None, None, mem))
+        H = Hierarchy.__new__(Hierarchy)
+        H._h, H._borrowed, H._owner, H.stream = h, True, self, self.stream
+        inf = H.info()
+        H.Np, H.nb = inf["Np"], inf["nb"]
+        H.n = H.nb[0] * H.Np
+        return H, list(mem[:m.value])
+
+    def solve(self, b, x, tol=1e-10, maxit=1000, precision=XDG_PREC_F64, raise_on_error=True) -> dict:
+        o = SolveOpts(tol, maxit, 1, precision, 0.0, 0.0)
+        info = SolveInfo()
+        res = (BatchResult * self.n)()
+        with _Ordered(self):
+            rc = load().xdg_solve_batch(self._h, _dptr(b), _dptr(x), C.byref(o), C.byref(info), res)
+        if raise_on_error:
+            _check(rc)
+        return _solve_result(rc, info, res)
+
+    def solve_host(self, b_host, x_host, tol=1e-10, maxit=1000, precision=XDG_PREC_F64,
+                   raise_on_error=True) -> dict:
+        for a in (b_host, x_host):
+            if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+                raise ValueError("host vectors must be contiguous float64")
+        o = SolveOpts(tol, maxit, 1, precision, 0.0, 0.0)
+        info = SolveInfo()
+        res = (BatchResult * self.n)()
+        with _Ordered(self):
+            rc = load().xdg_solve_batch_host(self._h, b_host.ctypes.data_as(_dp), x_host.ctypes.data_as(_dp),
+                                             C.byref(o), C.byref(info), res)
+        if raise_on_error:
+            _check(rc)
+        return _solve_result(rc, info, res)
+
+    def destroy(self):
+        if getattr(self, "_h", None):
+            load().xdg_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

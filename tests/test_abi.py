@@ -41,3 +41,48 @@ def test_strerror_without_gpu():
     lib = xdg.load()
     assert lib.xdg_strerror(0) == b"XDG_OK"
     assert lib.xdg_strerror(4) == b"XDG_ENOTCONV"
+
+
+def _batch_rc(problems):
+    import ctypes as C
+    keep = []
+    arr = (xdg.Problem * len(problems))()
+    for i, p in enumerate(problems):
+        arr[i] = xdg._marshal(p.Np, p.nb, p.row_ptr, p.col, p.val, p.agg, p.R, keep)
+    h = C.c_void_p()
+    lib = xdg.load()
+    rc = lib.xdg_create_batch(len(problems), arr, None, None, C.byref(h))
+    return rc, lib.xdg_last_error().decode()
+
+
+def test_batch_validation_names_the_problem_without_gpu():
+    """Every index of every batch member is checked on the host before any CUDA call."""
+    import numpy as np
+    import xdg_problem as xp
+    cfgs = xp.batch_configs(4, seed=5, N_range=(8, 12), ks=(2,), max_levels=3)
+    probs = [xp.Problem(c) for c in cfgs]
+
+    class P:  # a mutable copy of a problem's arrays
+        def __init__(self, p):
+            self.Np, self.nb = p.Np, list(p.nb)
+            self.row_ptr, self.col, self.val = p.row_ptr.copy(), p.col.copy(), p.val.copy()
+            self.agg, self.R = [a.copy() for a in p.agg], [r.copy() for r in p.R]
+
+    cases = []
+    bad = P(probs[2])
+    bad.agg[1][0] = bad.nb[2]  # coarse index out of range on level 2
+    cases.append((2, bad, "agg"))
+    bad = P(probs[1])
+    bad.col[0] = bad.nb[0]  # column index out of range
+    cases.append((1, bad, "col"))
+    bad = P(probs[3])
+    r = int(np.argmax(np.diff(bad.row_ptr) > 1))
+    z = int(bad.row_ptr[r])
+    bad.col[z], bad.col[z + 1] = bad.col[z + 1], bad.col[z]  # columns not increasing
+    cases.append((3, bad, "increasing"))
+    for idx, broken, word in cases:
+        lst = [P(p) for p in probs]
+        lst[idx] = broken
+        rc, msg = _batch_rc(lst)
+        assert rc == xdg.XDG_EINVAL, (idx, msg)
+        assert ("problem %d" % idx) in msg and word in msg, msg

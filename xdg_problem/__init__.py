@@ -142,6 +142,25 @@ def config_paper_twin(N: int, k: int, alpha: float = 0.1, **kw) -> Config:
     return Config(**base)
 
 
+def batch_configs(n: int, seed: int = 20030244, N_range=(32, 128), ks=(2, 3, 4), R_range=(0.1, 0.3),
+                  c_range=(0.3, 0.7), log10_mu_range=(0.0, 3.0), max_levels: int = 6) -> list:
+    """n independent 2D problems, drawn from numpy PCG64(seed) in this order per problem:
+    N ~ U{N_range}, k ~ U(ks), centre ~ U(c_range)^2, R ~ U(R_range), mu_B/mu_A = 10^U(log10_mu_range)
+    (mu_A = 1 inside). Every problem gets max_levels aggregation levels (no coarse-size stop),
+    so that problems of one block size share the depth of their hierarchy."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(n):
+        N = int(rng.integers(N_range[0], N_range[1] + 1))
+        k = int(ks[int(rng.integers(0, len(ks)))])
+        cx, cy = (float(v) for v in rng.uniform(c_range[0], c_range[1], size=2))
+        R = float(rng.uniform(*R_range))
+        mu = float(10.0 ** rng.uniform(*log10_mu_range))
+        out.append(Config(D=2, N=N, k=k, c=(cx, cy, 0.0), R=R, muA=1.0, muB=mu, max_coarse_dof=0,
+                          max_levels=max_levels))
+    return out
+
+
 class Problem:
     """Assembled agglomerated XDG system plus its aggregation hierarchy (numpy views)."""
 
