@@ -24,6 +24,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -126,6 +128,80 @@ def oracle_sample(P, iters_needed, budget_s=12.0):
             "est_solve_s": per * iters_needed, "cores": os.cpu_count()}
 
 
+BATCH_N = 256
+BATCH_SEED = 20030244
+BATCH_WORKLOAD = ("256 independent 2D XDG Poisson problems: N~U{32..128}^2, k~U{2,3,4}, circle centre "
+                  "U(0.3,0.7)^2, R~U(0.1,0.3), mu ratio 10^U(0,3), 6 aggregation levels, seed %d" % BATCH_SEED)
+
+
+def make_batch_problems(n=BATCH_N):
+    """The batched workload, generated on all host cores (one thread per problem)."""
+    import dataclasses
+    from concurrent.futures import ThreadPoolExecutor
+
+    import xdg_problem as xp
+    cfgs = [dataclasses.replace(c, nthreads=1) for c in xp.batch_configs(n, seed=BATCH_SEED)]
+    with ThreadPoolExecutor(os.cpu_count() or 1) as ex:
+        return list(ex.map(xp.Problem, cfgs))
+
+
+def batched_section(xdg, torch, dev, stream, steps, warmup):
+    """One step = one batched solve of all problems (a single graph launch) to TOL."""
+    t = time.perf_counter()
+    probs = make_batch_problems()
+    gen_s = time.perf_counter() - t
+    t = time.perf_counter()
+    bt = xdg.Batch(probs, gamma=GAMMA, w_levels=W_LEVELS, low_precision=1, stream=stream)
+    setup_s = time.perf_counter() - t
+    binfo = bt.info()
+    n = bt.total_dof
+    bh = np.concatenate([p.b.reshape(-1) for p in probs])
+    b = torch.from_numpy(bh).to(dev)
+    x = torch.zeros_like(b)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def run(prec):
+        for _ in range(warmup):
+            x.zero_()
+            bt.solve(b, x, tol=TOL, maxit=1000, precision=prec)
+        torch.cuda.synchronize()
+        res = []
+        ev0.record(stream)
+        for _ in range(steps):
+            x.zero_()
+            res.append(bt.solve(b, x, tol=TOL, maxit=1000, precision=prec))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / steps, res[-1], sum(r["launches"] for r in res)
+
+    ms32, r32, launches = run(xdg.XDG_PREC_F32)
+    ms64, r64, _ = run(xdg.XDG_PREC_F64)
+    its = [p["iterations"] for p in r32["problems"]]
+    # end to end: host vectors in pinned memory, copies inside the call
+    bp = torch.from_numpy(bh).pin_memory().numpy()
+    xp_ = torch.zeros(n, dtype=torch.float64).pin_memory().numpy()
+    bt.solve_host(bp, xp_, tol=TOL, maxit=1000, precision=xdg.XDG_PREC_F32)
+    t = time.perf_counter()
+    for _ in range(steps):
+        bt.solve_host(bp, xp_, tol=TOL, maxit=1000, precision=xdg.XDG_PREC_F32)
+    e2e_s = (time.perf_counter() - t) / steps
+    out = {
+        "workload": BATCH_WORKLOAD, "problems": len(probs), "dof": n, "groups": binfo["n_groups"],
+        "graph_launches_per_solve": 1,
+        "mixed_f32": {"solve_ms": ms32, "mdofs": n / ms32 / 1e3, "iterations_min_median_max":
+                      [min(its), int(np.median(its)), max(its)], "max_relres": r32["relres"]},
+        "plain_f64": {"solve_ms": ms64, "mdofs": n / ms64 / 1e3, "iterations_max": r64["iterations"],
+                      "max_relres": r64["relres"]},
+        "speedup_mixed_vs_f64": ms64 / ms32,
+        "e2e": {"value": n / e2e_s / 1e6, "unit": "MDOF/s", "h2d_bytes_per_step": n * 8,
+                "d2h_bytes_per_step": n * 8},
+        "kernel_nodes_per_solve": launches / steps,
+        "generate_s": gen_s, "setup_s": setup_s, "device_gb": binfo["device_bytes"] / 1e9,
+    }
+    bt.destroy()
+    return out
+
+
 def reference_arm(args):
     """The oracle (plain FP64 CPU code) on the same workload: each step is a bounded sample of
     5 PCG iterations, extrapolated with the iteration count of the oracle's full solve."""
@@ -161,6 +237,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="xdg", choices=["xdg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched 256-problem workload")
     ap.add_argument("--size", type=int, default=64,
                     help="cells per direction; 64 is the benchmark workload, smaller sizes serve profiling")
     args = ap.parse_args()
@@ -275,6 +352,11 @@ def main():
         e2e_s = float(tt.item())
     e2e = world * n * args.steps / e2e_s / 1e6
 
+    batched = None
+    if not args.no_batch:
+        H.destroy()  # free the single problem's hierarchy first
+        batched = batched_section(xdg, torch, dev, stream, args.steps, warmup)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         it64 = int(statistics.median(iters64))
@@ -312,6 +394,7 @@ def main():
             "roofline_fp32_apply": {"bound": "hbm", "kernel": "k_spmv_lp<10,float> FP32 operator apply, level 1",
                                     "achieved": ach32, "peak": hbm, "unit": "GB/s", "frac": ach32 / hbm,
                                     "peak_kind": hbm_kind, "bytes": bytes_apply32, "ms": ms_apply32},
+            "batched": batched,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": "MDOF/s", "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8},
             "gpu_launches": launches,

@@ -162,6 +162,11 @@ int xdg_export_level(xdg_hier_t h, int level, int64_t* row_ptr, int32_t* col, do
  * (XDG_PREC_F64, or F32 / BF16 when built with low_precision; FP32 accumulation then). */
 int xdg_apply(xdg_hier_t h, int level, const double* x, double* y, int prec);
 
+/* Replace the smoother damping of `level` (1 <= level < n_levels) by omega > 0 (default:
+ * 4 / (3 lambda_l) from the Lanczos estimate). Records the solve graphs again. Not for the
+ * hierarchy of a batch group (EINVAL). */
+int xdg_set_damping(xdg_hier_t h, int level, double omega);
+
 /* One damped block-Jacobi step on `level`: x_out = x_in + omega D^{-1} (b - M x_in), the
  * diagonal blocks D solved with their Cholesky factors. x_in == NULL means x_in = 0. x_out
  * must not alias x_in or b. */
@@ -278,6 +283,86 @@ int xdg_solve_batch(xdg_batch_t b, const double* bvec, double* x, const xdg_solv
 int xdg_solve_batch_host(xdg_batch_t b, const double* b_host, double* x_host,
                          const xdg_solve_opts* o, xdg_solve_info* info,
                          xdg_batch_result* results);
+
+/* ---------------------------------------------------------------------------------------------
+ * Learned cut-cell correction (an extension of the paper's smoothing step, not part of it).
+ *
+ * The paper's smoothers solve small local systems exactly (cell-local dense solves, Algorithm 1;
+ * block Schwarz, sec. 3.3). Here a small network proposes a correction on each "unit" -- the
+ * two level-1 blocks that hold the A and B parts of one cut background cell -- from the unit's
+ * geometry and its residual after the multigrid cycle. The target is the exact local solve
+ * delta* = M_uu^{-1} r_u, which minimises the energy of the true error over corrections on the
+ * unit: ||e - delta||_M^2 - ||e||_M^2 = delta^T M_uu delta - 2 delta^T r_u (r = M e). In the
+ * solve, a unit's correction is applied (damped by theta) only if this energy change is
+ * negative; otherwise the plain cycle's result stands for that unit. With the correction
+ * enabled the preconditioner is nonlinear and xdg_solve runs flexible CG in every precision.
+ *
+ * Network: n_in -> 64 -> 64 -> 64 -> n_out = 2 Np, GELU (x Phi(x)) on the hidden layers.
+ * Parameters, FP32, flat and row-major: W1[n_in][64] b1[64] W2[64][64] b2[64] W3[64][64]
+ * b3[64] W4[64][n_out] b4[n_out]; a layer computes a_out = act(a_in W + b). Inference in the
+ * solve uses a BF16 copy of the parameters (FP32 arithmetic).
+ * Coordinates: with X_a = L_a^{-1}, X_b = L_b^{-1} the inverse Cholesky factors of the
+ * diagonal blocks M_aa, M_bb (the factors of the block-Jacobi smoother), the unit works on
+ * rt = [X_a r_a; X_b r_b] and H = diag(X_a, X_b) M_uu diag(X_a, X_b)^T (identity diagonal
+ * blocks), so that its target y* = H^{-1} rt is of order one whatever the scale of M.
+ * Inputs of unit u: its geometry features (n_geo floats, given by the caller), then
+ * rhat = rt / s with s = ||rt||_2; for output y the correction is delta = s diag(X_a, X_b)^T y
+ * (y = rhat is a block-Jacobi step on the unit), and its energy change is
+ * s^2 (y^T H y - 2 y^T rhat).
+ * Training sample: inputs X, matrix H (FP32), rhat R, and c = rhat^T H^{-1} rhat; loss
+ * (y^T H y - 2 y^T rhat) / c (-1 = the exact local solve, 0 = no gain), averaged over the
+ * samples. */
+typedef struct xdg_mlp* xdg_mlp_t;
+
+typedef struct {
+  int epochs;          /* passes over the samples */
+  int batch;           /* samples per Adam step */
+  float lr;            /* Adam step size */
+  float beta1, beta2;  /* Adam moment decay (0: 0.9, 0.999) */
+  float eps;           /* Adam epsilon (0: 1e-8) */
+  uint64_t seed;       /* shuffling */
+} xdg_train_opts;
+
+/* Network with Glorot-uniform weights drawn from a counter-based generator (splitmix64 of
+ * seed and entry index) and zero biases; 1 <= n_in, n_out <= 64. stream as in
+ * xdg_create_hierarchy. */
+int xdg_mlp_create(int n_in, int n_out, uint64_t seed, void* stream, xdg_mlp_t* out);
+int xdg_mlp_destroy(xdg_mlp_t m);
+int xdg_mlp_num_params(xdg_mlp_t m, int64_t* n);
+/* FP32 parameters to / from host memory (n = xdg_mlp_num_params); set resets Adam's state. */
+int xdg_mlp_get_params(xdg_mlp_t m, float* host, int64_t n);
+int xdg_mlp_set_params(xdg_mlp_t m, const float* host, int64_t n);
+/* Y[n][n_out] = network(X[n][n_in]) (device arrays); prec XDG_PREC_F32 or XDG_PREC_BF16
+ * (parameters rounded to BF16, FP32 arithmetic). */
+int xdg_mlp_forward(xdg_mlp_t m, int prec, int64_t n, const float* X, float* Y);
+/* Mean loss over n samples (host *loss) and its gradient (device grad[num_params], optional)
+ * with the current parameters. Device arrays: X[n][n_in], uid[n] (row of Mloc of each sample),
+ * Mloc[*][n_out][n_out], R[n][n_out], C[n]. */
+int xdg_mlp_loss_grad(xdg_mlp_t m, int n, const float* X, const int32_t* uid, const float* Mloc,
+                      const float* R, const float* C, double* loss, float* grad);
+/* Adam on minibatches of the samples (arrays as in xdg_mlp_loss_grad), reshuffled every epoch;
+ * loss_per_epoch (host, optional) receives the mean training loss of each epoch. */
+int xdg_mlp_train(xdg_mlp_t m, int n, const float* X, const int32_t* uid, const float* Mloc,
+                  const float* R, const float* C, const xdg_train_opts* o, double* loss_per_epoch);
+
+/* Units of the hierarchy's level 1: pairs[u] = (block of the A part, block of the B part) of a
+ * cut cell (host int32[n_units][2], distinct blocks), geom = host float[n_units][n_geo]
+ * geometry features; n_geo + 2 Np <= 64. Computes the unit matrices and their inverses
+ * (EBREAKDOWN if one is not positive definite). Once per hierarchy. */
+int xdg_units_setup(xdg_hier_t h, int n_units, const int32_t* pairs, int n_geo, const float* geom);
+/* FP32 unit matrices in block-Jacobi coordinates (H above) into device
+ * Mloc[n_units][2Np][2Np]. */
+int xdg_units_local(xdg_hier_t h, float* Mloc);
+/* Training samples of all units from the level-1 right-hand side r (device): z = B r with the
+ * plain cycle of precision prec, then per unit, for the residual r - M z: X[u] (inputs),
+ * R[u] (rhat) and C[u] (optimal decrease rhat^T H^{-1} rhat); device outputs. */
+int xdg_units_samples(xdg_hier_t h, int prec, const double* r, float* X, float* R, float* C);
+/* Use network m (a BF16 snapshot of its current parameters) with damping theta > 0 in the
+ * preconditioner of xdg_solve; m = NULL switches the correction off. */
+int xdg_learned_enable(xdg_hier_t h, xdg_mlp_t m, double theta);
+/* One correction step on device vectors: z += theta * (kept corrections) for the residual
+ * r - M z; *n_kept (optional, synchronises) = units whose correction was kept. */
+int xdg_learned_step(xdg_hier_t h, const double* r, double* z, int* n_kept);
 
 /* Residual restriction for callers that cannot allocate device memory.
  *

@@ -24,6 +24,7 @@
 #include "xdg_kernels.cuh"
 #include "xdg_kernels_lp.cuh"
 #include "xdg_kernels_batch.cuh"
+#include "xdg_kernels_mlp.cuh"
 
 using namespace xdg;
 
@@ -241,6 +242,56 @@ bool ops_lp_for(int np, int prec, OpsLP* o) {
   }
 }
 
+// per-Np kernels of the learned cut-cell correction
+struct OpsU {
+  void (*factor)(cudaStream_t, int, const int64_t*, const double*, double*, double*, float*, double*, int*);
+  void (*resid_rows)(int, cudaStream_t, int64_t, const int32_t*, const int64_t*, const int32_t*, const double*,
+                     const double*, const double*, double*);
+  void (*samples)(cudaStream_t, int, int, const int32_t*, const float*, const double*, const double*, const double*,
+                  float*, float*, float*);
+  void (*apply)(cudaStream_t, int, MlpDims, int, const int32_t*, const float*, const double*, const __nv_bfloat16*,
+                const double*, const double*, double*, int*, double*);
+  void (*gather)(cudaStream_t, int, const int32_t*, const int64_t*, const int32_t*, const double*, double, double*);
+};
+
+template <int NP>
+struct OpsUT {
+  static void factor(cudaStream_t s, int U, const int64_t* z, const double* v, double* Li, double* Hm, float* M,
+                     double* Hi, int* e) {
+    k_unit_factor<NP><<<U, 32, 0, s>>>(U, z, v, Li, Hm, M, Hi, e);
+  }
+  static void resid_rows(int g, cudaStream_t s, int64_t nr, const int32_t* rows, const int64_t* rp,
+                         const int32_t* col, const double* val, const double* x, const double* b, double* y) {
+    k_resid_rows<NP><<<g, kThreads, 0, s>>>(nr, rows, rp, col, val, x, b, y);
+  }
+  static void samples(cudaStream_t s, int U, int ng, const int32_t* pr, const float* geo, const double* r,
+                      const double* Li, const double* Hi, float* X, float* R, float* C) {
+    k_unit_samples<NP><<<(U + 7) / 8, 256, 0, s>>>(U, ng, pr, geo, r, Li, Hi, X, R, C);
+  }
+  static void apply(cudaStream_t s, int U, MlpDims d, int ng, const int32_t* pr, const float* geo, const double* r,
+                    const __nv_bfloat16* W, const double* Li, const double* Hm, double* dl, int* kp, double* E) {
+    const size_t sm = (size_t)d.total * sizeof(__nv_bfloat16);  // <= 30 KB (n_in, n_out <= 64)
+    const int blocks = std::max(1, std::min((U + 7) / 8, 152 * 4));
+    k_unit_apply<NP><<<blocks, 256, sm, s>>>(U, d, ng, pr, geo, r, W, Li, Hm, dl, kp, E);
+  }
+  static void gather(cudaStream_t s, int nt, const int32_t* tb, const int64_t* tp, const int32_t* tl,
+                     const double* dl, double th, double* z) {
+    const int64_t n = (int64_t)nt * NP;
+    k_unit_gather<NP><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nt, tb, tp, tl, dl, th, z);
+  }
+  static OpsU make() { return OpsU{factor, resid_rows, samples, apply, gather}; }
+};
+
+bool ops_u_for(int np, OpsU* o) {
+  switch (np) {
+    case 6: *o = OpsUT<6>::make(); return true;
+    case 10: *o = OpsUT<10>::make(); return true;
+    case 15: *o = OpsUT<15>::make(); return true;
+    case 20: *o = OpsUT<20>::make(); return true;
+    default: return false;
+  }
+}
+
 // low-precision copy of one level
 struct LevelLP {
   void* val = nullptr;       // operator in the storage precision (smoothing sweeps, apply)
@@ -279,6 +330,31 @@ struct Level {
   std::vector<double> lmax_p, omega_p;
 };
 
+// learned cut-cell correction attached to a hierarchy (units on level 1)
+struct Learned {
+  int U = 0, n_geo = 0, nt = 0;
+  int32_t* pairs = nullptr;   // [U][2] level-1 blocks (A part, B part)
+  float* geom = nullptr;      // [U][n_geo] geometry features
+  int64_t* zidx = nullptr;    // [U][4] positions of the blocks (a,a), (a,b), (b,a), (b,b) in val
+  double* Linv = nullptr;     // [U][2][Np][Np] inverse Cholesky factors of M_aa, M_bb
+  double* Hm = nullptr;       // [U][m][m] unit matrices in block-Jacobi coordinates
+  float* Mloc = nullptr;      // [U][m][m] the same in FP32 (training)
+  double* Minv = nullptr;     // [U][m][m] their inverses
+  int32_t* tblk = nullptr;    // touched blocks (ascending)
+  int64_t* tptr = nullptr;    // their (unit, half) lists
+  int32_t* tlist = nullptr;
+  double *res = nullptr, *delta = nullptr, *E = nullptr;
+  int* keep = nullptr;
+  __nv_bfloat16* W = nullptr; // BF16 snapshot of the network parameters
+  int wcap = 0;
+  MlpDims d{};
+  double theta = 0.25;
+  bool on = false;
+  OpsU ops{};
+  cudaGraphExec_t g_iter[3] = {nullptr, nullptr, nullptr};
+  int64_t nodes[3] = {0, 0, 0};
+};
+
 }  // namespace
 
 struct xdg_hier {
@@ -304,6 +380,7 @@ struct xdg_hier {
   double* cpart = nullptr;
   int64_t* ioff = nullptr;      // offset of every problem in the caller's concatenated vectors
   int* gidx = nullptr;          // index of every problem in the caller's list
+  Learned lr;                   // learned cut-cell correction (off unless enabled)
   cudaStream_t body_stream = nullptr;
   int64_t bnodes_fixed[3] = {0, 0, 0};  // kernel nodes of a recorded batched solve outside
   int64_t bnodes_body[3] = {0, 0, 0};   // its loop, and inside one loop iteration
@@ -342,6 +419,8 @@ struct xdg_hier {
       if (g_iter_lp[p]) cudaGraphExecDestroy(g_iter_lp[p]);
       if (g_cyc_lp[p]) cudaGraphExecDestroy(g_cyc_lp[p]);
     }
+    for (int p = 0; p < 3; ++p)
+      if (lr.g_iter[p]) cudaGraphExecDestroy(lr.g_iter[p]);
     for (void* p : allocs) cudaFree(p);
     if (h_bsc) cudaFreeHost(h_bsc);
     if (body_stream) cudaStreamDestroy(body_stream);
@@ -545,6 +624,22 @@ struct xdg_hier {
     launches += 2;
   }
 
+  // z += theta * (kept learned corrections of the units) for the residual r - M z
+  void learned_apply(const double* r, double* z) {
+    Level& V = L[0];
+    lr.ops.resid_rows(grid(lr.nt), stream, lr.nt, lr.tblk, V.rp, V.col, V.val, z, r, lr.res);
+    lr.ops.apply(stream, lr.U, lr.d, lr.n_geo, lr.pairs, lr.geom, lr.res, lr.W, lr.Linv, lr.Hm, lr.delta, lr.keep,
+                 lr.E);
+    lr.ops.gather(stream, lr.nt, lr.tblk, lr.tptr, lr.tlist, lr.delta, lr.theta, z);
+    launches += 3;
+  }
+  // the preconditioner of the solve: cycle of precision p, then the learned correction when on
+  void precond_full(int p, const double* r, double* z) {
+    if (p == XDG_PREC_F64) cycle(0, r, z);
+    else cycle_lp_d(p, r, z);
+    if (lr.on) learned_apply(r, z);
+  }
+
   // one flexible-CG iteration (FP64 operator, residual and updates; low-precision cycle)
   void fcg_iteration(int p) {
     const int64_t n = L[0].nb * Np;
@@ -554,7 +649,7 @@ struct xdg_hier {
     k_pcg_xr<<<kRedBlocks, kThreads, 0, stream>>>(n, S, s_p, s_q, s_x, s_r, partial);
     k_sum_final<<<1, kThreads, 0, stream>>>(kRedBlocks, partial, &S->rr);
     launches += 3;
-    cycle_lp_d(p, s_r, s_z);
+    precond_full(p, s_r, s_z);
     dot(n, s_r, s_z, &S->rz);
     dot(n, s_z, s_q, &S->zq);
     k_fcg_beta<<<1, 1, 0, stream>>>(S);
@@ -572,13 +667,14 @@ struct xdg_hier {
     if (which == 0) cycle(0, b, x);
     else if (which == 1) pcg_iteration();
     else if (which == 2) cycle_lp_d(p, b, x);
-    else fcg_iteration(p);
+    else fcg_iteration(p);  // 3: low-precision cycle; 4: with the learned correction (lr.on)
     const int64_t recorded = launches - before;
     launches = before;
     if (which == 0) cycle_nodes = recorded;
     else if (which == 1) iter_nodes = recorded;
     else if (which == 2) cyc_lp_nodes[p] = recorded;
-    else iter_lp_nodes[p] = recorded;
+    else if (which == 3) iter_lp_nodes[p] = recorded;
+    else lr.nodes[p] = recorded;
     cudaError_t e = cudaStreamEndCapture(stream, &g);
     if (e != cudaSuccess) {
       set_err("graph capture: %s", cudaGetErrorString(e));
@@ -1388,8 +1484,10 @@ int xdg_hier::solve_dev(const double* b, double* x, const xdg_solve_opts* o, xdg
   }
   // FP64: CG with the FP64 cycle. FP32/BF16: flexible CG (FP64 operator, residuals and
   // updates) with the low-precision cycle as preconditioner.
-  cudaGraphExec_t gi = (prec == XDG_PREC_F64) ? g_iter : g_iter_lp[prec];
-  const int64_t gi_nodes = (prec == XDG_PREC_F64) ? iter_nodes : iter_lp_nodes[prec];
+  // with the learned correction the preconditioner is nonlinear: flexible CG in every precision
+  if (lr.on && !lr.g_iter[prec]) TRY(capture(&lr.g_iter[prec], 4, nullptr, nullptr, prec));
+  cudaGraphExec_t gi = lr.on ? lr.g_iter[prec] : (prec == XDG_PREC_F64) ? g_iter : g_iter_lp[prec];
+  const int64_t gi_nodes = lr.on ? lr.nodes[prec] : (prec == XDG_PREC_F64) ? iter_nodes : iter_lp_nodes[prec];
   CK(cudaMemcpyAsync(s_b, b, n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
   CK(cudaMemcpyAsync(s_x, x, n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
   CK(cudaMemsetAsync(S, 0, sizeof(PcgScal), stream));
@@ -1397,8 +1495,7 @@ int xdg_hier::solve_dev(const double* b, double* x, const xdg_solve_opts* o, xdg
   spmv(0, s_x, s_b, s_r, 1);
   dot(n, s_b, s_b, dsc);
   dot(n, s_r, s_r, &S->rr);
-  if (prec == XDG_PREC_F64) cycle(0, s_r, s_z);
-  else cycle_lp_d(prec, s_r, s_z);
+  precond_full(prec, s_r, s_z);
   k_copy<<<vgrid(n), kThreads, 0, stream>>>(n, s_z, s_p);
   ++launches;
   dot(n, s_r, s_z, &S->rz);
@@ -1588,6 +1685,87 @@ struct xdg_batch {
 };
 
 // ============================================================================================
+// The network of the learned correction: FP32 parameters (trained here), Adam moments, and
+// batch work buffers.
+struct xdg_mlp {
+  MlpDims d{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  float *P = nullptr, *m1 = nullptr, *m2 = nullptr, *grad = nullptr, *partial = nullptr;
+  __nv_bfloat16* Pb = nullptr;
+  int nsl = 32;   // sample slices of the gradient reduction
+  MlpTrainBuf T{};
+  int cap = 0;    // samples the work buffers hold
+  int32_t* idx = nullptr;
+  int64_t idx_cap = 0;
+  double* dloss = nullptr;   // [2]: batch loss, epoch sum
+  double* hloss = nullptr;   // pinned
+  int64_t step = 0;
+  std::vector<void*> tbufs;  // work buffers (reallocated when a larger batch comes)
+  std::vector<void*> allocs;
+
+  ~xdg_mlp() {
+    if (stream) cudaStreamSynchronize(stream);
+    for (void* p : tbufs) cudaFree(p);
+    for (void* p : allocs) cudaFree(p);
+    if (hloss) cudaFreeHost(hloss);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+  }
+  template <class T_>
+  int alloc(T_** p, size_t n, std::vector<void*>& list) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T_));
+    if (e != cudaSuccess) {
+      set_err("cudaMalloc: %s", cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? XDG_ENOMEM : XDG_ECUDA;
+    }
+    list.push_back(q);
+    *p = static_cast<T_*>(q);
+    return XDG_OK;
+  }
+  int ensure_batch(int n) {
+    if (n <= cap) return XDG_OK;
+    CK(cudaStreamSynchronize(stream));
+    for (void* p : tbufs) cudaFree(p);
+    tbufs.clear();
+    const size_t h = (size_t)n * kHid;
+    TRY(alloc(&T.A1, h, tbufs));
+    TRY(alloc(&T.A2, h, tbufs));
+    TRY(alloc(&T.A3, h, tbufs));
+    TRY(alloc(&T.dZ1, h, tbufs));
+    TRY(alloc(&T.dZ2, h, tbufs));
+    TRY(alloc(&T.dZ3, h, tbufs));
+    TRY(alloc(&T.dY, (size_t)n * d.n_out, tbufs));
+    TRY(alloc(&T.loss, (size_t)n, tbufs));
+    cap = n;
+    return XDG_OK;
+  }
+  int ensure_idx(int64_t n) {
+    if (n <= idx_cap) return XDG_OK;
+    CK(cudaStreamSynchronize(stream));
+    TRY(alloc(&idx, (size_t)n, allocs));
+    idx_cap = n;
+    return XDG_OK;
+  }
+  size_t train_smem() const { return (size_t)(d.total + d.n_out * kHid + 2 * kHid * kHid) * sizeof(float); }
+  // forward, loss, backward and the gradient of the mean loss of samples idx[0..n) (or 0..n-1)
+  int loss_grad(int n, const int32_t* ix, const float* X, const int32_t* uid, const float* Mloc, const float* R,
+                const float* C) {
+    TRY(ensure_batch(n));
+    const size_t sm = train_smem();
+    CK(cudaFuncSetAttribute(k_mlp_train_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const int blocks = std::max(1, std::min((n + 7) / 8, 152 * 2));
+    k_mlp_train_pass<<<blocks, 256, sm, stream>>>(n, ix, d, P, X, uid, Mloc, R, C, T);
+    dim3 gg((unsigned)((d.total + 255) / 256), (unsigned)nsl);
+    k_mlp_grad_partial<<<gg, 256, 0, stream>>>(n, nsl, ix, d, X, T, partial);
+    k_mlp_grad_final<<<(d.total + 255) / 256, 256, 0, stream>>>(d.total, nsl, partial, grad);
+    k_sum_ordered<<<1, kThreads, 0, stream>>>(n, T.loss, dloss, 0);
+    CKL();
+    return XDG_OK;
+  }
+};
+
+// ============================================================================================
 extern "C" {
 
 const char* xdg_strerror(int code) {
@@ -1687,6 +1865,35 @@ int xdg_apply(xdg_hier_t h, int level, const double* x, double* y, int prec) {
     h->launches += 3;
   }
   CKL();
+  return XDG_OK;
+}
+
+int xdg_set_damping(xdg_hier_t h, int level, double omega) {
+  if (!h || level < 1 || level >= h->nlev || !(omega > 0.0) || !std::isfinite(omega)) {
+    set_err("xdg_set_damping: bad level %d or omega %g", level, omega);
+    return XDG_EINVAL;
+  }
+  if (h->nprob > 1) {
+    set_err("xdg_set_damping: not for the hierarchy of a batch group");
+    return XDG_EINVAL;
+  }
+  Level& V = h->L[level - 1];
+  V.omega = omega;
+  std::fill(V.omega_p.begin(), V.omega_p.end(), omega);
+  // the recorded graphs hold the damping as a kernel argument: record them again
+  TRY(h->capture(&h->g_iter, 1, nullptr, nullptr));
+  for (int p = 1; p < 3; ++p)
+    if (h->has_lp[p]) TRY(h->capture(&h->g_iter_lp[p], 3, nullptr, nullptr, p));
+  if (h->g_cycle) cudaGraphExecDestroy(h->g_cycle);
+  h->g_cycle = nullptr;
+  h->g_cycle_b = nullptr;
+  for (int p = 0; p < 3; ++p) {
+    if (h->g_cyc_lp[p]) cudaGraphExecDestroy(h->g_cyc_lp[p]);
+    h->g_cyc_lp[p] = nullptr;
+    h->g_cyc_lp_b[p] = nullptr;
+    if (h->lr.g_iter[p]) cudaGraphExecDestroy(h->lr.g_iter[p]);
+    h->lr.g_iter[p] = nullptr;
+  }
   return XDG_OK;
 }
 
@@ -1922,6 +2129,332 @@ int xdg_solve_batch_host(xdg_batch_t bt, const double* b_host, double* x_host, c
   CK(cudaStreamSynchronize(bt->stream));
   if (info) info->ms = ms_since(t0);
   return rc;
+}
+
+// ------------------------------------------------------------------------------ learned
+static inline uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+// uniform in [-1, 1) from a counter
+static inline double unit_uniform(uint64_t seed, uint64_t i) {
+  return (double)(splitmix64(seed * 0x100000001B3ull + i) >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+int xdg_mlp_create(int n_in, int n_out, uint64_t seed, void* stream, xdg_mlp_t* out) {
+  if (!out || n_in < 1 || n_in > 64 || n_out < 1 || n_out > 64) {
+    set_err("xdg_mlp_create: n_in = %d, n_out = %d (1..64 each)", n_in, n_out);
+    return XDG_EINVAL;
+  }
+  *out = nullptr;
+  std::unique_ptr<xdg_mlp> m(new xdg_mlp());
+  m->d = mlp_dims(n_in, n_out);
+  m->stream = static_cast<cudaStream_t>(stream);
+  if (!m->stream) {
+    CK(cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking));
+    m->own_stream = true;
+  }
+  const int tot = m->d.total;
+  TRY(m->alloc(&m->P, tot, m->allocs));
+  TRY(m->alloc(&m->m1, tot, m->allocs));
+  TRY(m->alloc(&m->m2, tot, m->allocs));
+  TRY(m->alloc(&m->grad, tot, m->allocs));
+  TRY(m->alloc(&m->partial, (size_t)m->nsl * tot, m->allocs));
+  TRY(m->alloc(&m->Pb, tot, m->allocs));
+  TRY(m->alloc(&m->dloss, 2, m->allocs));
+  CK(cudaMallocHost(&m->hloss, 2 * sizeof(double)));
+  // Glorot-uniform weights from a counter-based generator, zero biases
+  std::vector<float> h(tot, 0.0f);
+  const int fan[4][2] = {{n_in, kHid}, {kHid, kHid}, {kHid, kHid}, {kHid, n_out}};
+  const int off[4] = {m->d.oW1, m->d.oW2, m->d.oW3, m->d.oW4};
+  for (int l = 0; l < 4; ++l) {
+    const double a = std::sqrt(6.0 / (fan[l][0] + fan[l][1]));
+    for (int e = 0; e < fan[l][0] * fan[l][1]; ++e) h[off[l] + e] = (float)(a * unit_uniform(seed, off[l] + e));
+  }
+  CK(cudaMemcpyAsync(m->P, h.data(), tot * sizeof(float), cudaMemcpyHostToDevice, m->stream));
+  CK(cudaMemsetAsync(m->m1, 0, tot * sizeof(float), m->stream));
+  CK(cudaMemsetAsync(m->m2, 0, tot * sizeof(float), m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+  *out = m.release();
+  return XDG_OK;
+}
+
+int xdg_mlp_destroy(xdg_mlp_t m) {
+  delete m;
+  return XDG_OK;
+}
+
+int xdg_mlp_num_params(xdg_mlp_t m, int64_t* n) {
+  if (!m || !n) {
+    set_err("null argument");
+    return XDG_EINVAL;
+  }
+  *n = m->d.total;
+  return XDG_OK;
+}
+
+int xdg_mlp_get_params(xdg_mlp_t m, float* host, int64_t n) {
+  if (!m || !host || n != m->d.total) {
+    set_err("xdg_mlp_get_params: need %d entries", m ? m->d.total : 0);
+    return XDG_EINVAL;
+  }
+  CK(cudaMemcpyAsync(host, m->P, n * sizeof(float), cudaMemcpyDeviceToHost, m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+  return XDG_OK;
+}
+
+int xdg_mlp_set_params(xdg_mlp_t m, const float* host, int64_t n) {
+  if (!m || !host || n != m->d.total) {
+    set_err("xdg_mlp_set_params: need %d entries", m ? m->d.total : 0);
+    return XDG_EINVAL;
+  }
+  CK(cudaMemcpyAsync(m->P, host, n * sizeof(float), cudaMemcpyHostToDevice, m->stream));
+  CK(cudaMemsetAsync(m->m1, 0, n * sizeof(float), m->stream));
+  CK(cudaMemsetAsync(m->m2, 0, n * sizeof(float), m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+  m->step = 0;
+  return XDG_OK;
+}
+
+int xdg_mlp_forward(xdg_mlp_t m, int prec, int64_t n, const float* X, float* Y) {
+  if (!m || n < 0 || (n > 0 && (!X || !Y)) || (prec != XDG_PREC_F32 && prec != XDG_PREC_BF16)) {
+    set_err("xdg_mlp_forward: bad arguments");
+    return XDG_EINVAL;
+  }
+  if (n == 0) return XDG_OK;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, 152 * 4));
+  if (prec == XDG_PREC_F32) {
+    const size_t sm = (size_t)m->d.total * sizeof(float);
+    CK(cudaFuncSetAttribute(k_mlp_forward<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_mlp_forward<float><<<blocks, 256, sm, m->stream>>>(n, m->d, m->P, X, Y);
+  } else {
+    k_to_bf16<<<(m->d.total + 255) / 256, 256, 0, m->stream>>>(m->d.total, m->P, m->Pb);
+    const size_t sm = (size_t)m->d.total * sizeof(__nv_bfloat16);
+    CK(cudaFuncSetAttribute(k_mlp_forward<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_mlp_forward<__nv_bfloat16><<<blocks, 256, sm, m->stream>>>(n, m->d, m->Pb, X, Y);
+  }
+  CKL();
+  return XDG_OK;
+}
+
+int xdg_mlp_loss_grad(xdg_mlp_t m, int n, const float* X, const int32_t* uid, const float* Mloc, const float* R,
+                      const float* C, double* loss, float* grad) {
+  if (!m || n < 1 || !X || !uid || !Mloc || !R || !C) {
+    set_err("xdg_mlp_loss_grad: bad arguments");
+    return XDG_EINVAL;
+  }
+  TRY(m->loss_grad(n, nullptr, X, uid, Mloc, R, C));
+  if (grad) CK(cudaMemcpyAsync(grad, m->grad, m->d.total * sizeof(float), cudaMemcpyDeviceToDevice, m->stream));
+  CK(cudaMemcpyAsync(m->hloss, m->dloss, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+  if (loss) *loss = m->hloss[0] / n;
+  return XDG_OK;
+}
+
+int xdg_mlp_train(xdg_mlp_t m, int n, const float* X, const int32_t* uid, const float* Mloc, const float* R,
+                  const float* C, const xdg_train_opts* o, double* loss_per_epoch) {
+  if (!m || n < 1 || !X || !uid || !Mloc || !R || !C || !o || o->epochs < 1 || o->batch < 1) {
+    set_err("xdg_mlp_train: bad arguments");
+    return XDG_EINVAL;
+  }
+  const int B = std::min(o->batch, n);
+  TRY(m->ensure_idx(n));
+  TRY(m->ensure_batch(B));
+  std::vector<int32_t> perm(n);
+  const float b1 = o->beta1 > 0 ? o->beta1 : 0.9f, b2 = o->beta2 > 0 ? o->beta2 : 0.999f;
+  const float eps = o->eps > 0 ? o->eps : 1e-8f;
+  for (int ep = 0; ep < o->epochs; ++ep) {
+    // Fisher-Yates shuffle from a counter-based generator (seed, epoch)
+    for (int i = 0; i < n; ++i) perm[i] = i;
+    for (int i = n - 1; i > 0; --i) {
+      const uint64_t r = splitmix64(o->seed * 0x9E3779B97F4A7C15ull + (uint64_t)ep * 0x100000001ull + i);
+      std::swap(perm[i], perm[r % (uint64_t)(i + 1)]);
+    }
+    CK(cudaMemcpyAsync(m->idx, perm.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, m->stream));
+    CK(cudaMemsetAsync(m->dloss + 1, 0, sizeof(double), m->stream));
+    for (int s0 = 0; s0 < n; s0 += B) {
+      const int nb = std::min(B, n - s0);
+      TRY(m->loss_grad(nb, m->idx + s0, X, uid, Mloc, R, C));
+      k_sum_ordered<<<1, kThreads, 0, m->stream>>>(nb, m->T.loss, m->dloss + 1, 1);
+      m->step += 1;
+      const float bc1 = 1.f - std::pow(b1, (float)m->step), bc2 = 1.f - std::pow(b2, (float)m->step);
+      k_adam<<<(m->d.total + 255) / 256, 256, 0, m->stream>>>(m->d.total, m->P, m->grad, m->m1, m->m2, o->lr, b1, b2,
+                                                              eps, bc1, bc2);
+    }
+    CKL();
+    CK(cudaMemcpyAsync(m->hloss, m->dloss, 2 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaStreamSynchronize(m->stream));  // also keeps perm alive until its copy is done
+    if (loss_per_epoch) loss_per_epoch[ep] = m->hloss[1] / n;
+  }
+  return XDG_OK;
+}
+
+int xdg_units_setup(xdg_hier_t h, int n_units, const int32_t* pairs, int n_geo, const float* geom) {
+  if (!h || n_units < 1 || !pairs || n_geo < 0 || (n_geo > 0 && !geom) || n_geo + 2 * h->Np > 64) {
+    set_err("xdg_units_setup: bad arguments (n_units %d, n_geo %d, Np %d)", n_units, n_geo, h ? h->Np : 0);
+    return XDG_EINVAL;
+  }
+  Learned& U = h->lr;
+  if (U.U) {
+    set_err("xdg_units_setup: units already set");
+    return XDG_EINVAL;
+  }
+  if (!ops_u_for(h->Np, &U.ops)) {
+    set_err("xdg_units_setup: Np = %d not supported", h->Np);
+    return XDG_EINVAL;
+  }
+  Level& V = h->L[0];
+  const int Np = h->Np, m = 2 * Np;
+  std::vector<int64_t> zi((size_t)n_units * 4, -1);
+  auto find = [&](int64_t i, int64_t j) -> int64_t {
+    auto b = V.h_col.begin() + V.h_rp[i], e = V.h_col.begin() + V.h_rp[i + 1];
+    auto it = std::lower_bound(b, e, (int32_t)j);
+    return (it != e && *it == j) ? (int64_t)(it - V.h_col.begin()) : -1;
+  };
+  std::vector<std::vector<int32_t>> lists(V.nb);
+  for (int u = 0; u < n_units; ++u) {
+    const int64_t a = pairs[2 * u], b = pairs[2 * u + 1];
+    if (a < 0 || a >= V.nb || b < 0 || b >= V.nb || a == b) {
+      set_err("xdg_units_setup: unit %d = (%lld, %lld) invalid", u, (long long)a, (long long)b);
+      return XDG_EINVAL;
+    }
+    zi[4 * u] = find(a, a);
+    zi[4 * u + 1] = find(a, b);
+    zi[4 * u + 2] = find(b, a);
+    zi[4 * u + 3] = find(b, b);
+    lists[a].push_back(2 * u);
+    lists[b].push_back(2 * u + 1);
+  }
+  std::vector<int32_t> tb, tl;
+  std::vector<int64_t> tp(1, 0);
+  for (int64_t i = 0; i < V.nb; ++i)
+    if (!lists[i].empty()) {
+      tb.push_back((int32_t)i);
+      tl.insert(tl.end(), lists[i].begin(), lists[i].end());
+      tp.push_back((int64_t)tl.size());
+    }
+  U.U = n_units;
+  U.n_geo = n_geo;
+  U.nt = (int)tb.size();
+  TRY(h->alloc(&U.pairs, 2 * (size_t)n_units));
+  TRY(h->alloc(&U.geom, (size_t)n_units * std::max(n_geo, 1)));
+  TRY(h->alloc(&U.zidx, 4 * (size_t)n_units));
+  TRY(h->alloc(&U.Linv, (size_t)n_units * 2 * Np * Np));
+  TRY(h->alloc(&U.Hm, (size_t)n_units * m * m));
+  TRY(h->alloc(&U.Mloc, (size_t)n_units * m * m));
+  TRY(h->alloc(&U.Minv, (size_t)n_units * m * m));
+  TRY(h->alloc(&U.tblk, tb.size()));
+  TRY(h->alloc(&U.tptr, tp.size()));
+  TRY(h->alloc(&U.tlist, tl.size()));
+  TRY(h->alloc(&U.res, V.nb * (size_t)Np));
+  TRY(h->alloc(&U.delta, (size_t)n_units * m));
+  TRY(h->alloc(&U.E, (size_t)n_units));
+  TRY(h->alloc(&U.keep, (size_t)n_units));
+  cudaStream_t st = h->stream;
+  CK(cudaMemcpyAsync(U.pairs, pairs, 2 * (size_t)n_units * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  if (n_geo > 0)
+    CK(cudaMemcpyAsync(U.geom, geom, (size_t)n_units * n_geo * sizeof(float), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(U.zidx, zi.data(), zi.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(U.tblk, tb.data(), tb.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(U.tptr, tp.data(), tp.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(U.tlist, tl.data(), tl.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(U.res, 0, V.nb * (size_t)Np * sizeof(double), st));
+  int* derr = nullptr;
+  TRY(h->alloc(&derr, 1));
+  CK(cudaMemsetAsync(derr, 0, sizeof(int), st));
+  U.ops.factor(st, n_units, U.zidx, V.val, U.Linv, U.Hm, U.Mloc, U.Minv, derr);
+  CKL();
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (herr) {
+    set_err("xdg_units_setup: a unit matrix is not positive definite");
+    return XDG_EBREAKDOWN;
+  }
+  return XDG_OK;
+}
+
+int xdg_units_local(xdg_hier_t h, float* Mloc) {
+  if (!h || !h->lr.U || !Mloc) {
+    set_err("xdg_units_local: no units or null output");
+    return XDG_EINVAL;
+  }
+  const size_t m = 2 * (size_t)h->Np;
+  CK(cudaMemcpyAsync(Mloc, h->lr.Mloc, h->lr.U * m * m * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+  return XDG_OK;
+}
+
+int xdg_units_samples(xdg_hier_t h, int prec, const double* r, float* X, float* R, float* C) {
+  if (!h || !h->lr.U || !r || !X || !R || !C || prec < 0 || prec > 2 ||
+      (prec != XDG_PREC_F64 && !h->has_lp[prec])) {
+    set_err("xdg_units_samples: bad arguments, no units or precision %d not stored", prec);
+    return XDG_EINVAL;
+  }
+  Learned& U = h->lr;
+  Level& V = h->L[0];
+  // z = B r with the plain cycle, then the residual r - M z on the units' rows
+  double* z = h->s_q;  // solve work vector, free outside a solve
+  if (prec == XDG_PREC_F64) h->cycle(0, r, z);
+  else h->cycle_lp_d(prec, r, z);
+  U.ops.resid_rows(h->grid(U.nt), h->stream, U.nt, U.tblk, V.rp, V.col, V.val, z, r, U.res);
+  U.ops.samples(h->stream, U.U, U.n_geo, U.pairs, U.geom, U.res, U.Linv, U.Minv, X, R, C);
+  h->launches += 2;
+  CKL();
+  return XDG_OK;
+}
+
+int xdg_learned_enable(xdg_hier_t h, xdg_mlp_t m, double theta) {
+  if (!h) {
+    set_err("null hierarchy");
+    return XDG_EINVAL;
+  }
+  Learned& U = h->lr;
+  for (int p = 0; p < 3; ++p)
+    if (U.g_iter[p]) {
+      cudaGraphExecDestroy(U.g_iter[p]);
+      U.g_iter[p] = nullptr;
+    }
+  if (!m) {
+    U.on = false;
+    return XDG_OK;
+  }
+  if (!U.U || m->d.n_in != U.n_geo + 2 * h->Np || m->d.n_out != 2 * h->Np || !(theta > 0.0)) {
+    set_err("xdg_learned_enable: network %d -> %d does not fit units of %d features, Np %d (or theta <= 0)",
+            m->d.n_in, m->d.n_out, U.n_geo, h->Np);
+    return XDG_EINVAL;
+  }
+  if (U.wcap < m->d.total) {
+    TRY(h->alloc(&U.W, m->d.total));
+    U.wcap = m->d.total;
+  }
+  CK(cudaStreamSynchronize(m->stream));
+  k_to_bf16<<<(m->d.total + 255) / 256, 256, 0, h->stream>>>(m->d.total, m->P, U.W);
+  CKL();
+  CK(cudaStreamSynchronize(h->stream));
+  U.d = m->d;
+  U.theta = theta;
+  U.on = true;
+  return XDG_OK;
+}
+
+int xdg_learned_step(xdg_hier_t h, const double* r, double* z, int* n_kept) {
+  if (!h || !h->lr.on || !r || !z) {
+    set_err("xdg_learned_step: learned correction not enabled or null vectors");
+    return XDG_EINVAL;
+  }
+  h->learned_apply(r, z);
+  CKL();
+  if (n_kept) {
+    std::vector<int> k(h->lr.U);
+    CK(cudaMemcpyAsync(k.data(), h->lr.keep, h->lr.U * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    int c = 0;
+    for (int v : k) c += v;
+    *n_kept = c;
+  }
+  return XDG_OK;
 }
 
 }  // extern "C"

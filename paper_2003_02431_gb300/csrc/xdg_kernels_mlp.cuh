@@ -1,0 +1,592 @@
+// Learned cut-cell correction: a small MLP per unit (the two species blocks of one cut
+// background cell) maps the unit's geometry and residual to a correction of both blocks.
+//
+// Network: n_in -> 64 -> 64 -> 64 -> n_out (= 2 Np), GELU (erf form) on the hidden layers.
+// Flat parameters (row-major): W1[n_in][64] b1[64] W2[64][64] b2[64] W3[64][64] b3[64]
+// W4[64][n_out] b4[n_out]; a layer computes a_out = act(a_in W + b).
+//
+// Loss of a sample (unit u, residual r_u = s rhat, network output yhat, correction s yhat):
+// the change of the energy norm of the true error, ||e - delta||_M^2 - ||e||_M^2 =
+// delta^T M_uu delta - 2 delta^T r_u, divided by s^2 and by the optimal decrease
+// c = rhat^T M_uu^{-1} rhat:  L = (yhat^T M_uu yhat - 2 yhat^T rhat) / c  (-1: exact local solve).
+//
+// Mapping: one warp per sample; lane l owns hidden units l and l + 32 and outputs l, l + 32;
+// the layer inputs are broadcast by shuffles and the weights are read from shared memory
+// (consecutive lanes read consecutive weights). FLOPs are ~12k FMA per sample: the network
+// is tiny next to the solve and runs on the FP32 pipe; training gradients are summed over
+// samples in a fixed order (deterministic).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "xdg_kernels.cuh"
+
+namespace xdg {
+
+constexpr int kHid = 64;
+
+struct MlpDims {
+  int n_in, n_out;
+  int oW1, ob1, oW2, ob2, oW3, ob3, oW4, ob4, total;
+};
+
+inline MlpDims mlp_dims(int n_in, int n_out) {
+  MlpDims d;
+  d.n_in = n_in;
+  d.n_out = n_out;
+  d.oW1 = 0;
+  d.ob1 = n_in * kHid;
+  d.oW2 = d.ob1 + kHid;
+  d.ob2 = d.oW2 + kHid * kHid;
+  d.oW3 = d.ob2 + kHid;
+  d.ob3 = d.oW3 + kHid * kHid;
+  d.oW4 = d.ob3 + kHid;
+  d.ob4 = d.oW4 + kHid * n_out;
+  d.total = d.ob4 + n_out;
+  return d;
+}
+
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_df(float x) {
+  return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
+}
+
+__device__ __forceinline__ float wload(const float* p, int i) { return p[i]; }
+__device__ __forceinline__ float wload(const __nv_bfloat16* p, int i) { return __bfloat162float(p[i]); }
+
+// a_out(l), a_out(l+32) = (a_in W + b) for a hidden layer of width 64; a_in held as two
+// registers per lane (entries l and l + 32), n inputs
+template <class W>
+__device__ __forceinline__ void dense64(const W* __restrict__ w, const W* __restrict__ b, int n, float in0, float in1,
+                                        int lane, float& o0, float& o1) {
+  float a0 = wload(b, lane), a1 = wload(b, lane + 32);
+  for (int i = 0; i < n; ++i) {
+    const float xi = __shfl_sync(0xffffffffu, i < 32 ? in0 : in1, i & 31);
+    a0 = fmaf(wload(w, i * kHid + lane), xi, a0);
+    a1 = fmaf(wload(w, i * kHid + 32 + lane), xi, a1);
+  }
+  o0 = a0;
+  o1 = a1;
+}
+
+// output layer: y(j) for j = lane and lane + 32 (< n_out)
+template <class W>
+__device__ __forceinline__ void dense_out(const W* __restrict__ w, const W* __restrict__ b, int n_out, float in0,
+                                          float in1, int lane, float& y0, float& y1) {
+  const bool h0 = lane < n_out, h1 = lane + 32 < n_out;
+  float a0 = h0 ? wload(b, lane) : 0.f, a1 = h1 ? wload(b, lane + 32) : 0.f;
+  for (int i = 0; i < kHid; ++i) {
+    const float xi = __shfl_sync(0xffffffffu, i < 32 ? in0 : in1, i & 31);
+    if (h0) a0 = fmaf(wload(w, i * n_out + lane), xi, a0);
+    if (h1) a1 = fmaf(wload(w, i * n_out + 32 + lane), xi, a1);
+  }
+  y0 = a0;
+  y1 = a1;
+}
+
+template <class W>
+__device__ __forceinline__ void mlp_forward(const W* __restrict__ P, const MlpDims& d, float x0, float x1, int lane,
+                                            float* z, float* a, float& y0, float& y1) {
+  // z[0..5], a[0..5]: pre-activations and activations of the 3 hidden layers (2 per lane)
+  dense64(P + d.oW1, P + d.ob1, d.n_in, x0, x1, lane, z[0], z[1]);
+  a[0] = gelu_f(z[0]);
+  a[1] = gelu_f(z[1]);
+  dense64(P + d.oW2, P + d.ob2, kHid, a[0], a[1], lane, z[2], z[3]);
+  a[2] = gelu_f(z[2]);
+  a[3] = gelu_f(z[3]);
+  dense64(P + d.oW3, P + d.ob3, kHid, a[2], a[3], lane, z[4], z[5]);
+  a[4] = gelu_f(z[4]);
+  a[5] = gelu_f(z[5]);
+  dense_out(P + d.oW4, P + d.ob4, d.n_out, a[4], a[5], lane, y0, y1);
+}
+
+template <class W>
+__device__ void stage_params(W* sp, const W* __restrict__ P, int total) {
+  for (int i = threadIdx.x; i < total; i += blockDim.x) sp[i] = P[i];
+  __syncthreads();
+}
+
+// Y[s] = network(X[s]) (inference or parity checks); W = float or bf16 parameters
+template <class W>
+__global__ void __launch_bounds__(256) k_mlp_forward(int64_t n, MlpDims d, const W* __restrict__ P,
+                                                    const float* __restrict__ X, float* __restrict__ Y) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  W* sp = reinterpret_cast<W*>(smem_raw);
+  stage_params(sp, P, d.total);
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < n; s += nw) {
+    const float* x = X + s * d.n_in;
+    const float x0 = lane < d.n_in ? x[lane] : 0.f, x1 = lane + 32 < d.n_in ? x[lane + 32] : 0.f;
+    float z[6], a[6], y0, y1;
+    mlp_forward(sp, d, x0, x1, lane, z, a, y0, y1);
+    if (lane < d.n_out) Y[s * d.n_out + lane] = y0;
+    if (lane + 32 < d.n_out) Y[s * d.n_out + lane + 32] = y1;
+  }
+}
+
+// One training pass over the samples idx[0..n) (idx == nullptr: 0..n-1): forward, loss and
+// backward of every sample. Writes per sample s (position in the batch): A1..A3, dZ1..dZ3
+// ([n][64] each), dY ([n][n_out]) and its loss; the gradient is the mean over the batch
+// (dY carries the factor 1 / n).
+struct MlpTrainBuf {
+  float *A1, *A2, *A3, *dZ1, *dZ2, *dZ3, *dY;
+  double* loss;
+};
+
+__global__ void __launch_bounds__(256) k_mlp_train_pass(int n, const int32_t* __restrict__ idx, MlpDims d,
+                                                       const float* __restrict__ P, const float* __restrict__ X,
+                                                       const int32_t* __restrict__ uid,
+                                                       const float* __restrict__ Mloc,
+                                                       const float* __restrict__ R, const float* __restrict__ C,
+                                                       MlpTrainBuf T) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* sp = reinterpret_cast<float*>(smem_raw);
+  float* w4t = sp + d.total;            // W4^T [n_out][64]
+  float* w3t = w4t + d.n_out * kHid;    // W3^T [64][64]
+  float* w2t = w3t + kHid * kHid;       // W2^T [64][64]
+  for (int i = threadIdx.x; i < d.total; i += blockDim.x) sp[i] = P[i];
+  for (int e = threadIdx.x; e < kHid * d.n_out; e += blockDim.x) {
+    const int i = e / d.n_out, j = e - i * d.n_out;
+    w4t[j * kHid + i] = P[d.oW4 + e];
+  }
+  for (int e = threadIdx.x; e < kHid * kHid; e += blockDim.x) {
+    const int i = e >> 6, j = e & 63;
+    w3t[j * kHid + i] = P[d.oW3 + e];
+    w2t[j * kHid + i] = P[d.oW2 + e];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int m = d.n_out;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < n; s += nw) {
+    const int g = idx ? idx[s] : s;
+    const float* x = X + (int64_t)g * d.n_in;
+    const float x0 = lane < d.n_in ? x[lane] : 0.f, x1 = lane + 32 < d.n_in ? x[lane + 32] : 0.f;
+    float z[6], a[6], y0, y1;
+    mlp_forward(sp, d, x0, x1, lane, z, a, y0, y1);
+    // loss and dL/dy
+    const float* M = Mloc + (int64_t)uid[g] * m * m;
+    const float* r = R + (int64_t)g * m;
+    const float c = C[g];
+    float my0 = 0.f, my1 = 0.f;
+    for (int k = 0; k < m; ++k) {
+      const float yk = __shfl_sync(0xffffffffu, k < 32 ? y0 : y1, k & 31);
+      if (lane < m) my0 = fmaf(M[lane * m + k], yk, my0);
+      if (lane + 32 < m) my1 = fmaf(M[(lane + 32) * m + k], yk, my1);
+    }
+    const float r0 = lane < m ? r[lane] : 0.f, r1 = lane + 32 < m ? r[lane + 32] : 0.f;
+    float part = (lane < m ? y0 * (my0 - 2.f * r0) : 0.f) + (lane + 32 < m ? y1 * (my1 - 2.f * r1) : 0.f);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    const float sc = 2.f / (c * (float)n);
+    const float dy0 = lane < m ? sc * (my0 - r0) : 0.f, dy1 = lane + 32 < m ? sc * (my1 - r1) : 0.f;
+    // backward
+    float da0 = 0.f, da1 = 0.f;
+    for (int j = 0; j < m; ++j) {
+      const float gj = __shfl_sync(0xffffffffu, j < 32 ? dy0 : dy1, j & 31);
+      da0 = fmaf(w4t[j * kHid + lane], gj, da0);
+      da1 = fmaf(w4t[j * kHid + 32 + lane], gj, da1);
+    }
+    const float d30 = da0 * gelu_df(z[4]), d31 = da1 * gelu_df(z[5]);
+    da0 = da1 = 0.f;
+    for (int j = 0; j < kHid; ++j) {
+      const float gj = __shfl_sync(0xffffffffu, j < 32 ? d30 : d31, j & 31);
+      da0 = fmaf(w3t[j * kHid + lane], gj, da0);
+      da1 = fmaf(w3t[j * kHid + 32 + lane], gj, da1);
+    }
+    const float d20 = da0 * gelu_df(z[2]), d21 = da1 * gelu_df(z[3]);
+    da0 = da1 = 0.f;
+    for (int j = 0; j < kHid; ++j) {
+      const float gj = __shfl_sync(0xffffffffu, j < 32 ? d20 : d21, j & 31);
+      da0 = fmaf(w2t[j * kHid + lane], gj, da0);
+      da1 = fmaf(w2t[j * kHid + 32 + lane], gj, da1);
+    }
+    const float d10 = da0 * gelu_df(z[0]), d11 = da1 * gelu_df(z[1]);
+    const int64_t o = (int64_t)s * kHid;
+    T.A1[o + lane] = a[0];
+    T.A1[o + 32 + lane] = a[1];
+    T.A2[o + lane] = a[2];
+    T.A2[o + 32 + lane] = a[3];
+    T.A3[o + lane] = a[4];
+    T.A3[o + 32 + lane] = a[5];
+    T.dZ1[o + lane] = d10;
+    T.dZ1[o + 32 + lane] = d11;
+    T.dZ2[o + lane] = d20;
+    T.dZ2[o + 32 + lane] = d21;
+    T.dZ3[o + lane] = d30;
+    T.dZ3[o + 32 + lane] = d31;
+    if (lane < m) T.dY[(int64_t)s * m + lane] = dy0;
+    if (lane + 32 < m) T.dY[(int64_t)s * m + 32 + lane] = dy1;
+    if (lane == 0) T.loss[s] = (double)(part / c);
+  }
+}
+
+// partial[sl][p] = sum over the samples of slice sl of dL/dparam p (fixed order within slices)
+__global__ void __launch_bounds__(256) k_mlp_grad_partial(int n, int nsl, const int32_t* __restrict__ idx, MlpDims d,
+                                                         const float* __restrict__ X, MlpTrainBuf T,
+                                                         float* __restrict__ partial) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int sl = blockIdx.y;
+  if (p >= d.total) return;
+  const int s0 = (int)((int64_t)n * sl / nsl), s1 = (int)((int64_t)n * (sl + 1) / nsl);
+  // which layer and entry
+  const float *A = nullptr, *G = nullptr;
+  int i = -1, j, ncol = kHid, in_x = 0;
+  if (p < d.ob1) {
+    i = p / kHid; j = p - i * kHid; G = T.dZ1; in_x = 1;
+  } else if (p < d.oW2) {
+    j = p - d.ob1; G = T.dZ1;
+  } else if (p < d.ob2) {
+    const int e = p - d.oW2; i = e / kHid; j = e - i * kHid; A = T.A1; G = T.dZ2;
+  } else if (p < d.oW3) {
+    j = p - d.ob2; G = T.dZ2;
+  } else if (p < d.ob3) {
+    const int e = p - d.oW3; i = e / kHid; j = e - i * kHid; A = T.A2; G = T.dZ3;
+  } else if (p < d.oW4) {
+    j = p - d.ob3; G = T.dZ3;
+  } else if (p < d.ob4) {
+    const int e = p - d.oW4; i = e / d.n_out; j = e - i * d.n_out; A = T.A3; G = T.dY; ncol = d.n_out;
+  } else {
+    j = p - d.ob4; G = T.dY; ncol = d.n_out;
+  }
+  float acc = 0.f;
+  for (int s = s0; s < s1; ++s) {
+    const float gj = G[(int64_t)s * ncol + j];
+    float ai = 1.f;
+    if (i >= 0) ai = in_x ? X[(int64_t)(idx ? idx[s] : s) * d.n_in + i] : A[(int64_t)s * kHid + i];
+    acc = fmaf(ai, gj, acc);
+  }
+  partial[(int64_t)sl * d.total + p] = acc;
+}
+
+__global__ void k_mlp_grad_final(int total, int nsl, const float* __restrict__ partial, float* __restrict__ grad) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= total) return;
+  float acc = 0.f;
+  for (int sl = 0; sl < nsl; ++sl) acc += partial[(int64_t)sl * total + p];
+  grad[p] = acc;
+}
+
+// Adam (Kingma & Ba) with bias correction; t = step number (1-based)
+__global__ void k_adam(int total, float* __restrict__ P, const float* __restrict__ G, float* __restrict__ m1,
+                       float* __restrict__ m2, float lr, float b1, float b2, float eps, float bc1, float bc2) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= total) return;
+  const float g = G[p];
+  const float a = b1 * m1[p] + (1.f - b1) * g;
+  const float v = b2 * m2[p] + (1.f - b2) * g * g;
+  m1[p] = a;
+  m2[p] = v;
+  P[p] -= lr * (a / bc1) / (sqrtf(v / bc2) + eps);
+}
+
+__global__ void k_to_bf16(int total, const float* __restrict__ P, __nv_bfloat16* __restrict__ Q) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < total) Q[p] = __float2bfloat16_rn(P[p]);
+}
+
+// sum of n doubles in index order by one CTA (each thread a contiguous range, then the block
+// sum in a fixed tree)
+__global__ void __launch_bounds__(kThreads) k_sum_ordered(int n, const double* __restrict__ v, double* __restrict__ out,
+                                                         int accumulate) {
+  const int per = (n + blockDim.x - 1) / blockDim.x;
+  const int i0 = threadIdx.x * per, i1 = min(n, i0 + per);
+  double acc = 0.0;
+  for (int i = i0; i < i1; ++i) acc += v[i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) *out = accumulate ? *out + acc : acc;
+}
+
+// ------------------------------------------------------------------------------------------
+// units on the hierarchy
+
+// warp helpers on small shared-memory matrices (row stride ld)
+// in-place lower Cholesky factor of A[0..n)[0..n); false if not positive definite
+__device__ bool warp_chol(double* A, int n, int ld, int lane) {
+  bool ok = true;
+  for (int j = 0; j < n; ++j) {
+    const double djj = A[j * ld + j];
+    if (!(djj > 0.0)) ok = false;
+    const double d = sqrt(djj > 0.0 ? djj : 1.0);
+    __syncwarp();
+    for (int i = j + 1 + lane; i < n; i += 32) A[i * ld + j] /= d;
+    if (lane == 0) A[j * ld + j] = d;
+    __syncwarp();
+    for (int i = j + 1 + lane; i < n; i += 32)
+      for (int k = j + 1; k <= i; ++k) A[i * ld + k] -= A[i * ld + j] * A[k * ld + j];
+    __syncwarp();
+  }
+  return ok;
+}
+// X = L^{-1} for the lower factor L (columns owned by lanes)
+__device__ void warp_trinv(const double* L, int ldl, double* X, int ldx, int n, int lane) {
+  for (int c = lane; c < n; c += 32)
+    for (int i = 0; i < n; ++i) {
+      if (i < c) {
+        X[i * ldx + c] = 0.0;
+        continue;
+      }
+      double v = (i == c) ? 1.0 : 0.0;
+      for (int k = c; k < i; ++k) v -= L[i * ldl + k] * X[k * ldx + c];
+      X[i * ldx + c] = v / L[i * ldl + i];
+    }
+  __syncwarp();
+}
+
+// Per unit (one warp): the inverse Cholesky factors X_a = L_a^{-1}, X_b = L_b^{-1} of the
+// diagonal blocks M_aa, M_bb; the unit matrix in these coordinates,
+// H = diag(X_a, X_b) M_uu diag(X_a, X_b)^T (identity diagonal blocks), in FP64 (Hm) and FP32
+// (Mloc); and H^{-1} (Hinv). zidx[u][0..3]: positions of the blocks (a,a), (a,b), (b,a), (b,b)
+// in val (-1: zero block). err: set when a matrix is not positive definite.
+template <int NP>
+__global__ void __launch_bounds__(32) k_unit_factor(int U, const int64_t* __restrict__ zidx,
+                                                    const double* __restrict__ val, double* __restrict__ Linv,
+                                                    double* __restrict__ Hm, float* __restrict__ Mloc,
+                                                    double* __restrict__ Hinv, int* err) {
+  constexpr int m = 2 * NP, ld = m + 1;
+  __shared__ double A[m * ld];
+  __shared__ double W[m * ld];
+  __shared__ double X[m * ld];
+  const int u = blockIdx.x, lane = threadIdx.x;
+  if (u >= U) return;
+  for (int e = lane; e < m * m; e += 32) {
+    const int r = e / m, c = e - r * m;
+    const int q = (r >= NP) * 2 + (c >= NP);
+    const int64_t z = zidx[(int64_t)u * 4 + q];
+    A[r * ld + c] = z >= 0 ? val[z * NP * NP + (r % NP) * NP + (c % NP)] : 0.0;
+    X[r * ld + c] = 0.0;
+  }
+  __syncwarp();
+  bool ok = true;
+  for (int h = 0; h < 2; ++h) {
+    const int o = h * NP;
+    for (int e = lane; e < NP * NP; e += 32) {
+      const int r = e / NP, c = e - r * NP;
+      W[r * ld + c] = A[(o + r) * ld + o + c];
+    }
+    __syncwarp();
+    ok = warp_chol(W, NP, ld, lane) && ok;
+    warp_trinv(W, ld, X + o * ld + o, ld, NP, lane);
+  }
+  for (int e = lane; e < 2 * NP * NP; e += 32) {
+    const int h = e / (NP * NP), q = e - h * NP * NP, r = q / NP, c = q - r * NP;
+    Linv[(int64_t)u * 2 * NP * NP + e] = X[(h * NP + r) * ld + h * NP + c];
+  }
+  // W = X A, then A = W X^T = H
+  for (int e = lane; e < m * m; e += 32) {
+    const int r = e / m, c = e - r * m;
+    const int o = (r >= NP) ? NP : 0;
+    double acc = 0.0;
+    for (int k = o; k <= r; ++k) acc += X[r * ld + k] * A[k * ld + c];
+    W[r * ld + c] = acc;
+  }
+  __syncwarp();
+  for (int e = lane; e < m * m; e += 32) {
+    const int r = e / m, c = e - r * m;
+    const int o = (c >= NP) ? NP : 0;
+    double acc = 0.0;
+    for (int k = o; k <= c; ++k) acc += W[r * ld + k] * X[c * ld + k];
+    A[r * ld + c] = acc;
+  }
+  __syncwarp();
+  for (int e = lane; e < m * m; e += 32) {
+    const int r = e / m, c = e - r * m;
+    const double v = 0.5 * (A[r * ld + c] + A[c * ld + r]);  // exact symmetry
+    Hm[(int64_t)u * m * m + e] = v;
+    Mloc[(int64_t)u * m * m + e] = (float)v;
+    W[r * ld + c] = v;
+  }
+  __syncwarp();
+  ok = warp_chol(W, m, ld, lane) && ok;
+  warp_trinv(W, ld, X, ld, m, lane);
+  for (int e = lane; e < m * m; e += 32) {
+    const int r = e / m, c = e - r * m;
+    double acc = 0.0;
+    for (int k = (r > c ? r : c); k < m; ++k) acc += X[k * ld + r] * X[k * ld + c];
+    Hinv[(int64_t)u * m * m + e] = acc;
+  }
+  if (!ok && lane == 0) atomicOr(err, 1);
+}
+
+// y[i] = b[i] - (M x)[i] for the listed block rows i = rows[t]
+template <int NP>
+__global__ void __launch_bounds__(kThreads) k_resid_rows(int64_t nr, const int32_t* __restrict__ rows,
+                                                        const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                        const double* __restrict__ val, const double* __restrict__ x,
+                                                        const double* __restrict__ b, double* __restrict__ y) {
+  constexpr int GPW = Grp<NP>::GPW;
+  const int lane = threadIdx.x & 31;
+  const int g = lane / NP, r = lane - g * NP;
+  if (g >= GPW) return;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = warp * GPW + g; t < nr; t += nw * GPW) {
+    const int64_t i = rows[t];
+    const double acc = row_dot<NP>(__ldg(rp + i), __ldg(rp + i + 1), r, col, val, x);
+    y[i * NP + r] = b[i * NP + r] - acc;
+  }
+}
+
+// one unit's residual in block-Jacobi coordinates, rt = [X_a r_a; X_b r_b]: entries lane and
+// lane + 32, and s = ||rt||_2
+template <int NP>
+__device__ __forceinline__ void unit_residual(const int32_t* __restrict__ pairs, const double* __restrict__ Linv,
+                                              int u, const double* __restrict__ r, int lane, double& r0, double& r1,
+                                              double& s) {
+  constexpr int m = 2 * NP;
+  const int blk[2] = {pairs[2 * u], pairs[2 * u + 1]};
+  const double* X = Linv + (int64_t)u * 2 * NP * NP;
+  double out[2] = {0.0, 0.0};
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const int e = lane + 32 * t;
+    if (e < m) {
+      const int h = e / NP, i = e - h * NP;
+      const double* xr = X + h * NP * NP + i * NP;
+      const double* rv = r + (int64_t)blk[h] * NP;
+      double acc = 0.0;
+      for (int k = 0; k <= i; ++k) acc = fma(xr[k], rv[k], acc);
+      out[t] = acc;
+    }
+  }
+  r0 = out[0];
+  r1 = out[1];
+  double q = r0 * r0 + r1 * r1;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+  s = sqrt(q);
+}
+
+// network input entry k of unit u: geometry features, then rhat
+__device__ __forceinline__ float unit_input(const float* __restrict__ geom, int n_geo, int u, int k, double r0,
+                                            double r1, double inv_s, int lane) {
+  // every lane evaluates the shuffles (all lanes participate)
+  const int j = k - n_geo;
+  const double rj0 = __shfl_sync(0xffffffffu, r0, (j < 0 ? 0 : j) & 31);
+  const double rj1 = __shfl_sync(0xffffffffu, r1, (j < 0 ? 0 : j) & 31);
+  if (k < n_geo) return geom[(int64_t)u * n_geo + k];
+  return (float)((j < 32 ? rj0 : rj1) * inv_s);
+}
+
+// training samples of every unit for the residual r (after a cycle): with rt the residual in
+// block-Jacobi coordinates and rhat = rt / ||rt||: X[u] = [geom, rhat], R[u] = rhat,
+// C[u] = rhat^T H^{-1} rhat (0 for a zero residual)
+template <int NP>
+__global__ void __launch_bounds__(256) k_unit_samples(int U, int n_geo, const int32_t* __restrict__ pairs,
+                                                     const float* __restrict__ geom, const double* __restrict__ r,
+                                                     const double* __restrict__ Linv, const double* __restrict__ Minv,
+                                                     float* __restrict__ X, float* __restrict__ R,
+                                                     float* __restrict__ C) {
+  constexpr int m = 2 * NP;
+  const int lane = threadIdx.x & 31;
+  const int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (u >= U) return;
+  double r0, r1, s;
+  unit_residual<NP>(pairs, Linv, u, r, lane, r0, r1, s);
+  const double inv = s > 0.0 ? 1.0 / s : 0.0;
+  const int n_in = n_geo + m;
+  for (int k0 = 0; k0 < n_in; k0 += 32) {
+    const int k = k0 + lane;
+    float v = unit_input(geom, n_geo, u, k < n_in ? k : 0, r0, r1, inv, lane);
+    if (k < n_in) X[(int64_t)u * n_in + k] = v;
+  }
+  if (lane < m) R[(int64_t)u * m + lane] = (float)(r0 * inv);
+  if (lane + 32 < m) R[(int64_t)u * m + lane + 32] = (float)(r1 * inv);
+  // c = rhat^T Minv rhat (rows lane and lane + 32 of Minv rhat, then a warp sum)
+  const double* Mi = Minv + (int64_t)u * m * m;
+  double row0 = 0.0, row1 = 0.0;
+  for (int k = 0; k < m; ++k) {
+    const double rk = __shfl_sync(0xffffffffu, k < 32 ? r0 : r1, k & 31) * inv;
+    if (lane < m) row0 = fma(Mi[lane * m + k], rk, row0);
+    if (lane + 32 < m) row1 = fma(Mi[(lane + 32) * m + k], rk, row1);
+  }
+  double q = (lane < m ? row0 * r0 * inv : 0.0) + (lane + 32 < m ? row1 * r1 * inv : 0.0);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+  if (lane == 0) C[u] = (float)q;
+}
+
+// learned correction of every unit for the residual r (after the cycle): y = network([geom,
+// rhat]) with BF16 parameters (FP32 arithmetic), rhat = rt / s; the correction in block-Jacobi
+// coordinates is s y, i.e. delta = s [X_a^T y_a; X_b^T y_b]. Kept when it lowers the error's
+// energy: E = s^2 (y^T H y - 2 y^T rhat) = delta^T M_uu delta - 2 delta^T r_u < 0 (FP64).
+// delta[u][0..m) = kept correction (zeros otherwise), keep[u], E[u].
+template <int NP>
+__global__ void __launch_bounds__(256) k_unit_apply(int U, MlpDims d, int n_geo, const int32_t* __restrict__ pairs,
+                                                   const float* __restrict__ geom, const double* __restrict__ r,
+                                                   const __nv_bfloat16* __restrict__ P,
+                                                   const double* __restrict__ Linv, const double* __restrict__ Hm,
+                                                   double* __restrict__ delta, int* __restrict__ keep,
+                                                   double* __restrict__ E) {
+  constexpr int m = 2 * NP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __nv_bfloat16* sp = reinterpret_cast<__nv_bfloat16*>(smem_raw);
+  stage_params(sp, P, d.total);
+  const int lane = threadIdx.x & 31;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < U; u += nw) {
+    double r0, r1, s;
+    unit_residual<NP>(pairs, Linv, u, r, lane, r0, r1, s);
+    const double inv = s > 0.0 ? 1.0 / s : 0.0;
+    const float x0 = unit_input(geom, n_geo, u, lane < d.n_in ? lane : 0, r0, r1, inv, lane);
+    const float x1 = unit_input(geom, n_geo, u, lane + 32 < d.n_in ? lane + 32 : 0, r0, r1, inv, lane);
+    float z[6], a[6], y0, y1;
+    mlp_forward(sp, d, lane < d.n_in ? x0 : 0.f, lane + 32 < d.n_in ? x1 : 0.f, lane, z, a, y0, y1);
+    const double yd0 = lane < m ? (double)y0 : 0.0, yd1 = lane + 32 < m ? (double)y1 : 0.0;
+    // energy in block-Jacobi coordinates
+    const double* H = Hm + (int64_t)u * m * m;
+    double hy0 = 0.0, hy1 = 0.0;
+    for (int k = 0; k < m; ++k) {
+      const double yk = __shfl_sync(0xffffffffu, k < 32 ? yd0 : yd1, k & 31);
+      if (lane < m) hy0 = fma(H[lane * m + k], yk, hy0);
+      if (lane + 32 < m) hy1 = fma(H[(lane + 32) * m + k], yk, hy1);
+    }
+    double e = yd0 * (hy0 - 2.0 * r0 * inv) + yd1 * (hy1 - 2.0 * r1 * inv);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    e *= s * s;
+    const bool k_ = (e < 0.0) && (s > 0.0);
+    // delta = s X^T y per half: delta_h[i] = s sum_{j >= i} X_h[j][i] y_h[j]
+    const double* Xu = Linv + (int64_t)u * 2 * NP * NP;
+    double dl[2] = {0.0, 0.0};
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int e2 = lane + 32 * t;
+      const int h = (e2 < m ? e2 : 0) / NP, i = (e2 < m ? e2 : 0) - h * NP;
+      double acc = 0.0;
+      for (int j = 0; j < NP; ++j) {
+        const int src = h * NP + j;
+        const double yj = __shfl_sync(0xffffffffu, src < 32 ? yd0 : yd1, src & 31);
+        if (j >= i) acc = fma(Xu[h * NP * NP + j * NP + i], yj, acc);
+      }
+      dl[t] = s * acc;
+    }
+    if (lane < m) delta[(int64_t)u * m + lane] = k_ ? dl[0] : 0.0;
+    if (lane + 32 < m) delta[(int64_t)u * m + lane + 32] = k_ ? dl[1] : 0.0;
+    if (lane == 0) {
+      keep[u] = k_;
+      E[u] = e;
+    }
+  }
+}
+
+// z[t] += theta * sum of the kept corrections of the units holding block t
+// (tlist[tptr[i] .. tptr[i+1]) = 2 u + half for touched block tblk[i], ascending u)
+template <int NP>
+__global__ void k_unit_gather(int nt, const int32_t* __restrict__ tblk, const int64_t* __restrict__ tptr,
+                              const int32_t* __restrict__ tlist, const double* __restrict__ delta, double theta,
+                              double* __restrict__ z) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)nt * NP) return;
+  const int i = (int)(e / NP), c = (int)(e - (int64_t)i * NP);
+  double acc = 0.0;
+  for (int64_t q = tptr[i]; q < tptr[i + 1]; ++q) {
+    const int uh = tlist[q];
+    acc += delta[(int64_t)(uh >> 1) * 2 * NP + (uh & 1) * NP + c];
+  }
+  z[(int64_t)tblk[i] * NP + c] += theta * acc;
+}
+
+}  // namespace xdg

@@ -20,6 +20,7 @@ _ROOT = os.path.dirname(_HERE)
 LIB_PATH = os.path.join(_HERE, "libxdg.so")
 _SRCS = [os.path.join(_HERE, "csrc", "xdg.cu"), os.path.join(_HERE, "csrc", "xdg_kernels.cuh"),
          os.path.join(_HERE, "csrc", "xdg_kernels_lp.cuh"), os.path.join(_HERE, "csrc", "xdg_kernels_batch.cuh"),
+         os.path.join(_HERE, "csrc", "xdg_kernels_mlp.cuh"),
          os.path.join(_ROOT, "include", "xdg.h")]
 
 XDG_OK, XDG_EINVAL, XDG_ECUDA, XDG_ENOMEM, XDG_ENOTCONV, XDG_EBREAKDOWN, XDG_ETIMEOUT = range(7)
@@ -82,6 +83,11 @@ class HierInfo(C.Structure):
                 ("device_bytes", C.c_size_t), ("setup_ms", C.c_double * 3)]
 
 
+class TrainOpts(C.Structure):
+    _fields_ = [("epochs", C.c_int), ("batch", C.c_int), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("seed", C.c_uint64)]
+
+
 class BatchResult(C.Structure):
     _fields_ = [("iterations", C.c_int), ("status", C.c_int), ("relres", C.c_double)]
 
@@ -103,6 +109,7 @@ SIGNATURES = [
     ("xdg_export_level", C.c_int, [_vp, _ip, C.POINTER(C.c_int64), C.POINTER(C.c_int32), _dp]),
     ("xdg_apply", C.c_int, [_vp, _ip, _vp, _vp, _ip]),
     ("xdg_smooth", C.c_int, [_vp, _ip, _vp, _vp, _vp]),
+    ("xdg_set_damping", C.c_int, [_vp, _ip, C.c_double]),
     ("xdg_restrict", C.c_int, [_vp, _ip, _vp, _vp, _vp]),
     ("xdg_prolong", C.c_int, [_vp, _ip, _vp, _vp, _vp]),
     ("xdg_coarse_solve", C.c_int, [_vp, _vp, _vp]),
@@ -113,6 +120,19 @@ SIGNATURES = [
     ("xdg_restrict_noalloc", C.c_int, [_ip, C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                       _vp]),
     ("xdg_fma_peak", C.c_int, [_ip, _dp]),
+    ("xdg_mlp_create", C.c_int, [_ip, _ip, C.c_uint64, _vp, C.POINTER(_vp)]),
+    ("xdg_mlp_destroy", C.c_int, [_vp]),
+    ("xdg_mlp_num_params", C.c_int, [_vp, C.POINTER(C.c_int64)]),
+    ("xdg_mlp_get_params", C.c_int, [_vp, C.POINTER(C.c_float), C.c_int64]),
+    ("xdg_mlp_set_params", C.c_int, [_vp, C.POINTER(C.c_float), C.c_int64]),
+    ("xdg_mlp_forward", C.c_int, [_vp, _ip, C.c_int64, _vp, _vp]),
+    ("xdg_mlp_loss_grad", C.c_int, [_vp, _ip, _vp, _vp, _vp, _vp, _vp, _dp, _vp]),
+    ("xdg_mlp_train", C.c_int, [_vp, _ip, _vp, _vp, _vp, _vp, _vp, C.POINTER(TrainOpts), _dp]),
+    ("xdg_units_setup", C.c_int, [_vp, _ip, C.POINTER(C.c_int32), _ip, C.POINTER(C.c_float)]),
+    ("xdg_units_local", C.c_int, [_vp, _vp]),
+    ("xdg_units_samples", C.c_int, [_vp, _ip, _vp, _vp, _vp, _vp]),
+    ("xdg_learned_enable", C.c_int, [_vp, _vp, C.c_double]),
+    ("xdg_learned_step", C.c_int, [_vp, _vp, _vp, C.POINTER(C.c_int)]),
     ("xdg_create_batch", C.c_int, [_ip, C.POINTER(Problem), C.POINTER(HierOpts), _vp, C.POINTER(_vp)]),
     ("xdg_batch_destroy", C.c_int, [_vp]),
     ("xdg_batch_get_info", C.c_int, [_vp, C.POINTER(BatchInfo)]),
@@ -160,6 +180,15 @@ def _dptr(t):
         return None
     if not (t.is_cuda and t.is_contiguous() and t.dtype == _torch().float64):
         raise ValueError("expected a contiguous float64 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _fptr(t, dtype=None):
+    """device pointer of a contiguous CUDA tensor of float32 (or `dtype`)"""
+    torch = _torch()
+    dt = dtype or torch.float32
+    if not (t.is_cuda and t.is_contiguous() and t.dtype == dt):
+        raise ValueError("expected a contiguous %s CUDA tensor" % dt)
     return C.c_void_p(t.data_ptr())
 
 
@@ -264,6 +293,10 @@ class Hierarchy:
         with _Ordered(self):
             _check(load().xdg_apply(self._h, level, _dptr(x), _dptr(y), prec))
 
+    def set_damping(self, level, omega):
+        with _Ordered(self):
+            _check(load().xdg_set_damping(self._h, level, omega))
+
     def smooth(self, level, b, x_in, x_out):
         with _Ordered(self):
             _check(load().xdg_smooth(self._h, level, _dptr(b), _dptr(x_in), _dptr(x_out)))
@@ -314,6 +347,48 @@ class Hierarchy:
             _check(rc)
         return {"iterations": info.iterations, "outer": info.outer, "relres": info.relres,
                 "ms": info.ms, "status": rc, "launches": info.launches}
+
+    # ------------------------------------------------------------------ learned correction
+    def units_setup(self, pairs, geom):
+        """pairs int32 [U][2] (A block, B block of a cut cell), geom float32 [U][n_geo]."""
+        pairs = np.ascontiguousarray(pairs, np.int32)
+        geom = np.ascontiguousarray(geom, np.float32)
+        self.n_units, self.n_geo = pairs.shape[0], (geom.shape[1] if geom.ndim == 2 else 0)
+        with _Ordered(self):
+            _check(load().xdg_units_setup(self._h, self.n_units, pairs.ctypes.data_as(C.POINTER(C.c_int32)),
+                                          self.n_geo, geom.ctypes.data_as(C.POINTER(C.c_float))))
+
+    def units_local(self):
+        """FP32 unit matrices [U][2Np][2Np] (CUDA tensor)."""
+        torch = _torch()
+        m = 2 * self.Np
+        out = torch.empty((self.n_units, m, m), dtype=torch.float32, device=self.stream.device)
+        with _Ordered(self):
+            _check(load().xdg_units_local(self._h, _fptr(out)))
+        return out
+
+    def units_samples(self, r, prec=XDG_PREC_F64):
+        """(X, R, C) CUDA tensors of the training samples of all units for right-hand side r."""
+        torch = _torch()
+        m = 2 * self.Np
+        dev = self.stream.device
+        X = torch.empty((self.n_units, self.n_geo + m), dtype=torch.float32, device=dev)
+        R = torch.empty((self.n_units, m), dtype=torch.float32, device=dev)
+        Cc = torch.empty((self.n_units,), dtype=torch.float32, device=dev)
+        with _Ordered(self):
+            _check(load().xdg_units_samples(self._h, prec, _dptr(r), _fptr(X), _fptr(R), _fptr(Cc)))
+        return X, R, Cc
+
+    def learned_enable(self, mlp, theta=0.25):
+        with _Ordered(self):
+            _check(load().xdg_learned_enable(self._h, mlp._h if mlp is not None else None, theta))
+        self._mlp = mlp
+
+    def learned_step(self, r, z) -> int:
+        k = C.c_int()
+        with _Ordered(self):
+            _check(load().xdg_learned_step(self._h, _dptr(r), _dptr(z), C.byref(k)))
+        return k.value
 
     def destroy(self):
         if getattr(self, "_h", None):
@@ -412,6 +487,70 @@ class Batch:
     def destroy(self):
         if getattr(self, "_h", None):
             load().xdg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class Mlp:
+    """Owner of an xdg_mlp_t: the network of the learned cut-cell correction."""
+
+    def __init__(self, n_in, n_out, seed=0, stream=None):
+        torch = _torch()
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        h = C.c_void_p()
+        self._h = None
+        with _Ordered(self):
+            _check(load().xdg_mlp_create(n_in, n_out, seed, C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        self._h = h
+        self.n_in, self.n_out = n_in, n_out
+        n = C.c_int64()
+        _check(load().xdg_mlp_num_params(h, C.byref(n)))
+        self.n_params = n.value
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.n_params, np.float32)
+        with _Ordered(self):
+            _check(load().xdg_mlp_get_params(self._h, out.ctypes.data_as(C.POINTER(C.c_float)), self.n_params))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        with _Ordered(self):
+            _check(load().xdg_mlp_set_params(self._h, p.ctypes.data_as(C.POINTER(C.c_float)), self.n_params))
+
+    def forward(self, X, prec=XDG_PREC_F32):
+        torch = _torch()
+        Y = torch.empty((X.shape[0], self.n_out), dtype=torch.float32, device=X.device)
+        with _Ordered(self):
+            _check(load().xdg_mlp_forward(self._h, prec, X.shape[0], _fptr(X), _fptr(Y)))
+        return Y
+
+    def loss_grad(self, X, uid, Mloc, R, Cc):
+        torch = _torch()
+        g = torch.empty(self.n_params, dtype=torch.float32, device=X.device)
+        loss = C.c_double()
+        with _Ordered(self):
+            _check(load().xdg_mlp_loss_grad(self._h, X.shape[0], _fptr(X), _fptr(uid, torch.int32), _fptr(Mloc),
+                                            _fptr(R), _fptr(Cc), C.byref(loss), _fptr(g)))
+        return loss.value, g
+
+    def train(self, X, uid, Mloc, R, Cc, epochs=20, batch=512, lr=1e-3, seed=1) -> np.ndarray:
+        torch = _torch()
+        hist = np.zeros(epochs)
+        o = TrainOpts(epochs, batch, lr, 0.0, 0.0, 0.0, seed)
+        with _Ordered(self):
+            _check(load().xdg_mlp_train(self._h, X.shape[0], _fptr(X), _fptr(uid, torch.int32), _fptr(Mloc),
+                                        _fptr(R), _fptr(Cc), C.byref(o), hist.ctypes.data_as(_dp)))
+        return hist
+
+    def destroy(self):
+        if getattr(self, "_h", None):
+            load().xdg_mlp_destroy(self._h)
             self._h = None
 
     def __del__(self):

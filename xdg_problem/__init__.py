@@ -90,6 +90,9 @@ def _load():
         L.xp_l2_error.restype = C.c_int
         L.xp_l2_error.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.xp_block_features.argtypes = [vp, C.POINTER(C.c_double)]
+        L.xp_cell_features.argtypes = [vp, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_double)]
+        L.xp_cut_cells.restype = C.c_int
+        L.xp_cut_cells.argtypes = [vp, C.POINTER(C.c_int32)]
         _lib = L
     return _lib
 
@@ -244,6 +247,49 @@ class Problem:
         out = np.zeros((self.nb[0], nv + 2))
         self._L.xp_block_features(self._h, out.ctypes.data_as(C.POINTER(C.c_double)))
         return out
+
+    def cut_cells(self) -> np.ndarray:
+        """int32 [n_cut, 3]: (cell, level-1 block of the A part, level-1 block of the B part) of
+        every background cell that holds both species, ascending cell index."""
+        n = self._L.xp_cut_cells(self._h, None)
+        out = np.zeros((max(n, 1), 3), np.int32)
+        self._L.xp_cut_cells(self._h, out.ctypes.data_as(C.POINTER(C.c_int32)))
+        return out[:n]
+
+    def cell_features(self, cells) -> np.ndarray:
+        """phi/h^2 at the 2^D vertices and the volume fractions of A and B of the given
+        background cells ([len(cells), 2^D + 2])."""
+        cells = np.ascontiguousarray(cells, np.int32)
+        nv = 1 << self.D
+        out = np.zeros((len(cells), nv + 2))
+        self._L.xp_cell_features(self._h, len(cells), cells.ctypes.data_as(C.POINTER(C.c_int32)),
+                                 out.ctypes.data_as(C.POINTER(C.c_double)))
+        return out
+
+    def learned_units(self):
+        """Units of the learned cut-cell correction: the distinct (A block, B block) pairs of
+        the cut cells, in order of their first cell, with that cell's geometry features
+        [phi / (2 R h) at the 2^D vertices (about the signed distance in cells), volume
+        fractions of A and B, log10(mu_B / mu_A) / 3]. Returns (pairs int32 [U][2], geom
+        float32 [U][2^D + 3], cells int32 [U])."""
+        cc = self.cut_cells()
+        seen, pairs, cells = set(), [], []
+        for cell, a, b in cc:
+            key = (int(a), int(b))
+            if key not in seen:
+                seen.add(key)
+                pairs.append(key)
+                cells.append(int(cell))
+        pairs = np.array(pairs, np.int32).reshape(-1, 2)
+        cells = np.array(cells, np.int32)
+        f = self.cell_features(cells)
+        nv = 1 << self.D
+        h = (self.cfg.hi - self.cfg.lo) / self.cfg.N
+        geom = np.zeros((len(cells), nv + 3), np.float32)
+        geom[:, :nv] = f[:, :nv] * h / (2.0 * self.cfg.R)
+        geom[:, nv:nv + 2] = f[:, nv:nv + 2]
+        geom[:, nv + 2] = math.log10(self.cfg.muB / self.cfg.muA) / 3.0
+        return pairs, geom, cells
 
     def close(self):
         if getattr(self, "_h", None):

@@ -1711,28 +1711,52 @@ int xp_l2_error(void* h, const double* x, double* err2, double* norm2) {
   return 0;
 }
 
+static void cell_features(const Problem* P, int j, double* o) {
+  const int D = P->D, nv = 1 << D;
+  const double hD = std::pow(P->h, D);
+  double a[3], bb[3];
+  P->cell_box(j, a, bb);
+  for (int v = 0; v < nv; ++v) {
+    double x[3] = {0, 0, 0};
+    for (int d = 0; d < D; ++d) x[d] = (v >> d) & 1 ? bb[d] : a[d];
+    o[v] = P->phi(x) / (P->h * P->h);
+  }
+  double fa = 0.0, fb = 0.0;
+  const int pa = P->cellpart[2 * j], pb = P->cellpart[2 * j + 1];
+  if (pa >= 0) fa = P->parts[pa].vol / hD;
+  if (pb >= 0) fb = P->parts[pb].vol / hD;
+  o[nv] = fa;
+  o[nv + 1] = fb;
+}
+
 void xp_block_features(void* h, double* out) {
   Problem* P = static_cast<Problem*>(h);
   const Level& L = P->levels[0];
-  const int D = P->D, nv = 1 << D;
-  const double hD = std::pow(P->h, D);
-  for (int b = 0; b < L.nb; ++b) {
-    int j = L.rep[b];
-    double a[3], bb[3];
-    P->cell_box(j, a, bb);
-    double* o = out + (size_t)b * (nv + 2);
-    for (int v = 0; v < nv; ++v) {
-      double x[3] = {0, 0, 0};
-      for (int d = 0; d < D; ++d) x[d] = (v >> d) & 1 ? bb[d] : a[d];
-      o[v] = P->phi(x) / (P->h * P->h);
+  const int nv = 1 << P->D;
+  for (int b = 0; b < L.nb; ++b) cell_features(P, L.rep[b], out + (size_t)b * (nv + 2));
+}
+
+void xp_cell_features(void* h, int n, const int32_t* cells, double* out) {
+  Problem* P = static_cast<Problem*>(h);
+  const int nv = 1 << P->D;
+  for (int i = 0; i < n; ++i) cell_features(P, cells[i], out + (size_t)i * (nv + 2));
+}
+
+int xp_cut_cells(void* h, int32_t* out) {
+  Problem* P = static_cast<Problem*>(h);
+  const Level& L = P->levels[0];
+  int cnt = 0;
+  for (int j = 0; j < P->ncell; ++j) {
+    const int pa = P->cellpart[2 * j], pb = P->cellpart[2 * j + 1];
+    if (pa < 0 || pb < 0) continue;
+    if (out) {
+      out[3 * cnt] = j;
+      out[3 * cnt + 1] = L.part_block[pa];
+      out[3 * cnt + 2] = L.part_block[pb];
     }
-    double fa = 0.0, fb = 0.0;
-    int pa = P->cellpart[2 * j], pb = P->cellpart[2 * j + 1];
-    if (pa >= 0) fa = P->parts[pa].vol / hD;
-    if (pb >= 0) fb = P->parts[pb].vol / hD;
-    o[nv] = fa;
-    o[nv + 1] = fb;
+    ++cnt;
   }
+  return cnt;
 }
 
 }  // extern "C"

@@ -90,6 +90,13 @@ int xp_l2_error(void* h, const double* x, double* err2, double* norm2);
  * volume fractions of A and B in that cell, writes 2^D + 2 doubles per block. */
 void xp_block_features(void* h, double* out);
 
+/* the same features for n given background cells (2^D + 2 doubles each) */
+void xp_cell_features(void* h, int n, const int32_t* cells, double* out);
+
+/* cells holding parts of both species: (cell, level-1 block of the A part, level-1 block of
+ * the B part) per cell, ascending cell index; returns the count (out == NULL: count only). */
+int xp_cut_cells(void* h, int32_t* out);
+
 #ifdef __cplusplus
 }
 #endif
