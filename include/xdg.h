@@ -100,6 +100,10 @@ typedef struct {
                          FP32 operators and block inverses, see xdg_cycle) */
   int w_levels;       /* > 0: only the w_levels finest levels repeat their coarse correction
                          gamma times (V-cycle below); <= 0: all levels */
+  int split_rows;     /* row mapping of the low-precision cycle kernels: 0 = autotuned per level
+                         at creation (one block row per group of Np lanes, or one row per warp
+                         with the warp's groups splitting the row, whichever sweeps faster);
+                         1 = never split; 2 = split on every level */
 } xdg_hier_opts;
 
 typedef struct {
@@ -132,6 +136,7 @@ typedef struct {
   int64_t coarse_n;       /* DOF of the coarsest level (dense direct solve) */
   size_t device_bytes;    /* device memory held by the handle */
   double setup_ms[3];     /* upload+validation, Galerkin products, factorisations+estimates */
+  uint64_t split_mask;    /* bit l set: level l+1's low-precision row kernels split rows */
 } xdg_hier_info;
 
 /* Build the hierarchy on the current CUDA device: validate every index on the host

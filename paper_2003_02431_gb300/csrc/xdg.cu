@@ -63,6 +63,26 @@ double ms_since(clk::time_point t0) {
   return std::chrono::duration<double, std::milli>(clk::now() - t0).count();
 }
 
+
+// One full wave: the grid-stride kernels get at most (resident CTAs per SM) x SMs CTAs, so that
+// no partial second wave of CTAs runs at the end of a launch (occupancy queried once per kernel).
+int wave_cap(const void* k) {
+  static std::mutex mu;
+  static std::vector<std::pair<const void*, int>> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  for (auto& e : cache)
+    if (e.first == k) return e.second;
+  int dev = 0, sms = 152, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kThreads, 0) != cudaSuccess || occ < 1) occ = 1;
+  const int cap = occ * sms;
+  cache.emplace_back(k, cap);
+  return cap;
+}
+inline int fit_grid(const void* k, int grid) { return std::max(1, std::min(grid, wave_cap(k))); }
+#define LFIT(G, S, ...) __VA_ARGS__<<<fit_grid((const void*)&__VA_ARGS__, G), kThreads, 0, S>>>
+
 // --------------------------------------------------------------------------------------------
 // per-Np kernel table
 struct Ops {
@@ -91,44 +111,44 @@ template <int NP>
 struct OpsT {
   static void spmv(int grid, cudaStream_t s, int64_t nb, const int64_t* rp, const int32_t* col,
                    const double* val, const double* x, const double* b, double* y, int mode) {
-    if (mode) k_spmv<NP, 1><<<grid, kThreads, 0, s>>>(nb, rp, col, val, x, b, y);
-    else k_spmv<NP, 0><<<grid, kThreads, 0, s>>>(nb, rp, col, val, x, b, y);
+    if (mode) LFIT(grid, s, k_spmv<NP, 1>)(nb, rp, col, val, x, b, y);
+    else LFIT(grid, s, k_spmv<NP, 0>)(nb, rp, col, val, x, b, y);
   }
   static void smooth(int grid, cudaStream_t s, int64_t nb, const int64_t* rp, const int32_t* col,
                      const double* val, const double* Dinv, double om, const double* omr, const double* b,
                      const double* xi, double* xo) {
-    if (xi) k_smooth<NP, false><<<grid, kThreads, 0, s>>>(nb, rp, col, val, Dinv, om, omr, b, xi, xo);
-    else k_smooth<NP, true><<<grid, kThreads, 0, s>>>(nb, rp, col, val, Dinv, om, omr, b, xi, xo);
+    if (xi) LFIT(grid, s, k_smooth<NP, false>)(nb, rp, col, val, Dinv, om, omr, b, xi, xo);
+    else LFIT(grid, s, k_smooth<NP, true>)(nb, rp, col, val, Dinv, om, omr, b, xi, xo);
   }
   static void bjsolve(int grid, cudaStream_t s, int64_t nb, const double* Dinv, const double* v, double* z) {
-    k_bjsolve<NP><<<grid, kThreads, 0, s>>>(nb, Dinv, v, z);
+    LFIT(grid, s, k_bjsolve<NP>)(nb, Dinv, v, z);
   }
   static void diagmul(int grid, cudaStream_t s, int64_t nb, const int64_t* dg, const double* val,
                       const double* v, double* w) {
-    k_diagmul<NP><<<grid, kThreads, 0, s>>>(nb, dg, val, v, w);
+    LFIT(grid, s, k_diagmul<NP>)(nb, dg, val, v, w);
   }
   static void resid_rt(int grid, cudaStream_t s, int64_t nbf, const int64_t* rp, const int32_t* col,
                        const double* val, const double* R, const double* b, const double* x, double* t) {
-    if (x) k_resid_rt<NP, true><<<grid, kThreads, 0, s>>>(nbf, rp, col, val, R, b, x, t);
-    else k_resid_rt<NP, false><<<grid, kThreads, 0, s>>>(nbf, rp, col, val, R, b, x, t);
+    if (x) LFIT(grid, s, k_resid_rt<NP, true>)(nbf, rp, col, val, R, b, x, t);
+    else LFIT(grid, s, k_resid_rt<NP, false>)(nbf, rp, col, val, R, b, x, t);
   }
   static void gather(int grid, cudaStream_t s, int64_t nbc, const int64_t* cptr, const int32_t* ch,
                      const double* t, double* rc) {
-    k_gather<NP><<<grid, kThreads, 0, s>>>(nbc, cptr, ch, t, rc);
+    LFIT(grid, s, k_gather<NP>)(nbc, cptr, ch, t, rc);
   }
   static void gather_smooth0(int grid, cudaStream_t s, int64_t nbc, const int64_t* cptr, const int32_t* ch,
                              const double* t, const double* Dinv, double om, const double* omr, double* bc,
                              double* xc) {
-    k_gather_smooth0<NP><<<grid, kThreads, 0, s>>>(nbc, cptr, ch, t, Dinv, om, omr, bc, xc);
+    LFIT(grid, s, k_gather_smooth0<NP>)(nbc, cptr, ch, t, Dinv, om, omr, bc, xc);
   }
   static void prolong(int grid, cudaStream_t s, int64_t nbf, const int32_t* agg, const double* R,
                       const double* zc, const double* xi, double* xo) {
-    k_prolong<NP><<<grid, kThreads, 0, s>>>(nbf, agg, R, zc, xi, xo);
+    LFIT(grid, s, k_prolong<NP>)(nbf, agg, R, zc, xi, xo);
   }
   static void galerkin(int grid, cudaStream_t s, int64_t nbc, const int64_t* cptr, const int32_t* ch,
                        const int64_t* rp, const int32_t* col, const double* val, const int32_t* agg,
                        const double* R, const int64_t* crp, const int32_t* ccol, double* cval) {
-    k_galerkin<NP><<<grid, kThreads, 0, s>>>(nbc, cptr, ch, rp, col, val, agg, R, crp, ccol, cval);
+    LFIT(grid, s, k_galerkin<NP>)(nbc, cptr, ch, rp, col, val, agg, R, crp, ccol, cval);
   }
   static void diag_inv(cudaStream_t s, int64_t nb, const int64_t* dg, const double* val, double* Dinv,
                        int* err) {
@@ -153,18 +173,18 @@ bool ops_for(int np, Ops* o) {
 // per-(Np, storage type) kernel table of the low-precision cycle (vectors in FP32)
 struct OpsLP {
   void (*make)(cudaStream_t, int64_t nblk, int np2, const double*, void*, float*);
-  void (*spmv_f)(int, cudaStream_t, int64_t, const int64_t*, const int32_t*, const void*, const float*,
+  void (*spmv_f)(int, bool, cudaStream_t, int64_t, const int64_t*, const int32_t*, const void*, const float*,
                  const float*, const float*, float*, int mode);
   void (*spmv_d)(int, cudaStream_t, int64_t, const int64_t*, const int32_t*, const void*, const float*,
                  const double*, double*);
-  void (*smooth)(int, cudaStream_t, int64_t, const int64_t*, const int32_t*, const void*, const float*,
+  void (*smooth)(int, bool, cudaStream_t, int64_t, const int64_t*, const int32_t*, const void*, const float*,
                  const void*, const float*, float, const float*, const float*, const float*, float*);
-  void (*resid_rt)(int, cudaStream_t, int64_t, const int64_t*, const int32_t*, const void*, const float*,
+  void (*resid_rt)(int, bool, cudaStream_t, int64_t, const int64_t*, const int32_t*, const void*, const float*,
                    const void*, const float*, const float*, const float*, float*);
   void (*gather)(int, cudaStream_t, int64_t, const int64_t*, const int32_t*, const float*, float*);
   void (*prolong)(int, cudaStream_t, int64_t, const int32_t*, const void*, const float*, const float*,
                   const float*, float*);
-  void (*resid32)(int, cudaStream_t, int64_t, const int64_t*, const int32_t*, const void*, const float*,
+  void (*resid32)(int, bool, cudaStream_t, int64_t, const int64_t*, const int32_t*, const void*, const float*,
                   const float*, const float*, float*);
   void (*gather_smooth0)(int, cudaStream_t, int64_t, const int64_t*, const int32_t*, const float*, const float*,
                          const float*, float, const float*, float*, float*);
@@ -176,54 +196,67 @@ struct OpsLPT {
   static void make(cudaStream_t s, int64_t nblk, int np2, const double* src, void* dst, float* sc) {
     k_make_lp<TS><<<(unsigned)((nblk * 32 + 255) / 256), 256, 0, s>>>(nblk, np2, src, (TS*)dst, sc);
   }
-  static void spmv_f(int grid, cudaStream_t s, int64_t nb, const int64_t* rp, const int32_t* col,
+  // spl: one block row per warp, the warp's groups splitting the row (small levels)
+  static void spmv_f(int grid, bool spl, cudaStream_t s, int64_t nb, const int64_t* rp, const int32_t* col,
                      const void* val, const float* sc, const float* x, const float* b, float* y, int mode) {
-    if (mode) k_spmv_lp<NP, TS, float, 1><<<grid, kThreads, 0, s>>>(nb, rp, col, (const TS*)val, sc, x, b, y);
-    else k_spmv_lp<NP, TS, float, 0><<<grid, kThreads, 0, s>>>(nb, rp, col, (const TS*)val, sc, x, b, y);
+    const TS* v = (const TS*)val;
+    if (spl) {
+      if (mode) LFIT(grid, s, k_spmv_lp<NP, TS, float, 1, true>)(nb, rp, col, v, sc, x, b, y);
+      else LFIT(grid, s, k_spmv_lp<NP, TS, float, 0, true>)(nb, rp, col, v, sc, x, b, y);
+    } else {
+      if (mode) LFIT(grid, s, k_spmv_lp<NP, TS, float, 1>)(nb, rp, col, v, sc, x, b, y);
+      else LFIT(grid, s, k_spmv_lp<NP, TS, float, 0>)(nb, rp, col, v, sc, x, b, y);
+    }
   }
   static void spmv_d(int grid, cudaStream_t s, int64_t nb, const int64_t* rp, const int32_t* col,
                      const void* val, const float* sc, const double* x, double* y) {
-    k_spmv_lp<NP, TS, double, 0><<<grid, kThreads, 0, s>>>(nb, rp, col, (const TS*)val, sc, x, nullptr, y);
+    LFIT(grid, s, k_spmv_lp<NP, TS, double, 0>)(nb, rp, col, (const TS*)val, sc, x, nullptr, y);
   }
   // val: the FP32 operator copy (a BF16 operator is not usable in the sweeps, see k_resid_rt_lp)
-  static void smooth(int grid, cudaStream_t s, int64_t nb, const int64_t* rp, const int32_t* col,
+  static void smooth(int grid, bool spl, cudaStream_t s, int64_t nb, const int64_t* rp, const int32_t* col,
                      const void* val, const float* sc, const void* Dinv, const float* dsc, float om,
                      const float* omr, const float* b, const float* xi, float* xo) {
-    if (xi)
-      k_smooth_lp<NP, float, false><<<grid, kThreads, 0, s>>>(nb, rp, col, (const float*)val, sc,
-                                                              (const float*)Dinv, dsc, om, omr, b, xi, xo);
+    const float* v = (const float*)val;
+    const float* D = (const float*)Dinv;
+    if (xi && spl)
+      LFIT(grid, s, k_smooth_lp<NP, float, false, true>)(nb, rp, col, v, sc, D, dsc, om, omr, b, xi, xo);
+    else if (xi)
+      LFIT(grid, s, k_smooth_lp<NP, float, false>)(nb, rp, col, v, sc, D, dsc, om, omr, b, xi, xo);
     else
-      k_smooth_lp<NP, float, true><<<grid, kThreads, 0, s>>>(nb, rp, col, (const float*)val, sc,
-                                                             (const float*)Dinv, dsc, om, omr, b, xi, xo);
+      LFIT(grid, s, k_smooth_lp<NP, float, true>)(nb, rp, col, v, sc, D, dsc, om, omr, b, xi, xo);
   }
   // val: the FP32 operator copy
-  static void resid_rt(int grid, cudaStream_t s, int64_t nbf, const int64_t* rp, const int32_t* col,
+  static void resid_rt(int grid, bool spl, cudaStream_t s, int64_t nbf, const int64_t* rp, const int32_t* col,
                        const void* val, const float* sc, const void* R, const float* rsc, const float* b,
                        const float* x, float* t) {
-    if (x)
-      k_resid_rt_lp<NP, float, TS, true><<<grid, kThreads, 0, s>>>(nbf, rp, col, (const float*)val, sc,
-                                                                   (const TS*)R, rsc, b, x, t);
+    const float* v = (const float*)val;
+    const TS* Rt = (const TS*)R;
+    if (x && spl)
+      LFIT(grid, s, k_resid_rt_lp<NP, float, TS, true, true>)(nbf, rp, col, v, sc, Rt, rsc, b, x, t);
+    else if (x)
+      LFIT(grid, s, k_resid_rt_lp<NP, float, TS, true>)(nbf, rp, col, v, sc, Rt, rsc, b, x, t);
     else
-      k_resid_rt_lp<NP, float, TS, false><<<grid, kThreads, 0, s>>>(nbf, rp, col, (const float*)val, sc,
-                                                                    (const TS*)R, rsc, b, x, t);
+      LFIT(grid, s, k_resid_rt_lp<NP, float, TS, false>)(nbf, rp, col, v, sc, Rt, rsc, b, x, t);
   }
   // W-cycle coarse residual b - M x with the FP32 operator copy
-  static void resid32(int grid, cudaStream_t s, int64_t nb, const int64_t* rp, const int32_t* col,
+  static void resid32(int grid, bool spl, cudaStream_t s, int64_t nb, const int64_t* rp, const int32_t* col,
                       const void* val, const float* sc, const float* x, const float* b, float* y) {
-    k_spmv_lp<NP, float, float, 1><<<grid, kThreads, 0, s>>>(nb, rp, col, (const float*)val, sc, x, b, y);
+    const float* v = (const float*)val;
+    if (spl) LFIT(grid, s, k_spmv_lp<NP, float, float, 1, true>)(nb, rp, col, v, sc, x, b, y);
+    else LFIT(grid, s, k_spmv_lp<NP, float, float, 1>)(nb, rp, col, v, sc, x, b, y);
   }
   static void gather(int grid, cudaStream_t s, int64_t nbc, const int64_t* cptr, const int32_t* ch,
                      const float* t, float* rc) {
-    k_gather_lp<NP><<<grid, kThreads, 0, s>>>(nbc, cptr, ch, t, rc);
+    LFIT(grid, s, k_gather_lp<NP>)(nbc, cptr, ch, t, rc);
   }
   static void prolong(int grid, cudaStream_t s, int64_t nbf, const int32_t* agg, const void* R, const float* rsc,
                       const float* zc, const float* xi, float* xo) {
-    k_prolong_lp<NP, TS><<<grid, kThreads, 0, s>>>(nbf, agg, (const TS*)R, rsc, zc, xi, xo);
+    LFIT(grid, s, k_prolong_lp<NP, TS>)(nbf, agg, (const TS*)R, rsc, zc, xi, xo);
   }
   static void gather_smooth0(int grid, cudaStream_t s, int64_t nbc, const int64_t* cptr, const int32_t* ch,
                              const float* t, const float* Dinv, const float* dsc, float om, const float* omr,
                              float* bc, float* xc) {
-    k_gather_smooth0_lp<NP><<<grid, kThreads, 0, s>>>(nbc, cptr, ch, t, Dinv, dsc, om, omr, bc, xc);
+    LFIT(grid, s, k_gather_smooth0_lp<NP>)(nbc, cptr, ch, t, Dinv, dsc, om, omr, bc, xc);
   }
   static OpsLP get() {
     return OpsLP{make, spmv_f, spmv_d, smooth, resid_rt, gather, prolong, resid32, gather_smooth0, sizeof(TS)};
@@ -322,6 +355,7 @@ struct Level {
   double *b = nullptr, *x = nullptr, *t = nullptr, *r = nullptr, *dz = nullptr;
   double* s = nullptr;       // restriction scratch R_f^T res_f (levels above the coarsest)
   double omega = 0.0, lmax = 0.0;
+  bool spl = false;          // low-precision row kernels split rows across a warp (autotuned)
   // batches: damping per block row (one value per problem), problem offsets on this level
   double* omr = nullptr;
   float* omr_f = nullptr;
@@ -449,6 +483,13 @@ struct xdg_hier {
     int64_t blocks = (warps + (kThreads / 32) - 1) / (kThreads / 32);
     return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sms * 8));
   }
+  // grid of the low-precision row kernels of level l (split rows: one row per warp)
+  int grid_lp(int l) const {
+    const Level& V = L[l];
+    if (!V.spl) return grid(V.nb);
+    const int64_t blocks = (V.nb + (kThreads / 32) - 1) / (kThreads / 32);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sms * 16));
+  }
   int vgrid(int64_t n) const {
     int64_t blocks = (n + kThreads - 1) / kThreads;
     return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sms * 8));
@@ -572,15 +613,16 @@ struct xdg_hier {
     float* cur = x;
     float* oth = W.t;
     if (!pre0) {
-      o.smooth(grid(V.nb), stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, V.omr_f, b, nullptr, cur);
+      o.smooth(grid_lp(l), V.spl, stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, V.omr_f, b, nullptr,
+               cur);
       ++launches;
     }
     for (int s = 1; s < nu; ++s) {
-      o.smooth(grid(V.nb), stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, V.omr_f, b, cur, oth);
+      o.smooth(grid_lp(l), V.spl, stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, V.omr_f, b, cur, oth);
       ++launches;
       std::swap(cur, oth);
     }
-    o.resid_rt(grid(V.nb), stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.R, W.rsc, b, cur, W.s);
+    o.resid_rt(grid_lp(l), V.spl, stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.R, W.rsc, b, cur, W.s);
     launches += 2;
     if (l + 2 < nlev) {
       o.gather_smooth0(grid(C.nb), stream, C.nb, V.cptr, V.ch, W.s, (const float*)WC.Dinv, WC.dsc, (float)C.omega,
@@ -592,7 +634,7 @@ struct xdg_hier {
     }
     if (gamma > 1 && l + 2 < nlev && l < wlev) {
       for (int g = 1; g < gamma; ++g) {
-        o.resid32(grid(C.nb), stream, C.nb, C.rp, C.col, WC.val32, WC.sc32, WC.x, WC.b, WC.r);
+        o.resid32(grid_lp(l + 1), C.spl, stream, C.nb, C.rp, C.col, WC.val32, WC.sc32, WC.x, WC.b, WC.r);
         cycle_lp(p, l + 1, WC.r, WC.dz);
         k_axpy_f<<<vgrid(C.nb * Np), kThreads, 0, stream>>>(C.nb * Np, 1.0f, WC.dz, WC.x);
         launches += 2;
@@ -604,7 +646,7 @@ struct xdg_hier {
     cur = after;
     oth = (cur == x) ? W.t : x;
     for (int s = 0; s < nu; ++s) {
-      o.smooth(grid(V.nb), stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, V.omr_f, b, cur, oth);
+      o.smooth(grid_lp(l), V.spl, stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, V.omr_f, b, cur, oth);
       ++launches;
       std::swap(cur, oth);
     }
@@ -658,6 +700,9 @@ struct xdg_hier {
   }
 
   int build_lp(int p);
+  int tune_split(int p);
+  bool tuned = false;
+  int split_mode = 0;  // xdg_hier_opts.split_rows
 
   // which: 0 FP64 cycle, 1 FP64 CG iteration, 2 low-precision cycle, 3 flexible-CG iteration
   int capture(cudaGraphExec_t* out, int which, const double* b, double* x, int p = 0) {
@@ -847,6 +892,7 @@ int xdg_hier::build(const xdg_problem* p, const xdg_hier_opts* o) {
   nu = o && o->nu > 0 ? o->nu : 1;
   gamma = o && o->gamma > 0 ? o->gamma : 1;
   wlev = o && o->w_levels > 0 ? o->w_levels : (1 << 20);
+  split_mode = o ? o->split_rows : 0;
   const int lsteps = o && o->lanczos_steps > 0 ? o->lanczos_steps : 12;
   const int64_t Np2 = (int64_t)Np * Np;
   CK(cudaGetDevice(&dev));
@@ -1255,7 +1301,62 @@ int xdg_hier::build_lp(int p) {
   }
   TRY(sync());
   has_lp[p] = true;
+  if (!tuned) {
+    if (split_mode == 0) {
+      TRY(tune_split(p));
+    } else {
+      for (int l = 0; l < nlev; ++l) L[l].spl = (split_mode == 2);
+      tuned = true;
+    }
+  }
   TRY(capture(&g_iter_lp[p], 3, nullptr, nullptr, p));
+  return XDG_OK;
+}
+
+// Autotuner of the low-precision row kernels: for every level with a smoother, time a sweep
+// with one block row per group (rows spread over the warp's groups) and with one row per warp
+// (the warp's groups splitting each row), and keep the faster (split only when >= 5 % faster).
+// The same mapping then serves the residual-restriction and operator kernels of that level.
+int xdg_hier::tune_split(int p) {
+  const OpsLP& o = opl[p];
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int rc = XDG_OK;
+  for (int l = 0; l + 1 < nlev && rc == XDG_OK; ++l) {
+    Level& V = L[l];
+    LevelLP& W = LP[p][l];
+    const int64_t n = V.nb * Np;
+    if (cudaMemsetAsync(W.b, 0, n * sizeof(float), stream) != cudaSuccess ||
+        cudaMemsetAsync(W.x, 0, n * sizeof(float), stream) != cudaSuccess) {
+      rc = XDG_ECUDA;
+      break;
+    }
+    float ms[2] = {0.f, 0.f};
+    for (int v = 0; v < 2; ++v) {
+      V.spl = (v == 1);
+      auto sweep = [&]() {
+        o.smooth(grid_lp(l), V.spl, stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, (float)V.omega,
+                 V.omr_f, W.b, W.x, W.t);
+      };
+      for (int k = 0; k < 3; ++k) sweep();
+      cudaEventRecord(e0, stream);
+      for (int k = 0; k < 10; ++k) sweep();
+      cudaEventRecord(e1, stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms[v], e0, e1) != cudaSuccess) {
+        rc = XDG_ECUDA;
+        break;
+      }
+    }
+    V.spl = ms[1] < 0.95f * ms[0];
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) {
+    set_err("split autotuning: %s", cudaGetErrorString(cudaGetLastError()));
+    return rc;
+  }
+  tuned = true;
   return XDG_OK;
 }
 
@@ -1819,6 +1920,8 @@ int xdg_get_info(xdg_hier_t h, xdg_hier_info* info) {
   info->coarse_n = h->nc;
   info->device_bytes = h->bytes;
   for (int i = 0; i < 3; ++i) info->setup_ms[i] = h->setup_ms[i];
+  for (int l = 0; l < h->nlev && l < 64; ++l)
+    if (h->L[l].spl) info->split_mask |= (uint64_t)1 << l;
   return XDG_OK;
 }
 
@@ -1860,7 +1963,8 @@ int xdg_apply(xdg_hier_t h, int level, const double* x, double* y, int prec) {
     // would run on the FP64 pipe); the level's FP32 work vectors r and dz hold x and y
     const int64_t n = V.nb * h->Np;
     k_d2f<<<h->vgrid(n), kThreads, 0, h->stream>>>(n, x, W.r);
-    h->opl[prec].spmv_f(h->grid(V.nb), h->stream, V.nb, V.rp, V.col, W.val, W.sc, W.r, nullptr, W.dz, 0);
+    h->opl[prec].spmv_f(h->grid_lp(level - 1), V.spl, h->stream, V.nb, V.rp, V.col, W.val, W.sc, W.r, nullptr,
+                        W.dz, 0);
     k_f2d<<<h->vgrid(n), kThreads, 0, h->stream>>>(n, W.dz, y);
     h->launches += 3;
   }

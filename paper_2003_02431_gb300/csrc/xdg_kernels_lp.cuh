@@ -75,8 +75,49 @@ __device__ __forceinline__ float row_dot_lp(int64_t z0, int64_t z1, int r, const
   return acc;
 }
 
+// Split rows (small levels): the GPW groups of a warp share one block row, group g taking the
+// blocks z0 + g, z0 + g + GPW, ...; split_sum adds the groups' partial sums in group order
+// (the same value in every group). This shortens the per-row chain of dependent loads, which
+// bounds the small levels, by the factor GPW.
+template <int NP, class TS, class VT>
+__device__ __forceinline__ float row_dot_lp_part(int64_t z0, int64_t z1, int g, int r,
+                                                 const int32_t* __restrict__ col, const TS* __restrict__ val,
+                                                 const float* __restrict__ sc, const VT* __restrict__ x) {
+  constexpr int GPW = Grp<NP>::GPW;
+  constexpr int CH = Chunk<NP>::F32;
+  float acc = 0.0f;
+  for (int64_t z = z0 + g; z < z1; z += (int64_t)CH * GPW) {
+    int32_t cc[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) cc[u] = (z + u * GPW < z1) ? __ldg(col + z + u * GPW) : -1;
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      if (cc[u] < 0) continue;
+      const int64_t zz = z + u * GPW;
+      float a[NP], xv[NP];
+      ldrow_f<NP, TS>(val + zz * (NP * NP) + r * NP, a);
+      ldrow_f<NP, VT>(x + (int64_t)cc[u] * NP, xv);
+      float s = 0.0f;
+#pragma unroll
+      for (int c = 0; c < NP; ++c) s = fmaf(a[c], xv[c], s);
+      acc = fmaf(__ldg(sc + zz), s, acc);
+    }
+  }
+  return acc;
+}
+
+template <int NP>
+__device__ __forceinline__ float split_sum(float part, int r) {
+  constexpr int GPW = Grp<NP>::GPW;
+  constexpr unsigned M = (GPW * NP == 32) ? 0xffffffffu : ((1u << (GPW * NP)) - 1u);
+  float t = __shfl_sync(M, part, r);
+#pragma unroll
+  for (int gg = 1; gg < GPW; ++gg) t += __shfl_sync(M, part, gg * NP + r);
+  return t;
+}
+
 // y = M x (MODE 0) or b - M x (MODE 1); VT = vector type of x, b and y (float or double)
-template <int NP, class TS, class VT, int MODE>
+template <int NP, class TS, class VT, int MODE, bool SPL = false>
 __global__ void __launch_bounds__(kThreads) k_spmv_lp(int64_t nb, const int64_t* __restrict__ rp,
                                                      const int32_t* __restrict__ col,
                                                      const TS* __restrict__ val, const float* __restrict__ sc,
@@ -88,9 +129,17 @@ __global__ void __launch_bounds__(kThreads) k_spmv_lp(int64_t nb, const int64_t*
   if (g >= GPW) return;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i = warp * GPW + g; i < nb; i += nw * GPW) {
-    float acc = row_dot_lp<NP, TS, VT>(__ldg(rp + i), __ldg(rp + i + 1), r, col, val, sc, x);
-    y[i * NP + r] = MODE ? (VT)(to_f<VT>(b[i * NP + r]) - acc) : (VT)acc;
+  if constexpr (SPL) {
+    for (int64_t i = warp; i < nb; i += nw) {
+      const float acc = split_sum<NP>(row_dot_lp_part<NP, TS, VT>(__ldg(rp + i), __ldg(rp + i + 1), g, r, col,
+                                                                  val, sc, x), r);
+      if (g == 0) y[i * NP + r] = MODE ? (VT)(to_f<VT>(b[i * NP + r]) - acc) : (VT)acc;
+    }
+  } else {
+    for (int64_t i = warp * GPW + g; i < nb; i += nw * GPW) {
+      float acc = row_dot_lp<NP, TS, VT>(__ldg(rp + i), __ldg(rp + i + 1), r, col, val, sc, x);
+      y[i * NP + r] = MODE ? (VT)(to_f<VT>(b[i * NP + r]) - acc) : (VT)acc;
+    }
   }
 }
 
@@ -108,7 +157,7 @@ __device__ __forceinline__ float block_gemv_lp(const TS* __restrict__ W, float s
 // damped block Jacobi in FP32: xo = xi + omega D^{-1} (b - M xi). The block inverses are
 // computed in FP64 and stored in FP32 in both modes: rounding the inverse of an ill-conditioned
 // cut-cell block to BF16 loses it.
-template <int NP, class TS, bool ZERO>
+template <int NP, class TS, bool ZERO, bool SPL = false>
 __global__ void __launch_bounds__(kThreads) k_smooth_lp(int64_t nb, const int64_t* __restrict__ rp,
                                                        const int32_t* __restrict__ col,
                                                        const TS* __restrict__ val, const float* __restrict__ sc,
@@ -123,19 +172,31 @@ __global__ void __launch_bounds__(kThreads) k_smooth_lp(int64_t nb, const int64_
   const unsigned mask = group_mask(g, NP);
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i = warp * GPW + g; i < nb; i += nw * GPW) {
-    float res = b[i * NP + r];
-    if (!ZERO) res -= row_dot_lp<NP, TS, float>(__ldg(rp + i), __ldg(rp + i + 1), r, col, val, sc, xi);
-    float z = block_gemv_lp<NP, float>(Dinv + i * (NP * NP), __ldg(dsc + i), r, g * NP, mask, res);
-    const float om = omr ? __ldg(omr + i) : omega;  // per-row damping in batches
-    xo[i * NP + r] = ZERO ? om * z : fmaf(om, z, xi[i * NP + r]);
+  if constexpr (SPL) {
+    for (int64_t i = warp; i < nb; i += nw) {
+      float res = b[i * NP + r];
+      if (!ZERO)
+        res -= split_sum<NP>(row_dot_lp_part<NP, TS, float>(__ldg(rp + i), __ldg(rp + i + 1), g, r, col, val, sc,
+                                                            xi), r);
+      float z = block_gemv_lp<NP, float>(Dinv + i * (NP * NP), __ldg(dsc + i), r, g * NP, mask, res);
+      const float om = omr ? __ldg(omr + i) : omega;
+      if (g == 0) xo[i * NP + r] = ZERO ? om * z : fmaf(om, z, xi[i * NP + r]);
+    }
+  } else {
+    for (int64_t i = warp * GPW + g; i < nb; i += nw * GPW) {
+      float res = b[i * NP + r];
+      if (!ZERO) res -= row_dot_lp<NP, TS, float>(__ldg(rp + i), __ldg(rp + i + 1), r, col, val, sc, xi);
+      float z = block_gemv_lp<NP, float>(Dinv + i * (NP * NP), __ldg(dsc + i), r, g * NP, mask, res);
+      const float om = omr ? __ldg(omr + i) : omega;  // per-row damping in batches
+      xo[i * NP + r] = ZERO ? om * z : fmaf(om, z, xi[i * NP + r]);
+    }
   }
 }
 
 // restriction phase 1 in FP32: t_f = R_f^T (b_f - M_f x). The operator is read from its FP32
 // copy in both modes (TA = float): a BF16-rounded operator is not positive definite on the
 // smooth modes the coarse levels correct (2^-9 cond(M) >> 1); TR is the transfer storage.
-template <int NP, class TA, class TR, bool RESID>
+template <int NP, class TA, class TR, bool RESID, bool SPL = false>
 __global__ void __launch_bounds__(kThreads) k_resid_rt_lp(int64_t nbf, const int64_t* __restrict__ rp,
                                                          const int32_t* __restrict__ col,
                                                          const TA* __restrict__ val, const float* __restrict__ sc,
@@ -150,14 +211,28 @@ __global__ void __launch_bounds__(kThreads) k_resid_rt_lp(int64_t nbf, const int
   const int base = g * NP;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t f = warp * GPW + g; f < nbf; f += nw * GPW) {
-    float res = b[f * NP + r];
-    if (RESID) res -= row_dot_lp<NP, TA, float>(__ldg(rp + f), __ldg(rp + f + 1), r, col, val, sc, x);
-    const TR* Rf = R + f * (NP * NP);
-    float s = 0.0f;
+  if constexpr (SPL) {
+    for (int64_t f = warp; f < nbf; f += nw) {
+      float res = b[f * NP + r];
+      if (RESID)
+        res -= split_sum<NP>(row_dot_lp_part<NP, TA, float>(__ldg(rp + f), __ldg(rp + f + 1), g, r, col, val, sc,
+                                                            x), r);
+      const TR* Rf = R + f * (NP * NP);
+      float s = 0.0f;
 #pragma unroll
-    for (int m = 0; m < NP; ++m) s = fmaf(to_f<TR>(Rf[m * NP + r]), __shfl_sync(mask, res, base + m), s);
-    t[f * NP + r] = __ldg(rsc + f) * s;
+      for (int m = 0; m < NP; ++m) s = fmaf(to_f<TR>(Rf[m * NP + r]), __shfl_sync(mask, res, base + m), s);
+      if (g == 0) t[f * NP + r] = __ldg(rsc + f) * s;
+    }
+  } else {
+    for (int64_t f = warp * GPW + g; f < nbf; f += nw * GPW) {
+      float res = b[f * NP + r];
+      if (RESID) res -= row_dot_lp<NP, TA, float>(__ldg(rp + f), __ldg(rp + f + 1), r, col, val, sc, x);
+      const TR* Rf = R + f * (NP * NP);
+      float s = 0.0f;
+#pragma unroll
+      for (int m = 0; m < NP; ++m) s = fmaf(to_f<TR>(Rf[m * NP + r]), __shfl_sync(mask, res, base + m), s);
+      t[f * NP + r] = __ldg(rsc + f) * s;
+    }
   }
 }
 

@@ -79,6 +79,38 @@ def test_lowprec_cycle_close_to_fp64(case, prec, tol):
     assert err < tol, (name, prec, err)
 
 
+def test_split_row_mapping_agrees(case):
+    """The two row mappings of the low-precision kernels (a row per group of Np lanes, or a row
+    per warp split over its groups) compute the same operator apply up to FP32 summation order
+    on every level, and cycles within the FP32 bound; the autotuned hierarchy reports which
+    levels split."""
+    name, P, O, G = case
+    gamma = CASES[name][1]
+    b = _t(P.b.reshape(-1))
+    rng = np.random.default_rng(12)
+    v = {l: _t(rng.standard_normal(P.nb[l - 1] * P.Np)) for l in range(1, P.n_levels + 1)}
+    out = []
+    for mode in (1, 2):
+        H = xdg.Hierarchy.from_problem(P, gamma=gamma, low_precision=1, split_rows=mode)
+        assert H.info()["split"] == [mode == 2] * P.n_levels
+        x = torch.empty(P.dof, dtype=torch.float64, device=DEV)
+        H.cycle(xdg.XDG_PREC_F32, b, x)
+        ys = []
+        for l in range(1, P.n_levels + 1):
+            y = torch.empty_like(v[l])
+            H.apply(l, v[l], y, prec=xdg.XDG_PREC_F32)
+            ys.append(_n(y))
+        out.append((_n(x), ys))
+        H.destroy()
+    # one apply: FP32 summation order only; a cycle amplifies rounding differences through the
+    # ill-conditioned coarse levels as much as FP32 vs FP64 does (the 1e-3 bound above)
+    for a, c in zip(out[0][1], out[1][1]):
+        assert _rel(a, c) < 1e-6, name
+    assert _rel(out[0][0], out[1][0]) < 1e-3, name
+    assert _rel(out[1][0], O.vcycle(P.b.reshape(-1))) < 1e-3
+    assert len(G.info()["split"]) == P.n_levels
+
+
 @pytest.mark.parametrize("prec", [xdg.XDG_PREC_F32, xdg.XDG_PREC_BF16])
 def test_mixed_solve_reaches_fp64_oracle_solution(case, prec):
     name, P, O, G = case
