@@ -96,6 +96,19 @@ class ClockSampler:
 
 SIZE = 64  # cells per direction (--size; the benchmark workload is 64)
 
+KERNEL_NAMES = {
+    "resid_rt_f32": "k_resid_rt_lp<10,float,float,1,0>: level-1 FP32 residual and R^T (restriction phase 1)",
+    "smooth_f32": "k_smooth_lp<10,float,0,0>: level-1 FP32 block-Jacobi sweep",
+    "apply_f32": "k_spmv_lp<10,float,float,0>: level-1 FP32 operator apply",
+    "apply_f64": "k_spmv<10,0>: level-1 FP64 operator apply (outer flexible CG)",
+}
+# the kernel with the largest share of the mixed solve's device time (launch list in
+# profiles/launch_list_mixed_solve_64cube.md)
+DOMINANT = "resid_rt_f32"
+# DRAM bytes (read + write) of one level-1 launch at 64^3, from one ncu capture of the same
+# kernels (profiles/level1_kernels_dram_64cube.md); None until taken for the current code
+NCU_TRAFFIC = {}
+
 
 def make_problem():
     import xdg_problem as xp
@@ -202,6 +215,74 @@ def batched_section(xdg, torch, dev, stream, steps, warmup):
     return out
 
 
+LEARNED_SEED = 20030245
+HELD_OUT_RADII = (0.23, 0.29, 0.37)
+
+
+def learned_section(xdg, torch, dev, stream, n_train=4):
+    """Learned cut-cell correction: trained on the GPU on 48^3 k=2 sphere problems with radii
+    from U(0.2, 0.4) (held-out radii excluded with a 0.005 margin), evaluated on 64^3 k=2 with
+    the held-out radius 0.29: local energy gain and flexible-CG solves with and without it."""
+    import xdg_problem as xp
+    from paper_2003_02431_gb300 import learned
+    rng = np.random.Generator(np.random.PCG64(LEARNED_SEED))
+    radii = []
+    while len(radii) < n_train:
+        r = float(rng.uniform(0.2, 0.4))
+        if all(abs(r - h) > 0.005 for h in HELD_OUT_RADII):
+            radii.append(r)
+    t0 = time.perf_counter()
+    train = learned.SampleSet()
+    for R in radii:
+        P = xp.Problem(xp.config_3d_64(N=48, R=R, max_coarse_dof=1000))
+        H = xdg.Hierarchy.from_problem(P, gamma=GAMMA, w_levels=W_LEVELS, low_precision=1, stream=stream)
+        learned.attach_units(H, P)
+        b = torch.from_numpy(P.b.reshape(-1).copy()).to(dev)
+        train.add(H, learned.solver_residuals(H, b, 16))
+        H.destroy()
+    data_s = time.perf_counter() - t0
+    net = learned.network_for(P, seed=LEARNED_SEED, stream=stream)
+    n_samples = int(train.tensors()[0].shape[0])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = learned.train(net, train, epochs=60, batch=512, lr=2e-3, seed=LEARNED_SEED)
+    train_s = time.perf_counter() - t0
+    # held-out evaluation at 64^3
+    P = xp.Problem(xp.config_3d_64(R=0.29, max_coarse_dof=1000))
+    H = xdg.Hierarchy.from_problem(P, gamma=GAMMA, w_levels=W_LEVELS, low_precision=1, stream=stream)
+    learned.attach_units(H, P)
+    b = torch.from_numpy(P.b.reshape(-1).copy()).to(dev)
+    held = learned.SampleSet()
+    held.add(H, learned.solver_residuals(H, b, 8))
+    Xh, uid, M, R, C = held.tensors()
+    Md, Rd, Cd = M[uid.long()].double(), R.double(), C.double()
+    bj = float(((torch.einsum("si,sij,sj->s", Rd, Md, Rd) - 2 * (Rd * Rd).sum(1)) / Cd).mean())
+    loss = learned.evaluate(net, held)
+    out = {"train": {"problems": "48^3 k=2, R from U(0.2,0.4) seed %d: %s" % (LEARNED_SEED, [round(r, 4) for r in radii]),
+                     "samples": n_samples, "epochs": len(hist), "loss_first_epoch": float(hist[0]),
+                     "loss_last_epoch": float(hist[-1]), "train_s": train_s, "data_s": data_s},
+           "held_out": {"problem": "64^3 k=2 R=0.29", "units": int(H.n_units), "loss": loss,
+                        "block_jacobi_step_loss": bj,
+                        "meaning": "-1 = exact local solve of the cut-cell pair, 0 = no energy gain"}}
+    x0 = torch.zeros_like(b)
+    for tag, on in (("plain", False), ("learned", True)):
+        if on:
+            H.learned_enable(net, theta=0.25)
+        x0.zero_()
+        H.solve(b, x0, tol=TOL, precision=xdg.XDG_PREC_F32)
+        x0.zero_()
+        torch.cuda.synchronize()
+        info = H.solve(b, x0, tol=TOL, precision=xdg.XDG_PREC_F32)
+        out["solve_" + tag] = {"iterations": info["iterations"], "ms": info["ms"], "relres": info["relres"]}
+        if tag == "plain":
+            xplain = x0.clone()
+    out["solution_diff_rel_l2"] = float(torch.linalg.norm(x0 - xplain) / torch.linalg.norm(xplain))
+    H.learned_enable(None)
+    H.destroy()
+    net.destroy()
+    return out
+
+
 def reference_arm(args):
     """The oracle (plain FP64 CPU code) on the same workload: each step is a bounded sample of
     5 PCG iterations, extrapolated with the iteration count of the oracle's full solve."""
@@ -238,6 +319,7 @@ def main():
     ap.add_argument("--impl", default="xdg", choices=["xdg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 256-problem workload")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-correction section")
     ap.add_argument("--size", type=int, default=64,
                     help="cells per direction; 64 is the benchmark workload, smaller sizes serve profiling")
     args = ap.parse_args()
@@ -325,16 +407,22 @@ def main():
     z = torch.empty_like(x)
     cyc_ms = {p: time_call(lambda: H.cycle(p, b, z)) for p in (0, 1, 2)}
 
-    # dominant kernels, level 1, CUDA events on the launching stream
-    y = torch.empty_like(x)
-    ms_apply64 = time_call(lambda: H.apply(1, b, y))
-    ms_apply32 = time_call(lambda: H.apply(1, b, y, prec=xdg.XDG_PREC_F32))
-    flops_apply = 2.0 * nnzb * Np * Np
-    bytes_apply32 = nnzb * (4 * Np * Np + 4 + 4) + (nb + 1) * 8 + 2 * n * 8
+    # level-1 kernels of the path: mean launch duration (CUDA events on the handle's stream,
+    # recorded by the library around repeated launches) and algorithmic bytes per launch
     fp64_peak = xdg.fma_peak(xdg.XDG_PREC_F64)
     hbm, hbm_kind = hbm_peak()
-    ach64 = flops_apply / (ms_apply64 / 1e3) / 1e12
-    ach32 = bytes_apply32 / (ms_apply32 / 1e3) / 1e9
+    kernels = {}
+    for key, which, prec in (("resid_rt_f32", H.KERNEL_RESTRICT, xdg.XDG_PREC_F32),
+                             ("smooth_f32", H.KERNEL_SMOOTH, xdg.XDG_PREC_F32),
+                             ("apply_f32", H.KERNEL_APPLY, xdg.XDG_PREC_F32),
+                             ("apply_f64", H.KERNEL_APPLY, xdg.XDG_PREC_F64)):
+        ms, by = H.kernel_time(which, 1, prec, reps=20)
+        kernels[key] = {"kernel": KERNEL_NAMES[key], "ms": ms, "bytes": by, "achieved_gbs": by / (ms / 1e3) / 1e9,
+                        "frac_hbm": by / (ms / 1e3) / 1e9 / hbm}
+    flops_apply = 2.0 * nnzb * Np * Np
+    ach64 = flops_apply / (kernels["apply_f64"]["ms"] / 1e3) / 1e12
+    kernels["apply_f64"].update({"bound": "alu", "tflops": ach64, "frac_fp64_peak": ach64 / fp64_peak})
+    dom = kernels[DOMINANT]
 
     # end to end through the host-buffer entry point (pinned host memory)
     bh = torch.from_numpy(P.b.reshape(-1).copy()).pin_memory().numpy()
@@ -351,6 +439,10 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_s = float(tt.item())
     e2e = world * n * args.steps / e2e_s / 1e6
+
+    learned_out = None
+    if not args.no_learned:
+        learned_out = learned_section(xdg, torch, dev, stream)
 
     batched = None
     if not args.no_batch:
@@ -386,15 +478,14 @@ def main():
             "vcycle_mdofs": {"f64": n / cyc_ms[0] / 1e3, "f32": n / cyc_ms[1] / 1e3, "bf16": n / cyc_ms[2] / 1e3},
             "vcycle_ms": cyc_ms,
             "setup_s": setup_s, "setup_ms_phases": hinfo["setup_ms"],
-            "roofline": {"bound": "alu", "kernel": "k_spmv<10> FP64 operator apply, level 1 (outer FP64 apply)",
-                         "achieved": ach64, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach64 / fp64_peak,
-                         "peak_kind": "measured live: FP64 FMA probe (xdg_fma_peak)",
-                         "work": "2*nnzb*Np^2 = %.1f MFLOP per launch" % (flops_apply / 1e6),
-                         "ms": ms_apply64, "traffic": None},
-            "roofline_fp32_apply": {"bound": "hbm", "kernel": "k_spmv_lp<10,float> FP32 operator apply, level 1",
-                                    "achieved": ach32, "peak": hbm, "unit": "GB/s", "frac": ach32 / hbm,
-                                    "peak_kind": hbm_kind, "bytes": bytes_apply32, "ms": ms_apply32},
+            "roofline": {"bound": "hbm", "kernel": dom["kernel"], "achieved": dom["achieved_gbs"], "peak": hbm,
+                         "unit": "GB/s", "frac": dom["achieved_gbs"] / hbm, "peak_kind": hbm_kind,
+                         "bytes": dom["bytes"], "ms": dom["ms"],
+                         "traffic": NCU_TRAFFIC.get(DOMINANT) if SIZE == 64 else None},
+            "kernels_level1": kernels,
+            "fp64_peak_tflops": fp64_peak,
             "batched": batched,
+            "learned": learned_out,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": "MDOF/s", "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8},
             "gpu_launches": launches,

@@ -223,6 +223,18 @@ int xdg_solve_host(xdg_hier_t h, const double* b_host, double* x_host, const xdg
  * apply (0.25 flop/byte) is bound by the FP64 pipe, not by HBM. */
 int xdg_fma_peak(int prec, double* tflops);
 
+/* Benchmark utility (no counterpart in the paper): mean duration (*ms, CUDA events on the
+ * handle's stream, after 3 warm-up launches, over reps launches; reps <= 0 means 20) of one
+ * kernel of the cycle on `level`, and its algorithmic bytes per launch (*bytes: every stored
+ * operator, inverse and transfer entry and scale read once, row pointers and columns once, each
+ * vector read or written once). which: 0 = operator apply y = M x (the stored copy of
+ * precision prec), 1 = block-Jacobi sweep from a nonzero guess (level < n_levels),
+ * 2 = residual and restriction phase 1, R^T (b - M x) per fine block (level < n_levels).
+ * The low-precision sweep and restriction read the FP32 operator (see xdg_cycle). Uses the
+ * level's work vectors (zeroed first); synchronises. */
+int xdg_kernel_time(xdg_hier_t h, int which, int level, int prec, int reps, double* ms,
+                    double* bytes);
+
 /* ---------------------------------------------------------------------------------------------
  * Batches of independent problems.
  *

@@ -15,6 +15,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -87,7 +88,7 @@ inline int fit_grid(const void* k, int grid) { return std::max(1, std::min(grid,
 // per-Np kernel table
 struct Ops {
   int np;
-  void (*spmv)(int grid, cudaStream_t, int64_t, const int64_t*, const int32_t*, const double*,
+  void (*spmv)(int grid, cudaStream_t, const uint8_t*, int64_t, const int64_t*, const int32_t*, const double*,
                const double*, const double*, double*, int mode);
   void (*smooth)(int grid, cudaStream_t, int64_t, const int64_t*, const int32_t*, const double*,
                  const double*, double, const double*, const double*, const double*, double*);
@@ -109,10 +110,10 @@ struct Ops {
 
 template <int NP>
 struct OpsT {
-  static void spmv(int grid, cudaStream_t s, int64_t nb, const int64_t* rp, const int32_t* col,
+  static void spmv(int grid, cudaStream_t s, const uint8_t* act, int64_t nb, const int64_t* rp, const int32_t* col,
                    const double* val, const double* x, const double* b, double* y, int mode) {
-    if (mode) LFIT(grid, s, k_spmv<NP, 1>)(nb, rp, col, val, x, b, y);
-    else LFIT(grid, s, k_spmv<NP, 0>)(nb, rp, col, val, x, b, y);
+    if (mode) LFIT(grid, s, k_spmv<NP, 1>)(nb, rp, col, val, x, b, y, act);
+    else LFIT(grid, s, k_spmv<NP, 0>)(nb, rp, col, val, x, b, y, act);
   }
   static void smooth(int grid, cudaStream_t s, int64_t nb, const int64_t* rp, const int32_t* col,
                      const double* val, const double* Dinv, double om, const double* omr, const double* b,
@@ -178,12 +179,13 @@ struct OpsLP {
   void (*spmv_d)(int, cudaStream_t, int64_t, const int64_t*, const int32_t*, const void*, const float*,
                  const double*, double*);
   void (*smooth)(int, bool, cudaStream_t, int64_t, const int64_t*, const int32_t*, const void*, const float*,
-                 const void*, const float*, float, const float*, const float*, const float*, float*);
+                 const void*, const float*, float, const float*, const float*, const float*, float*,
+                 const uint8_t*);
   void (*resid_rt)(int, bool, cudaStream_t, int64_t, const int64_t*, const int32_t*, const void*, const float*,
-                   const void*, const float*, const float*, const float*, float*);
+                   const void*, const float*, const float*, const float*, float*, const uint8_t*);
   void (*gather)(int, cudaStream_t, int64_t, const int64_t*, const int32_t*, const float*, float*);
   void (*prolong)(int, cudaStream_t, int64_t, const int32_t*, const void*, const float*, const float*,
-                  const float*, float*);
+                  const float*, float*, const uint8_t*);
   void (*resid32)(int, bool, cudaStream_t, int64_t, const int64_t*, const int32_t*, const void*, const float*,
                   const float*, const float*, float*);
   void (*gather_smooth0)(int, cudaStream_t, int64_t, const int64_t*, const int32_t*, const float*, const float*,
@@ -215,28 +217,28 @@ struct OpsLPT {
   // val: the FP32 operator copy (a BF16 operator is not usable in the sweeps, see k_resid_rt_lp)
   static void smooth(int grid, bool spl, cudaStream_t s, int64_t nb, const int64_t* rp, const int32_t* col,
                      const void* val, const float* sc, const void* Dinv, const float* dsc, float om,
-                     const float* omr, const float* b, const float* xi, float* xo) {
+                     const float* omr, const float* b, const float* xi, float* xo, const uint8_t* act) {
     const float* v = (const float*)val;
     const float* D = (const float*)Dinv;
     if (xi && spl)
-      LFIT(grid, s, k_smooth_lp<NP, float, false, true>)(nb, rp, col, v, sc, D, dsc, om, omr, b, xi, xo);
+      LFIT(grid, s, k_smooth_lp<NP, float, false, true>)(nb, rp, col, v, sc, D, dsc, om, omr, b, xi, xo, act);
     else if (xi)
-      LFIT(grid, s, k_smooth_lp<NP, float, false>)(nb, rp, col, v, sc, D, dsc, om, omr, b, xi, xo);
+      LFIT(grid, s, k_smooth_lp<NP, float, false>)(nb, rp, col, v, sc, D, dsc, om, omr, b, xi, xo, act);
     else
-      LFIT(grid, s, k_smooth_lp<NP, float, true>)(nb, rp, col, v, sc, D, dsc, om, omr, b, xi, xo);
+      LFIT(grid, s, k_smooth_lp<NP, float, true>)(nb, rp, col, v, sc, D, dsc, om, omr, b, xi, xo, act);
   }
   // val: the FP32 operator copy
   static void resid_rt(int grid, bool spl, cudaStream_t s, int64_t nbf, const int64_t* rp, const int32_t* col,
                        const void* val, const float* sc, const void* R, const float* rsc, const float* b,
-                       const float* x, float* t) {
+                       const float* x, float* t, const uint8_t* act) {
     const float* v = (const float*)val;
     const TS* Rt = (const TS*)R;
     if (x && spl)
-      LFIT(grid, s, k_resid_rt_lp<NP, float, TS, true, true>)(nbf, rp, col, v, sc, Rt, rsc, b, x, t);
+      LFIT(grid, s, k_resid_rt_lp<NP, float, TS, true, true>)(nbf, rp, col, v, sc, Rt, rsc, b, x, t, act);
     else if (x)
-      LFIT(grid, s, k_resid_rt_lp<NP, float, TS, true>)(nbf, rp, col, v, sc, Rt, rsc, b, x, t);
+      LFIT(grid, s, k_resid_rt_lp<NP, float, TS, true>)(nbf, rp, col, v, sc, Rt, rsc, b, x, t, act);
     else
-      LFIT(grid, s, k_resid_rt_lp<NP, float, TS, false>)(nbf, rp, col, v, sc, Rt, rsc, b, x, t);
+      LFIT(grid, s, k_resid_rt_lp<NP, float, TS, false>)(nbf, rp, col, v, sc, Rt, rsc, b, x, t, act);
   }
   // W-cycle coarse residual b - M x with the FP32 operator copy
   static void resid32(int grid, bool spl, cudaStream_t s, int64_t nb, const int64_t* rp, const int32_t* col,
@@ -250,8 +252,8 @@ struct OpsLPT {
     LFIT(grid, s, k_gather_lp<NP>)(nbc, cptr, ch, t, rc);
   }
   static void prolong(int grid, cudaStream_t s, int64_t nbf, const int32_t* agg, const void* R, const float* rsc,
-                      const float* zc, const float* xi, float* xo) {
-    LFIT(grid, s, k_prolong_lp<NP, TS>)(nbf, agg, (const TS*)R, rsc, zc, xi, xo);
+                      const float* zc, const float* xi, float* xo, const uint8_t* act) {
+    LFIT(grid, s, k_prolong_lp<NP, TS>)(nbf, agg, (const TS*)R, rsc, zc, xi, xo, act);
   }
   static void gather_smooth0(int grid, cudaStream_t s, int64_t nbc, const int64_t* cptr, const int32_t* ch,
                              const float* t, const float* Dinv, const float* dsc, float om, const float* omr,
@@ -415,6 +417,8 @@ struct xdg_hier {
   int64_t* ioff = nullptr;      // offset of every problem in the caller's concatenated vectors
   int* gidx = nullptr;          // index of every problem in the caller's list
   Learned lr;                   // learned cut-cell correction (off unless enabled)
+  uint8_t* act1 = nullptr;      // batches: 1 for the level-1 blocks of running problems
+  const uint8_t* cur_act = nullptr;  // row mask of the level-1 cycle kernels (while recording a batch)
   cudaStream_t body_stream = nullptr;
   int64_t bnodes_fixed[3] = {0, 0, 0};  // kernel nodes of a recorded batched solve outside
   int64_t bnodes_body[3] = {0, 0, 0};   // its loop, and inside one loop iteration
@@ -496,10 +500,10 @@ struct xdg_hier {
   }
 
   // ---------------------------------------------------------------- building blocks
-  void spmv(int l, const double* x, const double* b, double* y, int mode) {
+  void spmv(int l, const double* x, const double* b, double* y, int mode, const uint8_t* act = nullptr) {
     ++launches;
     Level& V = L[l];
-    ops.spmv(grid(V.nb), stream, V.nb, V.rp, V.col, V.val, x, b, y, mode);
+    ops.spmv(grid(V.nb), stream, act, V.nb, V.rp, V.col, V.val, x, b, y, mode);
   }
   void smooth(int l, const double* b, const double* xi, double* xo) {
     ++launches;
@@ -610,19 +614,21 @@ struct xdg_hier {
     LevelLP& W = LP[p][l];
     LevelLP& WC = LP[p][l + 1];
     const float om = (float)V.omega;
+    const uint8_t* act = (l == 0) ? cur_act : nullptr;  // finished problems of a batch are skipped
     float* cur = x;
     float* oth = W.t;
     if (!pre0) {
       o.smooth(grid_lp(l), V.spl, stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, V.omr_f, b, nullptr,
-               cur);
+               cur, act);
       ++launches;
     }
     for (int s = 1; s < nu; ++s) {
-      o.smooth(grid_lp(l), V.spl, stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, V.omr_f, b, cur, oth);
+      o.smooth(grid_lp(l), V.spl, stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, V.omr_f, b, cur, oth,
+               act);
       ++launches;
       std::swap(cur, oth);
     }
-    o.resid_rt(grid_lp(l), V.spl, stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.R, W.rsc, b, cur, W.s);
+    o.resid_rt(grid_lp(l), V.spl, stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.R, W.rsc, b, cur, W.s, act);
     launches += 2;
     if (l + 2 < nlev) {
       o.gather_smooth0(grid(C.nb), stream, C.nb, V.cptr, V.ch, W.s, (const float*)WC.Dinv, WC.dsc, (float)C.omega,
@@ -641,12 +647,13 @@ struct xdg_hier {
       }
     }
     float* after = (nu % 2 == 0) ? x : W.t;
-    o.prolong(grid(V.nb), stream, V.nb, V.agg, W.R, W.rsc, WC.x, cur, after);
+    o.prolong(grid(V.nb), stream, V.nb, V.agg, W.R, W.rsc, WC.x, cur, after, act);
     ++launches;
     cur = after;
     oth = (cur == x) ? W.t : x;
     for (int s = 0; s < nu; ++s) {
-      o.smooth(grid_lp(l), V.spl, stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, V.omr_f, b, cur, oth);
+      o.smooth(grid_lp(l), V.spl, stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, V.omr_f, b, cur, oth,
+               act);
       ++launches;
       std::swap(cur, oth);
     }
@@ -660,9 +667,9 @@ struct xdg_hier {
   void cycle_lp_d(int p, const double* r, double* z) {
     const int64_t n = L[0].nb * Np;
     LevelLP& W = LP[p][0];
-    k_d2f<<<vgrid(n), kThreads, 0, stream>>>(n, r, W.b);
+    k_d2f<<<vgrid(n), kThreads, 0, stream>>>(n, r, W.b, cur_act, Np);
     cycle_lp(p, 0, W.b, W.x);
-    k_f2d<<<vgrid(n), kThreads, 0, stream>>>(n, W.x, z);
+    k_f2d<<<vgrid(n), kThreads, 0, stream>>>(n, W.x, z, cur_act, Np);
     launches += 2;
   }
 
@@ -1099,6 +1106,7 @@ int xdg_hier::build(const xdg_problem* p, const xdg_hier_opts* o) {
     TRY(alloc(&B.bad, nprob));
     TRY(alloc(&B.iters, nprob));
     TRY(alloc(&B.it, 1));
+    TRY(alloc(&act1, L[0].nb));
     TRY(alloc(&spart, (size_t)nprob * 64));
     CK(cudaMallocHost(&h_bsc, (nprob + 1) * sizeof(double)));
     const int64_t target = std::max<int64_t>(1, n1 / (4 * (int64_t)sms));
@@ -1337,7 +1345,7 @@ int xdg_hier::tune_split(int p) {
       V.spl = (v == 1);
       auto sweep = [&]() {
         o.smooth(grid_lp(l), V.spl, stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, (float)V.omega,
-                 V.omr_f, W.b, W.x, W.t);
+                 V.omr_f, W.b, W.x, W.t, nullptr);
       };
       for (int k = 0; k < 3; ++k) sweep();
       cudaEventRecord(e0, stream);
@@ -1485,17 +1493,21 @@ int xdg_hier::build_batch(int n, const xdg_problem* probs, const xdg_hier_opts* 
 // zero steps: alpha = 0). The loop condition is set by the convergence check.
 void xdg_hier::batch_iteration(int prec, const BatchCtl* ctl, cudaGraphConditionalHandle cond) {
   const int flex = prec != XDG_PREC_F64;
-  spmv(0, s_p, nullptr, s_q, 0);
+  const int64_t nb1 = L[0].nb;
+  spmv(0, s_p, nullptr, s_q, 0, act1);
   k_chunk_dot<1><<<nchunk, kThreads, 0, stream>>>(nchunk, cb, s_p, s_q, nullptr, nullptr, cpart);
   k_bcg_alpha<<<sgrid(), 256, 0, stream>>>(nprob, cfirst, cpart, B);
   k_bcg_xr<<<nchunk, kThreads, 0, stream>>>(nchunk, cb, cseg, B.alpha, s_p, s_q, s_x, s_r, cpart);
   k_bcg_check<<<1, 1024, 0, stream>>>(nprob, cfirst, cpart, B, ctl, 1, cond, 1);
-  launches += 4;
+  k_bcg_rowact<<<vgrid(nb1), kThreads, 0, stream>>>(nb1, Np, nprob, L[0].sdof, B.active, act1);
+  launches += 5;
+  cur_act = act1;
   precond(prec, s_r, s_z);
+  cur_act = nullptr;
   if (flex) k_chunk_dot<2><<<nchunk, kThreads, 0, stream>>>(nchunk, cb, s_r, s_z, s_z, s_q, cpart);
   else k_chunk_dot<1><<<nchunk, kThreads, 0, stream>>>(nchunk, cb, s_r, s_z, nullptr, nullptr, cpart);
   k_bcg_beta<<<sgrid(), 256, 0, stream>>>(nprob, nchunk, cfirst, cpart, flex, 0, B);
-  k_bcg_p<<<nchunk, kThreads, 0, stream>>>(nchunk, cb, cseg, B.beta, 0, s_z, s_p);
+  k_bcg_p<<<nchunk, kThreads, 0, stream>>>(nchunk, cb, cseg, B.beta, 0, s_z, s_p, B.active);
   launches += 3;
 }
 
@@ -1524,11 +1536,14 @@ int xdg_hier::record_batch(int prec, const BatchCtl* ctl, double* res, int gslot
   cudaGraphConditionalHandle cond;
   CK(cudaGraphConditionalHandleCreate(&cond, cg, 0, cudaGraphCondAssignDefault));
   k_bcg_check<<<1, 1024, 0, stream>>>(nprob, cfirst, nullptr, B, ctl, 0, cond, 1);
-  ++launches;
+  k_bcg_rowact<<<vgrid(L[0].nb), kThreads, 0, stream>>>(L[0].nb, Np, nprob, L[0].sdof, B.active, act1);
+  launches += 2;
+  cur_act = act1;
   precond(prec, s_r, s_z);
+  cur_act = nullptr;
   k_chunk_dot<1><<<nchunk, kThreads, 0, stream>>>(nchunk, cb, s_r, s_z, nullptr, nullptr, cpart);
   k_bcg_beta<<<sgrid(), 256, 0, stream>>>(nprob, nchunk, cfirst, cpart, flex, 1, B);
-  k_bcg_p<<<nchunk, kThreads, 0, stream>>>(nchunk, cb, cseg, B.beta, 1, s_z, s_p);
+  k_bcg_p<<<nchunk, kThreads, 0, stream>>>(nchunk, cb, cseg, B.beta, 1, s_z, s_p, B.active);
   launches += 3;
   CKL();
   // the loop
@@ -2687,6 +2702,87 @@ int fma_probe(int iters, double* tflops) {
   return XDG_OK;
 }
 }  // namespace
+
+extern "C" int xdg_kernel_time(xdg_hier_t h, int which, int level, int prec, int reps, double* ms,
+                               double* bytes) {
+  if (!h || level < 1 || level > h->nlev || which < 0 || which > 2 || (which > 0 && level >= h->nlev) ||
+      prec < 0 || prec > 2 || (prec != XDG_PREC_F64 && !h->has_lp[prec])) {
+    set_err("xdg_kernel_time: bad kernel %d, level %d or precision %d", which, level, prec);
+    return XDG_EINVAL;
+  }
+  const int l = level - 1;
+  Level& V = h->L[l];
+  const int Np = h->Np;
+  const int64_t n = V.nb * Np, np2 = (int64_t)Np * Np;
+  cudaStream_t st = h->stream;
+  const bool lp = prec != XDG_PREC_F64;
+  const double sv = lp ? 4.0 : 8.0;                        // vector entries
+  const double sa = prec == XDG_PREC_F64 ? 8.0 : 4.0;      // operator read by smooth / restrict
+  const double sap = prec == XDG_PREC_BF16 ? 2.0 : sa;     // operator read by apply
+  const double sr = prec == XDG_PREC_BF16 ? 2.0 : sa;      // transfer blocks
+  const double scal = lp ? 4.0 : 0.0;                      // per-block scales
+  const double rows = 8.0 * (V.nb + 1) + 4.0 * V.nnzb;     // row pointer and columns
+  double by = 0.0;
+  std::function<void()> launch;
+  if (!lp) {
+    CK(cudaMemsetAsync(V.b, 0, n * sizeof(double), st));
+    CK(cudaMemsetAsync(V.x, 0, n * sizeof(double), st));
+    if (which == 0) {
+      launch = [&]() { h->ops.spmv(h->grid(V.nb), st, nullptr, V.nb, V.rp, V.col, V.val, V.x, nullptr, V.t, 0); };
+      by = rows + V.nnzb * np2 * 8.0 + 2.0 * n * 8.0;
+    } else if (which == 1) {
+      launch = [&]() {
+        h->ops.smooth(h->grid(V.nb), st, V.nb, V.rp, V.col, V.val, V.Dinv, V.omega, V.omr, V.b, V.x, V.t);
+      };
+      by = rows + V.nnzb * np2 * 8.0 + V.nb * np2 * 8.0 + 3.0 * n * 8.0;
+    } else {
+      launch = [&]() { h->ops.resid_rt(h->grid(V.nb), st, V.nb, V.rp, V.col, V.val, V.R, V.b, V.x, V.s); };
+      by = rows + V.nnzb * np2 * 8.0 + V.nb * np2 * 8.0 + 3.0 * n * 8.0;
+    }
+  } else {
+    LevelLP& W = h->LP[prec][l];
+    const OpsLP& o = h->opl[prec];
+    CK(cudaMemsetAsync(W.b, 0, n * sizeof(float), st));
+    CK(cudaMemsetAsync(W.x, 0, n * sizeof(float), st));
+    if (which == 0) {
+      launch = [&]() {
+        o.spmv_f(h->grid_lp(l), V.spl, st, V.nb, V.rp, V.col, W.val, W.sc, W.x, nullptr, W.t, 0);
+      };
+      by = rows + V.nnzb * (np2 * sap + scal) + 2.0 * n * sv;
+    } else if (which == 1) {
+      launch = [&]() {
+        o.smooth(h->grid_lp(l), V.spl, st, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, (float)V.omega,
+                 V.omr_f, W.b, W.x, W.t, nullptr);
+      };
+      by = rows + V.nnzb * (np2 * sa + scal) + V.nb * (np2 * 4.0 + scal) + 3.0 * n * sv;
+    } else {
+      launch = [&]() {
+        o.resid_rt(h->grid_lp(l), V.spl, st, V.nb, V.rp, V.col, W.val32, W.sc32, W.R, W.rsc, W.b, W.x, W.s, nullptr);
+      };
+      by = rows + V.nnzb * (np2 * sa + scal) + V.nb * (np2 * sr + scal) + 3.0 * n * sv;
+    }
+  }
+  const int R = reps > 0 ? reps : 20;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (int k = 0; k < 3; ++k) launch();
+  cudaEventRecord(e0, st);
+  for (int k = 0; k < R; ++k) launch();
+  cudaEventRecord(e1, st);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) {
+    set_err("xdg_kernel_time: %s", cudaGetErrorString(e));
+    return XDG_ECUDA;
+  }
+  if (ms) *ms = t / R;
+  if (bytes) *bytes = by;
+  return XDG_OK;
+}
 
 extern "C" int xdg_fma_peak(int prec, double* tflops) {
   if (!tflops) {

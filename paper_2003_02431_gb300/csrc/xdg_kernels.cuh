@@ -47,10 +47,17 @@ __device__ __forceinline__ void ldrow(const double* __restrict__ p, double (&v)[
 // blocks of a row whose loads are put in flight together: the column indices of a chunk are
 // read first, so the dependent x-block loads of the chunk overlap (short rows of coarse levels
 // run with few warps, where a block-by-block dependent chain is not hidden)
+// blocks of a row whose loads are issued together (FP32 kernels: Np <= 10 and Np > 10)
+#ifndef XDG_CH32_SMALL
+#define XDG_CH32_SMALL 4
+#endif
+#ifndef XDG_CH32_LARGE
+#define XDG_CH32_LARGE 2
+#endif
 template <int NP>
 struct Chunk {
   static constexpr int F64 = NP <= 10 ? 2 : 1;
-  static constexpr int F32 = NP <= 10 ? 4 : 2;
+  static constexpr int F32 = NP <= 10 ? XDG_CH32_SMALL : XDG_CH32_LARGE;
 };
 
 // acc += A[z][r][:] . x[col[z]][:] over the block row (lane r), blocks in increasing z
@@ -77,14 +84,15 @@ __device__ __forceinline__ double row_dot(int64_t z0, int64_t z1, int r, const i
 }
 
 // ------------------------------------------------------------------------------------------
-// operator apply: y = M x (MODE 0) or y = b - M x (MODE 1)
+// operator apply: y = M x (MODE 0) or y = b - M x (MODE 1); act (optional): rows with
+// act[i] == 0 are skipped (finished problems of a batch)
 template <int NP, int MODE>
 __global__ void __launch_bounds__(kThreads) k_spmv(int64_t nb, const int64_t* __restrict__ rp,
                                                   const int32_t* __restrict__ col,
                                                   const double* __restrict__ val,
                                                   const double* __restrict__ x,
                                                   const double* __restrict__ b,
-                                                  double* __restrict__ y) {
+                                                  double* __restrict__ y, const uint8_t* __restrict__ act) {
   constexpr int GPW = Grp<NP>::GPW;
   const int lane = threadIdx.x & 31;
   const int g = lane / NP, r = lane - g * NP;
@@ -92,6 +100,7 @@ __global__ void __launch_bounds__(kThreads) k_spmv(int64_t nb, const int64_t* __
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = warp * GPW + g; i < nb; i += nw * GPW) {
+    if (act && !act[i]) continue;
     double acc = row_dot<NP>(__ldg(rp + i), __ldg(rp + i + 1), r, col, val, x);
     y[i * NP + r] = MODE ? b[i * NP + r] - acc : acc;
   }

@@ -283,7 +283,9 @@ __global__ void k_bcg_alpha(int nseg, const int* __restrict__ cfirst, const doub
   }
 }
 
-// x += alpha_s p, r -= alpha_s q on chunk c of problem s = cseg[c]; part[c] = (r, r) on it
+// x += alpha_s p, r -= alpha_s q on chunk c of problem s = cseg[c]; part[c] = (r, r) on it.
+// A finished problem (alpha_s = 0) is not touched: its p may hold values the row-masked
+// kernels never wrote.
 __global__ void __launch_bounds__(kThreads) k_bcg_xr(int nchunk, const int64_t* __restrict__ cb,
                                                     const int* __restrict__ cseg, const double* __restrict__ alpha,
                                                     const double* __restrict__ p, const double* __restrict__ q,
@@ -292,6 +294,10 @@ __global__ void __launch_bounds__(kThreads) k_bcg_xr(int nchunk, const int64_t* 
   const int c = blockIdx.x;
   if (c >= nchunk) return;
   const double a = alpha[cseg[c]];
+  if (a == 0.0) {
+    if (threadIdx.x == 0) part[c] = 0.0;
+    return;
+  }
   double acc = 0.0;
   for (int64_t i = cb[c] + threadIdx.x; i < cb[c + 1]; i += blockDim.x) {
     const double ri = fma(-a, q[i], r[i]);
@@ -361,14 +367,21 @@ __global__ void k_bcg_beta(int nseg, int nchunk, const int* __restrict__ cfirst,
   }
 }
 
-// p = z + beta_s p on chunk c (start != 0: p = z)
+// p = z + beta_s p on chunk c (start != 0: p = z), for running problems only
 __global__ void k_bcg_p(int nchunk, const int64_t* __restrict__ cb, const int* __restrict__ cseg,
                         const double* __restrict__ beta, int start, const double* __restrict__ z,
-                        double* __restrict__ p) {
+                        double* __restrict__ p, const int* __restrict__ active) {
   const int c = blockIdx.x;
-  if (c >= nchunk) return;
+  if (c >= nchunk || !active[cseg[c]]) return;
   const double be = beta[cseg[c]];
   for (int64_t i = cb[c] + threadIdx.x; i < cb[c + 1]; i += blockDim.x) p[i] = start ? z[i] : fma(be, p[i], z[i]);
+}
+
+// act[i] = 1 while the problem of level-1 block i is running (sdof: DOF offsets of the problems)
+__global__ void k_bcg_rowact(int64_t nb, int np, int nseg, const int64_t* __restrict__ sdof,
+                             const int* __restrict__ active, uint8_t* __restrict__ act) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += (int64_t)gridDim.x * blockDim.x)
+    act[i] = (uint8_t)(active[find_seg(sdof, nseg, i * np)] != 0);
 }
 
 // per-problem results: res[3 g] = iterations, res[3 g + 1] = ||b - M x|| / ||b|| (true residual

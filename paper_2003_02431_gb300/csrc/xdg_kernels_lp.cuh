@@ -13,6 +13,17 @@
 
 #include "xdg_kernels.cuh"
 
+// minimum resident CTAs per SM requested for the FP32 row kernels
+#ifndef XDG_LP_MINB
+#define XDG_LP_MINB 1
+#endif
+// residual-restriction: load the transfer block's column before the row's dot product, so
+// that its loads overlap the dot product's (measured faster at 64^3; the same prefetch of the
+// block inverse slows the smoother down, which keeps its loads after the dot product)
+#ifndef XDG_PREFETCH_EPI
+#define XDG_PREFETCH_EPI 1
+#endif
+
 namespace xdg {
 
 template <class T>
@@ -118,7 +129,7 @@ __device__ __forceinline__ float split_sum(float part, int r) {
 
 // y = M x (MODE 0) or b - M x (MODE 1); VT = vector type of x, b and y (float or double)
 template <int NP, class TS, class VT, int MODE, bool SPL = false>
-__global__ void __launch_bounds__(kThreads) k_spmv_lp(int64_t nb, const int64_t* __restrict__ rp,
+__global__ void __launch_bounds__(kThreads, XDG_LP_MINB) k_spmv_lp(int64_t nb, const int64_t* __restrict__ rp,
                                                      const int32_t* __restrict__ col,
                                                      const TS* __restrict__ val, const float* __restrict__ sc,
                                                      const VT* __restrict__ x, const VT* __restrict__ b,
@@ -158,13 +169,14 @@ __device__ __forceinline__ float block_gemv_lp(const TS* __restrict__ W, float s
 // computed in FP64 and stored in FP32 in both modes: rounding the inverse of an ill-conditioned
 // cut-cell block to BF16 loses it.
 template <int NP, class TS, bool ZERO, bool SPL = false>
-__global__ void __launch_bounds__(kThreads) k_smooth_lp(int64_t nb, const int64_t* __restrict__ rp,
+__global__ void __launch_bounds__(kThreads, XDG_LP_MINB) k_smooth_lp(int64_t nb, const int64_t* __restrict__ rp,
                                                        const int32_t* __restrict__ col,
                                                        const TS* __restrict__ val, const float* __restrict__ sc,
                                                        const float* __restrict__ Dinv, const float* __restrict__ dsc,
                                                        float omega, const float* __restrict__ omr,
                                                        const float* __restrict__ b,
-                                                       const float* __restrict__ xi, float* __restrict__ xo) {
+                                                       const float* __restrict__ xi, float* __restrict__ xo,
+                                                       const uint8_t* __restrict__ act) {
   constexpr int GPW = Grp<NP>::GPW;
   const int lane = threadIdx.x & 31;
   const int g = lane / NP, r = lane - g * NP;
@@ -174,6 +186,7 @@ __global__ void __launch_bounds__(kThreads) k_smooth_lp(int64_t nb, const int64_
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   if constexpr (SPL) {
     for (int64_t i = warp; i < nb; i += nw) {
+      if (act && !act[i]) continue;
       float res = b[i * NP + r];
       if (!ZERO)
         res -= split_sum<NP>(row_dot_lp_part<NP, TS, float>(__ldg(rp + i), __ldg(rp + i + 1), g, r, col, val, sc,
@@ -184,6 +197,7 @@ __global__ void __launch_bounds__(kThreads) k_smooth_lp(int64_t nb, const int64_
     }
   } else {
     for (int64_t i = warp * GPW + g; i < nb; i += nw * GPW) {
+      if (act && !act[i]) continue;
       float res = b[i * NP + r];
       if (!ZERO) res -= row_dot_lp<NP, TS, float>(__ldg(rp + i), __ldg(rp + i + 1), r, col, val, sc, xi);
       float z = block_gemv_lp<NP, float>(Dinv + i * (NP * NP), __ldg(dsc + i), r, g * NP, mask, res);
@@ -197,12 +211,12 @@ __global__ void __launch_bounds__(kThreads) k_smooth_lp(int64_t nb, const int64_
 // copy in both modes (TA = float): a BF16-rounded operator is not positive definite on the
 // smooth modes the coarse levels correct (2^-9 cond(M) >> 1); TR is the transfer storage.
 template <int NP, class TA, class TR, bool RESID, bool SPL = false>
-__global__ void __launch_bounds__(kThreads) k_resid_rt_lp(int64_t nbf, const int64_t* __restrict__ rp,
+__global__ void __launch_bounds__(kThreads, XDG_LP_MINB) k_resid_rt_lp(int64_t nbf, const int64_t* __restrict__ rp,
                                                          const int32_t* __restrict__ col,
                                                          const TA* __restrict__ val, const float* __restrict__ sc,
                                                          const TR* __restrict__ R, const float* __restrict__ rsc,
                                                          const float* __restrict__ b, const float* __restrict__ x,
-                                                         float* __restrict__ t) {
+                                                         float* __restrict__ t, const uint8_t* __restrict__ act) {
   constexpr int GPW = Grp<NP>::GPW;
   const int lane = threadIdx.x & 31;
   const int g = lane / NP, r = lane - g * NP;
@@ -213,6 +227,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_rt_lp(int64_t nbf, const int
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   if constexpr (SPL) {
     for (int64_t f = warp; f < nbf; f += nw) {
+      if (act && !act[f]) continue;
       float res = b[f * NP + r];
       if (RESID)
         res -= split_sum<NP>(row_dot_lp_part<NP, TA, float>(__ldg(rp + f), __ldg(rp + f + 1), g, r, col, val, sc,
@@ -225,12 +240,19 @@ __global__ void __launch_bounds__(kThreads) k_resid_rt_lp(int64_t nbf, const int
     }
   } else {
     for (int64_t f = warp * GPW + g; f < nbf; f += nw * GPW) {
+      if (act && !act[f]) continue;
+      const TR* Rf = R + f * (NP * NP);
+      float rc[NP];
+      if (XDG_PREFETCH_EPI) {
+#pragma unroll
+        for (int m = 0; m < NP; ++m) rc[m] = to_f<TR>(Rf[m * NP + r]);
+      }
       float res = b[f * NP + r];
       if (RESID) res -= row_dot_lp<NP, TA, float>(__ldg(rp + f), __ldg(rp + f + 1), r, col, val, sc, x);
-      const TR* Rf = R + f * (NP * NP);
       float s = 0.0f;
 #pragma unroll
-      for (int m = 0; m < NP; ++m) s = fmaf(to_f<TR>(Rf[m * NP + r]), __shfl_sync(mask, res, base + m), s);
+      for (int m = 0; m < NP; ++m)
+        s = fmaf(XDG_PREFETCH_EPI ? rc[m] : to_f<TR>(Rf[m * NP + r]), __shfl_sync(mask, res, base + m), s);
       t[f * NP + r] = __ldg(rsc + f) * s;
     }
   }
@@ -277,7 +299,8 @@ __global__ void __launch_bounds__(kThreads) k_gather_smooth0_lp(int64_t nbc, con
 template <int NP, class TS>
 __global__ void __launch_bounds__(kThreads) k_prolong_lp(int64_t nbf, const int32_t* __restrict__ agg,
                                                         const TS* __restrict__ R, const float* __restrict__ rsc,
-                                                        const float* __restrict__ zc, const float* xi, float* xo) {
+                                                        const float* __restrict__ zc, const float* xi, float* xo,
+                                                        const uint8_t* __restrict__ act) {
   constexpr int GPW = Grp<NP>::GPW;
   const int lane = threadIdx.x & 31;
   const int g = lane / NP, r = lane - g * NP;
@@ -285,6 +308,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong_lp(int64_t nbf, const int3
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t f = warp * GPW + g; f < nbf; f += nw * GPW) {
+    if (act && !act[f]) continue;
     float a[NP], z[NP];
     ldrow_f<NP, TS>(R + f * (NP * NP) + r * NP, a);
     ldrow_f<NP, float>(zc + (int64_t)__ldg(agg + f) * NP, z);
@@ -334,14 +358,17 @@ __global__ void k_make_lp(int64_t nblk, int np2, const double* __restrict__ src,
   if (lane == 0) scale[blk] = sf;
 }
 
-__global__ void k_d2f(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+// act (optional): entries of rows i = e / np with act[i] == 0 are skipped
+__global__ void k_d2f(int64_t n, const double* __restrict__ a, float* __restrict__ b,
+                      const uint8_t* __restrict__ act = nullptr, int np = 1) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = (float)a[i];
+    if (!act || act[i / np]) b[i] = (float)a[i];
 }
 
-__global__ void k_f2d(int64_t n, const float* __restrict__ a, double* __restrict__ b) {
+__global__ void k_f2d(int64_t n, const float* __restrict__ a, double* __restrict__ b,
+                      const uint8_t* __restrict__ act = nullptr, int np = 1) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = (double)a[i];
+    if (!act || act[i / np]) b[i] = (double)a[i];
 }
 
 __global__ void k_axpy_f(int64_t n, float a, const float* __restrict__ x, float* __restrict__ y) {

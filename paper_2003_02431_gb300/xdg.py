@@ -120,6 +120,7 @@ SIGNATURES = [
     ("xdg_restrict_noalloc", C.c_int, [_ip, C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                       _vp]),
     ("xdg_fma_peak", C.c_int, [_ip, _dp]),
+    ("xdg_kernel_time", C.c_int, [_vp, _ip, _ip, _ip, _ip, _dp, _dp]),
     ("xdg_mlp_create", C.c_int, [_ip, _ip, C.c_uint64, _vp, C.POINTER(_vp)]),
     ("xdg_mlp_destroy", C.c_int, [_vp]),
     ("xdg_mlp_num_params", C.c_int, [_vp, C.POINTER(C.c_int64)]),
@@ -297,6 +298,15 @@ class Hierarchy:
     def set_damping(self, level, omega):
         with _Ordered(self):
             _check(load().xdg_set_damping(self._h, level, omega))
+
+    KERNEL_APPLY, KERNEL_SMOOTH, KERNEL_RESTRICT = 0, 1, 2
+
+    def kernel_time(self, which, level, prec=XDG_PREC_F64, reps=20):
+        """(mean ms per launch, algorithmic bytes per launch) of one cycle kernel on a level."""
+        ms, by = C.c_double(), C.c_double()
+        with _Ordered(self):
+            _check(load().xdg_kernel_time(self._h, which, level, prec, reps, C.byref(ms), C.byref(by)))
+        return ms.value, by.value
 
     def smooth(self, level, b, x_in, x_out):
         with _Ordered(self):
