@@ -102,12 +102,16 @@ KERNEL_NAMES = {
     "apply_f32": "k_spmv_lp<10,float,float,0>: level-1 FP32 operator apply",
     "apply_f64": "k_spmv<10,0>: level-1 FP64 operator apply (outer flexible CG)",
 }
-# the kernel with the largest share of the mixed solve's device time (launch list in
-# profiles/launch_list_mixed_solve_64cube.md)
-DOMINANT = "resid_rt_f32"
-# DRAM bytes (read + write) of one level-1 launch at 64^3, from one ncu capture of the same
-# kernels (profiles/level1_kernels_dram_64cube.md); None until taken for the current code
-NCU_TRAFFIC = {}
+# the kernel with the largest share of the mixed solve's device time, and the largest HBM-bound
+# one (launch list in profiles/launch_list_mixed_solve_64cube.md)
+DOMINANT = "apply_f64"
+DOMINANT_HBM = "resid_rt_f32"
+# DRAM bytes (read + write) of one level-1 launch at 64^3, from one ncu capture of the current
+# kernels (profiles/level1_kernels_dram_64cube.md)
+NCU_TRAFFIC = {"apply_f64": 1568570112, "resid_rt_f32": 898302720, "smooth_f32": 897740032}
+# FP64 ALU peak from unit counts and clocks: 152 SMs x 2070 MHz x 4 FP64 flop per SM and clock
+# (2 FMA), the rate of GB300's nominal 1.25 TFLOP/s FP64
+FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 
 
 def make_problem():
@@ -320,6 +324,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 256-problem workload")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-correction section")
+    ap.add_argument("--split-mask", type=int, default=-1,
+                    help="force the split-row mapping per level (bit l: level l+1) instead of the autotuned one "
+                         "(for profiler runs, where the autotuner's timings are distorted)")
     ap.add_argument("--size", type=int, default=64,
                     help="cells per direction; 64 is the benchmark workload, smaller sizes serve profiling")
     args = ap.parse_args()
@@ -351,6 +358,9 @@ def main():
     t = time.perf_counter()
     H = xdg.Hierarchy.from_problem(P, gamma=GAMMA, w_levels=W_LEVELS, low_precision=3, stream=stream)
     setup_s = time.perf_counter() - t
+    if args.split_mask >= 0:
+        for l in range(len(P.nb)):
+            H.set_split(l + 1, (args.split_mask >> l) & 1)
     hinfo = H.info()
     b = torch.from_numpy(P.b.reshape(-1).copy()).to(dev)
     x = torch.zeros(n, dtype=torch.float64, device=dev)
@@ -422,7 +432,7 @@ def main():
     flops_apply = 2.0 * nnzb * Np * Np
     ach64 = flops_apply / (kernels["apply_f64"]["ms"] / 1e3) / 1e12
     kernels["apply_f64"].update({"bound": "alu", "tflops": ach64, "frac_fp64_peak": ach64 / fp64_peak})
-    dom = kernels[DOMINANT]
+    dom, domh = kernels[DOMINANT], kernels[DOMINANT_HBM]
 
     # end to end through the host-buffer entry point (pinned host memory)
     bh = torch.from_numpy(P.b.reshape(-1).copy()).pin_memory().numpy()
@@ -466,6 +476,7 @@ def main():
                        "levels": hinfo["nb"], "cycle": "W(1,1) on the 2 finest levels, V below; block Jacobi",
                        "outer": "flexible CG, FP64 apply/residual/update", "tol": TOL, "iterations": iters,
                        "parallelism": "replicas" if world > 1 else "single",
+                       "split_rows_levels": hinfo["split"],
                        "l2": "inputs larger than L2 (operator 1.49 GB FP64 + 0.74 GB FP32)"},
             "paths": {
                 "mixed_f32": {"solve_ms": t_ms / args.steps, "iterations": iters, "mdofs": value / world},
@@ -478,12 +489,18 @@ def main():
             "vcycle_mdofs": {"f64": n / cyc_ms[0] / 1e3, "f32": n / cyc_ms[1] / 1e3, "bf16": n / cyc_ms[2] / 1e3},
             "vcycle_ms": cyc_ms,
             "setup_s": setup_s, "setup_ms_phases": hinfo["setup_ms"],
-            "roofline": {"bound": "hbm", "kernel": dom["kernel"], "achieved": dom["achieved_gbs"], "peak": hbm,
-                         "unit": "GB/s", "frac": dom["achieved_gbs"] / hbm, "peak_kind": hbm_kind,
-                         "bytes": dom["bytes"], "ms": dom["ms"],
+            "roofline": {"bound": "alu", "kernel": dom["kernel"], "achieved": ach64, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": ach64 / FP64_PEAK_TFLOPS,
+                         "peak_kind": "FP64 unit counts x clock (152 SMs x 2.07 GHz x 4 flop); the library's "
+                                      "FMA probe reaches %.3f TFLOP/s of it" % fp64_peak,
+                         "flops": flops_apply, "bytes": dom["bytes"], "ms": dom["ms"],
                          "traffic": NCU_TRAFFIC.get(DOMINANT) if SIZE == 64 else None},
+            "roofline_hbm": {"bound": "hbm", "kernel": domh["kernel"], "achieved": domh["achieved_gbs"], "peak": hbm,
+                             "unit": "GB/s", "frac": domh["achieved_gbs"] / hbm, "peak_kind": hbm_kind,
+                             "bytes": domh["bytes"], "ms": domh["ms"],
+                             "traffic": NCU_TRAFFIC.get(DOMINANT_HBM) if SIZE == 64 else None},
             "kernels_level1": kernels,
-            "fp64_peak_tflops": fp64_peak,
+            "fp64_fma_probe_tflops": fp64_peak,
             "batched": batched,
             "learned": learned_out,
             "cpu_baseline": cpu,

@@ -167,6 +167,13 @@ int xdg_export_level(xdg_hier_t h, int level, int64_t* row_ptr, int32_t* col, do
  * (XDG_PREC_F64, or F32 / BF16 when built with low_precision; FP32 accumulation then). */
 int xdg_apply(xdg_hier_t h, int level, const double* x, double* y, int prec);
 
+/* Set the row mapping of the low-precision kernels on `level` (1-based): on != 0 splits each
+ * block row over a warp's groups, 0 gives each group its own row (see
+ * xdg_hier_opts.split_rows; creation autotunes it). Records the low-precision solve graphs
+ * again. For reproducing a mapping, e.g. in a profiler where the autotuner's timings are not
+ * representative. */
+int xdg_set_split(xdg_hier_t h, int level, int on);
+
 /* Replace the smoother damping of `level` (1 <= level < n_levels) by omega > 0 (default:
  * 4 / (3 lambda_l) from the Lanczos estimate). Records the solve graphs again. Not for the
  * hierarchy of a batch group (EINVAL). */

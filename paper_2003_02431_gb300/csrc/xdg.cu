@@ -1987,6 +1987,27 @@ int xdg_apply(xdg_hier_t h, int level, const double* x, double* y, int prec) {
   return XDG_OK;
 }
 
+int xdg_set_split(xdg_hier_t h, int level, int on) {
+  if (!h || level < 1 || level > h->nlev) {
+    set_err("xdg_set_split: bad level %d", level);
+    return XDG_EINVAL;
+  }
+  h->L[level - 1].spl = (on != 0);
+  h->tuned = true;
+  // the recorded low-precision graphs hold the launch shapes: record them again
+  for (int p = 1; p < 3; ++p) {
+    if (h->has_lp[p]) TRY(h->capture(&h->g_iter_lp[p], 3, nullptr, nullptr, p));
+    if (h->g_cyc_lp[p]) cudaGraphExecDestroy(h->g_cyc_lp[p]);
+    h->g_cyc_lp[p] = nullptr;
+    h->g_cyc_lp_b[p] = nullptr;
+  }
+  for (int p = 0; p < 3; ++p) {
+    if (h->lr.g_iter[p]) cudaGraphExecDestroy(h->lr.g_iter[p]);
+    h->lr.g_iter[p] = nullptr;
+  }
+  return XDG_OK;
+}
+
 int xdg_set_damping(xdg_hier_t h, int level, double omega) {
   if (!h || level < 1 || level >= h->nlev || !(omega > 0.0) || !std::isfinite(omega)) {
     set_err("xdg_set_damping: bad level %d or omega %g", level, omega);

@@ -110,6 +110,7 @@ SIGNATURES = [
     ("xdg_apply", C.c_int, [_vp, _ip, _vp, _vp, _ip]),
     ("xdg_smooth", C.c_int, [_vp, _ip, _vp, _vp, _vp]),
     ("xdg_set_damping", C.c_int, [_vp, _ip, C.c_double]),
+    ("xdg_set_split", C.c_int, [_vp, _ip, _ip]),
     ("xdg_restrict", C.c_int, [_vp, _ip, _vp, _vp, _vp]),
     ("xdg_prolong", C.c_int, [_vp, _ip, _vp, _vp, _vp]),
     ("xdg_coarse_solve", C.c_int, [_vp, _vp, _vp]),
@@ -294,6 +295,10 @@ class Hierarchy:
     def apply(self, level, x, y, prec=XDG_PREC_F64):
         with _Ordered(self):
             _check(load().xdg_apply(self._h, level, _dptr(x), _dptr(y), prec))
+
+    def set_split(self, level, on):
+        with _Ordered(self):
+            _check(load().xdg_set_split(self._h, level, int(bool(on))))
 
     def set_damping(self, level, omega):
         with _Ordered(self):
