@@ -114,6 +114,21 @@ NCU_TRAFFIC = {"apply_f64": 1568570112, "resid_rt_f32": 898302720, "smooth_f32":
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 
 
+def max_over_ranks(value, dist, device=None):
+    """The largest of every rank's value (the job's time is its slowest rank's)."""
+    import torch
+    dev = "cpu" if dist.get_backend() == "gloo" else device
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_rank, steps, seconds):
+    """Whole-job throughput in millions of units per second: every rank processes its own
+    copy of the workload (replicas), the job takes its slowest rank's time."""
+    return world * units_per_rank * steps / seconds / 1e6
+
+
 def make_problem():
     import xdg_problem as xp
     return xp.Problem(xp.config_3d_64(N=SIZE, max_coarse_dof=1000))
@@ -390,16 +405,14 @@ def main():
             dist.barrier()
         ms = ev0.elapsed_time(ev1)
         if dist:
-            tt = torch.tensor([ms], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms = float(tt.item())
+            ms = max_over_ranks(ms, dist, dev)
         return ms, launches, iters
 
     # XDG_BENCH_PROFILE_RANGE=1 marks the headline timed region for `ncu --profile-from-start off`
     prof = os.environ.get("XDG_BENCH_PROFILE_RANGE") == "1"
     with ClockSampler(local) as clocks:
         t_ms, launches, iters = timed_solves(xdg.XDG_PREC_F32, args.steps, prof=prof)
-    value = world * n * args.steps / (t_ms / 1e3) / 1e6
+    value = job_throughput(world, n, args.steps, t_ms / 1e3)
     t64_ms, _, iters64 = timed_solves(xdg.XDG_PREC_F64, args.steps)
     tbf_ms, _, itersbf = timed_solves(xdg.XDG_PREC_BF16, args.steps)
 
@@ -445,10 +458,8 @@ def main():
         H.solve_host(bh, xh, tol=TOL, maxit=1000, precision=xdg.XDG_PREC_F32)
     e2e_s = time.perf_counter() - t
     if dist:
-        tt = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e = world * n * args.steps / e2e_s / 1e6
+        e2e_s = max_over_ranks(e2e_s, dist, dev)
+    e2e = job_throughput(world, n, args.steps, e2e_s)
 
     learned_out = None
     if not args.no_learned:

@@ -104,6 +104,11 @@ typedef struct {
                          at creation (one block row per group of Np lanes, or one row per warp
                          with the warp's groups splitting the row, whichever sweeps faster);
                          1 = never split; 2 = split on every level */
+  int fused_coarse;   /* low-precision cycle: the V-cycle of the small levels below the W levels
+                         (from the first of them with at most 16384 blocks) as one persistent
+                         cooperative launch with grid barriers between its steps: 0 = if it
+                         measures faster at creation, 1 = never, 2 = always (single problems
+                         only; batches launch every step) */
 } xdg_hier_opts;
 
 typedef struct {
@@ -137,6 +142,7 @@ typedef struct {
   size_t device_bytes;    /* device memory held by the handle */
   double setup_ms[3];     /* upload+validation, Galerkin products, factorisations+estimates */
   uint64_t split_mask;    /* bit l set: level l+1's low-precision row kernels split rows */
+  int fused_level;        /* > 0: the low-precision cycle runs levels fused_level.. in one launch */
 } xdg_hier_info;
 
 /* Build the hierarchy on the current CUDA device: validate every index on the host

@@ -26,6 +26,7 @@
 #include "xdg_kernels_lp.cuh"
 #include "xdg_kernels_batch.cuh"
 #include "xdg_kernels_mlp.cuh"
+#include "xdg_kernels_fused.cuh"
 
 using namespace xdg;
 
@@ -190,6 +191,8 @@ struct OpsLP {
                   const float*, const float*, float*);
   void (*gather_smooth0)(int, cudaStream_t, int64_t, const int64_t*, const int32_t*, const float*, const float*,
                          const float*, float, const float*, float*, float*);
+  cudaError_t (*fused)(cudaStream_t, int grid, const FusedCycle*, int pre0);
+  int (*fused_occupancy)();
   size_t elem;
 };
 
@@ -260,8 +263,28 @@ struct OpsLPT {
                              float* bc, float* xc) {
     LFIT(grid, s, k_gather_smooth0_lp<NP>)(nbc, cptr, ch, t, Dinv, dsc, om, omr, bc, xc);
   }
+  // the V-cycle of the small levels in one cooperative launch (all CTAs resident)
+  static cudaError_t fused(cudaStream_t s, int grid, const FusedCycle* F, int pre0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_fused_vcycle<NP, TS>, F, pre0);
+  }
+  static int fused_occupancy() {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused_vcycle<NP, TS>, kThreads, 0) != cudaSuccess) occ = 0;
+    return occ;
+  }
   static OpsLP get() {
-    return OpsLP{make, spmv_f, spmv_d, smooth, resid_rt, gather, prolong, resid32, gather_smooth0, sizeof(TS)};
+    return OpsLP{make, spmv_f, spmv_d, smooth, resid_rt, gather, prolong, resid32, gather_smooth0, fused,
+                 fused_occupancy, sizeof(TS)};
   }
 };
 
@@ -603,6 +626,12 @@ struct xdg_hier {
   // ---------------------------------------------------------------- low-precision cycle
   void cycle_lp(int p, int l, const float* b, float* x, bool pre0 = false) {
     const OpsLP& o = opl[p];
+    if (fused_on[p] && l == fused_lc && pre0 && b == LP[p][l].b && x == LP[p][l].x) {
+      cudaMemsetAsync(fbar, 0, sizeof(unsigned), stream);
+      o.fused(stream, fused_grid[p], fdesc[p], 1);
+      ++launches;
+      return;
+    }
     if (l == nlev - 1) {
       ++launches;
       int64_t blocks = (nc * 32 + kThreads - 1) / kThreads;
@@ -710,6 +739,17 @@ struct xdg_hier {
   int tune_split(int p);
   bool tuned = false;
   int split_mode = 0;  // xdg_hier_opts.split_rows
+  // small levels of the low-precision cycle as one persistent launch (levels fused_lc..)
+  int fused_mode = 0;  // xdg_hier_opts.fused_coarse
+  int fused_lc = -1;
+  bool fused_on[3] = {false, false, false};
+  int fused_grid[3] = {0, 0, 0};
+  FusedCycle* fdesc[3] = {nullptr, nullptr, nullptr};
+  unsigned* fbar = nullptr;
+  int* ferr = nullptr;
+  int write_fused(int p);
+  int tune_fused(int p);
+  int fused_error();
 
   // which: 0 FP64 cycle, 1 FP64 CG iteration, 2 low-precision cycle, 3 flexible-CG iteration
   int capture(cudaGraphExec_t* out, int which, const double* b, double* x, int p = 0) {
@@ -900,6 +940,7 @@ int xdg_hier::build(const xdg_problem* p, const xdg_hier_opts* o) {
   gamma = o && o->gamma > 0 ? o->gamma : 1;
   wlev = o && o->w_levels > 0 ? o->w_levels : (1 << 20);
   split_mode = o ? o->split_rows : 0;
+  fused_mode = o ? o->fused_coarse : 0;
   const int lsteps = o && o->lanczos_steps > 0 ? o->lanczos_steps : 12;
   const int64_t Np2 = (int64_t)Np * Np;
   CK(cudaGetDevice(&dev));
@@ -1317,6 +1358,11 @@ int xdg_hier::build_lp(int p) {
       tuned = true;
     }
   }
+  TRY(write_fused(p));
+  if (fused_lc >= 0 && nprob == 1 && fused_mode != 1) {
+    if (fused_mode == 2) fused_on[p] = true;
+    else TRY(tune_fused(p));
+  }
   TRY(capture(&g_iter_lp[p], 3, nullptr, nullptr, p));
   return XDG_OK;
 }
@@ -1325,6 +1371,112 @@ int xdg_hier::build_lp(int p) {
 // with one block row per group (rows spread over the warp's groups) and with one row per warp
 // (the warp's groups splitting each row), and keep the faster (split only when >= 5 % faster).
 // The same mapping then serves the residual-restriction and operator kernels of that level.
+// CTAs per SM of the fused small-level cycle (fewer CTAs: cheaper grid barriers)
+#ifndef XDG_FUSED_CTAS_PER_SM
+#define XDG_FUSED_CTAS_PER_SM 4
+#endif
+
+// The fused small-level cycle of precision p: the first fused level is the first level below
+// the W-cycle levels (at least level 2) with at most 16384 blocks, if it lies above the
+// coarsest; the descriptor lists every fused level's arrays.
+int xdg_hier::write_fused(int p) {
+  fused_lc = -1;
+  const int lc = std::max(1, std::min(wlev, nlev));
+  if (lc + 2 > nlev || L[lc].nb > 16384 || nlev - lc > kFusedMaxLevels) return XDG_OK;
+  fused_lc = lc;
+  if (!fbar) {
+    TRY(alloc(&fbar, 1));
+    TRY(alloc(&ferr, 1));
+    CK(cudaMemsetAsync(ferr, 0, sizeof(int), stream));
+  }
+  if (!fdesc[p]) TRY(alloc(&fdesc[p], 1));
+  FusedCycle h;
+  std::memset(&h, 0, sizeof(h));
+  h.n = nlev - lc;
+  h.nu = nu;
+  for (int l = lc; l < nlev; ++l) {
+    Level& V = L[l];
+    LevelLP& W = LP[p][l];
+    FusedLevel& f = h.L[l - lc];
+    f.nb = V.nb;
+    f.rp = V.rp;
+    f.col = V.col;
+    f.val = (const float*)W.val32;
+    f.sc = W.sc32;
+    f.Dinv = (const float*)W.Dinv;
+    f.dsc = W.dsc;
+    f.omega = (float)V.omega;
+    f.spl = V.spl ? 1 : 0;
+    f.R = W.R;
+    f.rsc = W.rsc;
+    f.agg = V.agg;
+    f.cptr = V.cptr;
+    f.ch = V.ch;
+    f.b = W.b;
+    f.x = W.x;
+    f.t = W.t;
+    f.s = W.s;
+  }
+  h.Minv = Minv;
+  h.doff = cs_doff;
+  h.moff = cs_moff;
+  h.nseg = nprob;
+  h.nc = nc;
+  h.bar = fbar;
+  h.err = ferr;
+  CK(cudaMemcpyAsync(fdesc[p], &h, sizeof(h), cudaMemcpyHostToDevice, stream));
+  const int occ = opl[p].fused_occupancy();
+  fused_grid[p] = std::max(1, std::min(occ, XDG_FUSED_CTAS_PER_SM)) * sms;
+  if (occ < 1) fused_lc = -1;
+  TRY(sync());
+  return XDG_OK;
+}
+
+// time the low-precision cycle with the small levels fused and launched per step; keep the faster
+int xdg_hier::tune_fused(int p) {
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  LevelLP& W = LP[p][0];
+  const int64_t n = L[0].nb * Np;
+  CK(cudaMemsetAsync(W.r, 0, n * sizeof(float), stream));
+  float ms[2] = {0.f, 0.f};
+  int rc = XDG_OK;
+  for (int v = 0; v < 2 && rc == XDG_OK; ++v) {
+    fused_on[p] = (v == 1);
+    for (int k = 0; k < 2; ++k) cycle_lp(p, 0, W.r, W.dz);
+    cudaEventRecord(e0, stream);
+    for (int k = 0; k < 10; ++k) cycle_lp(p, 0, W.r, W.dz);
+    cudaEventRecord(e1, stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms[v], e0, e1) != cudaSuccess)
+      rc = XDG_ECUDA;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) {
+    fused_on[p] = false;
+    set_err("fused-cycle tuning: %s", cudaGetErrorString(cudaGetLastError()));
+    return rc;
+  }
+  TRY(fused_error());
+  fused_on[p] = ms[1] < 0.97f * ms[0];
+  return XDG_OK;
+}
+
+// the error word of the fused cycle's barriers (XDG_ECUDA if one gave up; cleared)
+int xdg_hier::fused_error() {
+  if (!ferr) return XDG_OK;
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, ferr, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  CK(cudaStreamSynchronize(stream));
+  if (h) {
+    cudaMemsetAsync(ferr, 0, sizeof(int), stream);
+    set_err("fused small-level cycle: a grid barrier timed out");
+    return XDG_ECUDA;
+  }
+  return XDG_OK;
+}
+
 int xdg_hier::tune_split(int p) {
   const OpsLP& o = opl[p];
   cudaEvent_t e0, e1;
@@ -1638,6 +1790,7 @@ int xdg_hier::solve_dev(const double* b, double* x, const xdg_solve_opts* o, xdg
     if (hS->bad || !std::isfinite(rel)) status = XDG_EBREAKDOWN;
     if (budget > 0 && ms_since(t0) > budget && rel > tol) status = XDG_ETIMEOUT;
   }
+  if (prec != XDG_PREC_F64 && fused_on[prec]) TRY(fused_error());
   // true residual
   spmv(0, s_x, s_b, s_r, 1);
   dot(n, s_r, s_r, dsc);
@@ -1937,6 +2090,7 @@ int xdg_get_info(xdg_hier_t h, xdg_hier_info* info) {
   for (int i = 0; i < 3; ++i) info->setup_ms[i] = h->setup_ms[i];
   for (int l = 0; l < h->nlev && l < 64; ++l)
     if (h->L[l].spl) info->split_mask |= (uint64_t)1 << l;
+  info->fused_level = (h->fused_on[1] || h->fused_on[2]) ? h->fused_lc + 1 : 0;
   return XDG_OK;
 }
 
@@ -1994,6 +2148,8 @@ int xdg_set_split(xdg_hier_t h, int level, int on) {
   }
   h->L[level - 1].spl = (on != 0);
   h->tuned = true;
+  for (int p = 1; p < 3; ++p)
+    if (h->has_lp[p]) TRY(h->write_fused(p));
   // the recorded low-precision graphs hold the launch shapes: record them again
   for (int p = 1; p < 3; ++p) {
     if (h->has_lp[p]) TRY(h->capture(&h->g_iter_lp[p], 3, nullptr, nullptr, p));

@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_rt(int64_t nbf, const int64_
 
 // sum of t[f][r] over the children f = ch[q0..q1) in increasing q (child indices read in chunks
 // of 8 so the value loads overlap)
-template <int NP, class T, class A>
+template <int NP, class T, class A, bool COH = false>
 __device__ __forceinline__ A child_sum(int64_t q0, int64_t q1, int r, const int32_t* __restrict__ ch,
                                        const T* __restrict__ t) {
   A s = 0;
@@ -226,7 +226,10 @@ __device__ __forceinline__ A child_sum(int64_t q0, int64_t q1, int r, const int3
     for (int u = 0; u < 8; ++u) f[u] = (q + u < q1) ? __ldg(ch + q + u) : -1;
     T v[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = (f[u] >= 0) ? t[(int64_t)f[u] * NP + r] : (T)0;
+    for (int u = 0; u < 8; ++u) {
+      if constexpr (COH) v[u] = (f[u] >= 0) ? __ldcg(t + (int64_t)f[u] * NP + r) : (T)0;
+      else v[u] = (f[u] >= 0) ? t[(int64_t)f[u] * NP + r] : (T)0;
+    }
 #pragma unroll
     for (int u = 0; u < 8; ++u)
       if (f[u] >= 0) s += v[u];

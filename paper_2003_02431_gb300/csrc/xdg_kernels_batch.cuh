@@ -162,23 +162,38 @@ __global__ void k_xtx_seg(int nseg, const int64_t* __restrict__ nn, const int64_
   if (i < n && j < n) Minv[moff[s] + i * n + j] = acc;
 }
 
-// z = Minv_s r on every segment (one warp per row); VT = vector type (double or float)
+// z = Minv_s r on every segment (one warp per row, rows row = warp, warp + nw, ...); VT = vector
+// type (double or float)
+template <class VT, bool COH = false>
+__device__ __forceinline__ void gemv_seg_rows(int64_t warp, int64_t nw, int64_t ntot, int nseg,
+                                              const int64_t* __restrict__ doff, const int64_t* __restrict__ moff,
+                                              const double* __restrict__ Minv, const VT* __restrict__ r,
+                                              VT* __restrict__ z) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t row = warp; row < ntot; row += nw) {
+    const int s = find_seg(doff, nseg, row);
+    const int64_t d0 = __ldg(doff + s), n = __ldg(doff + s + 1) - d0;
+    const double* A = Minv + __ldg(moff + s) + (row - d0) * n;
+    double acc = 0.0;
+    for (int64_t c = lane; c < n; c += 32) {
+      VT rv;
+      if constexpr (COH) rv = __ldcg(r + d0 + c);
+      else rv = r[d0 + c];
+      acc = fma(__ldg(A + c), (double)rv, acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) z[row] = (VT)acc;
+  }
+}
+
 template <class VT>
 __global__ void __launch_bounds__(kThreads) k_gemv_seg(int64_t ntot, int nseg, const int64_t* __restrict__ doff,
                                                       const int64_t* __restrict__ moff,
                                                       const double* __restrict__ Minv, const VT* __restrict__ r,
                                                       VT* __restrict__ z) {
-  const int lane = threadIdx.x & 31;
-  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (row >= ntot) return;
-  const int s = find_seg(doff, nseg, row);
-  const int64_t d0 = __ldg(doff + s), n = __ldg(doff + s + 1) - d0;
-  const double* A = Minv + __ldg(moff + s) + (row - d0) * n;
-  double acc = 0.0;
-  for (int64_t c = lane; c < n; c += 32) acc = fma(__ldg(A + c), (double)r[d0 + c], acc);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) z[row] = (VT)acc;
+  gemv_seg_rows<VT>(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5, ((int64_t)gridDim.x * blockDim.x) >> 5,
+                    ntot, nseg, doff, moff, Minv, r, z);
 }
 
 // ------------------------------------------------------------------------------------------

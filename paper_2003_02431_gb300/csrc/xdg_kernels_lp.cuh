@@ -60,8 +60,34 @@ __device__ __forceinline__ void ldrow_f(const T* __restrict__ p, float (&v)[NP])
   }
 }
 
+// Loads of vectors that the same launch writes (the fused small-level cycle: COH = true) go
+// through L2 only (__ldcg), which the barrier's fences make coherent across SMs; the read-only
+// path (__ldg) serves vectors that no CTA writes during the launch (COH = false).
+template <bool COH>
+__device__ __forceinline__ float ldv(const float* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return *p;
+}
+template <int NP, class VT, bool COH>
+__device__ __forceinline__ void ldvec(const VT* __restrict__ p, float (&v)[NP]) {
+  if constexpr (COH && std::is_same<VT, float>::value && NP % 2 == 0) {
+    const float2* q = reinterpret_cast<const float2*>(p);
+#pragma unroll
+    for (int c = 0; c < NP / 2; ++c) {
+      float2 t = __ldcg(q + c);
+      v[2 * c] = t.x;
+      v[2 * c + 1] = t.y;
+    }
+  } else if constexpr (COH && std::is_same<VT, float>::value) {
+#pragma unroll
+    for (int c = 0; c < NP; ++c) v[c] = __ldcg(p + c);
+  } else {
+    ldrow_f<NP, VT>(p, v);
+  }
+}
+
 // sum_z s_z (A_z[r][:] . x[col z][:]) in FP32
-template <int NP, class TS, class VT>
+template <int NP, class TS, class VT, bool COH = false>
 __device__ __forceinline__ float row_dot_lp(int64_t z0, int64_t z1, int r, const int32_t* __restrict__ col,
                                             const TS* __restrict__ val, const float* __restrict__ sc,
                                             const VT* __restrict__ x) {
@@ -76,7 +102,7 @@ __device__ __forceinline__ float row_dot_lp(int64_t z0, int64_t z1, int r, const
       if (cc[u] < 0) continue;
       float a[NP], xv[NP];
       ldrow_f<NP, TS>(val + (z + u) * (NP * NP) + r * NP, a);
-      ldrow_f<NP, VT>(x + (int64_t)cc[u] * NP, xv);
+      ldvec<NP, VT, COH>(x + (int64_t)cc[u] * NP, xv);
       float s = 0.0f;
 #pragma unroll
       for (int c = 0; c < NP; ++c) s = fmaf(a[c], xv[c], s);
@@ -90,7 +116,7 @@ __device__ __forceinline__ float row_dot_lp(int64_t z0, int64_t z1, int r, const
 // blocks z0 + g, z0 + g + GPW, ...; split_sum adds the groups' partial sums in group order
 // (the same value in every group). This shortens the per-row chain of dependent loads, which
 // bounds the small levels, by the factor GPW.
-template <int NP, class TS, class VT>
+template <int NP, class TS, class VT, bool COH = false>
 __device__ __forceinline__ float row_dot_lp_part(int64_t z0, int64_t z1, int g, int r,
                                                  const int32_t* __restrict__ col, const TS* __restrict__ val,
                                                  const float* __restrict__ sc, const VT* __restrict__ x) {
@@ -107,7 +133,7 @@ __device__ __forceinline__ float row_dot_lp_part(int64_t z0, int64_t z1, int g, 
       const int64_t zz = z + u * GPW;
       float a[NP], xv[NP];
       ldrow_f<NP, TS>(val + zz * (NP * NP) + r * NP, a);
-      ldrow_f<NP, VT>(x + (int64_t)cc[u] * NP, xv);
+      ldvec<NP, VT, COH>(x + (int64_t)cc[u] * NP, xv);
       float s = 0.0f;
 #pragma unroll
       for (int c = 0; c < NP; ++c) s = fmaf(a[c], xv[c], s);
@@ -165,9 +191,54 @@ __device__ __forceinline__ float block_gemv_lp(const TS* __restrict__ W, float s
   return s * acc;
 }
 
+__device__ __forceinline__ int64_t grid_warp() { return ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
+__device__ __forceinline__ int64_t grid_warps() { return ((int64_t)gridDim.x * blockDim.x) >> 5; }
+__device__ __forceinline__ int64_t grid_thread() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int64_t grid_threads() { return (int64_t)gridDim.x * blockDim.x; }
+
+// The cycle's FP32 steps as functions of (warp index, number of warps) or (thread index, number
+// of threads): the kernels below run one step per launch, the fused coarse cycle runs several
+// steps in one launch with grid barriers between them.
+
 // damped block Jacobi in FP32: xo = xi + omega D^{-1} (b - M xi). The block inverses are
 // computed in FP64 and stored in FP32 in both modes: rounding the inverse of an ill-conditioned
 // cut-cell block to BF16 loses it.
+template <int NP, class TS, bool ZERO, bool SPL, bool COH = false>
+__device__ __forceinline__ void smooth_lp_rows(int64_t warp, int64_t nw, int64_t nb, const int64_t* __restrict__ rp,
+                                               const int32_t* __restrict__ col, const TS* __restrict__ val,
+                                               const float* __restrict__ sc, const float* __restrict__ Dinv,
+                                               const float* __restrict__ dsc, float omega,
+                                               const float* __restrict__ omr, const float* __restrict__ b,
+                                               const float* __restrict__ xi, float* __restrict__ xo,
+                                               const uint8_t* __restrict__ act) {
+  constexpr int GPW = Grp<NP>::GPW;
+  const int lane = threadIdx.x & 31;
+  const int g = lane / NP, r = lane - g * NP;
+  if (g >= GPW) return;
+  const unsigned mask = group_mask(g, NP);
+  if constexpr (SPL) {
+    for (int64_t i = warp; i < nb; i += nw) {
+      if (act && !act[i]) continue;
+      float res = ldv<COH>(b + i * NP + r);
+      if (!ZERO)
+        res -= split_sum<NP>(row_dot_lp_part<NP, TS, float, COH>(__ldg(rp + i), __ldg(rp + i + 1), g, r, col, val,
+                                                                 sc, xi), r);
+      float z = block_gemv_lp<NP, float>(Dinv + i * (NP * NP), __ldg(dsc + i), r, g * NP, mask, res);
+      const float om = omr ? __ldg(omr + i) : omega;
+      if (g == 0) xo[i * NP + r] = ZERO ? om * z : fmaf(om, z, ldv<COH>(xi + i * NP + r));
+    }
+  } else {
+    for (int64_t i = warp * GPW + g; i < nb; i += nw * GPW) {
+      if (act && !act[i]) continue;
+      float res = ldv<COH>(b + i * NP + r);
+      if (!ZERO) res -= row_dot_lp<NP, TS, float, COH>(__ldg(rp + i), __ldg(rp + i + 1), r, col, val, sc, xi);
+      float z = block_gemv_lp<NP, float>(Dinv + i * (NP * NP), __ldg(dsc + i), r, g * NP, mask, res);
+      const float om = omr ? __ldg(omr + i) : omega;  // per-row damping in batches
+      xo[i * NP + r] = ZERO ? om * z : fmaf(om, z, ldv<COH>(xi + i * NP + r));
+    }
+  }
+}
+
 template <int NP, class TS, bool ZERO, bool SPL = false>
 __global__ void __launch_bounds__(kThreads, XDG_LP_MINB) k_smooth_lp(int64_t nb, const int64_t* __restrict__ rp,
                                                        const int32_t* __restrict__ col,
@@ -177,61 +248,33 @@ __global__ void __launch_bounds__(kThreads, XDG_LP_MINB) k_smooth_lp(int64_t nb,
                                                        const float* __restrict__ b,
                                                        const float* __restrict__ xi, float* __restrict__ xo,
                                                        const uint8_t* __restrict__ act) {
-  constexpr int GPW = Grp<NP>::GPW;
-  const int lane = threadIdx.x & 31;
-  const int g = lane / NP, r = lane - g * NP;
-  if (g >= GPW) return;
-  const unsigned mask = group_mask(g, NP);
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  if constexpr (SPL) {
-    for (int64_t i = warp; i < nb; i += nw) {
-      if (act && !act[i]) continue;
-      float res = b[i * NP + r];
-      if (!ZERO)
-        res -= split_sum<NP>(row_dot_lp_part<NP, TS, float>(__ldg(rp + i), __ldg(rp + i + 1), g, r, col, val, sc,
-                                                            xi), r);
-      float z = block_gemv_lp<NP, float>(Dinv + i * (NP * NP), __ldg(dsc + i), r, g * NP, mask, res);
-      const float om = omr ? __ldg(omr + i) : omega;
-      if (g == 0) xo[i * NP + r] = ZERO ? om * z : fmaf(om, z, xi[i * NP + r]);
-    }
-  } else {
-    for (int64_t i = warp * GPW + g; i < nb; i += nw * GPW) {
-      if (act && !act[i]) continue;
-      float res = b[i * NP + r];
-      if (!ZERO) res -= row_dot_lp<NP, TS, float>(__ldg(rp + i), __ldg(rp + i + 1), r, col, val, sc, xi);
-      float z = block_gemv_lp<NP, float>(Dinv + i * (NP * NP), __ldg(dsc + i), r, g * NP, mask, res);
-      const float om = omr ? __ldg(omr + i) : omega;  // per-row damping in batches
-      xo[i * NP + r] = ZERO ? om * z : fmaf(om, z, xi[i * NP + r]);
-    }
-  }
+  smooth_lp_rows<NP, TS, ZERO, SPL>(grid_warp(), grid_warps(), nb, rp, col, val, sc, Dinv, dsc, omega, omr, b, xi,
+                                    xo, act);
 }
 
 // restriction phase 1 in FP32: t_f = R_f^T (b_f - M_f x). The operator is read from its FP32
 // copy in both modes (TA = float): a BF16-rounded operator is not positive definite on the
 // smooth modes the coarse levels correct (2^-9 cond(M) >> 1); TR is the transfer storage.
-template <int NP, class TA, class TR, bool RESID, bool SPL = false>
-__global__ void __launch_bounds__(kThreads, XDG_LP_MINB) k_resid_rt_lp(int64_t nbf, const int64_t* __restrict__ rp,
-                                                         const int32_t* __restrict__ col,
-                                                         const TA* __restrict__ val, const float* __restrict__ sc,
-                                                         const TR* __restrict__ R, const float* __restrict__ rsc,
-                                                         const float* __restrict__ b, const float* __restrict__ x,
-                                                         float* __restrict__ t, const uint8_t* __restrict__ act) {
+template <int NP, class TA, class TR, bool RESID, bool SPL, bool COH = false>
+__device__ __forceinline__ void resid_rt_lp_rows(int64_t warp, int64_t nw, int64_t nbf,
+                                                 const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                 const TA* __restrict__ val, const float* __restrict__ sc,
+                                                 const TR* __restrict__ R, const float* __restrict__ rsc,
+                                                 const float* __restrict__ b, const float* __restrict__ x,
+                                                 float* __restrict__ t, const uint8_t* __restrict__ act) {
   constexpr int GPW = Grp<NP>::GPW;
   const int lane = threadIdx.x & 31;
   const int g = lane / NP, r = lane - g * NP;
   if (g >= GPW) return;
   const unsigned mask = group_mask(g, NP);
   const int base = g * NP;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   if constexpr (SPL) {
     for (int64_t f = warp; f < nbf; f += nw) {
       if (act && !act[f]) continue;
-      float res = b[f * NP + r];
+      float res = ldv<COH>(b + f * NP + r);
       if (RESID)
-        res -= split_sum<NP>(row_dot_lp_part<NP, TA, float>(__ldg(rp + f), __ldg(rp + f + 1), g, r, col, val, sc,
-                                                            x), r);
+        res -= split_sum<NP>(row_dot_lp_part<NP, TA, float, COH>(__ldg(rp + f), __ldg(rp + f + 1), g, r, col, val,
+                                                                 sc, x), r);
       const TR* Rf = R + f * (NP * NP);
       float s = 0.0f;
 #pragma unroll
@@ -247,8 +290,8 @@ __global__ void __launch_bounds__(kThreads, XDG_LP_MINB) k_resid_rt_lp(int64_t n
 #pragma unroll
         for (int m = 0; m < NP; ++m) rc[m] = to_f<TR>(Rf[m * NP + r]);
       }
-      float res = b[f * NP + r];
-      if (RESID) res -= row_dot_lp<NP, TA, float>(__ldg(rp + f), __ldg(rp + f + 1), r, col, val, sc, x);
+      float res = ldv<COH>(b + f * NP + r);
+      if (RESID) res -= row_dot_lp<NP, TA, float, COH>(__ldg(rp + f), __ldg(rp + f + 1), r, col, val, sc, x);
       float s = 0.0f;
 #pragma unroll
       for (int m = 0; m < NP; ++m)
@@ -258,20 +301,56 @@ __global__ void __launch_bounds__(kThreads, XDG_LP_MINB) k_resid_rt_lp(int64_t n
   }
 }
 
+template <int NP, class TA, class TR, bool RESID, bool SPL = false>
+__global__ void __launch_bounds__(kThreads, XDG_LP_MINB) k_resid_rt_lp(int64_t nbf, const int64_t* __restrict__ rp,
+                                                         const int32_t* __restrict__ col,
+                                                         const TA* __restrict__ val, const float* __restrict__ sc,
+                                                         const TR* __restrict__ R, const float* __restrict__ rsc,
+                                                         const float* __restrict__ b, const float* __restrict__ x,
+                                                         float* __restrict__ t, const uint8_t* __restrict__ act) {
+  resid_rt_lp_rows<NP, TA, TR, RESID, SPL>(grid_warp(), grid_warps(), nbf, rp, col, val, sc, R, rsc, b, x, t, act);
+}
+
 // restriction phase 2 in FP32 (children in ascending order)
+template <int NP, bool COH = false>
+__device__ __forceinline__ void gather_lp_elems(int64_t tid, int64_t nt, int64_t nbc, const int64_t* __restrict__ cptr,
+                                                const int32_t* __restrict__ ch, const float* __restrict__ t,
+                                                float* __restrict__ rc) {
+  for (int64_t e = tid; e < nbc * NP; e += nt) {
+    const int64_t C = e / NP;
+    const int r = (int)(e - C * NP);
+    rc[e] = child_sum<NP, float, float, COH>(__ldg(cptr + C), __ldg(cptr + C + 1), r, ch, t);
+  }
+}
+
 template <int NP>
 __global__ void __launch_bounds__(kThreads) k_gather_lp(int64_t nbc, const int64_t* __restrict__ cptr,
                                                        const int32_t* __restrict__ ch,
                                                        const float* __restrict__ t, float* __restrict__ rc) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nbc * NP;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t C = e / NP;
-    const int r = (int)(e - C * NP);
-    rc[e] = child_sum<NP, float, float>(__ldg(cptr + C), __ldg(cptr + C + 1), r, ch, t);
-  }
+  gather_lp_elems<NP>(grid_thread(), grid_threads(), nbc, cptr, ch, t, rc);
 }
 
 // phase 2 fused with the first sweep of the coarse level from a zero guess (FP32)
+template <int NP, bool COH = false>
+__device__ __forceinline__ void gather_smooth0_lp_rows(int64_t warp, int64_t nw, int64_t nbc,
+                                                       const int64_t* __restrict__ cptr,
+                                                       const int32_t* __restrict__ ch, const float* __restrict__ t,
+                                                       const float* __restrict__ Dinv, const float* __restrict__ dsc,
+                                                       float omega, const float* __restrict__ omr,
+                                                       float* __restrict__ bc, float* __restrict__ xc) {
+  constexpr int GPW = Grp<NP>::GPW;
+  const int lane = threadIdx.x & 31;
+  const int g = lane / NP, r = lane - g * NP;
+  if (g >= GPW) return;
+  const unsigned mask = group_mask(g, NP);
+  for (int64_t C = warp * GPW + g; C < nbc; C += nw * GPW) {
+    float bv = child_sum<NP, float, float, COH>(__ldg(cptr + C), __ldg(cptr + C + 1), r, ch, t);
+    bc[C * NP + r] = bv;
+    float z = block_gemv_lp<NP, float>(Dinv + C * (NP * NP), __ldg(dsc + C), r, g * NP, mask, bv);
+    xc[C * NP + r] = (omr ? __ldg(omr + C) : omega) * z;
+  }
+}
+
 template <int NP>
 __global__ void __launch_bounds__(kThreads) k_gather_smooth0_lp(int64_t nbc, const int64_t* __restrict__ cptr,
                                                                const int32_t* __restrict__ ch,
@@ -280,56 +359,37 @@ __global__ void __launch_bounds__(kThreads) k_gather_smooth0_lp(int64_t nbc, con
                                                                const float* __restrict__ dsc, float omega,
                                                                const float* __restrict__ omr,
                                                                float* __restrict__ bc, float* __restrict__ xc) {
+  gather_smooth0_lp_rows<NP>(grid_warp(), grid_warps(), nbc, cptr, ch, t, Dinv, dsc, omega, omr, bc, xc);
+}
+
+// xo_f = xi_f + R_f zc[agg[f]] in FP32 (xo may equal xi)
+template <int NP, class TS, bool COH = false>
+__device__ __forceinline__ void prolong_lp_rows(int64_t warp, int64_t nw, int64_t nbf, const int32_t* __restrict__ agg,
+                                                const TS* __restrict__ R, const float* __restrict__ rsc,
+                                                const float* __restrict__ zc, const float* xi, float* xo,
+                                                const uint8_t* __restrict__ act) {
   constexpr int GPW = Grp<NP>::GPW;
   const int lane = threadIdx.x & 31;
   const int g = lane / NP, r = lane - g * NP;
   if (g >= GPW) return;
-  const unsigned mask = group_mask(g, NP);
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t C = warp * GPW + g; C < nbc; C += nw * GPW) {
-    float bv = child_sum<NP, float, float>(__ldg(cptr + C), __ldg(cptr + C + 1), r, ch, t);
-    bc[C * NP + r] = bv;
-    float z = block_gemv_lp<NP, float>(Dinv + C * (NP * NP), __ldg(dsc + C), r, g * NP, mask, bv);
-    xc[C * NP + r] = (omr ? __ldg(omr + C) : omega) * z;
+  for (int64_t f = warp * GPW + g; f < nbf; f += nw * GPW) {
+    if (act && !act[f]) continue;
+    float a[NP], z[NP];
+    ldrow_f<NP, TS>(R + f * (NP * NP) + r * NP, a);
+    ldvec<NP, float, COH>(zc + (int64_t)__ldg(agg + f) * NP, z);
+    float s = 0.0f;
+#pragma unroll
+    for (int n = 0; n < NP; ++n) s = fmaf(a[n], z[n], s);
+    xo[f * NP + r] = fmaf(__ldg(rsc + f), s, ldv<COH>(xi + f * NP + r));
   }
 }
 
-// xo_f = xi_f + R_f zc[agg[f]] in FP32 (xo may equal xi)
 template <int NP, class TS>
 __global__ void __launch_bounds__(kThreads) k_prolong_lp(int64_t nbf, const int32_t* __restrict__ agg,
                                                         const TS* __restrict__ R, const float* __restrict__ rsc,
                                                         const float* __restrict__ zc, const float* xi, float* xo,
                                                         const uint8_t* __restrict__ act) {
-  constexpr int GPW = Grp<NP>::GPW;
-  const int lane = threadIdx.x & 31;
-  const int g = lane / NP, r = lane - g * NP;
-  if (g >= GPW) return;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t f = warp * GPW + g; f < nbf; f += nw * GPW) {
-    if (act && !act[f]) continue;
-    float a[NP], z[NP];
-    ldrow_f<NP, TS>(R + f * (NP * NP) + r * NP, a);
-    ldrow_f<NP, float>(zc + (int64_t)__ldg(agg + f) * NP, z);
-    float s = 0.0f;
-#pragma unroll
-    for (int n = 0; n < NP; ++n) s = fmaf(a[n], z[n], s);
-    xo[f * NP + r] = fmaf(__ldg(rsc + f), s, xi[f * NP + r]);
-  }
-}
-
-// coarsest level: z = Minv r with the FP64 inverse, FP32 vectors (one warp per row)
-__global__ void __launch_bounds__(kThreads) k_gemv_coarse_lp(int64_t n, const double* __restrict__ A,
-                                                            const float* __restrict__ x, float* __restrict__ y) {
-  const int lane = threadIdx.x & 31;
-  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (row >= n) return;
-  double s = 0.0;
-  for (int64_t c = lane; c < n; c += 32) s = fma(__ldg(A + row * n + c), (double)__ldg(x + c), s);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) y[row] = (float)s;
+  prolong_lp_rows<NP, TS>(grid_warp(), grid_warps(), nbf, agg, R, rsc, zc, xi, xo, act);
 }
 
 // stored copy of Np x Np blocks: scale s = max |entry| (as float, 1 for a zero block),

@@ -63,7 +63,8 @@ class Problem(C.Structure):
 
 class HierOpts(C.Structure):
     _fields_ = [("omega", C.c_double), ("lanczos_steps", C.c_int), ("nu", C.c_int),
-                ("gamma", C.c_int), ("low_precision", C.c_int), ("w_levels", C.c_int), ("split_rows", C.c_int)]
+                ("gamma", C.c_int), ("low_precision", C.c_int), ("w_levels", C.c_int), ("split_rows", C.c_int),
+                ("fused_coarse", C.c_int)]
 
 
 class SolveOpts(C.Structure):
@@ -80,7 +81,8 @@ class HierInfo(C.Structure):
     _fields_ = [("Np", C.c_int), ("n_levels", C.c_int), ("nb", C.c_int64 * MAX_LEVELS),
                 ("nnzb", C.c_int64 * MAX_LEVELS), ("omega", C.c_double * MAX_LEVELS),
                 ("lambda_max", C.c_double * MAX_LEVELS), ("coarse_n", C.c_int64),
-                ("device_bytes", C.c_size_t), ("setup_ms", C.c_double * 3), ("split_mask", C.c_uint64)]
+                ("device_bytes", C.c_size_t), ("setup_ms", C.c_double * 3), ("split_mask", C.c_uint64),
+                ("fused_level", C.c_int)]
 
 
 class TrainOpts(C.Structure):
@@ -244,7 +246,7 @@ class Hierarchy:
     unless one is given); every call is ordered with torch's current stream by event waits."""
 
     def __init__(self, Np, nb, row_ptr, col, val, aggs, Rs, omega=0.0, lanczos_steps=12, nu=1,
-                 gamma=1, low_precision=0, stream=None, w_levels=0, split_rows=0):
+                 gamma=1, low_precision=0, stream=None, w_levels=0, split_rows=0, fused_coarse=0):
         L = load()
         torch = _torch()
         if stream is None:
@@ -253,7 +255,7 @@ class Hierarchy:
         self._keep = []
 
         prob = _marshal(Np, nb, row_ptr, col, val, aggs, Rs, self._keep)
-        opts = HierOpts(omega, lanczos_steps, nu, gamma, low_precision, w_levels, split_rows)
+        opts = HierOpts(omega, lanczos_steps, nu, gamma, low_precision, w_levels, split_rows, fused_coarse)
         h = C.c_void_p()
         st = C.c_void_p(stream.cuda_stream)
         self._h = None
@@ -278,7 +280,7 @@ class Hierarchy:
         return {"Np": i.Np, "n_levels": nl, "nb": list(i.nb[:nl]), "nnzb": list(i.nnzb[:nl]),
                 "omega": list(i.omega[:nl]), "lambda_max": list(i.lambda_max[:nl]),
                 "coarse_n": i.coarse_n, "device_bytes": i.device_bytes, "setup_ms": list(i.setup_ms),
-                "split": [bool((i.split_mask >> l) & 1) for l in range(nl)]}
+                "split": [bool((i.split_mask >> l) & 1) for l in range(nl)], "fused_level": i.fused_level}
 
     def export_level(self, level: int):
         _torch().cuda.synchronize(self.stream.device)
@@ -442,7 +444,7 @@ class Batch:
         arr = (Problem * len(problems))()
         for i, p in enumerate(problems):
             arr[i] = _marshal(p.Np, p.nb, p.row_ptr, p.col, p.val, p.agg, p.R, keep)
-        opts = HierOpts(omega, lanczos_steps, nu, gamma, low_precision, w_levels, split_rows)
+        opts = HierOpts(omega, lanczos_steps, nu, gamma, low_precision, w_levels, split_rows, 1)
         h = C.c_void_p()
         self._h = None
         with _Ordered(self):

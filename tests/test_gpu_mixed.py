@@ -112,6 +112,31 @@ def test_split_row_mapping_agrees(case):
 
 
 @pytest.mark.parametrize("prec", [xdg.XDG_PREC_F32, xdg.XDG_PREC_BF16])
+def test_fused_small_levels_match_launch_per_step(case, prec):
+    """The small levels' V-cycle as one persistent launch runs the same per-row arithmetic as the
+    launch-per-step cycle: identical results, bit for bit (same row mapping on both sides)."""
+    name, P, O, G = case
+    gamma = CASES[name][1]
+    b = _t(P.b.reshape(-1))
+    out = []
+    for mode in (1, 2):
+        H = xdg.Hierarchy.from_problem(P, gamma=gamma, w_levels=1, low_precision=3, split_rows=1,
+                                       fused_coarse=mode)
+        fused = H.info()["fused_level"]
+        if mode == 2 and P.n_levels >= 3 and P.nb[1] <= 16384:
+            assert fused == 2, (name, fused)
+        x = torch.empty(P.dof, dtype=torch.float64, device=DEV)
+        H.cycle(prec, b, x)
+        xs = torch.zeros_like(x)
+        res = H.solve(b, xs, tol=1e-10, precision=prec)
+        out.append((_n(x), _n(xs), res["iterations"], fused))
+        H.destroy()
+    assert out[0][3] == 0
+    assert np.array_equal(out[0][0], out[1][0]), name
+    assert np.array_equal(out[0][1], out[1][1]) and out[0][2] == out[1][2], name
+
+
+@pytest.mark.parametrize("prec", [xdg.XDG_PREC_F32, xdg.XDG_PREC_BF16])
 def test_mixed_solve_reaches_fp64_oracle_solution(case, prec):
     name, P, O, G = case
     ref, it_o, _, _ = O.pcg(P.b, tol=1e-14, maxit=600)

@@ -1,0 +1,59 @@
+"""Multi-process path of bench.py on CPU (gloo, world size 2): replicas with no data-path
+collective; the job time is the slowest rank's and the throughput counts every rank's work;
+the reference arm runs on rank 0 only."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    slow = bench.max_over_ranks(10.0 + 5.0 * rank, dist)
+    dist.barrier()
+    q.put((rank, slow))
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_gloo_world2():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = dict(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert got == {0: 15.0, 1: 15.0}
+
+
+def test_job_throughput_counts_every_replica():
+    import bench
+    one = bench.job_throughput(1, 2_662_320, 5, 0.4)
+    assert abs(bench.job_throughput(2, 2_662_320, 5, 0.4) - 2 * one) < 1e-9
+    assert abs(one - 2_662_320 * 5 / 0.4 / 1e6) < 1e-9
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    import argparse
+
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    called = []
+    monkeypatch.setattr(bench, "make_problem", lambda: called.append(1))
+    bench.reference_arm(argparse.Namespace(steps=1, warmup=1))
+    assert not called and capsys.readouterr().out == ""
