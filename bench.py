@@ -339,6 +339,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 256-problem workload")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-correction section")
+    ap.add_argument("--fused-coarse", type=int, default=0, choices=[0, 1, 2],
+                    help="small levels of the FP32 cycle as one launch: 0 autotuned, 1 never, 2 always "
+                         "(for profiler runs, where the autotuner's timings are distorted)")
     ap.add_argument("--split-mask", type=int, default=-1,
                     help="force the split-row mapping per level (bit l: level l+1) instead of the autotuned one "
                          "(for profiler runs, where the autotuner's timings are distorted)")
@@ -371,7 +374,8 @@ def main():
     P = make_problem()
     n, Np, nb, nnzb = P.dof, P.Np, P.nb[0], int(P.row_ptr[-1])
     t = time.perf_counter()
-    H = xdg.Hierarchy.from_problem(P, gamma=GAMMA, w_levels=W_LEVELS, low_precision=3, stream=stream)
+    H = xdg.Hierarchy.from_problem(P, gamma=GAMMA, w_levels=W_LEVELS, low_precision=3, stream=stream,
+                                   fused_coarse=args.fused_coarse)
     setup_s = time.perf_counter() - t
     if args.split_mask >= 0:
         for l in range(len(P.nb)):
@@ -488,6 +492,7 @@ def main():
                        "outer": "flexible CG, FP64 apply/residual/update", "tol": TOL, "iterations": iters,
                        "parallelism": "replicas" if world > 1 else "single",
                        "split_rows_levels": hinfo["split"],
+                       "fused_small_levels_from": hinfo["fused_level"],
                        "l2": "inputs larger than L2 (operator 1.49 GB FP64 + 0.74 GB FP32)"},
             "paths": {
                 "mixed_f32": {"solve_ms": t_ms / args.steps, "iterations": iters, "mdofs": value / world},

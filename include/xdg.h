@@ -181,9 +181,15 @@ int xdg_apply(xdg_hier_t h, int level, const double* x, double* y, int prec);
 int xdg_set_split(xdg_hier_t h, int level, int on);
 
 /* Replace the smoother damping of `level` (1 <= level < n_levels) by omega > 0 (default:
- * 4 / (3 lambda_l) from the Lanczos estimate). Records the solve graphs again. Not for the
- * hierarchy of a batch group (EINVAL). */
+ * 4 / (3 lambda_l) from the Lanczos estimate), for every problem of a batch group. Records the
+ * handle's solve graphs again (a batch records its own graphs at its next solve only if none
+ * exists: change the damping of a batch's groups before its first solve). */
 int xdg_set_damping(xdg_hier_t h, int level, double omega);
+
+/* The damping of `level` (1 <= level < n_levels) for problem `problem` of the hierarchy (0 for
+ * a single problem; the member index for a batch group), and the Lanczos estimate lambda_max it
+ * came from (host outputs, either may be NULL). */
+int xdg_get_damping(xdg_hier_t h, int level, int problem, double* omega, double* lambda_max);
 
 /* One damped block-Jacobi step on `level`: x_out = x_in + omega D^{-1} (b - M x_in), the
  * diagonal blocks D solved with their Cholesky factors. x_in == NULL means x_in = 0. x_out

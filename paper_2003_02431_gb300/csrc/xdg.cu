@@ -2141,6 +2141,17 @@ int xdg_apply(xdg_hier_t h, int level, const double* x, double* y, int prec) {
   return XDG_OK;
 }
 
+int xdg_get_damping(xdg_hier_t h, int level, int problem, double* omega, double* lambda_max) {
+  if (!h || level < 1 || level >= h->nlev || problem < 0 || problem >= h->nprob) {
+    set_err("xdg_get_damping: bad level %d or problem %d", level, problem);
+    return XDG_EINVAL;
+  }
+  const Level& V = h->L[level - 1];
+  if (omega) *omega = V.omega_p.empty() ? V.omega : V.omega_p[problem];
+  if (lambda_max) *lambda_max = V.lmax_p.empty() ? V.lmax : V.lmax_p[problem];
+  return XDG_OK;
+}
+
 int xdg_set_split(xdg_hier_t h, int level, int on) {
   if (!h || level < 1 || level > h->nlev) {
     set_err("xdg_set_split: bad level %d", level);
@@ -2169,13 +2180,16 @@ int xdg_set_damping(xdg_hier_t h, int level, double omega) {
     set_err("xdg_set_damping: bad level %d or omega %g", level, omega);
     return XDG_EINVAL;
   }
-  if (h->nprob > 1) {
-    set_err("xdg_set_damping: not for the hierarchy of a batch group");
-    return XDG_EINVAL;
-  }
   Level& V = h->L[level - 1];
   V.omega = omega;
   std::fill(V.omega_p.begin(), V.omega_p.end(), omega);
+  if (V.omr) {  // batch group: per-row damping of every problem
+    std::vector<double> om(V.nb, omega);
+    std::vector<float> omf(V.nb, (float)omega);
+    CK(cudaMemcpyAsync(V.omr, om.data(), V.nb * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(V.omr_f, omf.data(), V.nb * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
   // the recorded graphs hold the damping as a kernel argument: record them again
   TRY(h->capture(&h->g_iter, 1, nullptr, nullptr));
   for (int p = 1; p < 3; ++p)

@@ -113,6 +113,7 @@ SIGNATURES = [
     ("xdg_smooth", C.c_int, [_vp, _ip, _vp, _vp, _vp]),
     ("xdg_set_damping", C.c_int, [_vp, _ip, C.c_double]),
     ("xdg_set_split", C.c_int, [_vp, _ip, _ip]),
+    ("xdg_get_damping", C.c_int, [_vp, _ip, _ip, _dp, _dp]),
     ("xdg_restrict", C.c_int, [_vp, _ip, _vp, _vp, _vp]),
     ("xdg_prolong", C.c_int, [_vp, _ip, _vp, _vp, _vp]),
     ("xdg_coarse_solve", C.c_int, [_vp, _vp, _vp]),
@@ -301,6 +302,12 @@ class Hierarchy:
     def set_split(self, level, on):
         with _Ordered(self):
             _check(load().xdg_set_split(self._h, level, int(bool(on))))
+
+    def get_damping(self, level, problem=0):
+        """(omega, lambda_max) of a level for one problem of the hierarchy."""
+        om, lm = C.c_double(), C.c_double()
+        _check(load().xdg_get_damping(self._h, level, problem, C.byref(om), C.byref(lm)))
+        return om.value, lm.value
 
     def set_damping(self, level, omega):
         with _Ordered(self):
