@@ -66,6 +66,9 @@ double ms_since(clk::time_point t0) {
 }
 
 
+// partial sums a reduction may produce (grids of the fused apply-and-dot are capped at this)
+constexpr int kPartials = 4096;
+
 // One full wave: the grid-stride kernels get at most (resident CTAs per SM) x SMs CTAs, so that
 // no partial second wave of CTAs runs at the end of a launch (occupancy queried once per kernel).
 int wave_cap(const void* k) {
@@ -106,6 +109,8 @@ struct Ops {
                    const int32_t*, const double*, const int32_t*, const double*, const int64_t*,
                    const int32_t*, double*);
   void (*diag_inv)(cudaStream_t, int64_t, const int64_t*, const double*, double*, int*);
+  int (*spmv_dot)(int grid, cudaStream_t, int64_t, const int64_t*, const int32_t*, const double*, const double*,
+                  double*, double*);
   int gpw;
 };
 
@@ -156,9 +161,16 @@ struct OpsT {
                        int* err) {
     k_diag_inv<NP><<<(unsigned)((nb + 63) / 64), 64, 0, s>>>(nb, dg, val, Dinv, err);
   }
+  // returns the grid used (= the number of partial sums written)
+  static int spmv_dot(int grid, cudaStream_t s, int64_t nb, const int64_t* rp, const int32_t* col,
+                      const double* val, const double* x, double* y, double* partial) {
+    const int g = std::min(fit_grid((const void*)&k_spmv_dot<NP>, grid), kPartials);
+    k_spmv_dot<NP><<<g, kThreads, 0, s>>>(nb, rp, col, val, x, y, partial);
+    return g;
+  }
   static Ops make() {
     return Ops{NP, spmv, smooth, bjsolve, diagmul, resid_rt, gather, gather_smooth0, prolong, galerkin, diag_inv,
-               Grp<NP>::GPW};
+               spmv_dot, Grp<NP>::GPW};
   }
 };
 
@@ -608,13 +620,19 @@ struct xdg_hier {
     }
   }
 
+  // q = M p on level 1 with p . q into S->pq and alpha = rz / pq (3 launches)
+  void apply_alpha() {
+    Level& V = L[0];
+    const int g = ops.spmv_dot(grid(V.nb), stream, V.nb, V.rp, V.col, V.val, s_p, s_q, partial);
+    k_cg_alpha_final<<<1, kThreads, 0, stream>>>(g, partial, S);
+    launches += 2;
+  }
+
   // one CG iteration on level 1 (buffers s_*), scalars in S
   void pcg_iteration() {
     const int64_t n = L[0].nb * Np;
-    spmv(0, s_p, nullptr, s_q, 0);
-    dot(n, s_p, s_q, &S->pq);
-    k_pcg_alpha<<<1, 1, 0, stream>>>(S);
-    launches += 5;
+    apply_alpha();
+    launches += 4;  // x/r update, its sum, beta, direction
     k_pcg_xr<<<kRedBlocks, kThreads, 0, stream>>>(n, S, s_p, s_q, s_x, s_r, partial);
     k_sum_final<<<1, kThreads, 0, stream>>>(kRedBlocks, partial, &S->rr);
     cycle(0, s_r, s_z);
@@ -718,21 +736,32 @@ struct xdg_hier {
     if (lr.on) learned_apply(r, z);
   }
 
-  // one flexible-CG iteration (FP64 operator, residual and updates; low-precision cycle)
+  // one flexible-CG iteration (FP64 operator, residual and updates; low-precision cycle):
+  // q = M p with p . q; alpha; x, r updated with r . r and the FP32 copy of r; the cycle;
+  // z widened with r . z and z . q; beta; p = z + beta p
   void fcg_iteration(int p) {
     const int64_t n = L[0].nb * Np;
-    spmv(0, s_p, nullptr, s_q, 0);
-    dot(n, s_p, s_q, &S->pq);
-    k_pcg_alpha<<<1, 1, 0, stream>>>(S);
-    k_pcg_xr<<<kRedBlocks, kThreads, 0, stream>>>(n, S, s_p, s_q, s_x, s_r, partial);
-    k_sum_final<<<1, kThreads, 0, stream>>>(kRedBlocks, partial, &S->rr);
-    launches += 3;
-    precond_full(p, s_r, s_z);
-    dot(n, s_r, s_z, &S->rz);
-    dot(n, s_z, s_q, &S->zq);
-    k_fcg_beta<<<1, 1, 0, stream>>>(S);
+    apply_alpha();
+    if (p == XDG_PREC_F64 || lr.on) {  // FP64 cycle or learned correction: generic tail
+      k_pcg_xr<<<kRedBlocks, kThreads, 0, stream>>>(n, S, s_p, s_q, s_x, s_r, partial);
+      k_sum_final<<<1, kThreads, 0, stream>>>(kRedBlocks, partial, &S->rr);
+      launches += 2;
+      precond_full(p, s_r, s_z);
+      dot(n, s_r, s_z, &S->rz);
+      dot(n, s_z, s_q, &S->zq);
+      k_fcg_beta<<<1, 1, 0, stream>>>(S);
+      ++launches;
+    } else {
+      LevelLP& W = LP[p][0];
+      k_pcg_xr<<<kRedBlocks, kThreads, 0, stream>>>(n, S, s_p, s_q, s_x, s_r, partial, W.b);
+      k_sum_final<<<1, kThreads, 0, stream>>>(kRedBlocks, partial, &S->rr);
+      cycle_lp(p, 0, W.b, W.x);
+      k_fcg_tail<<<kRedBlocks, kThreads, 0, stream>>>(n, W.x, s_r, s_q, s_z, partial);
+      k_fcg_beta_final<<<1, kThreads, 0, stream>>>(kRedBlocks, partial, S);
+      launches += 4;
+    }
     k_pcg_p<<<vgrid(n), kThreads, 0, stream>>>(n, S, s_z, s_p);
-    launches += 2;
+    ++launches;
   }
 
   int build_lp(int p);
@@ -1123,7 +1152,7 @@ int xdg_hier::build(const xdg_problem* p, const xdg_hier_opts* o) {
   TRY(alloc(&s_z, n1));
   TRY(alloc(&s_p, n1));
   TRY(alloc(&s_q, n1));
-  TRY(alloc(&partial, kRedBlocks));
+  TRY(alloc(&partial, 2 * (size_t)kPartials));
   TRY(alloc(&dsc, 8));
   TRY(alloc(&S, 1));
   TRY(alloc(&Minv, minv_len));

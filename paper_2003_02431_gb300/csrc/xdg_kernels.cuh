@@ -581,21 +581,71 @@ __global__ void k_pcg_beta(PcgScal* S) {
   S->rz = rn;
 }
 
-// x += alpha p; r -= alpha q; partial[] of r.r
+// x += alpha p; r -= alpha q; partial[] of r.r; rf (optional) = r rounded to FP32 (the input
+// of a low-precision cycle)
 __global__ void __launch_bounds__(kThreads) k_pcg_xr(int64_t n, const PcgScal* __restrict__ S,
                                                     const double* __restrict__ p,
                                                     const double* __restrict__ q, double* __restrict__ x,
-                                                    double* __restrict__ r, double* __restrict__ partial) {
+                                                    double* __restrict__ r, double* __restrict__ partial,
+                                                    float* __restrict__ rf = nullptr) {
   const double a = S->alpha;
   double s = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     x[i] = fma(a, p[i], x[i]);
     double ri = fma(-a, q[i], r[i]);
     r[i] = ri;
+    if (rf) rf[i] = (float)ri;
     s = fma(ri, ri, s);
   }
   s = block_sum(s);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// y = M x (block rows spread as in k_spmv) and partial[blockIdx.x] = this CTA's part of x . y
+template <int NP>
+__global__ void __launch_bounds__(kThreads) k_spmv_dot(int64_t nb, const int64_t* __restrict__ rp,
+                                                      const int32_t* __restrict__ col, const double* __restrict__ val,
+                                                      const double* __restrict__ x, double* __restrict__ y,
+                                                      double* __restrict__ partial) {
+  constexpr int GPW = Grp<NP>::GPW;
+  const int lane = threadIdx.x & 31;
+  const int g = lane / NP, r = lane - g * NP;
+  double d = 0.0;
+  if (g < GPW) {
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp * GPW + g; i < nb; i += nw * GPW) {
+      const double acc = row_dot<NP>(__ldg(rp + i), __ldg(rp + i + 1), r, col, val, x);
+      y[i * NP + r] = acc;
+      d = fma(x[i * NP + r], acc, d);
+    }
+  }
+  d = block_sum(d);
+  if (threadIdx.x == 0) partial[blockIdx.x] = d;
+}
+
+// sum of partial[0..np) (stride, offset) in a fixed order by one CTA; valid in thread 0
+__device__ __forceinline__ double sum_partials(int np, const double* __restrict__ partial, int stride, int off) {
+  const int per = (np + blockDim.x - 1) / blockDim.x;
+  const int i0 = threadIdx.x * per, i1 = min(np, i0 + per);
+  double s = 0.0;
+  for (int i = i0; i < i1; ++i) s += partial[i * stride + off];
+  return block_sum(s);
+}
+
+// pq from the partial sums, then alpha = rz / pq (breakdown flagged)
+__global__ void __launch_bounds__(kThreads) k_cg_alpha_final(int np, const double* __restrict__ partial,
+                                                            PcgScal* S) {
+  const double pq = sum_partials(np, partial, 1, 0);
+  if (threadIdx.x == 0) {
+    S->pq = pq;
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      S->bad = 1;
+      S->alpha = 0.0;
+    } else {
+      S->alpha = S->rz / pq;
+    }
+  }
 }
 
 // p = z + beta p

@@ -442,6 +442,43 @@ __global__ void k_copy_f(int64_t n, const float* __restrict__ a, float* __restri
 }
 
 // flexible CG (one previous direction kept): beta = -(z_new . q) / (p . q), q = M p
+// end of a flexible-CG step: z = widened FP32 cycle result; per-CTA parts of r . z and z . q
+// (partial[2 b], partial[2 b + 1])
+__global__ void __launch_bounds__(kThreads) k_fcg_tail(int64_t n, const float* __restrict__ zf,
+                                                      const double* __restrict__ r, const double* __restrict__ q,
+                                                      double* __restrict__ z, double* __restrict__ partial) {
+  double a = 0.0, c = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double zi = (double)zf[i];
+    z[i] = zi;
+    a = fma(r[i], zi, a);
+    c = fma(zi, q[i], c);
+  }
+  a = block_sum(a);
+  c = block_sum(c);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = a;
+    partial[2 * blockIdx.x + 1] = c;
+  }
+}
+
+// rz, zq from the partial sums, then the flexible-CG beta = -zq / pq
+__global__ void __launch_bounds__(kThreads) k_fcg_beta_final(int np, const double* __restrict__ partial, PcgScal* S) {
+  const double rz = sum_partials(np, partial, 2, 0);
+  const double zq = sum_partials(np, partial, 2, 1);
+  if (threadIdx.x == 0) {
+    S->rz = rz;
+    S->zq = zq;
+    const double pq = S->pq;
+    if (!(pq > 0.0) || !isfinite(zq)) {
+      S->bad = 1;
+      S->beta = 0.0;
+    } else {
+      S->beta = -zq / pq;
+    }
+  }
+}
+
 __global__ void k_fcg_beta(PcgScal* S) {
   double pq = S->pq, zq = S->zq;
   if (!(pq > 0.0) || !isfinite(zq)) {
