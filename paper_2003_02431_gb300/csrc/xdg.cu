@@ -452,6 +452,19 @@ struct xdg_hier {
   int64_t* ioff = nullptr;      // offset of every problem in the caller's concatenated vectors
   int* gidx = nullptr;          // index of every problem in the caller's list
   Learned lr;                   // learned cut-cell correction (off unless enabled)
+  // device-side iteration loops of the solve, by precision and learned correction off/on
+  cudaGraphExec_t g_loop[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+  int64_t loop_nodes[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  LoopCtl* lctl = nullptr;
+  LoopCtl* hlctl = nullptr;
+  int record_loop(int prec);
+  void drop_loops() {
+    for (auto& a : g_loop)
+      for (auto& g : a) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
+  }
   uint8_t* act1 = nullptr;      // batches: 1 for the level-1 blocks of running problems
   const uint8_t* cur_act = nullptr;  // row mask of the level-1 cycle kernels (while recording a batch)
   cudaStream_t body_stream = nullptr;
@@ -494,6 +507,8 @@ struct xdg_hier {
     }
     for (int p = 0; p < 3; ++p)
       if (lr.g_iter[p]) cudaGraphExecDestroy(lr.g_iter[p]);
+    drop_loops();
+    if (hlctl) cudaFreeHost(hlctl);
     for (void* p : allocs) cudaFree(p);
     if (h_bsc) cudaFreeHost(h_bsc);
     if (body_stream) cudaStreamDestroy(body_stream);
@@ -1765,6 +1780,64 @@ int xdg_hier::record_batch(int prec, const BatchCtl* ctl, double* res, int gslot
   return XDG_OK;
 }
 
+// The solve's iteration loop as a graph: a conditional while node whose body is one CG /
+// flexible-CG iteration (as recorded for the host loop) and the convergence check, which sets
+// the loop condition; bounded by the iteration limit.
+int xdg_hier::record_loop(int prec) {
+  const int li = lr.on ? 1 : 0;
+  if (!lctl) {
+    TRY(alloc(&lctl, 1));
+    CK(cudaMallocHost(&hlctl, sizeof(LoopCtl)));
+  }
+  if (!body_stream) CK(cudaStreamCreateWithFlags(&body_stream, cudaStreamNonBlocking));
+  CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+  cudaStreamCaptureStatus st;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaGraphConditionalHandle cond;
+  cudaGraphNodeParams cp = {};
+  cudaGraphNode_t wnode;
+  cudaError_t e = cudaStreamGetCaptureInfo(stream, &st, nullptr, &cg, &deps, nullptr, &nd);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, cg, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&wnode, cg, deps, nullptr, nd, &cp);
+  }
+  if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(stream, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(body_stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaStream_t main_stream = stream;
+    stream = body_stream;
+    const int64_t l0 = launches;
+    if (prec == XDG_PREC_F64 && !lr.on) pcg_iteration();
+    else fcg_iteration(prec);
+    k_cg_loop_check<<<1, 1, 0, stream>>>(S, lctl, cond);
+    loop_nodes[prec][li] = launches - l0 + 1;
+    launches = l0;
+    stream = main_stream;
+    e = cudaGetLastError();
+    cudaGraph_t bout = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(body_stream, &bout);
+    if (e == cudaSuccess) e = e2;
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e3 = cudaStreamEndCapture(stream, &graph);
+  if (e == cudaSuccess) e = e3;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&g_loop[prec][li], graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    set_err("solve loop graph: %s", cudaGetErrorString(e));
+    return XDG_ECUDA;
+  }
+  return XDG_OK;
+}
+
 int xdg_hier::solve_dev(const double* b, double* x, const xdg_solve_opts* o, xdg_solve_info* info) {
   auto t0 = clk::now();
   const int64_t launches0 = launches;
@@ -1805,6 +1878,26 @@ int xdg_hier::solve_dev(const double* b, double* x, const xdg_solve_opts* o, xdg
   int status = XDG_OK, it = 0;
   double rel = std::sqrt(hS->rr) / bn;
   if (!std::isfinite(rel)) status = XDG_EBREAKDOWN;
+  int64_t loop_launches = 0;
+  if (status == XDG_OK && rel > tol && budget <= 0 && every == 1) {
+    // the whole iteration loop on the device: one graph launch, one read-back
+    const int li = lr.on ? 1 : 0;
+    if (!g_loop[prec][li]) TRY(record_loop(prec));
+    hlctl->tol2 = tol * tol;
+    hlctl->bb = bb > 0 ? bb : 1.0;
+    hlctl->maxit = maxit;
+    hlctl->it = 0;
+    CK(cudaMemcpyAsync(lctl, hlctl, sizeof(LoopCtl), cudaMemcpyHostToDevice, stream));
+    CK(cudaGraphLaunch(g_loop[prec][li], stream));
+    CK(cudaMemcpyAsync(hS, S, sizeof(PcgScal), cudaMemcpyDeviceToHost, stream));
+    CK(cudaMemcpyAsync(hlctl, lctl, sizeof(LoopCtl), cudaMemcpyDeviceToHost, stream));
+    TRY(sync());
+    it = hlctl->it;
+    loop_launches = (int64_t)it * loop_nodes[prec][li];
+    rel = std::sqrt(hS->rr) / bn;
+    if (hS->bad || !std::isfinite(rel)) status = XDG_EBREAKDOWN;
+    else if (rel > tol) status = XDG_ENOTCONV;
+  }
   while (status == XDG_OK && rel > tol) {
     if (it >= maxit) {
       status = XDG_ENOTCONV;
@@ -1832,7 +1925,7 @@ int xdg_hier::solve_dev(const double* b, double* x, const xdg_solve_opts* o, xdg
     info->relres = std::sqrt(rr) / bn;
     info->ms = ms_since(t0);
     info->status = status;
-    info->launches = launches - launches0 + (int64_t)it * gi_nodes;
+    info->launches = launches - launches0 + (loop_launches ? loop_launches : (int64_t)it * gi_nodes);
   }
   if (status) set_err("solve stopped: %s after %d iterations (relres %.3e)", xdg_strerror(status), it,
                       std::sqrt(rr) / bn);
@@ -2188,6 +2281,7 @@ int xdg_set_split(xdg_hier_t h, int level, int on) {
   }
   h->L[level - 1].spl = (on != 0);
   h->tuned = true;
+  h->drop_loops();
   for (int p = 1; p < 3; ++p)
     if (h->has_lp[p]) TRY(h->write_fused(p));
   // the recorded low-precision graphs hold the launch shapes: record them again
@@ -2220,6 +2314,7 @@ int xdg_set_damping(xdg_hier_t h, int level, double omega) {
     CK(cudaStreamSynchronize(h->stream));
   }
   // the recorded graphs hold the damping as a kernel argument: record them again
+  h->drop_loops();
   TRY(h->capture(&h->g_iter, 1, nullptr, nullptr));
   for (int p = 1; p < 3; ++p)
     if (h->has_lp[p]) TRY(h->capture(&h->g_iter_lp[p], 3, nullptr, nullptr, p));
@@ -2750,6 +2845,7 @@ int xdg_learned_enable(xdg_hier_t h, xdg_mlp_t m, double theta) {
     return XDG_EINVAL;
   }
   Learned& U = h->lr;
+  h->drop_loops();
   for (int p = 0; p < 3; ++p)
     if (U.g_iter[p]) {
       cudaGraphExecDestroy(U.g_iter[p]);

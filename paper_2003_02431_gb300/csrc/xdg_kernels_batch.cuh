@@ -399,6 +399,20 @@ __global__ void k_bcg_rowact(int64_t nb, int np, int nseg, const int64_t* __rest
     act[i] = (uint8_t)(active[find_seg(sdof, nseg, i * np)] != 0);
 }
 
+// device-side loop of a single-problem solve: one more iteration done; continue while the
+// residual is above tolerance, no breakdown occurred and the iteration limit is not reached
+struct LoopCtl {
+  double tol2, bb;
+  int maxit, it;
+};
+__global__ void k_cg_loop_check(const PcgScal* __restrict__ S, LoopCtl* c, cudaGraphConditionalHandle cond) {
+  const int it = c->it + 1;
+  c->it = it;
+  const double rr = S->rr;
+  const bool go = !S->bad && isfinite(rr) && rr > c->tol2 * c->bb && it < c->maxit;
+  cudaGraphSetConditional(cond, go ? 1u : 0u);
+}
+
 // per-problem results: res[3 g] = iterations, res[3 g + 1] = ||b - M x|| / ||b|| (true residual
 // from the chunk sums), res[3 g + 2] = status (0 converged, 4 not converged, 5 breakdown);
 // g = gidx[s], the problem's index in the caller's list; res[gslot] = loop iterations
