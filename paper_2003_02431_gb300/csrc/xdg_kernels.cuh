@@ -420,97 +420,6 @@ __global__ void k_diag_inv(int64_t nb, const int64_t* __restrict__ diag, const d
 }
 
 // ------------------------------------------------------------------------------------------
-// coarsest level: dense matrix, Cholesky, inverse, GEMV
-
-// dense[(i*NP+r)*n + col*NP+c] = block values
-__global__ void k_bsr_to_dense(int64_t nb, int np, const int64_t* __restrict__ rp,
-                               const int32_t* __restrict__ col, const double* __restrict__ val,
-                               int64_t n, double* __restrict__ A) {
-  int64_t i = blockIdx.x;
-  if (i >= nb) return;
-  const int np2 = np * np;
-  for (int64_t z = rp[i]; z < rp[i + 1]; ++z)
-    for (int e = threadIdx.x; e < np2; e += blockDim.x) {
-      int r = e / np, c = e - r * np;
-      A[(i * np + r) * n + (int64_t)col[z] * np + c] = val[z * np2 + e];
-    }
-}
-
-// in-place right-looking Cholesky of the n x n matrix (single CTA); lower triangle holds L
-__global__ void __launch_bounds__(1024) k_dense_chol(int64_t n, double* A, int* err) {
-  __shared__ double djj;
-  __shared__ int bad;
-  if (threadIdx.x == 0) bad = 0;
-  __syncthreads();
-  for (int64_t j = 0; j < n; ++j) {
-    if (threadIdx.x == 0) {
-      double s = A[j * n + j];
-      if (!(s > 0.0)) {
-        bad = 1;
-        s = 1.0;
-      }
-      djj = sqrt(s);
-      A[j * n + j] = djj;
-    }
-    __syncthreads();
-    if (bad) break;
-    for (int64_t i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[i * n + j] /= djj;
-    __syncthreads();
-    const int64_t m = n - j - 1;
-    const int64_t tot = m * m;
-    for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
-      int64_t a = j + 1 + e / m, c = j + 1 + e % m;
-      if (c <= a) A[a * n + c] -= A[a * n + j] * A[c * n + j];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0 && bad) *err = 1;
-}
-
-// column j of L^{-1} (one thread per column)
-__global__ void k_tri_inverse(int64_t n, const double* __restrict__ L, double* __restrict__ X) {
-  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  for (int64_t i = 0; i < j; ++i) X[i * n + j] = 0.0;
-  for (int64_t i = j; i < n; ++i) {
-    double s = (i == j) ? 1.0 : 0.0;
-    for (int64_t p = j; p < i; ++p) s -= L[i * n + p] * X[p * n + j];
-    X[i * n + j] = s / L[i * n + i];
-  }
-}
-
-// Minv = X^T X with X = L^{-1} lower triangular (16x16 tiles)
-__global__ void k_xtx(int64_t n, const double* __restrict__ X, double* __restrict__ Minv) {
-  __shared__ double As[16][17], Bs[16][17];
-  int64_t i = (int64_t)blockIdx.y * 16 + threadIdx.y, j = (int64_t)blockIdx.x * 16 + threadIdx.x;
-  double s = 0.0;
-  for (int64_t k0 = 0; k0 < n; k0 += 16) {
-    int64_t ka = k0 + threadIdx.x, kb = k0 + threadIdx.y;
-    As[threadIdx.y][threadIdx.x] = (ka < n && (int64_t)blockIdx.y * 16 + threadIdx.y < n)
-                                       ? X[ka * n + (int64_t)blockIdx.y * 16 + threadIdx.y] : 0.0;
-    Bs[threadIdx.y][threadIdx.x] = (kb < n && j < n) ? X[kb * n + j] : 0.0;
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 16; ++q) s = fma(As[threadIdx.y][q], Bs[q][threadIdx.x], s);
-    __syncthreads();
-  }
-  if (i < n && j < n) Minv[i * n + j] = s;
-}
-
-// y = A x for a dense row-major n x n matrix: one warp per row
-__global__ void __launch_bounds__(kThreads) k_gemv(int64_t n, const double* __restrict__ A,
-                                                  const double* __restrict__ x, double* __restrict__ y) {
-  const int lane = threadIdx.x & 31;
-  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (row >= n) return;
-  double s = 0.0;
-  for (int64_t c = lane; c < n; c += 32) s = fma(__ldg(A + row * n + c), __ldg(x + c), s);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) y[row] = s;
-}
-
-// ------------------------------------------------------------------------------------------
 // deterministic reductions and Krylov vector updates
 
 constexpr int kRedBlocks = 608;  // 4 x 152 SMs; fixed so that the summation order is fixed
@@ -557,17 +466,6 @@ struct PcgScal {
   double rz, rz_new, pq, rr, alpha, beta, zq;
   int bad;
 };
-
-// alpha = rz / pq
-__global__ void k_pcg_alpha(PcgScal* S) {
-  double pq = S->pq;
-  if (!(pq > 0.0) || !isfinite(pq)) {
-    S->bad = 1;
-    S->alpha = 0.0;
-  } else {
-    S->alpha = S->rz / pq;
-  }
-}
 
 // beta = rz_new / rz; rz = rz_new
 __global__ void k_pcg_beta(PcgScal* S) {
@@ -665,26 +563,6 @@ __global__ void k_copy(int64_t n, const double* __restrict__ a, double* __restri
 __global__ void k_axpy(int64_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = fma(a, x[i], y[i]);
-}
-
-// y = a x + b y, with a, b on the host
-__global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = a * x[i] + b * y[i];
-}
-
-// x *= a
-__global__ void k_scale(int64_t n, double a, double* __restrict__ x) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    x[i] *= a;
-}
-
-// v_i = ((i+1) * 2654435761 mod 2^32) / 2^32 - 0.5 (Knuth's multiplicative hash)
-__global__ void k_hash_vector(int64_t n, double* __restrict__ v) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t h = (uint32_t)((uint64_t)(i + 1) * 2654435761ull);
-    v[i] = (double)h / 4294967296.0 - 0.5;
-  }
 }
 
 }  // namespace xdg
