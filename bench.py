@@ -297,6 +297,13 @@ def learned_section(xdg, torch, dev, stream, n_train=4):
             xplain = x0.clone()
     out["solution_diff_rel_l2"] = float(torch.linalg.norm(x0 - xplain) / torch.linalg.norm(xplain))
     H.learned_enable(None)
+    # the plain FP64 path on the same problem (CG with the FP64 cycle)
+    x0.zero_()
+    H.solve(b, x0, tol=TOL, precision=xdg.XDG_PREC_F64)
+    x0.zero_()
+    info = H.solve(b, x0, tol=TOL, precision=xdg.XDG_PREC_F64)
+    out["solve_plain_f64"] = {"iterations": info["iterations"], "ms": info["ms"], "relres": info["relres"]}
+    out["speedup_learned_vs_plain_f64"] = info["ms"] / out["solve_learned"]["ms"]
     H.destroy()
     net.destroy()
     return out

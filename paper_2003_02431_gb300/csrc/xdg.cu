@@ -320,7 +320,7 @@ struct OpsU {
   void (*samples)(cudaStream_t, int, int, const int32_t*, const float*, const double*, const double*, const double*,
                   float*, float*, float*);
   void (*apply)(cudaStream_t, int, MlpDims, int, const int32_t*, const float*, const double*, const __nv_bfloat16*,
-                const double*, const double*, double*, int*, double*);
+                const double*, const float*, double*, int*, double*);
   void (*gather)(cudaStream_t, int, const int32_t*, const int64_t*, const int32_t*, const double*, double, double*);
 };
 
@@ -339,10 +339,10 @@ struct OpsUT {
     k_unit_samples<NP><<<(U + 7) / 8, 256, 0, s>>>(U, ng, pr, geo, r, Li, Hi, X, R, C);
   }
   static void apply(cudaStream_t s, int U, MlpDims d, int ng, const int32_t* pr, const float* geo, const double* r,
-                    const __nv_bfloat16* W, const double* Li, const double* Hm, double* dl, int* kp, double* E) {
-    const size_t sm = (size_t)d.total * sizeof(__nv_bfloat16);  // <= 30 KB (n_in, n_out <= 64)
-    const int blocks = std::max(1, std::min((U + 7) / 8, 152 * 4));
-    k_unit_apply<NP><<<blocks, 256, sm, s>>>(U, d, ng, pr, geo, r, W, Li, Hm, dl, kp, E);
+                    const __nv_bfloat16* W, const double* Li, const float* Hm, double* dl, int* kp, double* E) {
+    // BF16 weights (<= 30.2 KB for n_in <= 64, n_out <= 40) and 32 units x 2 x 65 floats
+    const size_t sm = (size_t)((d.total * 2 + 15) / 16) * 16 + 32 * 2 * kActStride * sizeof(float);
+    k_unit_apply<NP><<<(U + 31) / 32, 128, sm, s>>>(U, d, ng, pr, geo, r, W, Li, Hm, dl, kp, E);
   }
   static void gather(cudaStream_t s, int nt, const int32_t* tb, const int64_t* tp, const int32_t* tl,
                      const double* dl, double th, double* z) {
@@ -739,7 +739,7 @@ struct xdg_hier {
   void learned_apply(const double* r, double* z) {
     Level& V = L[0];
     lr.ops.resid_rows(grid(lr.nt), stream, lr.nt, lr.tblk, V.rp, V.col, V.val, z, r, lr.res);
-    lr.ops.apply(stream, lr.U, lr.d, lr.n_geo, lr.pairs, lr.geom, lr.res, lr.W, lr.Linv, lr.Hm, lr.delta, lr.keep,
+    lr.ops.apply(stream, lr.U, lr.d, lr.n_geo, lr.pairs, lr.geom, lr.res, lr.W, lr.Linv, lr.Mloc, lr.delta, lr.keep,
                  lr.E);
     lr.ops.gather(stream, lr.nt, lr.tblk, lr.tptr, lr.tlist, lr.delta, lr.theta, z);
     launches += 3;

@@ -101,9 +101,14 @@ __device__ __forceinline__ void mlp_forward(const W* __restrict__ P, const MlpDi
   dense_out(P + d.oW4, P + d.ob4, d.n_out, a[4], a[5], lane, y0, y1);
 }
 
+// parameters to shared memory: 16-byte loads for the aligned bulk, element loads for the tail
 template <class W>
 __device__ void stage_params(W* sp, const W* __restrict__ P, int total) {
-  for (int i = threadIdx.x; i < total; i += blockDim.x) sp[i] = P[i];
+  const int nvec = (int)(((size_t)total * sizeof(W)) / 16);
+  const uint4* src = reinterpret_cast<const uint4*>(P);
+  uint4* dst = reinterpret_cast<uint4*>(sp);
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) dst[i] = __ldg(src + i);
+  for (int i = nvec * (int)(16 / sizeof(W)) + threadIdx.x; i < total; i += blockDim.x) sp[i] = P[i];
   __syncthreads();
 }
 
@@ -513,62 +518,151 @@ __global__ void __launch_bounds__(256) k_unit_samples(int U, int n_geo, const in
 // coordinates is s y, i.e. delta = s [X_a^T y_a; X_b^T y_b]. Kept when it lowers the error's
 // energy: E = s^2 (y^T H y - 2 y^T rhat) = delta^T M_uu delta - 2 delta^T r_u < 0 (FP64).
 // delta[u][0..m) = kept correction (zeros otherwise), keep[u], E[u].
+//
+// Mapping: four lanes per unit (eight units per warp); in every layer lane q of a unit computes
+// outputs q*16 .. q*16+15 with sixteen independent accumulators, reading the layer input from
+// the unit's row of a padded shared-memory buffer (stride 65: the eight units of a warp fall in
+// different banks) and the weights from shared memory. Sums over the four lanes use shuffles in
+// a fixed order.
+constexpr int kUnitLanes = 4;
+constexpr int kActStride = 65;
+
+__device__ __forceinline__ double quad_sum(double v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  return v;
+}
+
 template <int NP>
-__global__ void __launch_bounds__(256) k_unit_apply(int U, MlpDims d, int n_geo, const int32_t* __restrict__ pairs,
+__global__ void __launch_bounds__(128) k_unit_apply(int U, MlpDims d, int n_geo, const int32_t* __restrict__ pairs,
                                                    const float* __restrict__ geom, const double* __restrict__ r,
                                                    const __nv_bfloat16* __restrict__ P,
-                                                   const double* __restrict__ Linv, const double* __restrict__ Hm,
+                                                   const double* __restrict__ Linv, const float* __restrict__ Hf,
                                                    double* __restrict__ delta, int* __restrict__ keep,
                                                    double* __restrict__ E) {
   constexpr int m = 2 * NP;
+  constexpr int T = (m + kUnitLanes - 1) / kUnitLanes;  // residual / output entries per lane
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __nv_bfloat16* sp = reinterpret_cast<__nv_bfloat16*>(smem_raw);
+  const int wbytes = ((d.total * 2 + 15) / 16) * 16;
+  float* act = reinterpret_cast<float*>(smem_raw + wbytes);
   stage_params(sp, P, d.total);
-  const int lane = threadIdx.x & 31;
-  const int nw = gridDim.x * (blockDim.x >> 5);
-  for (int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < U; u += nw) {
-    double r0, r1, s;
-    unit_residual<NP>(pairs, Linv, u, r, lane, r0, r1, s);
-    const double inv = s > 0.0 ? 1.0 / s : 0.0;
-    const float x0 = unit_input(geom, n_geo, u, lane < d.n_in ? lane : 0, r0, r1, inv, lane);
-    const float x1 = unit_input(geom, n_geo, u, lane + 32 < d.n_in ? lane + 32 : 0, r0, r1, inv, lane);
-    float z[6], a[6], y0, y1;
-    mlp_forward(sp, d, lane < d.n_in ? x0 : 0.f, lane + 32 < d.n_in ? x1 : 0.f, lane, z, a, y0, y1);
-    const double yd0 = lane < m ? (double)y0 : 0.0, yd1 = lane + 32 < m ? (double)y1 : 0.0;
-    // energy in block-Jacobi coordinates
-    const double* H = Hm + (int64_t)u * m * m;
-    double hy0 = 0.0, hy1 = 0.0;
-    for (int k = 0; k < m; ++k) {
-      const double yk = __shfl_sync(0xffffffffu, k < 32 ? yd0 : yd1, k & 31);
-      if (lane < m) hy0 = fma(H[lane * m + k], yk, hy0);
-      if (lane + 32 < m) hy1 = fma(H[(lane + 32) * m + k], yk, hy1);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int uu = lane >> 2, q = lane & 3;
+  const int slot = w * 8 + uu;
+  float* A0 = act + slot * 2 * kActStride;
+  float* A1 = A0 + kActStride;
+  const int u = blockIdx.x * 32 + slot;
+  const bool valid = u < U;
+  // residual of the unit in block-Jacobi coordinates: entries e = q + 4 t
+  double rt[T];
+  double ss = 0.0;
+  const double* X = Linv + (int64_t)(valid ? u : 0) * 2 * NP * NP;
+  const int blk[2] = {valid ? pairs[2 * u] : 0, valid ? pairs[2 * u + 1] : 0};
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const int e = q + kUnitLanes * t;
+    double acc = 0.0;
+    if (valid && e < m) {
+      const int h = e / NP, i = e - h * NP;
+      const double* xr = X + h * NP * NP + i * NP;
+      const double* rv = r + (int64_t)blk[h] * NP;
+      for (int k = 0; k <= i; ++k) acc = fma(xr[k], rv[k], acc);
     }
-    double e = yd0 * (hy0 - 2.0 * r0 * inv) + yd1 * (hy1 - 2.0 * r1 * inv);
+    rt[t] = acc;
+    ss = fma(acc, acc, ss);
+  }
+  ss = quad_sum(ss);
+  const double s = sqrt(ss);
+  const double inv = s > 0.0 ? 1.0 / s : 0.0;
+  // network input
+  for (int e = q; e < n_geo; e += kUnitLanes) A0[e] = valid ? geom[(int64_t)u * n_geo + e] : 0.f;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-    e *= s * s;
-    const bool k_ = (e < 0.0) && (s > 0.0);
-    // delta = s X^T y per half: delta_h[i] = s sum_{j >= i} X_h[j][i] y_h[j]
-    const double* Xu = Linv + (int64_t)u * 2 * NP * NP;
-    double dl[2] = {0.0, 0.0};
+  for (int t = 0; t < T; ++t) {
+    const int e = q + kUnitLanes * t;
+    if (e < m) A0[n_geo + e] = (float)(rt[t] * inv);
+  }
+  __syncwarp();
+  // three hidden layers (GELU), 16 outputs per lane
+  const int nin[3] = {d.n_in, kHid, kHid};
+  const int ow[3] = {d.oW1, d.oW2, d.oW3};
+  const int ob[3] = {d.ob1, d.ob2, d.ob3};
+  float* in = A0;
+  float* out = A1;
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      const int e2 = lane + 32 * t;
-      const int h = (e2 < m ? e2 : 0) / NP, i = (e2 < m ? e2 : 0) - h * NP;
-      double acc = 0.0;
-      for (int j = 0; j < NP; ++j) {
-        const int src = h * NP + j;
-        const double yj = __shfl_sync(0xffffffffu, src < 32 ? yd0 : yd1, src & 31);
-        if (j >= i) acc = fma(Xu[h * NP * NP + j * NP + i], yj, acc);
+  for (int layer = 0; layer < 3; ++layer) {
+    float acc[16];
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj) acc[jj] = wload(sp + ob[layer], q * 16 + jj);
+    const __nv_bfloat16* Wl = sp + ow[layer] + q * 16;
+    for (int i = 0; i < nin[layer]; ++i) {
+      const float xi = in[i];
+#pragma unroll
+      for (int jj = 0; jj < 16; ++jj) acc[jj] = fmaf(wload(Wl, i * kHid + jj), xi, acc[jj]);
+    }
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj) out[q * 16 + jj] = gelu_f(acc[jj]);
+    __syncwarp();
+    float* tmp = in;
+    in = out;
+    out = tmp;
+  }
+  // output layer: y_e, e = q + 4 t
+  double y[T];
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const int e = q + kUnitLanes * t;
+    float acc = 0.f;
+    if (e < m) {
+      acc = wload(sp + d.ob4, e);
+      for (int i = 0; i < kHid; ++i) acc = fmaf(wload(sp + d.oW4, i * m + e), in[i], acc);
+      out[e] = acc;
+    }
+    y[t] = (double)acc;
+  }
+  __syncwarp();
+  // energy change s^2 (y^T H y - 2 y^T rhat), H from its FP32 copy (rows of 2 Np floats, 16-byte
+  // aligned: 2 Np is a multiple of 4 for Np in {6, 10, 20}; element loads otherwise)
+  const float* Hu = Hf + (int64_t)(valid ? u : 0) * m * m;
+  double part = 0.0;
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const int e = q + kUnitLanes * t;
+    if (valid && e < m) {
+      float hy = 0.f;
+      if constexpr (m % 4 == 0) {
+        const float4* hr = reinterpret_cast<const float4*>(Hu + e * m);
+#pragma unroll
+        for (int k4 = 0; k4 < m / 4; ++k4) {
+          const float4 h4 = __ldg(hr + k4);
+          hy = fmaf(h4.x, out[4 * k4], hy);
+          hy = fmaf(h4.y, out[4 * k4 + 1], hy);
+          hy = fmaf(h4.z, out[4 * k4 + 2], hy);
+          hy = fmaf(h4.w, out[4 * k4 + 3], hy);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < m; ++k) hy = fmaf(__ldg(Hu + e * m + k), out[k], hy);
       }
-      dl[t] = s * acc;
+      part += y[t] * ((double)hy - 2.0 * rt[t] * inv);
     }
-    if (lane < m) delta[(int64_t)u * m + lane] = k_ ? dl[0] : 0.0;
-    if (lane + 32 < m) delta[(int64_t)u * m + lane + 32] = k_ ? dl[1] : 0.0;
-    if (lane == 0) {
-      keep[u] = k_;
-      E[u] = e;
+  }
+  const double en = quad_sum(part) * ss;
+  const bool kp = valid && (en < 0.0) && (s > 0.0);
+  // delta = s X^T y per half: delta_e = s sum_{j >= i} X_h[j][i] y_{h NP + j}
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const int e = q + kUnitLanes * t;
+    if (valid && e < m) {
+      const int h = e / NP, i = e - h * NP;
+      double acc = 0.0;
+      for (int j = i; j < NP; ++j) acc = fma(X[h * NP * NP + j * NP + i], (double)out[h * NP + j], acc);
+      delta[(int64_t)u * m + e] = kp ? s * acc : 0.0;
     }
+  }
+  if (valid && q == 0) {
+    keep[u] = kp;
+    E[u] = en;
   }
 }
 
