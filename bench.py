@@ -100,7 +100,8 @@ KERNEL_NAMES = {
     "resid_rt_f32": "k_resid_rt_lp<10,float,float,1,0>: level-1 FP32 residual and R^T (restriction phase 1)",
     "smooth_f32": "k_smooth_lp<10,float,0,0>: level-1 FP32 block-Jacobi sweep",
     "apply_f32": "k_spmv_lp<10,float,float,0>: level-1 FP32 operator apply",
-    "apply_f64": "k_spmv<10,0>: level-1 FP64 operator apply (outer flexible CG)",
+    "apply_f64": "k_spmv<10,0>: level-1 FP64 operator apply (FP64 path)",
+    "apply_pair": "k_spmv_dot_df<10>: level-1 FP64-accurate apply from FP32 pairs (outer flexible CG)",
 }
 # the kernel with the largest share of the mixed solve's device time, and the largest HBM-bound
 # one (launch list in profiles/launch_list_mixed_solve_64cube.md)
@@ -352,6 +353,14 @@ def main():
     ap.add_argument("--split-mask", type=int, default=-1,
                     help="force the split-row mapping per level (bit l: level l+1) instead of the autotuned one "
                          "(for profiler runs, where the autotuner's timings are distorted)")
+    ap.add_argument("--outer-apply", type=int, default=0, choices=[0, 1, 2],
+                    help="operator apply of the outer flexible CG: 0 autotuned, 1 FP64, 2 FP32 pairs")
+    ap.add_argument("--symmetric", type=int, default=0, choices=[0, 1, 2],
+                    help="symmetric storage of level 1: 0 autotuned, 1 never, 2 always")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="drive the solve's iterations from the host (one graph launch per iteration) instead "
+                         "of the device-side loop; same kernels and arithmetic, for profilers that cannot list "
+                         "the kernels of a graph with conditional nodes")
     ap.add_argument("--size", type=int, default=64,
                     help="cells per direction; 64 is the benchmark workload, smaller sizes serve profiling")
     args = ap.parse_args()
@@ -382,7 +391,8 @@ def main():
     n, Np, nb, nnzb = P.dof, P.Np, P.nb[0], int(P.row_ptr[-1])
     t = time.perf_counter()
     H = xdg.Hierarchy.from_problem(P, gamma=GAMMA, w_levels=W_LEVELS, low_precision=3, stream=stream,
-                                   fused_coarse=args.fused_coarse)
+                                   fused_coarse=args.fused_coarse, outer_apply=args.outer_apply,
+                                   symmetric=args.symmetric)
     setup_s = time.perf_counter() - t
     if args.split_mask >= 0:
         for l in range(len(P.nb)):
@@ -392,10 +402,13 @@ def main():
     x = torch.zeros(n, dtype=torch.float64, device=dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
+    # a time budget (never reached) selects the host-driven iteration loop
+    budget = 1e9 if args.host_loop else 0.0
+
     def timed_solves(prec, steps, prof=False):
         for _ in range(warmup):
             x.zero_()
-            H.solve(b, x, tol=TOL, maxit=1000, precision=prec)
+            H.solve(b, x, tol=TOL, maxit=1000, precision=prec, time_budget_ms=budget)
         launches, iters = 0, []
         if dist:
             dist.barrier()
@@ -405,7 +418,7 @@ def main():
         ev0.record(stream)
         for _ in range(steps):
             x.zero_()
-            info = H.solve(b, x, tol=TOL, maxit=1000, precision=prec)
+            info = H.solve(b, x, tol=TOL, maxit=1000, precision=prec, time_budget_ms=budget)
             launches += info["launches"]
             iters.append(info["iterations"])
         ev1.record(stream)
@@ -449,7 +462,10 @@ def main():
     for key, which, prec in (("resid_rt_f32", H.KERNEL_RESTRICT, xdg.XDG_PREC_F32),
                              ("smooth_f32", H.KERNEL_SMOOTH, xdg.XDG_PREC_F32),
                              ("apply_f32", H.KERNEL_APPLY, xdg.XDG_PREC_F32),
-                             ("apply_f64", H.KERNEL_APPLY, xdg.XDG_PREC_F64)):
+                             ("apply_f64", H.KERNEL_APPLY, xdg.XDG_PREC_F64),
+                             ("apply_pair", H.KERNEL_APPLY, xdg.XDG_PREC_F64_PAIR)):
+        if key == "apply_pair" and args.outer_apply == 1:
+            continue  # no pair copy
         ms, by = H.kernel_time(which, 1, prec, reps=20)
         kernels[key] = {"kernel": KERNEL_NAMES[key], "ms": ms, "bytes": by, "achieved_gbs": by / (ms / 1e3) / 1e9,
                         "frac_hbm": by / (ms / 1e3) / 1e9 / hbm}
@@ -499,6 +515,8 @@ def main():
                        "outer": "flexible CG, FP64 apply/residual/update", "tol": TOL, "iterations": iters,
                        "parallelism": "replicas" if world > 1 else "single",
                        "split_rows_levels": hinfo["split"],
+                       "outer_apply_pair": hinfo["outer_pair"],
+                       "symmetric_level1": {"cycle": hinfo["symmetric_cycle"], "pair": hinfo["symmetric_pair"]},
                        "fused_small_levels_from": hinfo["fused_level"],
                        "l2": "inputs larger than L2 (operator 1.49 GB FP64 + 0.74 GB FP32)"},
             "paths": {

@@ -38,6 +38,10 @@
  *     fail with XDG_ECUDA when no usable GPU is present.
  *   - A handle is not thread-safe; concurrent calls on one handle must be serialised by the
  *     caller. Different handles are independent.
+ *   - Kernels are launched with programmatic dependent launch (each kernel waits for its
+ *     predecessor's completion before touching memory, but is dispatched while the
+ *     predecessor drains). The environment variable XDG_PDL=0, read once per process, turns it
+ *     off; results are bitwise the same either way.
  */
 #ifndef XDG_H
 #define XDG_H
@@ -60,8 +64,13 @@ enum {
   XDG_ETIMEOUT = 6     /* the solve exceeded its time budget; x and info hold the last iterate */
 };
 
-/* storage precision of the operator blocks used by an apply or an inner solve */
-enum { XDG_PREC_F64 = 0, XDG_PREC_F32 = 1, XDG_PREC_BF16 = 2 };
+/* storage precision of the operator blocks used by an apply or an inner solve.
+ * XDG_PREC_F64_PAIR (xdg_apply and xdg_kernel_time on level 1 only): the FP64-accurate product
+ * computed on the FP32 pipe from a copy of the operator as pairs of FP32 numbers (hi + lo,
+ * scaled by a power of two per block) and double-float accumulation within each block, the
+ * blocks summed in FP64; error a few units of 2^-48 relative to sum |M||x| per row. It is the
+ * outer apply of the mixed-precision solves when xdg_hier_opts.outer_apply selects it. */
+enum { XDG_PREC_F64 = 0, XDG_PREC_F32 = 1, XDG_PREC_BF16 = 2, XDG_PREC_F64_PAIR = 3 };
 
 typedef struct xdg_hier* xdg_hier_t;
 
@@ -109,21 +118,32 @@ typedef struct {
                          cooperative launch with grid barriers between its steps: 0 = if it
                          measures faster at creation, 1 = never, 2 = always (single problems
                          only; batches launch every step) */
+  int outer_apply;    /* operator apply q = M p of the flexible CG around a low-precision cycle:
+                         0 = the FP32-pair product (XDG_PREC_F64_PAIR) if it measures faster at
+                         creation, 1 = FP64, 2 = FP32 pairs (single problems; batches and the
+                         FP64 solve use FP64) */
+  int symmetric;      /* level 1 also in symmetric storage (diagonal and right blocks; a left
+                         block read as the transpose of its mirror, bitwise the same results,
+                         about half the operator streamed from HBM), used by the low-precision
+                         level-1 sweep and restriction and by the pair product when the operator
+                         is exactly symmetric: 0 = where it measures faster at creation,
+                         1 = never, 2 = always */
 } xdg_hier_opts;
 
 typedef struct {
   double tol;           /* stop when ||b - M x||_2 <= tol ||b||_2 (FP64 residual) */
   int maxit;            /* iteration limit (outer CG steps, or inner steps in total) */
   int check_every;      /* read the residual norm back every this many iterations (>= 1) */
-  int precision;        /* XDG_PREC_F64: CG with the FP64 cycle; F32 / BF16: FP64 iterative
-                           refinement around CG with the low-precision cycle and operator */
-  double inner_tol;     /* mixed precision: relative reduction of each inner solve */
+  int precision;        /* XDG_PREC_F64: CG with the FP64 cycle; F32 / BF16: flexible CG
+                           (FP64 residuals, updates and inner products) preconditioned by the
+                           low-precision cycle (xdg_cycle) */
+  double inner_tol;     /* reserved (ignored) */
   double time_budget_ms;/* > 0: return XDG_ETIMEOUT once exceeded (checked with the residual) */
 } xdg_solve_opts;
 
 typedef struct {
-  int iterations;      /* CG iterations (mixed precision: inner iterations in total) */
-  int outer;           /* refinement steps (mixed precision), 1 otherwise */
+  int iterations;      /* CG iterations */
+  int outer;           /* 1 (reserved) */
   double relres;       /* final ||b - M x||_2 / ||b||_2, recomputed in FP64 */
   double ms;           /* wall time of the call */
   int status;          /* same as the return value */
@@ -143,6 +163,9 @@ typedef struct {
   double setup_ms[3];     /* upload+validation, Galerkin products, factorisations+estimates */
   uint64_t split_mask;    /* bit l set: level l+1's low-precision row kernels split rows */
   int fused_level;        /* > 0: the low-precision cycle runs levels fused_level.. in one launch */
+  int outer_pair;         /* 1: the mixed-precision solves apply M with FP32 pairs */
+  int symmetric;          /* bit 0: symmetric storage of level 1 exists; bit 1: the
+                             low-precision cycle reads it; bit 2: the pair product reads it */
 } xdg_hier_info;
 
 /* Build the hierarchy on the current CUDA device: validate every index on the host
@@ -170,7 +193,9 @@ int xdg_get_info(xdg_hier_t h, xdg_hier_info* info);
 int xdg_export_level(xdg_hier_t h, int level, int64_t* row_ptr, int32_t* col, double* val);
 
 /* y = M^level x (device vectors of length nb[level-1]*Np). prec selects the stored operator
- * (XDG_PREC_F64, or F32 / BF16 when built with low_precision; FP32 accumulation then). */
+ * (XDG_PREC_F64, or F32 / BF16 when built with low_precision; FP32 accumulation then), or
+ * XDG_PREC_F64_PAIR on level 1 of a hierarchy that holds the pair copy (xdg_get_info's
+ * outer_pair, or outer_apply = 2); x is split into scaled FP32 pairs in the handle's scratch. */
 int xdg_apply(xdg_hier_t h, int level, const double* x, double* y, int prec);
 
 /* Set the row mapping of the low-precision kernels on `level` (1-based): on != 0 splits each
@@ -247,7 +272,8 @@ int xdg_fma_peak(int prec, double* tflops);
  * kernel of the cycle on `level`, and its algorithmic bytes per launch (*bytes: every stored
  * operator, inverse and transfer entry and scale read once, row pointers and columns once, each
  * vector read or written once). which: 0 = operator apply y = M x (the stored copy of
- * precision prec), 1 = block-Jacobi sweep from a nonzero guess (level < n_levels),
+ * precision prec; XDG_PREC_F64_PAIR: the pair product on level 1 from an already split
+ * vector), 1 = block-Jacobi sweep from a nonzero guess (level < n_levels),
  * 2 = residual and restriction phase 1, R^T (b - M x) per fine block (level < n_levels).
  * The low-precision sweep and restriction read the FP32 operator (see xdg_cycle). Uses the
  * level's work vectors (zeroed first); synchronises. */

@@ -14,11 +14,13 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <memory>
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/xdg.h"
@@ -27,6 +29,7 @@
 #include "xdg_kernels_batch.cuh"
 #include "xdg_kernels_mlp.cuh"
 #include "xdg_kernels_fused.cuh"
+#include "xdg_kernels_df.cuh"
 
 using namespace xdg;
 
@@ -86,7 +89,44 @@ int wave_cap(const void* k) {
   return cap;
 }
 inline int fit_grid(const void* k, int grid) { return std::max(1, std::min(grid, wave_cap(k))); }
-#define LFIT(G, S, ...) __VA_ARGS__<<<fit_grid((const void*)&__VA_ARGS__, G), kThreads, 0, S>>>
+
+// Kernel launches: kl(kernel, grid, block, shared bytes, stream)(arguments). Each launch carries
+// the programmatic-stream-serialization attribute (every kernel begins with griddepcontrol.wait,
+// see pdl_entry), so that inside captured graphs a kernel's CTAs are dispatched while its
+// predecessor drains. XDG_PDL=0 in the environment launches without it (plain serialization).
+inline bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("XDG_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+template <class... P>
+struct KLaunch {
+  void (*k)(P...);
+  dim3 g, b;
+  size_t sm;
+  cudaStream_t s;
+  template <class... A>
+  void operator()(A&&... a) const {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, k, std::forward<A>(a)...);  // errors surface through cudaGetLastError
+  }
+};
+template <class... P>
+inline KLaunch<P...> kl(void (*k)(P...), dim3 g, dim3 b, size_t sm, cudaStream_t s) {
+  return KLaunch<P...>{k, g, b, sm, s};
+}
+#define LFIT(G, S, ...) kl(__VA_ARGS__, fit_grid((const void*)&__VA_ARGS__, G), kThreads, 0, S)
 
 // --------------------------------------------------------------------------------------------
 // per-Np kernel table
@@ -111,6 +151,13 @@ struct Ops {
   void (*diag_inv)(cudaStream_t, int64_t, const int64_t*, const double*, double*, int*);
   int (*spmv_dot)(int grid, cudaStream_t, int64_t, const int64_t*, const int32_t*, const double*, const double*,
                   double*, double*);
+  // FP32-pair (double-float) product and the direction update writing the pair copy
+  int (*spmv_dot_df)(int grid, cudaStream_t, int64_t, const int64_t*, const int32_t*, const float2*, const int*,
+                     const float2*, const int*, const double*, double*, double*);
+  void (*pcg_p_df)(int grid, cudaStream_t, int64_t, const PcgScal*, int, const double*, double*, float2*, int*);
+  void (*split_df)(int grid, cudaStream_t, int64_t, const double*, float2*, int*);
+  int (*spmv_dot_df_sym)(int grid, cudaStream_t, int64_t, const int64_t*, const int32_t*, const float2*, const int*,
+                         SymL, const float2*, const int*, const double*, double*, double*);
   int gpw;
 };
 
@@ -159,18 +206,39 @@ struct OpsT {
   }
   static void diag_inv(cudaStream_t s, int64_t nb, const int64_t* dg, const double* val, double* Dinv,
                        int* err) {
-    k_diag_inv<NP><<<(unsigned)((nb + 63) / 64), 64, 0, s>>>(nb, dg, val, Dinv, err);
+    kl(k_diag_inv<NP>, (unsigned)((nb + 63) / 64), 64, 0, s)(nb, dg, val, Dinv, err);
   }
   // returns the grid used (= the number of partial sums written)
   static int spmv_dot(int grid, cudaStream_t s, int64_t nb, const int64_t* rp, const int32_t* col,
                       const double* val, const double* x, double* y, double* partial) {
     const int g = std::min(fit_grid((const void*)&k_spmv_dot<NP>, grid), kPartials);
-    k_spmv_dot<NP><<<g, kThreads, 0, s>>>(nb, rp, col, val, x, y, partial);
+    kl(k_spmv_dot<NP>, g, kThreads, 0, s)(nb, rp, col, val, x, y, partial);
+    return g;
+  }
+  static int spmv_dot_df(int grid, cudaStream_t s, int64_t nb, const int64_t* rp, const int32_t* col,
+                         const float2* v2, const int* ea, const float2* x2, const int* ex, const double* x, double* y,
+                         double* partial) {
+    const int g = std::min(fit_grid((const void*)&k_spmv_dot_df<NP>, grid), kPartials);
+    kl(k_spmv_dot_df<NP>, g, kThreads, 0, s)(nb, rp, col, v2, ea, x2, ex, x, y, partial);
+    return g;
+  }
+  static void pcg_p_df(int grid, cudaStream_t s, int64_t nb, const PcgScal* S, int first, const double* z, double* p,
+                       float2* p2, int* ex) {
+    LFIT(grid, s, k_pcg_p_df<NP>)(nb, S, first, z, p, p2, ex);
+  }
+  static void split_df(int grid, cudaStream_t s, int64_t nb, const double* x, float2* x2, int* ex) {
+    LFIT(grid, s, k_split_df<NP>)(nb, x, x2, ex);
+  }
+  static int spmv_dot_df_sym(int grid, cudaStream_t s, int64_t nb, const int64_t* urp, const int32_t* ucol,
+                             const float2* uv2, const int* uea, SymL Ls, const float2* x2, const int* ex,
+                             const double* x, double* y, double* partial) {
+    const int g = std::min(fit_grid((const void*)&k_spmv_dot_df_sym<NP>, grid), kPartials);
+    kl(k_spmv_dot_df_sym<NP>, g, kThreads, 0, s)(nb, urp, ucol, uv2, uea, Ls, x2, ex, x, y, partial);
     return g;
   }
   static Ops make() {
     return Ops{NP, spmv, smooth, bjsolve, diagmul, resid_rt, gather, gather_smooth0, prolong, galerkin, diag_inv,
-               spmv_dot, Grp<NP>::GPW};
+               spmv_dot, spmv_dot_df, pcg_p_df, split_df, spmv_dot_df_sym, Grp<NP>::GPW};
   }
 };
 
@@ -205,13 +273,19 @@ struct OpsLP {
                          const float*, float, const float*, float*, float*);
   cudaError_t (*fused)(cudaStream_t, int grid, const FusedCycle*, int pre0);
   int (*fused_occupancy)();
+  // level 1 on the symmetric storage (sweep from a nonzero guess; residual-restriction)
+  void (*smooth_sym)(int, cudaStream_t, int64_t, const int64_t*, const int32_t*, const float*, const float*, SymL,
+                     const float*, const float*, float, const float*, const float*, const float*, float*,
+                     const uint8_t*);
+  void (*resid_rt_sym)(int, cudaStream_t, int64_t, const int64_t*, const int32_t*, const float*, const float*, SymL,
+                       const void*, const float*, const float*, const float*, float*, const uint8_t*);
   size_t elem;
 };
 
 template <int NP, class TS>
 struct OpsLPT {
   static void make(cudaStream_t s, int64_t nblk, int np2, const double* src, void* dst, float* sc) {
-    k_make_lp<TS><<<(unsigned)((nblk * 32 + 255) / 256), 256, 0, s>>>(nblk, np2, src, (TS*)dst, sc);
+    kl(k_make_lp<TS>, (unsigned)((nblk * 32 + 255) / 256), 256, 0, s)(nblk, np2, src, (TS*)dst, sc);
   }
   // spl: one block row per warp, the warp's groups splitting the row (small levels)
   static void spmv_f(int grid, bool spl, cudaStream_t s, int64_t nb, const int64_t* rp, const int32_t* col,
@@ -294,9 +368,19 @@ struct OpsLPT {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused_vcycle<NP, TS>, kThreads, 0) != cudaSuccess) occ = 0;
     return occ;
   }
+  static void smooth_sym(int grid, cudaStream_t s, int64_t nb, const int64_t* urp, const int32_t* ucol,
+                         const float* uval, const float* usc, SymL Ls, const float* Dinv, const float* dsc, float om,
+                         const float* omr, const float* b, const float* xi, float* xo, const uint8_t* act) {
+    LFIT(grid, s, k_smooth_lp_sym<NP>)(nb, urp, ucol, uval, usc, Ls, Dinv, dsc, om, omr, b, xi, xo, act);
+  }
+  static void resid_rt_sym(int grid, cudaStream_t s, int64_t nbf, const int64_t* urp, const int32_t* ucol,
+                           const float* uval, const float* usc, SymL Ls, const void* R, const float* rsc,
+                           const float* b, const float* x, float* t, const uint8_t* act) {
+    LFIT(grid, s, k_resid_rt_lp_sym<NP, TS>)(nbf, urp, ucol, uval, usc, Ls, (const TS*)R, rsc, b, x, t, act);
+  }
   static OpsLP get() {
     return OpsLP{make, spmv_f, spmv_d, smooth, resid_rt, gather, prolong, resid32, gather_smooth0, fused,
-                 fused_occupancy, sizeof(TS)};
+                 fused_occupancy, smooth_sym, resid_rt_sym, sizeof(TS)};
   }
 };
 
@@ -328,26 +412,26 @@ template <int NP>
 struct OpsUT {
   static void factor(cudaStream_t s, int U, const int64_t* z, const double* v, double* Li, double* Hm, float* M,
                      double* Hi, int* e) {
-    k_unit_factor<NP><<<U, 32, 0, s>>>(U, z, v, Li, Hm, M, Hi, e);
+    kl(k_unit_factor<NP>, U, 32, 0, s)(U, z, v, Li, Hm, M, Hi, e);
   }
   static void resid_rows(int g, cudaStream_t s, int64_t nr, const int32_t* rows, const int64_t* rp,
                          const int32_t* col, const double* val, const double* x, const double* b, double* y) {
-    k_resid_rows<NP><<<g, kThreads, 0, s>>>(nr, rows, rp, col, val, x, b, y);
+    kl(k_resid_rows<NP>, g, kThreads, 0, s)(nr, rows, rp, col, val, x, b, y);
   }
   static void samples(cudaStream_t s, int U, int ng, const int32_t* pr, const float* geo, const double* r,
                       const double* Li, const double* Hi, float* X, float* R, float* C) {
-    k_unit_samples<NP><<<(U + 7) / 8, 256, 0, s>>>(U, ng, pr, geo, r, Li, Hi, X, R, C);
+    kl(k_unit_samples<NP>, (U + 7) / 8, 256, 0, s)(U, ng, pr, geo, r, Li, Hi, X, R, C);
   }
   static void apply(cudaStream_t s, int U, MlpDims d, int ng, const int32_t* pr, const float* geo, const double* r,
                     const __nv_bfloat16* W, const double* Li, const float* Hm, double* dl, int* kp, double* E) {
     // BF16 weights (<= 30.2 KB for n_in <= 64, n_out <= 40) and 32 units x 2 x 65 floats
     const size_t sm = (size_t)((d.total * 2 + 15) / 16) * 16 + 32 * 2 * kActStride * sizeof(float);
-    k_unit_apply<NP><<<(U + 31) / 32, 128, sm, s>>>(U, d, ng, pr, geo, r, W, Li, Hm, dl, kp, E);
+    kl(k_unit_apply<NP>, (U + 31) / 32, 128, sm, s)(U, d, ng, pr, geo, r, W, Li, Hm, dl, kp, E);
   }
   static void gather(cudaStream_t s, int nt, const int32_t* tb, const int64_t* tp, const int32_t* tl,
                      const double* dl, double th, double* z) {
     const int64_t n = (int64_t)nt * NP;
-    k_unit_gather<NP><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nt, tb, tp, tl, dl, th, z);
+    kl(k_unit_gather<NP>, (unsigned)((n + 255) / 256), 256, 0, s)(nt, tb, tp, tl, dl, th, z);
   }
   static OpsU make() { return OpsU{factor, resid_rows, samples, apply, gather}; }
 };
@@ -471,6 +555,37 @@ struct xdg_hier {
   int64_t bnodes_fixed[3] = {0, 0, 0};  // kernel nodes of a recorded batched solve outside
   int64_t bnodes_body[3] = {0, 0, 0};   // its loop, and inside one loop iteration
   double *s_b = nullptr, *s_x = nullptr, *s_r = nullptr, *s_z = nullptr, *s_p = nullptr, *s_q = nullptr;
+  // level 1 as scaled FP32 pairs (the outer apply of the mixed-precision solves) and the pair
+  // copy of the direction p with its per-block exponents
+  float2* val2 = nullptr;
+  int* ea2 = nullptr;
+  float2* p2 = nullptr;
+  int* ex2 = nullptr;
+  int pair_mode = 0;      // xdg_hier_opts.outer_apply
+  bool pair_on = false;   // the mixed-precision iterations use the pair product
+  int build_pair();
+  int tune_pair();
+  // level 1 in symmetric storage: diagonal and right blocks (compact BSR urp/ucol, umap = their
+  // indices in the full storage), left blocks as mirrors (SymL); FP32 and pair values
+  struct SymLevel {
+    int64_t nu = 0, nl = 0;
+    int64_t *urp = nullptr, *umap = nullptr, *lrp = nullptr;
+    int32_t *ucol = nullptr, *lcol = nullptr, *lblk = nullptr;
+    float* uval = nullptr;
+    float* usc = nullptr;
+    float2* uval2 = nullptr;
+    int* uea = nullptr;
+    SymL L() const { return SymL{lrp, lcol, lblk}; }
+  } sy;
+  int sym_mode = 0;        // xdg_hier_opts.symmetric
+  bool sym_tried = false;
+  bool sym_built = false;  // the operator of level 1 is exactly symmetric and its storage exists
+  bool sym_on = false;     // the low-precision level-1 sweep and restriction read it
+  bool sym_pair = false;   // the pair product reads it
+  int build_sym();
+  int tune_sym(int p);
+  bool lvl1_sym(int l) const { return l == 0 && sym_on && !L[0].spl; }
+  bool use_pair(int p) const { return pair_on && p != XDG_PREC_F64; }
   double* partial = nullptr;
   double* dsc = nullptr;       // device scalars for setup reductions
   PcgScal* S = nullptr;
@@ -575,12 +690,12 @@ struct xdg_hier {
   void coarse(const double* r, double* z) {
     ++launches;
     int64_t blocks = (nc * 32 + kThreads - 1) / kThreads;
-    k_gemv_seg<double><<<(unsigned)blocks, kThreads, 0, stream>>>(nc, nprob, cs_doff, cs_moff, Minv, r, z);
+    kl(k_gemv_seg<double>, (unsigned)blocks, kThreads, 0, stream)(nc, nprob, cs_doff, cs_moff, Minv, r, z);
   }
   void dot(int64_t n, const double* a, const double* b, double* out) {
     launches += 2;
-    k_dot_partial<<<kRedBlocks, kThreads, 0, stream>>>(n, a, b, partial);
-    k_sum_final<<<1, kThreads, 0, stream>>>(kRedBlocks, partial, out);
+    kl(k_dot_partial, kRedBlocks, kThreads, 0, stream)(n, a, b, partial);
+    kl(k_sum_final, 1, kThreads, 0, stream)(kRedBlocks, partial, out);
   }
 
   // one symmetric cycle on level l from a zero initial guess: x = B_l b. pre0: x already
@@ -615,7 +730,7 @@ struct xdg_hier {
       for (int g = 1; g < gamma; ++g) {
         spmv(l + 1, C.x, C.b, C.r, 1);
         cycle(l + 1, C.r, C.dz);
-        k_axpy<<<vgrid(C.nb * Np), kThreads, 0, stream>>>(C.nb * Np, 1.0, C.dz, C.x);
+        kl(k_axpy, vgrid(C.nb * Np), kThreads, 0, stream)(C.nb * Np, 1.0, C.dz, C.x);
         ++launches;
       }
     }
@@ -630,16 +745,20 @@ struct xdg_hier {
       std::swap(cur, oth);
     }
     if (cur != x) {
-      k_copy<<<vgrid(V.nb * Np), kThreads, 0, stream>>>(V.nb * Np, cur, x);
+      kl(k_copy, vgrid(V.nb * Np), kThreads, 0, stream)(V.nb * Np, cur, x);
       ++launches;
     }
   }
 
   // q = M p on level 1 with p . q into S->pq and alpha = rz / pq (3 launches)
-  void apply_alpha() {
+  void apply_alpha(bool pair = false) {
     Level& V = L[0];
-    const int g = ops.spmv_dot(grid(V.nb), stream, V.nb, V.rp, V.col, V.val, s_p, s_q, partial);
-    k_cg_alpha_final<<<1, kThreads, 0, stream>>>(g, partial, S);
+    const int g = (pair && sym_pair)
+                      ? ops.spmv_dot_df_sym(grid(V.nb), stream, V.nb, sy.urp, sy.ucol, sy.uval2, sy.uea, sy.L(), p2,
+                                            ex2, s_p, s_q, partial)
+                  : pair ? ops.spmv_dot_df(grid(V.nb), stream, V.nb, V.rp, V.col, val2, ea2, p2, ex2, s_p, s_q, partial)
+                         : ops.spmv_dot(grid(V.nb), stream, V.nb, V.rp, V.col, V.val, s_p, s_q, partial);
+    kl(k_cg_alpha_final, 1, kThreads, 0, stream)(g, partial, S);
     launches += 2;
   }
 
@@ -648,12 +767,12 @@ struct xdg_hier {
     const int64_t n = L[0].nb * Np;
     apply_alpha();
     launches += 4;  // x/r update, its sum, beta, direction
-    k_pcg_xr<<<kRedBlocks, kThreads, 0, stream>>>(n, S, s_p, s_q, s_x, s_r, partial);
-    k_sum_final<<<1, kThreads, 0, stream>>>(kRedBlocks, partial, &S->rr);
+    kl(k_pcg_xr, kRedBlocks, kThreads, 0, stream)(n, S, s_p, s_q, s_x, s_r, partial, nullptr);
+    kl(k_sum_final, 1, kThreads, 0, stream)(kRedBlocks, partial, &S->rr);
     cycle(0, s_r, s_z);
     dot(n, s_r, s_z, &S->rz_new);
-    k_pcg_beta<<<1, 1, 0, stream>>>(S);
-    k_pcg_p<<<vgrid(n), kThreads, 0, stream>>>(n, S, s_z, s_p);
+    kl(k_pcg_beta, 1, 1, 0, stream)(S);
+    kl(k_pcg_p, vgrid(n), kThreads, 0, stream)(n, S, s_z, s_p);
   }
 
   // ---------------------------------------------------------------- low-precision cycle
@@ -668,7 +787,7 @@ struct xdg_hier {
     if (l == nlev - 1) {
       ++launches;
       int64_t blocks = (nc * 32 + kThreads - 1) / kThreads;
-      k_gemv_seg<float><<<(unsigned)blocks, kThreads, 0, stream>>>(nc, nprob, cs_doff, cs_moff, Minv, b, x);
+      kl(k_gemv_seg<float>, (unsigned)blocks, kThreads, 0, stream)(nc, nprob, cs_doff, cs_moff, Minv, b, x);
       return;
     }
     Level& V = L[l];
@@ -684,13 +803,24 @@ struct xdg_hier {
                cur, act);
       ++launches;
     }
+    const bool sym = lvl1_sym(l);
+    auto sweep = [&](const float* xi, float* xo) {
+      if (sym)
+        o.smooth_sym(grid_lp(l), stream, V.nb, sy.urp, sy.ucol, sy.uval, sy.usc, sy.L(), (const float*)W.Dinv, W.dsc, om, V.omr_f,
+                     b, xi, xo, act);
+      else
+        o.smooth(grid_lp(l), V.spl, stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, V.omr_f, b, xi,
+                 xo, act);
+    };
     for (int s = 1; s < nu; ++s) {
-      o.smooth(grid_lp(l), V.spl, stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, V.omr_f, b, cur, oth,
-               act);
+      sweep(cur, oth);
       ++launches;
       std::swap(cur, oth);
     }
-    o.resid_rt(grid_lp(l), V.spl, stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.R, W.rsc, b, cur, W.s, act);
+    if (sym)
+      o.resid_rt_sym(grid_lp(l), stream, V.nb, sy.urp, sy.ucol, sy.uval, sy.usc, sy.L(), W.R, W.rsc, b, cur, W.s, act);
+    else
+      o.resid_rt(grid_lp(l), V.spl, stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.R, W.rsc, b, cur, W.s, act);
     launches += 2;
     if (l + 2 < nlev) {
       o.gather_smooth0(grid(C.nb), stream, C.nb, V.cptr, V.ch, W.s, (const float*)WC.Dinv, WC.dsc, (float)C.omega,
@@ -704,7 +834,7 @@ struct xdg_hier {
       for (int g = 1; g < gamma; ++g) {
         o.resid32(grid_lp(l + 1), C.spl, stream, C.nb, C.rp, C.col, WC.val32, WC.sc32, WC.x, WC.b, WC.r);
         cycle_lp(p, l + 1, WC.r, WC.dz);
-        k_axpy_f<<<vgrid(C.nb * Np), kThreads, 0, stream>>>(C.nb * Np, 1.0f, WC.dz, WC.x);
+        kl(k_axpy_f, vgrid(C.nb * Np), kThreads, 0, stream)(C.nb * Np, 1.0f, WC.dz, WC.x);
         launches += 2;
       }
     }
@@ -714,13 +844,12 @@ struct xdg_hier {
     cur = after;
     oth = (cur == x) ? W.t : x;
     for (int s = 0; s < nu; ++s) {
-      o.smooth(grid_lp(l), V.spl, stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, V.omr_f, b, cur, oth,
-               act);
+      sweep(cur, oth);
       ++launches;
       std::swap(cur, oth);
     }
     if (cur != x) {
-      k_copy_f<<<vgrid(V.nb * Np), kThreads, 0, stream>>>(V.nb * Np, cur, x);
+      kl(k_copy_f, vgrid(V.nb * Np), kThreads, 0, stream)(V.nb * Np, cur, x);
       ++launches;
     }
   }
@@ -729,9 +858,9 @@ struct xdg_hier {
   void cycle_lp_d(int p, const double* r, double* z) {
     const int64_t n = L[0].nb * Np;
     LevelLP& W = LP[p][0];
-    k_d2f<<<vgrid(n), kThreads, 0, stream>>>(n, r, W.b, cur_act, Np);
+    kl(k_d2f, vgrid(n), kThreads, 0, stream)(n, r, W.b, cur_act, Np);
     cycle_lp(p, 0, W.b, W.x);
-    k_f2d<<<vgrid(n), kThreads, 0, stream>>>(n, W.x, z, cur_act, Np);
+    kl(k_f2d, vgrid(n), kThreads, 0, stream)(n, W.x, z, cur_act, Np);
     launches += 2;
   }
 
@@ -756,26 +885,28 @@ struct xdg_hier {
   // z widened with r . z and z . q; beta; p = z + beta p
   void fcg_iteration(int p) {
     const int64_t n = L[0].nb * Np;
-    apply_alpha();
+    const bool pair = use_pair(p);
+    apply_alpha(pair);
     if (p == XDG_PREC_F64 || lr.on) {  // FP64 cycle or learned correction: generic tail
-      k_pcg_xr<<<kRedBlocks, kThreads, 0, stream>>>(n, S, s_p, s_q, s_x, s_r, partial);
-      k_sum_final<<<1, kThreads, 0, stream>>>(kRedBlocks, partial, &S->rr);
+      kl(k_pcg_xr, kRedBlocks, kThreads, 0, stream)(n, S, s_p, s_q, s_x, s_r, partial, nullptr);
+      kl(k_sum_final, 1, kThreads, 0, stream)(kRedBlocks, partial, &S->rr);
       launches += 2;
       precond_full(p, s_r, s_z);
       dot(n, s_r, s_z, &S->rz);
       dot(n, s_z, s_q, &S->zq);
-      k_fcg_beta<<<1, 1, 0, stream>>>(S);
+      kl(k_fcg_beta, 1, 1, 0, stream)(S);
       ++launches;
     } else {
       LevelLP& W = LP[p][0];
-      k_pcg_xr<<<kRedBlocks, kThreads, 0, stream>>>(n, S, s_p, s_q, s_x, s_r, partial, W.b);
-      k_sum_final<<<1, kThreads, 0, stream>>>(kRedBlocks, partial, &S->rr);
+      kl(k_pcg_xr, kRedBlocks, kThreads, 0, stream)(n, S, s_p, s_q, s_x, s_r, partial, W.b);
+      kl(k_sum_final, 1, kThreads, 0, stream)(kRedBlocks, partial, &S->rr);
       cycle_lp(p, 0, W.b, W.x);
-      k_fcg_tail<<<kRedBlocks, kThreads, 0, stream>>>(n, W.x, s_r, s_q, s_z, partial);
-      k_fcg_beta_final<<<1, kThreads, 0, stream>>>(kRedBlocks, partial, S);
+      kl(k_fcg_tail, kRedBlocks, kThreads, 0, stream)(n, W.x, s_r, s_q, s_z, partial);
+      kl(k_fcg_beta_final, 1, kThreads, 0, stream)(kRedBlocks, partial, S);
       launches += 4;
     }
-    k_pcg_p<<<vgrid(n), kThreads, 0, stream>>>(n, S, s_z, s_p);
+    if (pair) ops.pcg_p_df(grid(L[0].nb), stream, L[0].nb, S, 0, s_z, s_p, p2, ex2);
+    else kl(k_pcg_p, vgrid(n), kThreads, 0, stream)(n, S, s_z, s_p);
     ++launches;
   }
 
@@ -843,8 +974,8 @@ struct xdg_hier {
   // out[s] = (x, y) restricted to problem s on level l (fixed-order slice sums)
   void seg_dot(int l, const double* x, const double* y, double* out) {
     const int spl = std::max(1, std::min(64, 4 * sms / nprob));
-    k_seg_dot<<<dim3((unsigned)spl, (unsigned)nprob), kThreads, 0, stream>>>(nprob, L[l].sdof, x, y, spart);
-    k_seg_sum<<<(nprob + 255) / 256, 256, 0, stream>>>(nprob, spl, spart, out);
+    kl(k_seg_dot, dim3((unsigned)spl, (unsigned)nprob), kThreads, 0, stream)(nprob, L[l].sdof, x, y, spart);
+    kl(k_seg_sum, (nprob + 255) / 256, 256, 0, stream)(nprob, spl, spart, out);
   }
   int sgrid() const { return (nprob + 255) / 256; }
   // z = B r with the FP64 cycle (prec = F64) or the low-precision one
@@ -913,7 +1044,7 @@ int xdg_hier::lanczos(int l, int m) {
   double *q = V.b, *qp = V.x, *u = V.t, *w = V.r, *Dw = V.dz;
   const int vg = vgrid(n);
   double* dv = B.alpha;  // device scratch of nprob doubles (free during setup)
-  k_hash_vector_seg<<<vg, kThreads, 0, stream>>>(n, P, V.sdof, q);
+  kl(k_hash_vector_seg, vg, kThreads, 0, stream)(n, P, V.sdof, q);
   CK(cudaMemsetAsync(qp, 0, n * sizeof(double), stream));
   ops.diagmul(grid(V.nb), stream, V.nb, V.diag, V.val, q, Dw);
   seg_dot(l, q, Dw, dv);
@@ -927,7 +1058,7 @@ int xdg_hier::lanczos(int l, int m) {
     return XDG_OK;
   };
   TRY(put(fac));
-  k_seg_scale<<<vg, kThreads, 0, stream>>>(n, P, V.sdof, dv, q);
+  kl(k_seg_scale, vg, kThreads, 0, stream)(n, P, V.sdof, dv, q);
   std::vector<std::vector<double>> al(P), be(P);
   std::vector<char> live(P, 1);
   for (int j = 0; j < m; ++j) {
@@ -939,10 +1070,10 @@ int xdg_hier::lanczos(int l, int m) {
     ops.bjsolve(grid(V.nb), stream, V.nb, V.Dinv, u, w);
     for (int s = 0; s < P; ++s) coef[s] = -a[s];
     TRY(put(coef));
-    k_seg_axpy<<<vg, kThreads, 0, stream>>>(n, P, V.sdof, dv, q, w);
+    kl(k_seg_axpy, vg, kThreads, 0, stream)(n, P, V.sdof, dv, q, w);
     for (int s = 0; s < P; ++s) coef[s] = -bprev[s];
     TRY(put(coef));
-    k_seg_axpy<<<vg, kThreads, 0, stream>>>(n, P, V.sdof, dv, qp, w);
+    kl(k_seg_axpy, vg, kThreads, 0, stream)(n, P, V.sdof, dv, qp, w);
     ops.diagmul(grid(V.nb), stream, V.nb, V.diag, V.val, w, Dw);
     seg_dot(l, w, Dw, dv);
     TRY(read_scalars(dv, P, b2.data()));
@@ -957,10 +1088,10 @@ int xdg_hier::lanczos(int l, int m) {
       any = any || live[s];
     }
     if (!any) break;
-    k_copy<<<vg, kThreads, 0, stream>>>(n, q, qp);
-    k_copy<<<vg, kThreads, 0, stream>>>(n, w, q);
+    kl(k_copy, vg, kThreads, 0, stream)(n, q, qp);
+    kl(k_copy, vg, kThreads, 0, stream)(n, w, q);
     TRY(put(fac));
-    k_seg_scale<<<vg, kThreads, 0, stream>>>(n, P, V.sdof, dv, q);
+    kl(k_seg_scale, vg, kThreads, 0, stream)(n, P, V.sdof, dv, q);
   }
   CKL();
   V.lmax_p.resize(P);
@@ -985,6 +1116,8 @@ int xdg_hier::build(const xdg_problem* p, const xdg_hier_opts* o) {
   wlev = o && o->w_levels > 0 ? o->w_levels : (1 << 20);
   split_mode = o ? o->split_rows : 0;
   fused_mode = o ? o->fused_coarse : 0;
+  pair_mode = o ? o->outer_apply : 0;
+  sym_mode = o ? o->symmetric : 0;
   const int lsteps = o && o->lanczos_steps > 0 ? o->lanczos_steps : 12;
   const int64_t Np2 = (int64_t)Np * Np;
   CK(cudaGetDevice(&dev));
@@ -1295,7 +1428,7 @@ int xdg_hier::build(const xdg_problem* p, const xdg_hier_opts* o) {
     TRY(alloc(&cs_blk, nprob + 1));
     CK(cudaMemcpyAsync(cs_blk, C.hseg.data(), (nprob + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
     CK(cudaMemsetAsync(A, 0, minv_len * sizeof(double), stream));
-    k_bsr_to_dense_seg<<<(unsigned)C.nb, 128, 0, stream>>>(C.nb, Np, nprob, cs_blk, cs_moff, C.rp, C.col, C.val, A);
+    kl(k_bsr_to_dense_seg, (unsigned)C.nb, 128, 0, stream)(C.nb, Np, nprob, cs_blk, cs_moff, C.rp, C.col, C.val, A);
     CK(cudaMemsetAsync(derr, 0, sizeof(int), stream));
     int64_t* cs_n = nullptr;
     TRY(alloc(&cs_n, nprob));
@@ -1308,11 +1441,11 @@ int xdg_hier::build(const xdg_problem* p, const xdg_hier_opts* o) {
       }
       CK(cudaMemcpyAsync(cs_n, hn.data(), nprob * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
     }
-    k_dense_chol_seg<<<(unsigned)nprob, 1024, 0, stream>>>(nprob, cs_n, cs_moff, A, derr);
-    k_tri_inverse_seg<<<dim3((unsigned)((nmax + 127) / 128), (unsigned)nprob), 128, 0, stream>>>(nprob, cs_n, cs_moff,
+    kl(k_dense_chol_seg, (unsigned)nprob, 1024, 0, stream)(nprob, cs_n, cs_moff, A, derr);
+    kl(k_tri_inverse_seg, dim3((unsigned)((nmax + 127) / 128), (unsigned)nprob), 128, 0, stream)(nprob, cs_n, cs_moff,
                                                                                                 A, X);
     dim3 tb(16, 16), tg((unsigned)((nmax + 15) / 16), (unsigned)((nmax + 15) / 16), (unsigned)nprob);
-    k_xtx_seg<<<tg, tb, 0, stream>>>(nprob, cs_n, cs_moff, X, Minv);
+    kl(k_xtx_seg, tg, tb, 0, stream)(nprob, cs_n, cs_moff, X, Minv);
     CKL();
     int h_err = 0;
     CK(cudaMemcpyAsync(&h_err, derr, sizeof(int), cudaMemcpyDeviceToHost, stream));
@@ -1369,7 +1502,7 @@ int xdg_hier::build_lp(int p) {
       float* v32 = nullptr;
       TRY(alloc(&v32, V.nnzb * np2));
       TRY(alloc(&W.sc32, V.nnzb));
-      k_make_lp<float><<<(unsigned)((V.nnzb * 32 + 255) / 256), 256, 0, stream>>>(V.nnzb, np2, V.val, v32,
+      kl(k_make_lp<float>, (unsigned)((V.nnzb * 32 + 255) / 256), 256, 0, stream)(V.nnzb, np2, V.val, v32,
                                                                                    W.sc32);
       W.val32 = v32;
     }
@@ -1383,7 +1516,7 @@ int xdg_hier::build_lp(int p) {
       TRY(alloc(&dinv, V.nb * np2));
       W.Dinv = dinv;
       TRY(alloc(&W.dsc, V.nb));
-      k_make_lp<float><<<(unsigned)((V.nb * 32 + 255) / 256), 256, 0, stream>>>(V.nb, np2, V.Dinv, dinv, W.dsc);
+      kl(k_make_lp<float>, (unsigned)((V.nb * 32 + 255) / 256), 256, 0, stream)(V.nb, np2, V.Dinv, dinv, W.dsc);
       TRY(alloc(&raw, V.nb * np2 * el));
       W.R = raw;
       TRY(alloc(&W.rsc, V.nb));
@@ -1401,6 +1534,22 @@ int xdg_hier::build_lp(int p) {
       for (int l = 0; l < nlev; ++l) L[l].spl = (split_mode == 2);
       tuned = true;
     }
+  }
+  if (!sym_tried && sym_mode != 1 && nlev > 1) {
+    sym_tried = true;
+    TRY(build_sym());
+    if (sym_built) {
+      if (sym_mode == 2) sym_on = !L[0].spl;
+      else TRY(tune_sym(p));
+    }
+  }
+  if (nprob == 1 && pair_mode != 1 && !val2) {
+    TRY(build_pair());
+    if (pair_mode == 2) {
+      pair_on = true;
+      sym_pair = sym_built && sym_mode == 2;
+    }
+    if (pair_mode != 2 || sym_mode == 0) TRY(tune_pair());
   }
   TRY(write_fused(p));
   if (fused_lc >= 0 && nprob == 1 && fused_mode != 1) {
@@ -1518,6 +1667,193 @@ int xdg_hier::fused_error() {
     set_err("fused small-level cycle: a grid barrier timed out");
     return XDG_ECUDA;
   }
+  return XDG_OK;
+}
+
+// Level 1 as scaled FP32 pairs (XDG_PREC_F64_PAIR) and the pair copy of the direction
+int xdg_hier::build_pair() {
+  Level& V = L[0];
+  const int64_t np2 = (int64_t)Np * Np;
+  TRY(alloc(&val2, V.nnzb * np2));
+  TRY(alloc(&ea2, V.nnzb));
+  TRY(alloc(&p2, V.nb * Np));
+  TRY(alloc(&ex2, V.nb));
+  kl(k_make_df, (unsigned)std::min<int64_t>((V.nnzb * 32 + 255) / 256, 65535 * 8), 256, 0, stream)(V.nnzb, (int)np2,
+                                                                                                 V.val, val2, ea2);
+  if (sym_built) {
+    TRY(alloc(&sy.uval2, sy.nu * np2));
+    TRY(alloc(&sy.uea, sy.nu));
+    kl(k_gather_blocks_df, (unsigned)((sy.nu * 32 + 255) / 256), 256, 0, stream)(sy.nu, (int)np2, sy.umap, val2, ea2,
+                                                                                 sy.uval2, sy.uea);
+  }
+  CKL();
+  return sync();
+}
+
+// Outer apply: the FP64 product, the pair product and the pair product on the symmetric storage
+// are timed with the direction update that precedes them in an iteration (FP64, or the update
+// that also writes the pair copy). A pair variant is kept when it takes at least 3 % less time
+// than the FP64 one (outer_apply = 0), the symmetric one when it is the faster pair variant
+// (symmetric = 0).
+int xdg_hier::tune_pair() {
+  Level& V = L[0];
+  const int64_t n = V.nb * Np;
+  CK(cudaMemsetAsync(s_z, 0, n * sizeof(double), stream));
+  CK(cudaMemsetAsync(s_p, 0, n * sizeof(double), stream));
+  CK(cudaMemsetAsync(S, 0, sizeof(PcgScal), stream));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float ms[3] = {0.f, 0.f, 1e30f};
+  const int nv = sym_built ? 3 : 2;
+  int rc = XDG_OK;
+  for (int v = 0; v < nv && rc == XDG_OK; ++v) {
+    auto step = [&]() {
+      if (v == 0) {
+        kl(k_pcg_p, vgrid(n), kThreads, 0, stream)(n, S, s_z, s_p);
+        ops.spmv_dot(grid(V.nb), stream, V.nb, V.rp, V.col, V.val, s_p, s_q, partial);
+      } else {
+        ops.pcg_p_df(grid(V.nb), stream, V.nb, S, 0, s_z, s_p, p2, ex2);
+        if (v == 1) ops.spmv_dot_df(grid(V.nb), stream, V.nb, V.rp, V.col, val2, ea2, p2, ex2, s_p, s_q, partial);
+        else
+          ops.spmv_dot_df_sym(grid(V.nb), stream, V.nb, sy.urp, sy.ucol, sy.uval2, sy.uea, sy.L(), p2, ex2, s_p, s_q,
+                              partial);
+      }
+    };
+    for (int k = 0; k < 3; ++k) step();
+    cudaEventRecord(e0, stream);
+    for (int k = 0; k < 10; ++k) step();
+    cudaEventRecord(e1, stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms[v], e0, e1) != cudaSuccess) rc = XDG_ECUDA;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) {
+    set_err("outer apply autotuning: %s", cudaGetErrorString(cudaGetLastError()));
+    return rc;
+  }
+  const float best_pair = std::min(ms[1], ms[2]);
+  if (pair_mode == 0) pair_on = best_pair < 0.97f * ms[0];
+  if (sym_mode == 0) sym_pair = sym_built && ms[2] < ms[1];
+  return XDG_OK;
+}
+
+// Symmetric storage of level 1 (see k_smooth_lp_sym), built when every left block has a right
+// mirror and the two are exact transposes (checked on the device); the FP32 values are gathered
+// from the low-precision copy of precision p, the pair values (when built) in build_pair.
+int xdg_hier::build_sym() {
+  Level& V = L[0];
+  const int64_t nb = V.nb, np2 = (int64_t)Np * Np;
+  std::vector<int64_t> urp(nb + 1, 0), umap, lrp(nb + 1, 0), pos;
+  std::vector<int32_t> ucol, lcol, lblk;
+  umap.reserve((V.nnzb + nb) / 2 + 1);
+  ucol.reserve((V.nnzb + nb) / 2 + 1);
+  for (int64_t i = 0; i < nb; ++i) {
+    for (int64_t z = V.h_rp[i]; z < V.h_rp[i + 1]; ++z)
+      if (V.h_col[z] >= i) {
+        ucol.push_back(V.h_col[z]);
+        umap.push_back(z);
+      }
+    urp[i + 1] = (int64_t)ucol.size();
+  }
+  for (int64_t i = 0; i < nb; ++i) {
+    for (int64_t z = V.h_rp[i]; z < V.h_rp[i + 1] && V.h_col[z] < i; ++z) {
+      const int32_t j = V.h_col[z];
+      auto b0 = ucol.begin() + urp[j], b1 = ucol.begin() + urp[j + 1];
+      auto it = std::lower_bound(b0, b1, (int32_t)i);
+      if (it == b1 || *it != (int32_t)i) return XDG_OK;  // structurally not symmetric: full storage only
+      const int64_t u = it - ucol.begin();
+      lcol.push_back(j);
+      lblk.push_back((int32_t)u);
+      pos.push_back(z);
+      pos.push_back(umap[u]);
+    }
+    lrp[i + 1] = (int64_t)lcol.size();
+  }
+  if ((int64_t)lcol.size() != (int64_t)ucol.size() - nb || (int64_t)ucol.size() > INT32_MAX) return XDG_OK;
+  sy.nu = (int64_t)ucol.size();
+  sy.nl = (int64_t)lcol.size();
+  TRY(alloc(&sy.urp, nb + 1));
+  TRY(alloc(&sy.umap, sy.nu));
+  TRY(alloc(&sy.ucol, sy.nu));
+  TRY(alloc(&sy.lrp, nb + 1));
+  TRY(alloc(&sy.lcol, sy.nl));
+  TRY(alloc(&sy.lblk, sy.nl));
+  int64_t* dpos = nullptr;
+  int* dbad = nullptr;
+  TRY(alloc(&dpos, 2 * sy.nl));
+  TRY(alloc(&dbad, 1));
+  CK(cudaMemcpyAsync(sy.urp, urp.data(), (nb + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(sy.umap, umap.data(), sy.nu * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(sy.ucol, ucol.data(), sy.nu * sizeof(int32_t), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(sy.lrp, lrp.data(), (nb + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+  if (sy.nl) {
+    CK(cudaMemcpyAsync(sy.lcol, lcol.data(), sy.nl * sizeof(int32_t), cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(sy.lblk, lblk.data(), sy.nl * sizeof(int32_t), cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(dpos, pos.data(), 2 * sy.nl * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+  }
+  CK(cudaMemsetAsync(dbad, 0, sizeof(int), stream));
+  if (sy.nl)
+    kl(k_check_mirror, (unsigned)std::min<int64_t>((sy.nl * np2 + 255) / 256, 1 << 20), 256, 0, stream)(sy.nl, Np,
+                                                                                                      dpos, V.val, dbad);
+  int h_bad = 0;
+  CK(cudaMemcpyAsync(&h_bad, dbad, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  TRY(sync());
+  if (h_bad) return XDG_OK;  // not exactly symmetric: full storage only
+  // FP32 values from the low-precision copy (the cycle's operator)
+  int p = has_lp[XDG_PREC_F32] ? XDG_PREC_F32 : XDG_PREC_BF16;
+  const LevelLP& W = LP[p][0];
+  TRY(alloc(&sy.uval, sy.nu * np2));
+  TRY(alloc(&sy.usc, sy.nu));
+  kl(k_gather_blocks, (unsigned)((sy.nu * 32 + 255) / 256), 256, 0, stream)(sy.nu, (int)np2, sy.umap,
+                                                                            (const float*)W.val32, W.sc32, sy.uval,
+                                                                            sy.usc);
+  CKL();
+  TRY(sync());
+  sym_built = true;
+  return XDG_OK;
+}
+
+// The level-1 sweep on the full and on the symmetric storage, timed as in tune_split; the
+// symmetric one is kept when it is at least 3 % faster (the restriction follows the sweep).
+int xdg_hier::tune_sym(int p) {
+  Level& V = L[0];
+  if (V.spl) {
+    sym_on = false;
+    return XDG_OK;
+  }
+  const OpsLP& o = opl[p];
+  LevelLP& W = LP[p][0];
+  const int64_t n = V.nb * Np;
+  CK(cudaMemsetAsync(W.b, 0, n * sizeof(float), stream));
+  CK(cudaMemsetAsync(W.x, 0, n * sizeof(float), stream));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float ms[2] = {0.f, 0.f};
+  int rc = XDG_OK;
+  for (int v = 0; v < 2 && rc == XDG_OK; ++v) {
+    auto sweep = [&]() {
+      if (v == 1)
+        o.smooth_sym(grid_lp(0), stream, V.nb, sy.urp, sy.ucol, sy.uval, sy.usc, sy.L(), (const float*)W.Dinv, W.dsc,
+                     (float)V.omega, V.omr_f, W.b, W.x, W.t, nullptr);
+      else
+        o.smooth(grid_lp(0), false, stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, (float)V.omega,
+                 V.omr_f, W.b, W.x, W.t, nullptr);
+    };
+    for (int k = 0; k < 3; ++k) sweep();
+    cudaEventRecord(e0, stream);
+    for (int k = 0; k < 10; ++k) sweep();
+    cudaEventRecord(e1, stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms[v], e0, e1) != cudaSuccess) rc = XDG_ECUDA;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) {
+    set_err("symmetric storage autotuning: %s", cudaGetErrorString(cudaGetLastError()));
+    return rc;
+  }
+  sym_on = ms[1] < 0.97f * ms[0];
   return XDG_OK;
 }
 
@@ -1691,19 +2027,19 @@ void xdg_hier::batch_iteration(int prec, const BatchCtl* ctl, cudaGraphCondition
   const int flex = prec != XDG_PREC_F64;
   const int64_t nb1 = L[0].nb;
   spmv(0, s_p, nullptr, s_q, 0, act1);
-  k_chunk_dot<1><<<nchunk, kThreads, 0, stream>>>(nchunk, cb, s_p, s_q, nullptr, nullptr, cpart);
-  k_bcg_alpha<<<sgrid(), 256, 0, stream>>>(nprob, cfirst, cpart, B);
-  k_bcg_xr<<<nchunk, kThreads, 0, stream>>>(nchunk, cb, cseg, B.alpha, s_p, s_q, s_x, s_r, cpart);
-  k_bcg_check<<<1, 1024, 0, stream>>>(nprob, cfirst, cpart, B, ctl, 1, cond, 1);
-  k_bcg_rowact<<<vgrid(nb1), kThreads, 0, stream>>>(nb1, Np, nprob, L[0].sdof, B.active, act1);
+  kl(k_chunk_dot<1>, nchunk, kThreads, 0, stream)(nchunk, cb, s_p, s_q, nullptr, nullptr, cpart);
+  kl(k_bcg_alpha, sgrid(), 256, 0, stream)(nprob, cfirst, cpart, B);
+  kl(k_bcg_xr, nchunk, kThreads, 0, stream)(nchunk, cb, cseg, B.alpha, s_p, s_q, s_x, s_r, cpart);
+  kl(k_bcg_check, 1, 1024, 0, stream)(nprob, cfirst, cpart, B, ctl, 1, cond, 1);
+  kl(k_bcg_rowact, vgrid(nb1), kThreads, 0, stream)(nb1, Np, nprob, L[0].sdof, B.active, act1);
   launches += 5;
   cur_act = act1;
   precond(prec, s_r, s_z);
   cur_act = nullptr;
-  if (flex) k_chunk_dot<2><<<nchunk, kThreads, 0, stream>>>(nchunk, cb, s_r, s_z, s_z, s_q, cpart);
-  else k_chunk_dot<1><<<nchunk, kThreads, 0, stream>>>(nchunk, cb, s_r, s_z, nullptr, nullptr, cpart);
-  k_bcg_beta<<<sgrid(), 256, 0, stream>>>(nprob, nchunk, cfirst, cpart, flex, 0, B);
-  k_bcg_p<<<nchunk, kThreads, 0, stream>>>(nchunk, cb, cseg, B.beta, 0, s_z, s_p, B.active);
+  if (flex) kl(k_chunk_dot<2>, nchunk, kThreads, 0, stream)(nchunk, cb, s_r, s_z, s_z, s_q, cpart);
+  else kl(k_chunk_dot<1>, nchunk, kThreads, 0, stream)(nchunk, cb, s_r, s_z, nullptr, nullptr, cpart);
+  kl(k_bcg_beta, sgrid(), 256, 0, stream)(nprob, nchunk, cfirst, cpart, flex, 0, B);
+  kl(k_bcg_p, nchunk, kThreads, 0, stream)(nchunk, cb, cseg, B.beta, 0, s_z, s_p, B.active);
   launches += 3;
 }
 
@@ -1715,10 +2051,10 @@ int xdg_hier::record_batch(int prec, const BatchCtl* ctl, double* res, int gslot
   const int64_t n = L[0].nb * Np;
   const int flex = prec != XDG_PREC_F64;
   const int64_t l0 = launches;
-  k_batch_gather<<<vgrid(n), kThreads, 0, stream>>>(n, nprob, L[0].sdof, ioff, ctl, s_b, s_x);
+  kl(k_batch_gather, vgrid(n), kThreads, 0, stream)(n, nprob, L[0].sdof, ioff, ctl, s_b, s_x);
   spmv(0, s_x, s_b, s_r, 1);
-  k_chunk_dot<2><<<nchunk, kThreads, 0, stream>>>(nchunk, cb, s_r, s_r, s_b, s_b, cpart);
-  k_bcg_start<<<sgrid(), 256, 0, stream>>>(nprob, nchunk, cfirst, cpart, B);
+  kl(k_chunk_dot<2>, nchunk, kThreads, 0, stream)(nchunk, cb, s_r, s_r, s_b, s_b, cpart);
+  kl(k_bcg_start, sgrid(), 256, 0, stream)(nprob, nchunk, cfirst, cpart, B);
   launches += 3;
   cudaStreamCaptureStatus st;
   cudaGraph_t cg = nullptr;
@@ -1731,15 +2067,15 @@ int xdg_hier::record_batch(int prec, const BatchCtl* ctl, double* res, int gslot
   }
   cudaGraphConditionalHandle cond;
   CK(cudaGraphConditionalHandleCreate(&cond, cg, 0, cudaGraphCondAssignDefault));
-  k_bcg_check<<<1, 1024, 0, stream>>>(nprob, cfirst, nullptr, B, ctl, 0, cond, 1);
-  k_bcg_rowact<<<vgrid(L[0].nb), kThreads, 0, stream>>>(L[0].nb, Np, nprob, L[0].sdof, B.active, act1);
+  kl(k_bcg_check, 1, 1024, 0, stream)(nprob, cfirst, nullptr, B, ctl, 0, cond, 1);
+  kl(k_bcg_rowact, vgrid(L[0].nb), kThreads, 0, stream)(L[0].nb, Np, nprob, L[0].sdof, B.active, act1);
   launches += 2;
   cur_act = act1;
   precond(prec, s_r, s_z);
   cur_act = nullptr;
-  k_chunk_dot<1><<<nchunk, kThreads, 0, stream>>>(nchunk, cb, s_r, s_z, nullptr, nullptr, cpart);
-  k_bcg_beta<<<sgrid(), 256, 0, stream>>>(nprob, nchunk, cfirst, cpart, flex, 1, B);
-  k_bcg_p<<<nchunk, kThreads, 0, stream>>>(nchunk, cb, cseg, B.beta, 1, s_z, s_p, B.active);
+  kl(k_chunk_dot<1>, nchunk, kThreads, 0, stream)(nchunk, cb, s_r, s_z, nullptr, nullptr, cpart);
+  kl(k_bcg_beta, sgrid(), 256, 0, stream)(nprob, nchunk, cfirst, cpart, flex, 1, B);
+  kl(k_bcg_p, nchunk, kThreads, 0, stream)(nchunk, cb, cseg, B.beta, 1, s_z, s_p, B.active);
   launches += 3;
   CKL();
   // the loop
@@ -1770,9 +2106,9 @@ int xdg_hier::record_batch(int prec, const BatchCtl* ctl, double* res, int gslot
   }
   // results and scatter
   spmv(0, s_x, s_b, s_r, 1);
-  k_chunk_dot<1><<<nchunk, kThreads, 0, stream>>>(nchunk, cb, s_r, s_r, nullptr, nullptr, cpart);
-  k_bcg_result<<<sgrid(), 256, 0, stream>>>(nprob, cfirst, cpart, gidx, B, res, gslot);
-  k_batch_scatter<<<vgrid(n), kThreads, 0, stream>>>(n, nprob, L[0].sdof, ioff, ctl, s_x);
+  kl(k_chunk_dot<1>, nchunk, kThreads, 0, stream)(nchunk, cb, s_r, s_r, nullptr, nullptr, cpart);
+  kl(k_bcg_result, sgrid(), 256, 0, stream)(nprob, cfirst, cpart, gidx, B, res, gslot);
+  kl(k_batch_scatter, vgrid(n), kThreads, 0, stream)(n, nprob, L[0].sdof, ioff, ctl, s_x);
   launches += 3;
   CKL();
   bnodes_fixed[prec] = launches - l0 - bnodes_body[prec];
@@ -1817,7 +2153,7 @@ int xdg_hier::record_loop(int prec) {
     const int64_t l0 = launches;
     if (prec == XDG_PREC_F64 && !lr.on) pcg_iteration();
     else fcg_iteration(prec);
-    k_cg_loop_check<<<1, 1, 0, stream>>>(S, lctl, cond);
+    kl(k_cg_loop_check, 1, 1, 0, stream)(S, lctl, cond);
     loop_nodes[prec][li] = launches - l0 + 1;
     launches = l0;
     stream = main_stream;
@@ -1866,7 +2202,8 @@ int xdg_hier::solve_dev(const double* b, double* x, const xdg_solve_opts* o, xdg
   dot(n, s_b, s_b, dsc);
   dot(n, s_r, s_r, &S->rr);
   precond_full(prec, s_r, s_z);
-  k_copy<<<vgrid(n), kThreads, 0, stream>>>(n, s_z, s_p);
+  if (use_pair(prec)) ops.pcg_p_df(grid(L[0].nb), stream, L[0].nb, S, 1, s_z, s_p, p2, ex2);
+  else kl(k_copy, vgrid(n), kThreads, 0, stream)(n, s_z, s_p);
   ++launches;
   dot(n, s_r, s_z, &S->rz);
   CKL();
@@ -2146,11 +2483,11 @@ struct xdg_mlp {
     const size_t sm = train_smem();
     CK(cudaFuncSetAttribute(k_mlp_train_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int blocks = std::max(1, std::min((n + 7) / 8, 152 * 2));
-    k_mlp_train_pass<<<blocks, 256, sm, stream>>>(n, ix, d, P, X, uid, Mloc, R, C, T);
+    kl(k_mlp_train_pass, blocks, 256, sm, stream)(n, ix, d, P, X, uid, Mloc, R, C, T);
     dim3 gg((unsigned)((d.total + 255) / 256), (unsigned)nsl);
-    k_mlp_grad_partial<<<gg, 256, 0, stream>>>(n, nsl, ix, d, X, T, partial);
-    k_mlp_grad_final<<<(d.total + 255) / 256, 256, 0, stream>>>(d.total, nsl, partial, grad);
-    k_sum_ordered<<<1, kThreads, 0, stream>>>(n, T.loss, dloss, 0);
+    kl(k_mlp_grad_partial, gg, 256, 0, stream)(n, nsl, ix, d, X, T, partial);
+    kl(k_mlp_grad_final, (d.total + 255) / 256, 256, 0, stream)(d.total, nsl, partial, grad);
+    kl(k_sum_ordered, 1, kThreads, 0, stream)(n, T.loss, dloss, 0);
     CKL();
     return XDG_OK;
   }
@@ -2213,6 +2550,8 @@ int xdg_get_info(xdg_hier_t h, xdg_hier_info* info) {
   for (int l = 0; l < h->nlev && l < 64; ++l)
     if (h->L[l].spl) info->split_mask |= (uint64_t)1 << l;
   info->fused_level = (h->fused_on[1] || h->fused_on[2]) ? h->fused_lc + 1 : 0;
+  info->outer_pair = h->pair_on ? 1 : 0;
+  info->symmetric = (h->sym_built ? 1 : 0) | (h->sym_on && !h->L[0].spl ? 2 : 0) | (h->sym_pair ? 4 : 0);
   return XDG_OK;
 }
 
@@ -2243,6 +2582,16 @@ int xdg_apply(xdg_hier_t h, int level, const double* x, double* y, int prec) {
   }
   if (prec == XDG_PREC_F64) {
     h->spmv(level - 1, x, nullptr, y, 0);
+  } else if (prec == XDG_PREC_F64_PAIR) {
+    if (level != 1 || !h->val2) {
+      set_err("xdg_apply: the FP32-pair operator exists on level 1 only, and only when outer_apply != 1 with "
+              "low_precision set");
+      return XDG_EINVAL;
+    }
+    Level& V = h->L[0];
+    h->ops.split_df(h->grid(V.nb), h->stream, V.nb, x, h->p2, h->ex2);
+    h->ops.spmv_dot_df(h->grid(V.nb), h->stream, V.nb, V.rp, V.col, h->val2, h->ea2, h->p2, h->ex2, x, y, nullptr);
+    h->launches += 2;
   } else {
     if (prec < 0 || prec > 2 || !h->has_lp[prec]) {
       set_err("xdg_apply: precision %d not stored (xdg_hier_opts.low_precision)", prec);
@@ -2253,10 +2602,10 @@ int xdg_apply(xdg_hier_t h, int level, const double* x, double* y, int prec) {
     // vectors rounded to FP32 once (a per-element FP64 -> FP32 conversion inside the product
     // would run on the FP64 pipe); the level's FP32 work vectors r and dz hold x and y
     const int64_t n = V.nb * h->Np;
-    k_d2f<<<h->vgrid(n), kThreads, 0, h->stream>>>(n, x, W.r);
+    kl(k_d2f, h->vgrid(n), kThreads, 0, h->stream)(n, x, W.r, nullptr, 1);
     h->opl[prec].spmv_f(h->grid_lp(level - 1), V.spl, h->stream, V.nb, V.rp, V.col, W.val, W.sc, W.r, nullptr,
                         W.dz, 0);
-    k_f2d<<<h->vgrid(n), kThreads, 0, h->stream>>>(n, W.dz, y);
+    kl(k_f2d, h->vgrid(n), kThreads, 0, h->stream)(n, W.dz, y, nullptr, 1);
     h->launches += 3;
   }
   CKL();
@@ -2662,12 +3011,12 @@ int xdg_mlp_forward(xdg_mlp_t m, int prec, int64_t n, const float* X, float* Y) 
   if (prec == XDG_PREC_F32) {
     const size_t sm = (size_t)m->d.total * sizeof(float);
     CK(cudaFuncSetAttribute(k_mlp_forward<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_mlp_forward<float><<<blocks, 256, sm, m->stream>>>(n, m->d, m->P, X, Y);
+    kl(k_mlp_forward<float>, blocks, 256, sm, m->stream)(n, m->d, m->P, X, Y);
   } else {
-    k_to_bf16<<<(m->d.total + 255) / 256, 256, 0, m->stream>>>(m->d.total, m->P, m->Pb);
+    kl(k_to_bf16, (m->d.total + 255) / 256, 256, 0, m->stream)(m->d.total, m->P, m->Pb);
     const size_t sm = (size_t)m->d.total * sizeof(__nv_bfloat16);
     CK(cudaFuncSetAttribute(k_mlp_forward<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_mlp_forward<__nv_bfloat16><<<blocks, 256, sm, m->stream>>>(n, m->d, m->Pb, X, Y);
+    kl(k_mlp_forward<__nv_bfloat16>, blocks, 256, sm, m->stream)(n, m->d, m->Pb, X, Y);
   }
   CKL();
   return XDG_OK;
@@ -2711,10 +3060,10 @@ int xdg_mlp_train(xdg_mlp_t m, int n, const float* X, const int32_t* uid, const 
     for (int s0 = 0; s0 < n; s0 += B) {
       const int nb = std::min(B, n - s0);
       TRY(m->loss_grad(nb, m->idx + s0, X, uid, Mloc, R, C));
-      k_sum_ordered<<<1, kThreads, 0, m->stream>>>(nb, m->T.loss, m->dloss + 1, 1);
+      kl(k_sum_ordered, 1, kThreads, 0, m->stream)(nb, m->T.loss, m->dloss + 1, 1);
       m->step += 1;
       const float bc1 = 1.f - std::pow(b1, (float)m->step), bc2 = 1.f - std::pow(b2, (float)m->step);
-      k_adam<<<(m->d.total + 255) / 256, 256, 0, m->stream>>>(m->d.total, m->P, m->grad, m->m1, m->m2, o->lr, b1, b2,
+      kl(k_adam, (m->d.total + 255) / 256, 256, 0, m->stream)(m->d.total, m->P, m->grad, m->m1, m->m2, o->lr, b1, b2,
                                                               eps, bc1, bc2);
     }
     CKL();
@@ -2865,7 +3214,7 @@ int xdg_learned_enable(xdg_hier_t h, xdg_mlp_t m, double theta) {
     U.wcap = m->d.total;
   }
   CK(cudaStreamSynchronize(m->stream));
-  k_to_bf16<<<(m->d.total + 255) / 256, 256, 0, h->stream>>>(m->d.total, m->P, U.W);
+  kl(k_to_bf16, (m->d.total + 255) / 256, 256, 0, h->stream)(m->d.total, m->P, U.W);
   CKL();
   CK(cudaStreamSynchronize(h->stream));
   U.d = m->d;
@@ -3021,8 +3370,10 @@ int fma_probe(int iters, double* tflops) {
 
 extern "C" int xdg_kernel_time(xdg_hier_t h, int which, int level, int prec, int reps, double* ms,
                                double* bytes) {
+  const bool pair = prec == XDG_PREC_F64_PAIR;
   if (!h || level < 1 || level > h->nlev || which < 0 || which > 2 || (which > 0 && level >= h->nlev) ||
-      prec < 0 || prec > 2 || (prec != XDG_PREC_F64 && !h->has_lp[prec])) {
+      prec < 0 || prec > 3 || (pair && (which != 0 || level != 1 || !h->val2)) ||
+      (!pair && prec != XDG_PREC_F64 && !h->has_lp[prec])) {
     set_err("xdg_kernel_time: bad kernel %d, level %d or precision %d", which, level, prec);
     return XDG_EINVAL;
   }
@@ -3031,16 +3382,36 @@ extern "C" int xdg_kernel_time(xdg_hier_t h, int which, int level, int prec, int
   const int Np = h->Np;
   const int64_t n = V.nb * Np, np2 = (int64_t)Np * Np;
   cudaStream_t st = h->stream;
-  const bool lp = prec != XDG_PREC_F64;
+  const bool lp = prec != XDG_PREC_F64 && !pair;
   const double sv = lp ? 4.0 : 8.0;                        // vector entries
   const double sa = prec == XDG_PREC_F64 ? 8.0 : 4.0;      // operator read by smooth / restrict
   const double sap = prec == XDG_PREC_BF16 ? 2.0 : sa;     // operator read by apply
   const double sr = prec == XDG_PREC_BF16 ? 2.0 : sa;      // transfer blocks
   const double scal = lp ? 4.0 : 0.0;                      // per-block scales
   const double rows = 8.0 * (V.nb + 1) + 4.0 * V.nnzb;     // row pointer and columns
+  // symmetric storage of level 1: compact row pointer and columns, left-block lists
+  const xdg_hier::SymLevel& sy = h->sy;
+  const double srows = 16.0 * (V.nb + 1) + 4.0 * sy.nu + 8.0 * sy.nl;
+  const bool sym = lp && h->lvl1_sym(l) && which > 0;
   double by = 0.0;
   std::function<void()> launch;
-  if (!lp) {
+  if (pair) {
+    CK(cudaMemsetAsync(V.x, 0, n * sizeof(double), st));
+    h->ops.split_df(h->grid(V.nb), st, V.nb, V.x, h->p2, h->ex2);
+    // pairs (8 bytes) and an exponent per block; the split vector and its exponents; y in FP64
+    if (h->sym_pair) {
+      launch = [&]() {
+        h->ops.spmv_dot_df_sym(h->grid(V.nb), st, V.nb, sy.urp, sy.ucol, sy.uval2, sy.uea, sy.L(), h->p2, h->ex2, V.x,
+                               V.t, nullptr);
+      };
+      by = srows + sy.nu * (np2 * 8.0 + 4.0) + n * 8.0 + V.nb * 4.0 + n * 8.0;
+    } else {
+      launch = [&]() {
+        h->ops.spmv_dot_df(h->grid(V.nb), st, V.nb, V.rp, V.col, h->val2, h->ea2, h->p2, h->ex2, V.x, V.t, nullptr);
+      };
+      by = rows + V.nnzb * (np2 * 8.0 + 4.0) + n * 8.0 + V.nb * 4.0 + n * 8.0;
+    }
+  } else if (!lp) {
     CK(cudaMemsetAsync(V.b, 0, n * sizeof(double), st));
     CK(cudaMemsetAsync(V.x, 0, n * sizeof(double), st));
     if (which == 0) {
@@ -3066,16 +3437,31 @@ extern "C" int xdg_kernel_time(xdg_hier_t h, int which, int level, int prec, int
       };
       by = rows + V.nnzb * (np2 * sap + scal) + 2.0 * n * sv;
     } else if (which == 1) {
-      launch = [&]() {
-        o.smooth(h->grid_lp(l), V.spl, st, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, (float)V.omega,
-                 V.omr_f, W.b, W.x, W.t, nullptr);
-      };
-      by = rows + V.nnzb * (np2 * sa + scal) + V.nb * (np2 * 4.0 + scal) + 3.0 * n * sv;
+      if (sym)
+        launch = [&]() {
+          o.smooth_sym(h->grid_lp(l), st, V.nb, sy.urp, sy.ucol, sy.uval, sy.usc, sy.L(), (const float*)W.Dinv, W.dsc,
+                       (float)V.omega, V.omr_f, W.b, W.x, W.t, nullptr);
+        };
+      else
+        launch = [&]() {
+          o.smooth(h->grid_lp(l), V.spl, st, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, (float)V.omega,
+                   V.omr_f, W.b, W.x, W.t, nullptr);
+        };
+      by = (sym ? srows + sy.nu * (np2 * 4.0 + scal) : rows + V.nnzb * (np2 * sa + scal)) +
+           V.nb * (np2 * 4.0 + scal) + 3.0 * n * sv;
     } else {
-      launch = [&]() {
-        o.resid_rt(h->grid_lp(l), V.spl, st, V.nb, V.rp, V.col, W.val32, W.sc32, W.R, W.rsc, W.b, W.x, W.s, nullptr);
-      };
-      by = rows + V.nnzb * (np2 * sa + scal) + V.nb * (np2 * sr + scal) + 3.0 * n * sv;
+      if (sym)
+        launch = [&]() {
+          o.resid_rt_sym(h->grid_lp(l), st, V.nb, sy.urp, sy.ucol, sy.uval, sy.usc, sy.L(), W.R, W.rsc, W.b, W.x, W.s,
+                         nullptr);
+        };
+      else
+        launch = [&]() {
+          o.resid_rt(h->grid_lp(l), V.spl, st, V.nb, V.rp, V.col, W.val32, W.sc32, W.R, W.rsc, W.b, W.x, W.s,
+                     nullptr);
+        };
+      by = (sym ? srows + sy.nu * (np2 * 4.0 + scal) : rows + V.nnzb * (np2 * sa + scal)) +
+           V.nb * (np2 * sr + scal) + 3.0 * n * sv;
     }
   }
   const int R = reps > 0 ? reps : 20;

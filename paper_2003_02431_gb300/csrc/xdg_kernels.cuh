@@ -17,6 +17,19 @@ namespace xdg {
 
 constexpr int kThreads = 256;
 
+// Programmatic dependent launch (sm_90+): a kernel may be launched before its predecessor in
+// the stream has finished; it then waits at griddepcontrol.wait, which returns once every
+// prerequisite grid has completed and its memory operations are visible. Every kernel of the
+// library waits first, before any global memory access, so reads after writes and writes after
+// reads across consecutive kernels keep their order. It then lets its own dependents launch,
+// so their CTAs are scheduled as soon as SM slots free up instead of after a launch gap. For a
+// kernel launched without the attribute both instructions have no effect.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_entry() {
+  pdl_wait();
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 template <int NP>
 struct Grp {
   static constexpr int GPW = 32 / NP;              // groups per warp
@@ -93,6 +106,7 @@ __global__ void __launch_bounds__(kThreads) k_spmv(int64_t nb, const int64_t* __
                                                   const double* __restrict__ x,
                                                   const double* __restrict__ b,
                                                   double* __restrict__ y, const uint8_t* __restrict__ act) {
+  pdl_entry();
   constexpr int GPW = Grp<NP>::GPW;
   const int lane = threadIdx.x & 31;
   const int g = lane / NP, r = lane - g * NP;
@@ -130,6 +144,7 @@ __global__ void __launch_bounds__(kThreads) k_smooth(int64_t nb, const int64_t* 
                                                     const double* __restrict__ b,
                                                     const double* __restrict__ xi,
                                                     double* __restrict__ xo) {
+  pdl_entry();
   constexpr int GPW = Grp<NP>::GPW;
   const int lane = threadIdx.x & 31;
   const int g = lane / NP, r = lane - g * NP;
@@ -151,6 +166,7 @@ template <int NP>
 __global__ void __launch_bounds__(kThreads) k_bjsolve(int64_t nb, const double* __restrict__ Dinv,
                                                      const double* __restrict__ v,
                                                      double* __restrict__ z) {
+  pdl_entry();
   constexpr int GPW = Grp<NP>::GPW;
   const int lane = threadIdx.x & 31;
   const int g = lane / NP, r = lane - g * NP;
@@ -168,6 +184,7 @@ __global__ void __launch_bounds__(kThreads) k_diagmul(int64_t nb, const int64_t*
                                                      const double* __restrict__ val,
                                                      const double* __restrict__ v,
                                                      double* __restrict__ w) {
+  pdl_entry();
   constexpr int GPW = Grp<NP>::GPW;
   const int lane = threadIdx.x & 31;
   const int g = lane / NP, r = lane - g * NP;
@@ -195,6 +212,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_rt(int64_t nbf, const int64_
                                                       const double* __restrict__ b,
                                                       const double* __restrict__ x,
                                                       double* __restrict__ t) {
+  pdl_entry();
   constexpr int GPW = Grp<NP>::GPW;
   const int lane = threadIdx.x & 31;
   const int g = lane / NP, r = lane - g * NP;
@@ -244,6 +262,7 @@ __global__ void __launch_bounds__(kThreads) k_gather(int64_t nbc, const int64_t*
                                                     const int32_t* __restrict__ ch,
                                                     const double* __restrict__ t,
                                                     double* __restrict__ rc) {
+  pdl_entry();
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nbc * NP;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t C = e / NP;
@@ -261,6 +280,7 @@ __global__ void __launch_bounds__(kThreads) k_gather_smooth0(int64_t nbc, const 
                                                             const double* __restrict__ Dinv, double omega,
                                                             const double* __restrict__ omr,
                                                             double* __restrict__ bc, double* __restrict__ xc) {
+  pdl_entry();
   constexpr int GPW = Grp<NP>::GPW;
   const int lane = threadIdx.x & 31;
   const int g = lane / NP, r = lane - g * NP;
@@ -286,6 +306,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong(int64_t nbf, const int32_t
                                                      const double* __restrict__ R,
                                                      const double* __restrict__ zc,
                                                      const double* xi, double* xo) {
+  pdl_entry();
   constexpr int GPW = Grp<NP>::GPW;
   const int lane = threadIdx.x & 31;
   const int g = lane / NP, r = lane - g * NP;
@@ -318,6 +339,7 @@ __global__ void __launch_bounds__(kThreads) k_galerkin(int64_t nbc, const int64_
                                                       const int64_t* __restrict__ crp,
                                                       const int32_t* __restrict__ ccol,
                                                       double* __restrict__ cval) {
+  pdl_entry();
   constexpr int GPW = Grp<NP>::GPW;
   __shared__ double T[kThreads / 32][GPW][NP * NP];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -379,6 +401,7 @@ __global__ void __launch_bounds__(kThreads) k_galerkin(int64_t nbc, const int64_
 template <int NP>
 __global__ void k_diag_inv(int64_t nb, const int64_t* __restrict__ diag, const double* __restrict__ val,
                            double* __restrict__ Dinv, int* err) {
+  pdl_entry();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nb) return;
   double A[NP * NP];
@@ -445,6 +468,7 @@ __device__ __forceinline__ double block_sum(double v) {
 __global__ void __launch_bounds__(kThreads) k_dot_partial(int64_t n, const double* __restrict__ x,
                                                          const double* __restrict__ y,
                                                          double* __restrict__ partial) {
+  pdl_entry();
   double s = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     s = fma(x[i], y[i], s);
@@ -455,6 +479,7 @@ __global__ void __launch_bounds__(kThreads) k_dot_partial(int64_t n, const doubl
 // out = sum of partial[0..np) in a fixed order
 __global__ void __launch_bounds__(kThreads) k_sum_final(int np, const double* __restrict__ partial,
                                                        double* __restrict__ out) {
+  pdl_entry();
   double s = 0.0;
   for (int i = threadIdx.x; i < np; i += blockDim.x) s += partial[i];
   s = block_sum(s);
@@ -469,6 +494,7 @@ struct PcgScal {
 
 // beta = rz_new / rz; rz = rz_new
 __global__ void k_pcg_beta(PcgScal* S) {
+  pdl_entry();
   double rn = S->rz_new;
   if (!(rn > 0.0) || !isfinite(rn)) {
     S->bad = 1;
@@ -485,7 +511,8 @@ __global__ void __launch_bounds__(kThreads) k_pcg_xr(int64_t n, const PcgScal* _
                                                     const double* __restrict__ p,
                                                     const double* __restrict__ q, double* __restrict__ x,
                                                     double* __restrict__ r, double* __restrict__ partial,
-                                                    float* __restrict__ rf = nullptr) {
+                                                    float* __restrict__ rf) {
+  pdl_entry();
   const double a = S->alpha;
   double s = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -505,6 +532,7 @@ __global__ void __launch_bounds__(kThreads) k_spmv_dot(int64_t nb, const int64_t
                                                       const int32_t* __restrict__ col, const double* __restrict__ val,
                                                       const double* __restrict__ x, double* __restrict__ y,
                                                       double* __restrict__ partial) {
+  pdl_entry();
   constexpr int GPW = Grp<NP>::GPW;
   const int lane = threadIdx.x & 31;
   const int g = lane / NP, r = lane - g * NP;
@@ -534,6 +562,7 @@ __device__ __forceinline__ double sum_partials(int np, const double* __restrict_
 // pq from the partial sums, then alpha = rz / pq (breakdown flagged)
 __global__ void __launch_bounds__(kThreads) k_cg_alpha_final(int np, const double* __restrict__ partial,
                                                             PcgScal* S) {
+  pdl_entry();
   const double pq = sum_partials(np, partial, 1, 0);
   if (threadIdx.x == 0) {
     S->pq = pq;
@@ -549,18 +578,21 @@ __global__ void __launch_bounds__(kThreads) k_cg_alpha_final(int np, const doubl
 // p = z + beta p
 __global__ void __launch_bounds__(kThreads) k_pcg_p(int64_t n, const PcgScal* __restrict__ S,
                                                    const double* __restrict__ z, double* __restrict__ p) {
+  pdl_entry();
   const double be = S->beta;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = fma(be, p[i], z[i]);
 }
 
 __global__ void k_copy(int64_t n, const double* __restrict__ a, double* __restrict__ b) {
+  pdl_entry();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     b[i] = a[i];
 }
 
 // y += a x (a on the host)
 __global__ void k_axpy(int64_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
+  pdl_entry();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = fma(a, x[i], y[i]);
 }

@@ -26,6 +26,7 @@ __device__ __forceinline__ int find_seg(const int64_t* __restrict__ off, int nse
 __global__ void __launch_bounds__(kThreads) k_seg_dot(int nseg, const int64_t* __restrict__ off,
                                                      const double* __restrict__ x, const double* __restrict__ y,
                                                      double* __restrict__ part) {
+  pdl_entry();
   const int s = blockIdx.y, spl = gridDim.x;
   if (s >= nseg) return;
   const int64_t lo = off[s], len = off[s + 1] - lo;
@@ -36,6 +37,7 @@ __global__ void __launch_bounds__(kThreads) k_seg_dot(int nseg, const int64_t* _
   if (threadIdx.x == 0) part[(int64_t)s * spl + blockIdx.x] = acc;
 }
 __global__ void k_seg_sum(int nseg, int spl, const double* __restrict__ part, double* __restrict__ out) {
+  pdl_entry();
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
     double acc = 0.0;
     for (int j = 0; j < spl; ++j) acc += part[(int64_t)s * spl + j];
@@ -46,11 +48,13 @@ __global__ void k_seg_sum(int nseg, int spl, const double* __restrict__ part, do
 // x_i *= a[s(i)] ; y_i += a[s(i)] x_i  (segment-wise scalars; seg = entry -> segment via off)
 __global__ void k_seg_scale(int64_t n, int nseg, const int64_t* __restrict__ off, const double* __restrict__ a,
                             double* __restrict__ x) {
+  pdl_entry();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] *= a[find_seg(off, nseg, i)];
 }
 __global__ void k_seg_axpy(int64_t n, int nseg, const int64_t* __restrict__ off, const double* __restrict__ a,
                            const double* __restrict__ x, double* __restrict__ y) {
+  pdl_entry();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = fma(a[find_seg(off, nseg, i)], x[i], y[i]);
 }
@@ -58,6 +62,7 @@ __global__ void k_seg_axpy(int64_t n, int nseg, const int64_t* __restrict__ off,
 // v_i = ((j+1) * 2654435761 mod 2^32) / 2^32 - 0.5 with j the index of i inside its segment
 // (Knuth's multiplicative hash, restarted at every problem)
 __global__ void k_hash_vector_seg(int64_t n, int nseg, const int64_t* __restrict__ off, double* __restrict__ v) {
+  pdl_entry();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t j = i - __ldg(off + find_seg(off, nseg, i));
     uint32_t h = (uint32_t)((uint64_t)(j + 1) * 2654435761ull);
@@ -71,6 +76,7 @@ __global__ void k_bsr_to_dense_seg(int64_t nb, int np, int nseg, const int64_t* 
                                    const int64_t* __restrict__ moff, const int64_t* __restrict__ rp,
                                    const int32_t* __restrict__ col, const double* __restrict__ val,
                                    double* __restrict__ A) {
+  pdl_entry();
   const int64_t i = blockIdx.x;
   if (i >= nb) return;
   const int s = find_seg(sblk, nseg, i);
@@ -89,6 +95,7 @@ __global__ void k_bsr_to_dense_seg(int64_t nb, int np, int nseg, const int64_t* 
 // right-looking Cholesky of every segment's matrix (one CTA per segment), lower triangle = L
 __global__ void __launch_bounds__(1024) k_dense_chol_seg(int nseg, const int64_t* __restrict__ nn,
                                                         const int64_t* __restrict__ moff, double* A, int* err) {
+  pdl_entry();
   const int s = blockIdx.x;
   if (s >= nseg) return;
   const int64_t n = nn[s];
@@ -124,6 +131,7 @@ __global__ void __launch_bounds__(1024) k_dense_chol_seg(int nseg, const int64_t
 // X_s = L_s^{-1}: column j of segment blockIdx.y (one thread per column)
 __global__ void k_tri_inverse_seg(int nseg, const int64_t* __restrict__ nn, const int64_t* __restrict__ moff,
                                   const double* __restrict__ L, double* __restrict__ X) {
+  pdl_entry();
   const int s = blockIdx.y;
   if (s >= nseg) return;
   const int64_t n = nn[s], j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -141,6 +149,7 @@ __global__ void k_tri_inverse_seg(int nseg, const int64_t* __restrict__ nn, cons
 // Minv_s = X_s^T X_s (16x16 tiles, blockIdx.z = segment)
 __global__ void k_xtx_seg(int nseg, const int64_t* __restrict__ nn, const int64_t* __restrict__ moff,
                           const double* __restrict__ X, double* __restrict__ Minv) {
+  pdl_entry();
   const int s = blockIdx.z;
   if (s >= nseg) return;
   const int64_t n = nn[s];
@@ -192,6 +201,7 @@ __global__ void __launch_bounds__(kThreads) k_gemv_seg(int64_t ntot, int nseg, c
                                                       const int64_t* __restrict__ moff,
                                                       const double* __restrict__ Minv, const VT* __restrict__ r,
                                                       VT* __restrict__ z) {
+  pdl_entry();
   gemv_seg_rows<VT>(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5, ((int64_t)gridDim.x * blockDim.x) >> 5,
                     ntot, nseg, doff, moff, Minv, r, z);
 }
@@ -221,6 +231,7 @@ struct BatchScal {
 __global__ void k_batch_gather(int64_t n, int nseg, const int64_t* __restrict__ sdof,
                                const int64_t* __restrict__ ioff, const BatchCtl* __restrict__ ctl,
                                double* __restrict__ sb, double* __restrict__ sx) {
+  pdl_entry();
   const double* b = ctl->b;
   const double* x = ctl->x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -233,6 +244,7 @@ __global__ void k_batch_gather(int64_t n, int nseg, const int64_t* __restrict__ 
 __global__ void k_batch_scatter(int64_t n, int nseg, const int64_t* __restrict__ sdof,
                                 const int64_t* __restrict__ ioff, const BatchCtl* __restrict__ ctl,
                                 const double* __restrict__ sx) {
+  pdl_entry();
   double* x = ctl->x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int s = find_seg(sdof, nseg, i);
@@ -246,6 +258,7 @@ __global__ void __launch_bounds__(kThreads) k_chunk_dot(int nchunk, const int64_
                                                        const double* __restrict__ x0, const double* __restrict__ y0,
                                                        const double* __restrict__ x1, const double* __restrict__ y1,
                                                        double* __restrict__ part) {
+  pdl_entry();
   const int c = blockIdx.x;
   if (c >= nchunk) return;
   double a0 = 0.0, a1 = 0.0;
@@ -270,6 +283,7 @@ __device__ __forceinline__ double chunk_total(const int* __restrict__ cfirst, co
 // start of a solve: rr, bb from the chunk sums of (r, r), (b, b); every problem active
 __global__ void k_bcg_start(int nseg, int nchunk, const int* __restrict__ cfirst, const double* __restrict__ part,
                             BatchScal S) {
+  pdl_entry();
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
     S.rr[s] = chunk_total(cfirst, part, s);
     S.bb[s] = chunk_total(cfirst, part + nchunk, s);
@@ -282,6 +296,7 @@ __global__ void k_bcg_start(int nseg, int nchunk, const int* __restrict__ cfirst
 
 // pq = (p, q); alpha = rz / pq for active problems (0 for finished ones); counts the step
 __global__ void k_bcg_alpha(int nseg, const int* __restrict__ cfirst, const double* __restrict__ part, BatchScal S) {
+  pdl_entry();
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
     const double pq = chunk_total(cfirst, part, s);
     S.pq[s] = pq;
@@ -306,6 +321,7 @@ __global__ void __launch_bounds__(kThreads) k_bcg_xr(int nchunk, const int64_t* 
                                                     const double* __restrict__ p, const double* __restrict__ q,
                                                     double* __restrict__ x, double* __restrict__ r,
                                                     double* __restrict__ part) {
+  pdl_entry();
   const int c = blockIdx.x;
   if (c >= nchunk) return;
   const double a = alpha[cseg[c]];
@@ -332,6 +348,7 @@ __global__ void __launch_bounds__(1024) k_bcg_check(int nseg, const int* __restr
                                                    const double* __restrict__ part, BatchScal S,
                                                    const BatchCtl* __restrict__ ctl, int count,
                                                    cudaGraphConditionalHandle cond, int use_cond) {
+  pdl_entry();
   __shared__ int cnt;
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
@@ -361,6 +378,7 @@ __global__ void __launch_bounds__(1024) k_bcg_check(int nseg, const int* __restr
 // CG: rz_new / rz;  flexible CG: -zq / pq;  start != 0: beta = 0 (first direction p = z)
 __global__ void k_bcg_beta(int nseg, int nchunk, const int* __restrict__ cfirst, const double* __restrict__ part,
                            int flexible, int start, BatchScal S) {
+  pdl_entry();
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
     const double rzn = chunk_total(cfirst, part, s);
     double be = 0.0;
@@ -386,6 +404,7 @@ __global__ void k_bcg_beta(int nseg, int nchunk, const int* __restrict__ cfirst,
 __global__ void k_bcg_p(int nchunk, const int64_t* __restrict__ cb, const int* __restrict__ cseg,
                         const double* __restrict__ beta, int start, const double* __restrict__ z,
                         double* __restrict__ p, const int* __restrict__ active) {
+  pdl_entry();
   const int c = blockIdx.x;
   if (c >= nchunk || !active[cseg[c]]) return;
   const double be = beta[cseg[c]];
@@ -395,6 +414,7 @@ __global__ void k_bcg_p(int nchunk, const int64_t* __restrict__ cb, const int* _
 // act[i] = 1 while the problem of level-1 block i is running (sdof: DOF offsets of the problems)
 __global__ void k_bcg_rowact(int64_t nb, int np, int nseg, const int64_t* __restrict__ sdof,
                              const int* __restrict__ active, uint8_t* __restrict__ act) {
+  pdl_entry();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += (int64_t)gridDim.x * blockDim.x)
     act[i] = (uint8_t)(active[find_seg(sdof, nseg, i * np)] != 0);
 }
@@ -406,6 +426,7 @@ struct LoopCtl {
   int maxit, it;
 };
 __global__ void k_cg_loop_check(const PcgScal* __restrict__ S, LoopCtl* c, cudaGraphConditionalHandle cond) {
+  pdl_entry();
   const int it = c->it + 1;
   c->it = it;
   const double rr = S->rr;
@@ -418,6 +439,7 @@ __global__ void k_cg_loop_check(const PcgScal* __restrict__ S, LoopCtl* c, cudaG
 // g = gidx[s], the problem's index in the caller's list; res[gslot] = loop iterations
 __global__ void k_bcg_result(int nseg, const int* __restrict__ cfirst, const double* __restrict__ part,
                              const int* __restrict__ gidx, BatchScal S, double* __restrict__ res, int gslot) {
+  pdl_entry();
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
     const double rr = chunk_total(cfirst, part, s);
     const double bb = S.bb[s];

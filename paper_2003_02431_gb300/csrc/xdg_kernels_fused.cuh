@@ -89,6 +89,7 @@ __device__ __forceinline__ void fused_smooth(const FusedLevel& V, int64_t warp, 
 // pre0: the first sweep on the fused part's first level has been done (x holds it)
 template <int NP, class TS>
 __global__ void __launch_bounds__(kThreads) k_fused_vcycle(const FusedCycle* __restrict__ F, int pre0) {
+  pdl_entry();
   const int64_t warp = grid_warp(), nw = grid_warps();
   const int64_t tid = grid_thread(), nt = grid_threads();
   const int n = F->n, nu = F->nu;

@@ -160,6 +160,7 @@ __global__ void __launch_bounds__(kThreads, XDG_LP_MINB) k_spmv_lp(int64_t nb, c
                                                      const TS* __restrict__ val, const float* __restrict__ sc,
                                                      const VT* __restrict__ x, const VT* __restrict__ b,
                                                      VT* __restrict__ y) {
+  pdl_entry();
   constexpr int GPW = Grp<NP>::GPW;
   const int lane = threadIdx.x & 31;
   const int g = lane / NP, r = lane - g * NP;
@@ -248,6 +249,7 @@ __global__ void __launch_bounds__(kThreads, XDG_LP_MINB) k_smooth_lp(int64_t nb,
                                                        const float* __restrict__ b,
                                                        const float* __restrict__ xi, float* __restrict__ xo,
                                                        const uint8_t* __restrict__ act) {
+  pdl_entry();
   smooth_lp_rows<NP, TS, ZERO, SPL>(grid_warp(), grid_warps(), nb, rp, col, val, sc, Dinv, dsc, omega, omr, b, xi,
                                     xo, act);
 }
@@ -308,7 +310,164 @@ __global__ void __launch_bounds__(kThreads, XDG_LP_MINB) k_resid_rt_lp(int64_t n
                                                          const TR* __restrict__ R, const float* __restrict__ rsc,
                                                          const float* __restrict__ b, const float* __restrict__ x,
                                                          float* __restrict__ t, const uint8_t* __restrict__ act) {
+  pdl_entry();
   resid_rt_lp_rows<NP, TA, TR, RESID, SPL>(grid_warp(), grid_warps(), nbf, rp, col, val, sc, R, rsc, b, x, t, act);
+}
+
+// ------------------------------------------------------------------------------------------
+// Level 1 with symmetric storage. M = M^T (the SIP operator is symmetric, sec. 4) is kept as its
+// diagonal and right-of-diagonal blocks only, in a compact BSR (urp, ucol, uval, usc: ascending
+// columns, the diagonal block first in each row); a block left of the diagonal, (i, j) with
+// j < i, is read as the transpose of its mirror (j, i) (SymL: per row i the columns j in
+// ascending order and the mirror blocks' indices in the compact storage). A row's sum runs over
+// its left blocks, then its diagonal and right blocks: ascending columns with the same values,
+// scales and operation order as the full storage, so the results are bitwise those of the
+// full-storage kernels. Mirror blocks belong to rows at most about one mesh plane apart, all of
+// which are in flight together: the second read is an L2 hit and HBM streams about half the
+// operator.
+struct SymL {
+  const int64_t* lrp;
+  const int32_t* lcol;
+  const int32_t* lblk;
+};
+
+// sum over the blocks of row i (lane r): left blocks transposed, then the stored ones
+template <int NP>
+__device__ __forceinline__ float row_dot_sym(int64_t i, int r, const int64_t* __restrict__ urp,
+                                             const int32_t* __restrict__ ucol, const float* __restrict__ uval,
+                                             const float* __restrict__ usc, SymL L, const float* __restrict__ x) {
+  constexpr int CH = Chunk<NP>::F32;
+  float acc = 0.0f;
+  const int64_t l0 = __ldg(L.lrp + i), l1 = __ldg(L.lrp + i + 1);
+  for (int64_t z = l0; z < l1; z += CH) {
+    int32_t cc[CH], bb[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      cc[u] = (z + u < l1) ? __ldg(L.lcol + z + u) : -1;
+      bb[u] = (z + u < l1) ? __ldg(L.lblk + z + u) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      if (cc[u] < 0) continue;
+      const float* B = uval + (int64_t)bb[u] * (NP * NP) + r;  // column r of the mirror block
+      float a[NP], xv[NP];
+#pragma unroll
+      for (int c = 0; c < NP; ++c) a[c] = __ldg(B + c * NP);
+      ldvec<NP, float, false>(x + (int64_t)cc[u] * NP, xv);
+      float sv = 0.0f;
+#pragma unroll
+      for (int c = 0; c < NP; ++c) sv = fmaf(a[c], xv[c], sv);
+      acc = fmaf(__ldg(usc + bb[u]), sv, acc);
+    }
+  }
+  const int64_t z0 = __ldg(urp + i), z1 = __ldg(urp + i + 1);
+  for (int64_t z = z0; z < z1; z += CH) {
+    int32_t cc[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) cc[u] = (z + u < z1) ? __ldg(ucol + z + u) : -1;
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      if (cc[u] < 0) continue;
+      float a[NP], xv[NP];
+      ldrow_f<NP, float>(uval + (z + u) * (NP * NP) + r * NP, a);
+      ldvec<NP, float, false>(x + (int64_t)cc[u] * NP, xv);
+      float sv = 0.0f;
+#pragma unroll
+      for (int c = 0; c < NP; ++c) sv = fmaf(a[c], xv[c], sv);
+      acc = fmaf(__ldg(usc + z + u), sv, acc);
+    }
+  }
+  return acc;
+}
+
+// the block-Jacobi sweep of smooth_lp_rows (one row per group, nonzero guess) on the symmetric
+// storage
+// resident CTAs per SM requested for the symmetric-storage row kernels (their two loops need
+// more registers than the full-storage ones; without the cap the restriction drops to 2 CTAs)
+#ifndef XDG_SYM_MINB
+#define XDG_SYM_MINB 3
+#endif
+template <int NP>
+__global__ void __launch_bounds__(kThreads, XDG_SYM_MINB) k_smooth_lp_sym(
+    int64_t nb, const int64_t* __restrict__ urp, const int32_t* __restrict__ ucol, const float* __restrict__ uval,
+    const float* __restrict__ usc, SymL L, const float* __restrict__ Dinv, const float* __restrict__ dsc, float omega,
+    const float* __restrict__ omr, const float* __restrict__ b, const float* __restrict__ xi, float* __restrict__ xo,
+    const uint8_t* __restrict__ act) {
+  pdl_entry();
+  constexpr int GPW = Grp<NP>::GPW;
+  const int lane = threadIdx.x & 31;
+  const int g = lane / NP, r = lane - g * NP;
+  if (g >= GPW) return;
+  const unsigned mask = group_mask(g, NP);
+  const int64_t warp = grid_warp(), nw = grid_warps();
+  for (int64_t i = warp * GPW + g; i < nb; i += nw * GPW) {
+    if (act && !act[i]) continue;
+    float res = b[i * NP + r];
+    res -= row_dot_sym<NP>(i, r, urp, ucol, uval, usc, L, xi);
+    float z = block_gemv_lp<NP, float>(Dinv + i * (NP * NP), __ldg(dsc + i), r, g * NP, mask, res);
+    const float om = omr ? __ldg(omr + i) : omega;
+    xo[i * NP + r] = fmaf(om, z, xi[i * NP + r]);
+  }
+}
+
+// restriction phase 1 of resid_rt_lp_rows (one row per group) on the symmetric storage
+template <int NP, class TR>
+__global__ void __launch_bounds__(kThreads, XDG_SYM_MINB) k_resid_rt_lp_sym(
+    int64_t nbf, const int64_t* __restrict__ urp, const int32_t* __restrict__ ucol, const float* __restrict__ uval,
+    const float* __restrict__ usc, SymL L, const TR* __restrict__ R, const float* __restrict__ rsc,
+    const float* __restrict__ b, const float* __restrict__ x, float* __restrict__ t, const uint8_t* __restrict__ act) {
+  pdl_entry();
+  constexpr int GPW = Grp<NP>::GPW;
+  const int lane = threadIdx.x & 31;
+  const int g = lane / NP, r = lane - g * NP;
+  if (g >= GPW) return;
+  const unsigned mask = group_mask(g, NP);
+  const int base = g * NP;
+  const int64_t warp = grid_warp(), nw = grid_warps();
+  for (int64_t f = warp * GPW + g; f < nbf; f += nw * GPW) {
+    if (act && !act[f]) continue;
+    const TR* Rf = R + f * (NP * NP);
+    float rc[NP];
+    if (XDG_PREFETCH_EPI) {
+#pragma unroll
+      for (int m = 0; m < NP; ++m) rc[m] = to_f<TR>(Rf[m * NP + r]);
+    }
+    float res = b[f * NP + r];
+    res -= row_dot_sym<NP>(f, r, urp, ucol, uval, usc, L, x);
+    float s = 0.0f;
+#pragma unroll
+    for (int m = 0; m < NP; ++m)
+      s = fmaf(XDG_PREFETCH_EPI ? rc[m] : to_f<TR>(Rf[m * NP + r]), __shfl_sync(mask, res, base + m), s);
+    t[f * NP + r] = __ldg(rsc + f) * s;
+  }
+}
+
+// the compact storage's values gathered from the full copy (umap: full index of each block)
+__global__ void k_gather_blocks(int64_t nblk, int np2, const int64_t* __restrict__ umap, const float* __restrict__ v,
+                                const float* __restrict__ sc, float* __restrict__ uv, float* __restrict__ usc) {
+  pdl_entry();
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t z = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; z < nblk; z += nw) {
+    const int64_t zf = __ldg(umap + z);
+    for (int k = lane; k < np2; k += 32) uv[z * np2 + k] = v[zf * np2 + k];
+    if (lane == 0) usc[z] = sc[zf];
+  }
+}
+
+// flag (*bad = 1) any pair of mirror blocks (i, j), (j, i) of the FP64 operator that are not
+// exact transposes of each other (pos: full index of every left block and of its mirror)
+__global__ void k_check_mirror(int64_t npair, int np, const int64_t* __restrict__ pos, const double* __restrict__ val,
+                               int* __restrict__ bad) {
+  pdl_entry();
+  const int64_t np2 = (int64_t)np * np;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < npair * np2; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = e / np2;
+    const int rc = (int)(e - k * np2);
+    const int rr = rc / np, cc = rc - rr * np;
+    const int64_t zl = __ldg(pos + 2 * k), zu = __ldg(pos + 2 * k + 1);
+    if (val[zl * np2 + rr * np + cc] != val[zu * np2 + cc * np + rr]) atomicOr(bad, 1);
+  }
 }
 
 // restriction phase 2 in FP32 (children in ascending order)
@@ -327,6 +486,7 @@ template <int NP>
 __global__ void __launch_bounds__(kThreads) k_gather_lp(int64_t nbc, const int64_t* __restrict__ cptr,
                                                        const int32_t* __restrict__ ch,
                                                        const float* __restrict__ t, float* __restrict__ rc) {
+  pdl_entry();
   gather_lp_elems<NP>(grid_thread(), grid_threads(), nbc, cptr, ch, t, rc);
 }
 
@@ -359,6 +519,7 @@ __global__ void __launch_bounds__(kThreads) k_gather_smooth0_lp(int64_t nbc, con
                                                                const float* __restrict__ dsc, float omega,
                                                                const float* __restrict__ omr,
                                                                float* __restrict__ bc, float* __restrict__ xc) {
+  pdl_entry();
   gather_smooth0_lp_rows<NP>(grid_warp(), grid_warps(), nbc, cptr, ch, t, Dinv, dsc, omega, omr, bc, xc);
 }
 
@@ -389,6 +550,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong_lp(int64_t nbf, const int3
                                                         const TS* __restrict__ R, const float* __restrict__ rsc,
                                                         const float* __restrict__ zc, const float* xi, float* xo,
                                                         const uint8_t* __restrict__ act) {
+  pdl_entry();
   prolong_lp_rows<NP, TS>(grid_warp(), grid_warps(), nbf, agg, R, rsc, zc, xi, xo, act);
 }
 
@@ -404,6 +566,7 @@ __device__ __forceinline__ __nv_bfloat16 store_lp<__nv_bfloat16>(double v) { ret
 template <class TS>
 __global__ void k_make_lp(int64_t nblk, int np2, const double* __restrict__ src, TS* __restrict__ dst,
                           float* __restrict__ scale) {
+  pdl_entry();
   const int lane = threadIdx.x & 31;
   const int64_t blk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (blk >= nblk) return;
@@ -420,23 +583,27 @@ __global__ void k_make_lp(int64_t nblk, int np2, const double* __restrict__ src,
 
 // act (optional): entries of rows i = e / np with act[i] == 0 are skipped
 __global__ void k_d2f(int64_t n, const double* __restrict__ a, float* __restrict__ b,
-                      const uint8_t* __restrict__ act = nullptr, int np = 1) {
+                      const uint8_t* __restrict__ act, int np) {
+  pdl_entry();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     if (!act || act[i / np]) b[i] = (float)a[i];
 }
 
 __global__ void k_f2d(int64_t n, const float* __restrict__ a, double* __restrict__ b,
-                      const uint8_t* __restrict__ act = nullptr, int np = 1) {
+                      const uint8_t* __restrict__ act, int np) {
+  pdl_entry();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     if (!act || act[i / np]) b[i] = (double)a[i];
 }
 
 __global__ void k_axpy_f(int64_t n, float a, const float* __restrict__ x, float* __restrict__ y) {
+  pdl_entry();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = fmaf(a, x[i], y[i]);
 }
 
 __global__ void k_copy_f(int64_t n, const float* __restrict__ a, float* __restrict__ b) {
+  pdl_entry();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     b[i] = a[i];
 }
@@ -447,6 +614,7 @@ __global__ void k_copy_f(int64_t n, const float* __restrict__ a, float* __restri
 __global__ void __launch_bounds__(kThreads) k_fcg_tail(int64_t n, const float* __restrict__ zf,
                                                       const double* __restrict__ r, const double* __restrict__ q,
                                                       double* __restrict__ z, double* __restrict__ partial) {
+  pdl_entry();
   double a = 0.0, c = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double zi = (double)zf[i];
@@ -464,6 +632,7 @@ __global__ void __launch_bounds__(kThreads) k_fcg_tail(int64_t n, const float* _
 
 // rz, zq from the partial sums, then the flexible-CG beta = -zq / pq
 __global__ void __launch_bounds__(kThreads) k_fcg_beta_final(int np, const double* __restrict__ partial, PcgScal* S) {
+  pdl_entry();
   const double rz = sum_partials(np, partial, 2, 0);
   const double zq = sum_partials(np, partial, 2, 1);
   if (threadIdx.x == 0) {
@@ -480,6 +649,7 @@ __global__ void __launch_bounds__(kThreads) k_fcg_beta_final(int np, const doubl
 }
 
 __global__ void k_fcg_beta(PcgScal* S) {
+  pdl_entry();
   double pq = S->pq, zq = S->zq;
   if (!(pq > 0.0) || !isfinite(zq)) {
     S->bad = 1;

@@ -116,6 +116,7 @@ __device__ void stage_params(W* sp, const W* __restrict__ P, int total) {
 template <class W>
 __global__ void __launch_bounds__(256) k_mlp_forward(int64_t n, MlpDims d, const W* __restrict__ P,
                                                     const float* __restrict__ X, float* __restrict__ Y) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   W* sp = reinterpret_cast<W*>(smem_raw);
   stage_params(sp, P, d.total);
@@ -146,6 +147,7 @@ __global__ void __launch_bounds__(256) k_mlp_train_pass(int n, const int32_t* __
                                                        const float* __restrict__ Mloc,
                                                        const float* __restrict__ R, const float* __restrict__ C,
                                                        MlpTrainBuf T) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sp = reinterpret_cast<float*>(smem_raw);
   float* w4t = sp + d.total;            // W4^T [n_out][64]
@@ -232,6 +234,7 @@ __global__ void __launch_bounds__(256) k_mlp_train_pass(int n, const int32_t* __
 __global__ void __launch_bounds__(256) k_mlp_grad_partial(int n, int nsl, const int32_t* __restrict__ idx, MlpDims d,
                                                          const float* __restrict__ X, MlpTrainBuf T,
                                                          float* __restrict__ partial) {
+  pdl_entry();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   const int sl = blockIdx.y;
   if (p >= d.total) return;
@@ -267,6 +270,7 @@ __global__ void __launch_bounds__(256) k_mlp_grad_partial(int n, int nsl, const 
 }
 
 __global__ void k_mlp_grad_final(int total, int nsl, const float* __restrict__ partial, float* __restrict__ grad) {
+  pdl_entry();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= total) return;
   float acc = 0.f;
@@ -277,6 +281,7 @@ __global__ void k_mlp_grad_final(int total, int nsl, const float* __restrict__ p
 // Adam (Kingma & Ba) with bias correction; t = step number (1-based)
 __global__ void k_adam(int total, float* __restrict__ P, const float* __restrict__ G, float* __restrict__ m1,
                        float* __restrict__ m2, float lr, float b1, float b2, float eps, float bc1, float bc2) {
+  pdl_entry();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= total) return;
   const float g = G[p];
@@ -288,6 +293,7 @@ __global__ void k_adam(int total, float* __restrict__ P, const float* __restrict
 }
 
 __global__ void k_to_bf16(int total, const float* __restrict__ P, __nv_bfloat16* __restrict__ Q) {
+  pdl_entry();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < total) Q[p] = __float2bfloat16_rn(P[p]);
 }
@@ -296,6 +302,7 @@ __global__ void k_to_bf16(int total, const float* __restrict__ P, __nv_bfloat16*
 // sum in a fixed tree)
 __global__ void __launch_bounds__(kThreads) k_sum_ordered(int n, const double* __restrict__ v, double* __restrict__ out,
                                                          int accumulate) {
+  pdl_entry();
   const int per = (n + blockDim.x - 1) / blockDim.x;
   const int i0 = threadIdx.x * per, i1 = min(n, i0 + per);
   double acc = 0.0;
@@ -350,6 +357,7 @@ __global__ void __launch_bounds__(32) k_unit_factor(int U, const int64_t* __rest
                                                     const double* __restrict__ val, double* __restrict__ Linv,
                                                     double* __restrict__ Hm, float* __restrict__ Mloc,
                                                     double* __restrict__ Hinv, int* err) {
+  pdl_entry();
   constexpr int m = 2 * NP, ld = m + 1;
   __shared__ double A[m * ld];
   __shared__ double W[m * ld];
@@ -421,6 +429,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_rows(int64_t nr, const int32
                                                         const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                                         const double* __restrict__ val, const double* __restrict__ x,
                                                         const double* __restrict__ b, double* __restrict__ y) {
+  pdl_entry();
   constexpr int GPW = Grp<NP>::GPW;
   const int lane = threadIdx.x & 31;
   const int g = lane / NP, r = lane - g * NP;
@@ -484,6 +493,7 @@ __global__ void __launch_bounds__(256) k_unit_samples(int U, int n_geo, const in
                                                      const double* __restrict__ Linv, const double* __restrict__ Minv,
                                                      float* __restrict__ X, float* __restrict__ R,
                                                      float* __restrict__ C) {
+  pdl_entry();
   constexpr int m = 2 * NP;
   const int lane = threadIdx.x & 31;
   const int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -540,6 +550,7 @@ __global__ void __launch_bounds__(128) k_unit_apply(int U, MlpDims d, int n_geo,
                                                    const double* __restrict__ Linv, const float* __restrict__ Hf,
                                                    double* __restrict__ delta, int* __restrict__ keep,
                                                    double* __restrict__ E) {
+  pdl_entry();
   constexpr int m = 2 * NP;
   constexpr int T = (m + kUnitLanes - 1) / kUnitLanes;  // residual / output entries per lane
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -672,6 +683,7 @@ template <int NP>
 __global__ void k_unit_gather(int nt, const int32_t* __restrict__ tblk, const int64_t* __restrict__ tptr,
                               const int32_t* __restrict__ tlist, const double* __restrict__ delta, double theta,
                               double* __restrict__ z) {
+  pdl_entry();
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)nt * NP) return;
   const int i = (int)(e / NP), c = (int)(e - (int64_t)i * NP);

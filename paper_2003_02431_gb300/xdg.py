@@ -24,7 +24,7 @@ _SRCS = [os.path.join(_HERE, "csrc", "xdg.cu"), os.path.join(_HERE, "csrc", "xdg
          os.path.join(_ROOT, "include", "xdg.h")]
 
 XDG_OK, XDG_EINVAL, XDG_ECUDA, XDG_ENOMEM, XDG_ENOTCONV, XDG_EBREAKDOWN, XDG_ETIMEOUT = range(7)
-XDG_PREC_F64, XDG_PREC_F32, XDG_PREC_BF16 = 0, 1, 2
+XDG_PREC_F64, XDG_PREC_F32, XDG_PREC_BF16, XDG_PREC_F64_PAIR = 0, 1, 2, 3
 MAX_LEVELS = 24
 
 NVCC_FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
@@ -64,7 +64,7 @@ class Problem(C.Structure):
 class HierOpts(C.Structure):
     _fields_ = [("omega", C.c_double), ("lanczos_steps", C.c_int), ("nu", C.c_int),
                 ("gamma", C.c_int), ("low_precision", C.c_int), ("w_levels", C.c_int), ("split_rows", C.c_int),
-                ("fused_coarse", C.c_int)]
+                ("fused_coarse", C.c_int), ("outer_apply", C.c_int), ("symmetric", C.c_int)]
 
 
 class SolveOpts(C.Structure):
@@ -82,7 +82,7 @@ class HierInfo(C.Structure):
                 ("nnzb", C.c_int64 * MAX_LEVELS), ("omega", C.c_double * MAX_LEVELS),
                 ("lambda_max", C.c_double * MAX_LEVELS), ("coarse_n", C.c_int64),
                 ("device_bytes", C.c_size_t), ("setup_ms", C.c_double * 3), ("split_mask", C.c_uint64),
-                ("fused_level", C.c_int)]
+                ("fused_level", C.c_int), ("outer_pair", C.c_int), ("symmetric", C.c_int)]
 
 
 class TrainOpts(C.Structure):
@@ -247,7 +247,8 @@ class Hierarchy:
     unless one is given); every call is ordered with torch's current stream by event waits."""
 
     def __init__(self, Np, nb, row_ptr, col, val, aggs, Rs, omega=0.0, lanczos_steps=12, nu=1,
-                 gamma=1, low_precision=0, stream=None, w_levels=0, split_rows=0, fused_coarse=0):
+                 gamma=1, low_precision=0, stream=None, w_levels=0, split_rows=0, fused_coarse=0, outer_apply=0,
+                 symmetric=0):
         L = load()
         torch = _torch()
         if stream is None:
@@ -256,7 +257,8 @@ class Hierarchy:
         self._keep = []
 
         prob = _marshal(Np, nb, row_ptr, col, val, aggs, Rs, self._keep)
-        opts = HierOpts(omega, lanczos_steps, nu, gamma, low_precision, w_levels, split_rows, fused_coarse)
+        opts = HierOpts(omega, lanczos_steps, nu, gamma, low_precision, w_levels, split_rows, fused_coarse,
+                        outer_apply, symmetric)
         h = C.c_void_p()
         st = C.c_void_p(stream.cuda_stream)
         self._h = None
@@ -281,7 +283,9 @@ class Hierarchy:
         return {"Np": i.Np, "n_levels": nl, "nb": list(i.nb[:nl]), "nnzb": list(i.nnzb[:nl]),
                 "omega": list(i.omega[:nl]), "lambda_max": list(i.lambda_max[:nl]),
                 "coarse_n": i.coarse_n, "device_bytes": i.device_bytes, "setup_ms": list(i.setup_ms),
-                "split": [bool((i.split_mask >> l) & 1) for l in range(nl)], "fused_level": i.fused_level}
+                "split": [bool((i.split_mask >> l) & 1) for l in range(nl)], "fused_level": i.fused_level,
+                "outer_pair": bool(i.outer_pair), "symmetric_built": bool(i.symmetric & 1),
+                "symmetric_cycle": bool(i.symmetric & 2), "symmetric_pair": bool(i.symmetric & 4)}
 
     def export_level(self, level: int):
         _torch().cuda.synchronize(self.stream.device)
@@ -441,7 +445,7 @@ class Batch:
     Vectors are the problems' level-1 vectors concatenated in list order (`offsets`)."""
 
     def __init__(self, problems, omega=0.0, lanczos_steps=12, nu=1, gamma=1, low_precision=0,
-                 w_levels=0, stream=None, split_rows=0):
+                 w_levels=0, stream=None, split_rows=0, symmetric=0):
         L = load()
         torch = _torch()
         if stream is None:
@@ -451,7 +455,7 @@ class Batch:
         arr = (Problem * len(problems))()
         for i, p in enumerate(problems):
             arr[i] = _marshal(p.Np, p.nb, p.row_ptr, p.col, p.val, p.agg, p.R, keep)
-        opts = HierOpts(omega, lanczos_steps, nu, gamma, low_precision, w_levels, split_rows, 1)
+        opts = HierOpts(omega, lanczos_steps, nu, gamma, low_precision, w_levels, split_rows, 1, 1, symmetric)
         h = C.c_void_p()
         self._h = None
         with _Ordered(self):

@@ -1,0 +1,118 @@
+"""Symmetric storage of level 1 (diagonal and right blocks; a left block read as the transpose
+of its mirror): it holds the same values and the kernels sum in the same order, so every
+result equals the full-storage result bit for bit -- the FP32 and BF16-transfer cycles, the
+pair product, mixed-precision solves and a batched solve. The full-storage path is itself
+compared with the oracle in the parity tests; here the symmetric solve is also checked against
+the oracle's FP64 solution (1e-8 relative L2). An operator that is not exactly symmetric gets
+no symmetric storage (and stays correct).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+import xdg_problem as xp  # noqa: E402
+from paper_2003_02431_gb300 import xdg  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+CASES = {
+    "2d_k2": xp.config_2d_16(max_coarse_dof=60),
+    "2d_k4": xp.Config(D=2, N=13, k=4, c=(0.5, 0.5, 0), R=0.27, muA=1, muB=10, max_coarse_dof=120),
+    "3d_k2": xp.Config(D=3, N=14, k=2, c=(0.5, 0.5, 0.5), R=0.31, muA=1, muB=1000, max_coarse_dof=300),
+    "3d_k3": xp.Config(D=3, N=7, k=3, c=(0.48, 0.51, 0.5), R=0.3, muA=1, muB=1000, max_coarse_dof=200),
+}
+# every timing-based choice pinned, so that the two hierarchies differ only in the storage
+PINNED = dict(gamma=2, w_levels=2, low_precision=3, split_rows=1, fused_coarse=1, outer_apply=2)
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).reshape(-1)).to(DEV)
+
+
+def _n(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def pair(request):
+    P = xp.Problem(CASES[request.param])
+    S = xdg.Hierarchy.from_problem(P, symmetric=2, **PINNED)
+    F = xdg.Hierarchy.from_problem(P, symmetric=1, **PINNED)
+    yield request.param, P, S, F
+    S.destroy()
+    F.destroy()
+
+
+def test_storage_flags(pair):
+    name, P, S, F = pair
+    si, fi = S.info(), F.info()
+    assert si["symmetric_built"] and si["symmetric_cycle"] and si["symmetric_pair"], si
+    assert not (fi["symmetric_built"] or fi["symmetric_cycle"] or fi["symmetric_pair"])
+
+
+def test_cycles_and_pair_product_bitwise(pair):
+    name, P, S, F = pair
+    rng = np.random.default_rng(11)
+    b = _t(rng.standard_normal(P.dof))
+    for prec in (xdg.XDG_PREC_F32, xdg.XDG_PREC_BF16):
+        z1, z2 = torch.empty_like(b), torch.empty_like(b)
+        S.cycle(prec, b, z1)
+        F.cycle(prec, b, z2)
+        assert np.array_equal(_n(z1), _n(z2)), (name, prec)
+    y1, y2 = torch.empty_like(b), torch.empty_like(b)
+    S.apply(1, b, y1, prec=xdg.XDG_PREC_F64_PAIR)
+    F.apply(1, b, y2, prec=xdg.XDG_PREC_F64_PAIR)
+    assert np.array_equal(_n(y1), _n(y2)), name
+
+
+def test_solves_bitwise_and_against_oracle(pair):
+    name, P, S, F = pair
+    b = _t(P.b)
+    for prec in (xdg.XDG_PREC_F32, xdg.XDG_PREC_BF16):
+        x1, x2 = torch.zeros_like(b), torch.zeros_like(b)
+        i1 = S.solve(b, x1, tol=1e-10, maxit=300, precision=prec)
+        i2 = F.solve(b, x2, tol=1e-10, maxit=300, precision=prec)
+        assert i1["iterations"] == i2["iterations"]
+        assert np.array_equal(_n(x1), _n(x2)), (name, prec)
+    O = oracle.Hierarchy(P, gamma=2)
+    xref, _, rr, _ = O.pcg(P.b, tol=1e-13, maxit=500)
+    O.close()
+    assert rr < 1e-12
+    assert np.linalg.norm(_n(x1) - xref.reshape(-1)) / np.linalg.norm(xref) < 1e-8
+
+
+def test_not_exactly_symmetric_operator_keeps_full_storage():
+    P = xp.Problem(CASES["3d_k2"])
+    rp, col = P.row_ptr, P.col
+    # perturb one right block in the last bit, not its mirror
+    i = P.nb[0] // 2
+    z = next(z for z in range(rp[i], rp[i + 1]) if col[z] > i)
+    val = P.val.copy()
+    val[z, 0, 1] = np.nextafter(val[z, 0, 1], np.inf)
+    H = xdg.Hierarchy(P.Np, P.nb, rp, col, val, P.agg, P.R, symmetric=2, **PINNED)
+    inf = H.info()
+    assert not (inf["symmetric_built"] or inf["symmetric_cycle"] or inf["symmetric_pair"])
+    x = np.random.default_rng(2).standard_normal(P.dof)
+    y = torch.empty(P.dof, dtype=torch.float64, device=DEV)
+    H.apply(1, _t(x), y)
+    ref = oracle.bsr_spmv(rp, col, val, x).reshape(-1)
+    assert np.linalg.norm(_n(y) - ref) / np.linalg.norm(ref) < 1e-12
+    H.destroy()
+
+
+def test_batched_solve_bitwise():
+    probs = [xp.Problem(c) for c in xp.batch_configs(4, seed=9, N_range=(10, 18), ks=(2, 3), max_levels=4)]
+    bb = _t(np.concatenate([p.b.reshape(-1) for p in probs]))
+    out = []
+    for sym in (2, 1):
+        bt = xdg.Batch(probs, gamma=2, low_precision=1, split_rows=1, symmetric=sym)
+        x = torch.zeros_like(bb)
+        res = bt.solve(bb, x, tol=1e-10, maxit=300, precision=xdg.XDG_PREC_F32)
+        out.append((_n(x), [r["iterations"] for r in res["problems"]]))
+        bt.destroy()
+    assert out[0][1] == out[1][1]
+    assert np.array_equal(out[0][0], out[1][0])
