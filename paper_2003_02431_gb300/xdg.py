@@ -20,8 +20,8 @@ _ROOT = os.path.dirname(_HERE)
 LIB_PATH = os.path.join(_HERE, "libxdg.so")
 _SRCS = [os.path.join(_HERE, "csrc", "xdg.cu"), os.path.join(_HERE, "csrc", "xdg_kernels.cuh"),
          os.path.join(_HERE, "csrc", "xdg_kernels_lp.cuh"), os.path.join(_HERE, "csrc", "xdg_kernels_batch.cuh"),
-         os.path.join(_HERE, "csrc", "xdg_kernels_mlp.cuh"),
-         os.path.join(_ROOT, "include", "xdg.h")]
+         os.path.join(_HERE, "csrc", "xdg_kernels_mlp.cuh"), os.path.join(_HERE, "csrc", "xdg_kernels_fused.cuh"),
+         os.path.join(_HERE, "csrc", "xdg_kernels_df.cuh"), os.path.join(_ROOT, "include", "xdg.h")]
 
 XDG_OK, XDG_EINVAL, XDG_ECUDA, XDG_ENOMEM, XDG_ENOTCONV, XDG_EBREAKDOWN, XDG_ETIMEOUT = range(7)
 XDG_PREC_F64, XDG_PREC_F32, XDG_PREC_BF16, XDG_PREC_F64_PAIR = 0, 1, 2, 3
