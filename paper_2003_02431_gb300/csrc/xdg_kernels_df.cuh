@@ -46,6 +46,19 @@ __device__ __forceinline__ float2 split_df(double v) {
   return make_float2(h, l);
 }
 
+// Sum of a row's block results (hi + lo) 2^k: each block scaled by 2^k and added in FP64 (four
+// FP64-pipe operations a block). A double-float sum relative to the row's first block, converted
+// to FP64 once per row, measured slower (more registers; the FP64 pipe is 8 % busy here).
+struct RowAcc {
+  double acc = 0.0;
+  __device__ __forceinline__ void add(float hi, float lo, int k) {
+    const double sc = pow2_d(k);
+    acc = fma((double)hi, sc, acc);
+    acc = fma((double)lo, sc, acc);
+  }
+  __device__ __forceinline__ double result() const { return acc; }
+};
+
 // NP consecutive float2 -> registers (16-byte loads when the row is 16-byte aligned)
 template <int NP>
 __device__ __forceinline__ void ldrow_df(const float2* __restrict__ p, float2 (&v)[NP]) {
@@ -92,7 +105,7 @@ __device__ __forceinline__ double row_dot_df(int64_t z0, int64_t z1, int r, cons
                                              const float2* __restrict__ val2, const int* __restrict__ ea,
                                              const float2* __restrict__ x2, const int* __restrict__ ex) {
   constexpr int CH = Chunk<NP>::F64;
-  double acc = 0.0;
+  RowAcc acc;
   for (int64_t z = z0; z < z1; z += CH) {
     int32_t cc[CH];
     int ee[CH];
@@ -110,12 +123,10 @@ __device__ __forceinline__ double row_dot_df(int64_t z0, int64_t z1, int r, cons
       const int k = ee[u] + __ldg(ex + cc[u]);
       float hi, lo;
       block_dot_df<NP>(a, xv, hi, lo);
-      const double sc = pow2_d(k);
-      acc = fma((double)hi, sc, acc);
-      acc = fma((double)lo, sc, acc);
+      acc.add(hi, lo, k);
     }
   }
-  return acc;
+  return acc.result();
 }
 
 // y = M x from the double-float operator and vector (rows spread as in k_spmv_dot) and
@@ -156,7 +167,7 @@ __device__ __forceinline__ double row_dot_df_sym(int64_t i, int r, const int64_t
                                                  const int* __restrict__ uea, SymL L, const float2* __restrict__ x2,
                                                  const int* __restrict__ ex) {
   constexpr int CH = Chunk<NP>::F64;
-  double acc = 0.0;
+  RowAcc acc;
   const int64_t l0 = __ldg(L.lrp + i), l1 = __ldg(L.lrp + i + 1);
   for (int64_t z = l0; z < l1; z += CH) {
     int32_t cc[CH], bb[CH];
@@ -176,9 +187,7 @@ __device__ __forceinline__ double row_dot_df_sym(int64_t i, int r, const int64_t
       const int k = __ldg(uea + bb[u]) + __ldg(ex + cc[u]);
       float hi, lo;
       block_dot_df<NP>(a, xv, hi, lo);
-      const double sc = pow2_d(k);
-      acc = fma((double)hi, sc, acc);
-      acc = fma((double)lo, sc, acc);
+      acc.add(hi, lo, k);
     }
   }
   const int64_t z0 = __ldg(urp + i), z1 = __ldg(urp + i + 1);
@@ -199,12 +208,10 @@ __device__ __forceinline__ double row_dot_df_sym(int64_t i, int r, const int64_t
       const int k = ee[u] + __ldg(ex + cc[u]);
       float hi, lo;
       block_dot_df<NP>(a, xv, hi, lo);
-      const double sc = pow2_d(k);
-      acc = fma((double)hi, sc, acc);
-      acc = fma((double)lo, sc, acc);
+      acc.add(hi, lo, k);
     }
   }
-  return acc;
+  return acc.result();
 }
 
 template <int NP>

@@ -385,7 +385,7 @@ __device__ __forceinline__ float row_dot_sym(int64_t i, int r, const int64_t* __
 // resident CTAs per SM requested for the symmetric-storage row kernels (their two loops need
 // more registers than the full-storage ones; without the cap the restriction drops to 2 CTAs)
 #ifndef XDG_SYM_MINB
-#define XDG_SYM_MINB 3
+#define XDG_SYM_MINB 4
 #endif
 template <int NP>
 __global__ void __launch_bounds__(kThreads, XDG_SYM_MINB) k_smooth_lp_sym(

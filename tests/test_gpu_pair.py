@@ -7,8 +7,8 @@ Error bound per output entry i, from the arithmetic (u = 2^-24, the FP32 unit ro
     error e: at most 6 u^2 per product
   * TwoSum keeps the running sum's errors exactly; their FP32 sum over the 2 Np values of one
     block adds at most sum_k u (4 k u) T <= 2 Np^2 u^2 T (T: the block's sum |a||x|)
-  * the blocks' results are scaled by powers of two (exact) and summed in FP64: at most
-    (nnz per row) 2^-53 of the row's sum |a||x|
+  * the blocks' results (hi + lo) are scaled by powers of two (exact) and summed in FP64: at
+    most 2 nnz_row 2^-53 of the row's sum |a||x|
 so |y_pair - y|_i <= ((9 + 2 Np^2) u^2 + 64 * 2^-53) (|M||x|)_i, with the oracle's own FP64
 rounding (at most (Np nnz_row) 2^-53, inside the last term's slack for these sizes) beside it.
 The test asserts that bound, the 1e-12 norm-wise bound of the FP64 apply test, the range
