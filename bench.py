@@ -96,20 +96,25 @@ class ClockSampler:
 
 SIZE = 64  # cells per direction (--size; the benchmark workload is 64)
 
+# level-1 kernels timed by the bench: (full storage, symmetric storage) kernel names
 KERNEL_NAMES = {
-    "resid_rt_f32": "k_resid_rt_lp<10,float,float,1,0>: level-1 FP32 residual and R^T (restriction phase 1)",
-    "smooth_f32": "k_smooth_lp<10,float,0,0>: level-1 FP32 block-Jacobi sweep",
-    "apply_f32": "k_spmv_lp<10,float,float,0>: level-1 FP32 operator apply",
-    "apply_f64": "k_spmv<10,0>: level-1 FP64 operator apply (FP64 path)",
-    "apply_pair": "k_spmv_dot_df<10>: level-1 FP64-accurate apply from FP32 pairs (outer flexible CG)",
+    "resid_rt_f32": ("k_resid_rt_lp<10,float,float,1,0>", "k_resid_rt_lp_sym<10,float>",
+                     "level-1 FP32 residual and R^T (restriction phase 1)"),
+    "smooth_f32": ("k_smooth_lp<10,float,0,0>", "k_smooth_lp_sym<10>", "level-1 FP32 block-Jacobi sweep"),
+    "apply_f32": ("k_spmv_lp<10,float,float,0>", None, "level-1 FP32 operator apply"),
+    "apply_f64": ("k_spmv<10,0>", None, "level-1 FP64 operator apply (the FP64 path's CG)"),
+    "apply_pair": ("k_spmv_dot_df<10>", "k_spmv_dot_df_sym<10>",
+                   "level-1 FP64-accurate apply from FP32 pairs (the mixed solve's flexible CG)"),
 }
-# the kernel with the largest share of the mixed solve's device time, and the largest HBM-bound
-# one (launch list in profiles/launch_list_mixed_solve_64cube.md)
-DOMINANT = "apply_f64"
+# the largest kernel of the mixed solve's device time (launch list in
+# profiles/launch_list_mixed_solve_64cube.md), the largest kernel of the cycle, and the FP64
+# path's apply (ALU-bound)
+DOMINANT = "apply_pair"
 DOMINANT_HBM = "resid_rt_f32"
-# DRAM bytes (read + write) of one level-1 launch at 64^3, from one ncu capture of the current
-# kernels (profiles/level1_kernels_dram_64cube.md)
-NCU_TRAFFIC = {"apply_f64": 1568570112, "resid_rt_f32": 898302720, "smooth_f32": 897740032}
+DOMINANT_FP64 = "apply_f64"
+# DRAM bytes (read + write) of one launch at 64^3, from one ncu capture of the current kernels
+# (profiles/level1_kernels_dram_64cube.md), by kernel name
+NCU_TRAFFIC = {"k_spmv<10,0>": 1568570112}
 # FP64 ALU peak from unit counts and clocks: 152 SMs x 2070 MHz x 4 FP64 flop per SM and clock
 # (2 FMA), the rate of GB300's nominal 1.25 TFLOP/s FP64
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
@@ -467,12 +472,18 @@ def main():
         if key == "apply_pair" and args.outer_apply == 1:
             continue  # no pair copy
         ms, by = H.kernel_time(which, 1, prec, reps=20)
-        kernels[key] = {"kernel": KERNEL_NAMES[key], "ms": ms, "bytes": by, "achieved_gbs": by / (ms / 1e3) / 1e9,
-                        "frac_hbm": by / (ms / 1e3) / 1e9 / hbm}
+        full, symk, what = KERNEL_NAMES[key]
+        use_sym = symk is not None and (hinfo["symmetric_pair"] if key == "apply_pair" else hinfo["symmetric_cycle"])
+        name = symk if use_sym else full
+        kernels[key] = {"kernel": "%s: %s" % (name, what), "name": name, "ms": ms, "bytes": by,
+                        "achieved_gbs": by / (ms / 1e3) / 1e9, "frac_hbm": by / (ms / 1e3) / 1e9 / hbm,
+                        "storage": "symmetric (diagonal and right blocks)" if use_sym else "full"}
     flops_apply = 2.0 * nnzb * Np * Np
     ach64 = flops_apply / (kernels["apply_f64"]["ms"] / 1e3) / 1e12
     kernels["apply_f64"].update({"bound": "alu", "tflops": ach64, "frac_fp64_peak": ach64 / fp64_peak})
-    dom, domh = kernels[DOMINANT], kernels[DOMINANT_HBM]
+    # the headline's largest kernel: the pair apply when the solve uses it, else the FP64 apply
+    dom_key = DOMINANT if (hinfo["outer_pair"] and DOMINANT in kernels) else DOMINANT_FP64
+    dom, domh, d64 = kernels[dom_key], kernels[DOMINANT_HBM], kernels[DOMINANT_FP64]
 
     # end to end through the host-buffer entry point (pinned host memory)
     bh = torch.from_numpy(P.b.reshape(-1).copy()).pin_memory().numpy()
@@ -509,10 +520,13 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "MDOF/s", "n_gpus": world, "steps": args.steps,
             "warmup": warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64 outer / f32 cycle", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 outer (apply: f32 pairs) / f32 cycle" if hinfo["outer_pair"] else "f64 outer / f32 cycle",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD, "dof": n, "blocks": nb, "nnz_blocks": nnzb, "Np": Np,
                        "levels": hinfo["nb"], "cycle": "W(1,1) on the 2 finest levels, V below; block Jacobi",
-                       "outer": "flexible CG, FP64 apply/residual/update", "tol": TOL, "iterations": iters,
+                       "outer": "flexible CG, FP64 residual/update/inner products; apply %s" % (
+                           "from FP32 pairs (FP64-accurate, double-float)" if hinfo["outer_pair"] else "in FP64"),
+                       "tol": TOL, "iterations": iters,
                        "parallelism": "replicas" if world > 1 else "single",
                        "split_rows_levels": hinfo["split"],
                        "outer_apply_pair": hinfo["outer_pair"],
@@ -530,16 +544,25 @@ def main():
             "vcycle_mdofs": {"f64": n / cyc_ms[0] / 1e3, "f32": n / cyc_ms[1] / 1e3, "bf16": n / cyc_ms[2] / 1e3},
             "vcycle_ms": cyc_ms,
             "setup_s": setup_s, "setup_ms_phases": hinfo["setup_ms"],
-            "roofline": {"bound": "alu", "kernel": dom["kernel"], "achieved": ach64, "peak": FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": ach64 / FP64_PEAK_TFLOPS,
-                         "peak_kind": "FP64 unit counts x clock (152 SMs x 2.07 GHz x 4 flop); the library's "
-                                      "FMA probe reaches %.3f TFLOP/s of it" % fp64_peak,
-                         "flops": flops_apply, "bytes": dom["bytes"], "ms": dom["ms"],
-                         "traffic": NCU_TRAFFIC.get(DOMINANT) if SIZE == 64 else None},
+            "roofline": (
+                {"bound": "hbm", "kernel": dom["kernel"], "achieved": dom["achieved_gbs"], "peak": hbm,
+                 "unit": "GB/s", "frac": dom["achieved_gbs"] / hbm, "peak_kind": hbm_kind, "bytes": dom["bytes"],
+                 "ms": dom["ms"], "traffic": NCU_TRAFFIC.get(dom["name"]) if SIZE == 64 else None}
+                if dom_key != DOMINANT_FP64 else
+                {"bound": "alu", "kernel": dom["kernel"], "achieved": ach64, "peak": FP64_PEAK_TFLOPS,
+                 "unit": "TFLOP/s", "frac": ach64 / FP64_PEAK_TFLOPS, "flops": flops_apply, "bytes": dom["bytes"],
+                 "ms": dom["ms"], "traffic": NCU_TRAFFIC.get(dom["name"]) if SIZE == 64 else None,
+                 "peak_kind": "FP64 unit counts x clock (152 SMs x 2.07 GHz x 4 flop)"}),
+            "roofline_fp64": {"bound": "alu", "kernel": d64["kernel"], "achieved": ach64, "peak": FP64_PEAK_TFLOPS,
+                              "unit": "TFLOP/s", "frac": ach64 / FP64_PEAK_TFLOPS,
+                              "peak_kind": "FP64 unit counts x clock (152 SMs x 2.07 GHz x 4 flop); the library's "
+                                           "FMA probe reaches %.3f TFLOP/s of it" % fp64_peak,
+                              "flops": flops_apply, "bytes": d64["bytes"], "ms": d64["ms"],
+                              "traffic": NCU_TRAFFIC.get(d64["name"]) if SIZE == 64 else None},
             "roofline_hbm": {"bound": "hbm", "kernel": domh["kernel"], "achieved": domh["achieved_gbs"], "peak": hbm,
                              "unit": "GB/s", "frac": domh["achieved_gbs"] / hbm, "peak_kind": hbm_kind,
                              "bytes": domh["bytes"], "ms": domh["ms"],
-                             "traffic": NCU_TRAFFIC.get(DOMINANT_HBM) if SIZE == 64 else None},
+                             "traffic": NCU_TRAFFIC.get(domh["name"]) if SIZE == 64 else None},
             "kernels_level1": kernels,
             "fp64_fma_probe_tflops": fp64_peak,
             "batched": batched,

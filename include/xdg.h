@@ -120,8 +120,7 @@ typedef struct {
                          only; batches launch every step) */
   int outer_apply;    /* operator apply q = M p of the flexible CG around a low-precision cycle:
                          0 = the FP32-pair product (XDG_PREC_F64_PAIR) if it measures faster at
-                         creation, 1 = FP64, 2 = FP32 pairs (single problems; batches and the
-                         FP64 solve use FP64) */
+                         creation, 1 = FP64, 2 = FP32 pairs (the FP64 solve uses FP64) */
   int symmetric;      /* level 1 also in symmetric storage (diagonal and right blocks; a left
                          block read as the transpose of its mirror, bitwise the same results,
                          about half the operator streamed from HBM), used by the low-precision

@@ -153,11 +153,11 @@ struct Ops {
                   double*, double*);
   // FP32-pair (double-float) product and the direction update writing the pair copy
   int (*spmv_dot_df)(int grid, cudaStream_t, int64_t, const int64_t*, const int32_t*, const float2*, const int*,
-                     const float2*, const int*, const double*, double*, double*);
+                     const float2*, const int*, const double*, double*, double*, const uint8_t*);
   void (*pcg_p_df)(int grid, cudaStream_t, int64_t, const PcgScal*, int, const double*, double*, float2*, int*);
   void (*split_df)(int grid, cudaStream_t, int64_t, const double*, float2*, int*);
   int (*spmv_dot_df_sym)(int grid, cudaStream_t, int64_t, const int64_t*, const int32_t*, const float2*, const int*,
-                         SymL, const float2*, const int*, const double*, double*, double*);
+                         SymL, const float2*, const int*, const double*, double*, double*, const uint8_t*);
   int gpw;
 };
 
@@ -217,9 +217,9 @@ struct OpsT {
   }
   static int spmv_dot_df(int grid, cudaStream_t s, int64_t nb, const int64_t* rp, const int32_t* col,
                          const float2* v2, const int* ea, const float2* x2, const int* ex, const double* x, double* y,
-                         double* partial) {
+                         double* partial, const uint8_t* act) {
     const int g = std::min(fit_grid((const void*)&k_spmv_dot_df<NP>, grid), kPartials);
-    kl(k_spmv_dot_df<NP>, g, kThreads, 0, s)(nb, rp, col, v2, ea, x2, ex, x, y, partial);
+    kl(k_spmv_dot_df<NP>, g, kThreads, 0, s)(nb, rp, col, v2, ea, x2, ex, x, y, partial, act);
     return g;
   }
   static void pcg_p_df(int grid, cudaStream_t s, int64_t nb, const PcgScal* S, int first, const double* z, double* p,
@@ -231,9 +231,9 @@ struct OpsT {
   }
   static int spmv_dot_df_sym(int grid, cudaStream_t s, int64_t nb, const int64_t* urp, const int32_t* ucol,
                              const float2* uv2, const int* uea, SymL Ls, const float2* x2, const int* ex,
-                             const double* x, double* y, double* partial) {
+                             const double* x, double* y, double* partial, const uint8_t* act) {
     const int g = std::min(fit_grid((const void*)&k_spmv_dot_df_sym<NP>, grid), kPartials);
-    kl(k_spmv_dot_df_sym<NP>, g, kThreads, 0, s)(nb, urp, ucol, uv2, uea, Ls, x2, ex, x, y, partial);
+    kl(k_spmv_dot_df_sym<NP>, g, kThreads, 0, s)(nb, urp, ucol, uv2, uea, Ls, x2, ex, x, y, partial, act);
     return g;
   }
   static Ops make() {
@@ -755,8 +755,9 @@ struct xdg_hier {
     Level& V = L[0];
     const int g = (pair && sym_pair)
                       ? ops.spmv_dot_df_sym(grid(V.nb), stream, V.nb, sy.urp, sy.ucol, sy.uval2, sy.uea, sy.L(), p2,
-                                            ex2, s_p, s_q, partial)
-                  : pair ? ops.spmv_dot_df(grid(V.nb), stream, V.nb, V.rp, V.col, val2, ea2, p2, ex2, s_p, s_q, partial)
+                                            ex2, s_p, s_q, partial, nullptr)
+                  : pair ? ops.spmv_dot_df(grid(V.nb), stream, V.nb, V.rp, V.col, val2, ea2, p2, ex2, s_p, s_q, partial,
+                                           nullptr)
                          : ops.spmv_dot(grid(V.nb), stream, V.nb, V.rp, V.col, V.val, s_p, s_q, partial);
     kl(k_cg_alpha_final, 1, kThreads, 0, stream)(g, partial, S);
     launches += 2;
@@ -1543,7 +1544,7 @@ int xdg_hier::build_lp(int p) {
       else TRY(tune_sym(p));
     }
   }
-  if (nprob == 1 && pair_mode != 1 && !val2) {
+  if (pair_mode != 1 && !val2) {
     TRY(build_pair());
     if (pair_mode == 2) {
       pair_on = true;
@@ -1714,10 +1715,11 @@ int xdg_hier::tune_pair() {
         ops.spmv_dot(grid(V.nb), stream, V.nb, V.rp, V.col, V.val, s_p, s_q, partial);
       } else {
         ops.pcg_p_df(grid(V.nb), stream, V.nb, S, 0, s_z, s_p, p2, ex2);
-        if (v == 1) ops.spmv_dot_df(grid(V.nb), stream, V.nb, V.rp, V.col, val2, ea2, p2, ex2, s_p, s_q, partial);
+        if (v == 1)
+          ops.spmv_dot_df(grid(V.nb), stream, V.nb, V.rp, V.col, val2, ea2, p2, ex2, s_p, s_q, partial, nullptr);
         else
           ops.spmv_dot_df_sym(grid(V.nb), stream, V.nb, sy.urp, sy.ucol, sy.uval2, sy.uea, sy.L(), p2, ex2, s_p, s_q,
-                              partial);
+                              partial, nullptr);
       }
     };
     for (int k = 0; k < 3; ++k) step();
@@ -2026,7 +2028,17 @@ int xdg_hier::build_batch(int n, const xdg_problem* probs, const xdg_hier_opts* 
 void xdg_hier::batch_iteration(int prec, const BatchCtl* ctl, cudaGraphConditionalHandle cond) {
   const int flex = prec != XDG_PREC_F64;
   const int64_t nb1 = L[0].nb;
-  spmv(0, s_p, nullptr, s_q, 0, act1);
+  if (use_pair(prec)) {  // q = M p from FP32 pairs: split p first (all rows; the product skips finished ones)
+    ops.split_df(grid(nb1), stream, nb1, s_p, p2, ex2);
+    if (sym_pair)
+      ops.spmv_dot_df_sym(grid(nb1), stream, nb1, sy.urp, sy.ucol, sy.uval2, sy.uea, sy.L(), p2, ex2, s_p, s_q,
+                          nullptr, act1);
+    else
+      ops.spmv_dot_df(grid(nb1), stream, nb1, L[0].rp, L[0].col, val2, ea2, p2, ex2, s_p, s_q, nullptr, act1);
+    ++launches;
+  } else {
+    spmv(0, s_p, nullptr, s_q, 0, act1);
+  }
   kl(k_chunk_dot<1>, nchunk, kThreads, 0, stream)(nchunk, cb, s_p, s_q, nullptr, nullptr, cpart);
   kl(k_bcg_alpha, sgrid(), 256, 0, stream)(nprob, cfirst, cpart, B);
   kl(k_bcg_xr, nchunk, kThreads, 0, stream)(nchunk, cb, cseg, B.alpha, s_p, s_q, s_x, s_r, cpart);
@@ -2590,7 +2602,8 @@ int xdg_apply(xdg_hier_t h, int level, const double* x, double* y, int prec) {
     }
     Level& V = h->L[0];
     h->ops.split_df(h->grid(V.nb), h->stream, V.nb, x, h->p2, h->ex2);
-    h->ops.spmv_dot_df(h->grid(V.nb), h->stream, V.nb, V.rp, V.col, h->val2, h->ea2, h->p2, h->ex2, x, y, nullptr);
+    h->ops.spmv_dot_df(h->grid(V.nb), h->stream, V.nb, V.rp, V.col, h->val2, h->ea2, h->p2, h->ex2, x, y, nullptr,
+                       nullptr);
     h->launches += 2;
   } else {
     if (prec < 0 || prec > 2 || !h->has_lp[prec]) {
@@ -3402,12 +3415,13 @@ extern "C" int xdg_kernel_time(xdg_hier_t h, int which, int level, int prec, int
     if (h->sym_pair) {
       launch = [&]() {
         h->ops.spmv_dot_df_sym(h->grid(V.nb), st, V.nb, sy.urp, sy.ucol, sy.uval2, sy.uea, sy.L(), h->p2, h->ex2, V.x,
-                               V.t, nullptr);
+                               V.t, nullptr, nullptr);
       };
       by = srows + sy.nu * (np2 * 8.0 + 4.0) + n * 8.0 + V.nb * 4.0 + n * 8.0;
     } else {
       launch = [&]() {
-        h->ops.spmv_dot_df(h->grid(V.nb), st, V.nb, V.rp, V.col, h->val2, h->ea2, h->p2, h->ex2, V.x, V.t, nullptr);
+        h->ops.spmv_dot_df(h->grid(V.nb), st, V.nb, V.rp, V.col, h->val2, h->ea2, h->p2, h->ex2, V.x, V.t, nullptr,
+                           nullptr);
       };
       by = rows + V.nnzb * (np2 * 8.0 + 4.0) + n * 8.0 + V.nb * 4.0 + n * 8.0;
     }

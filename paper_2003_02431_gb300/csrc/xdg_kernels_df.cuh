@@ -46,6 +46,14 @@ __device__ __forceinline__ float2 split_df(double v) {
   return make_float2(h, l);
 }
 
+// blocks of a row whose loads are issued together, and resident CTAs per SM requested
+#ifndef XDG_CH_PAIR
+#define XDG_CH_PAIR 4
+#endif
+#ifndef XDG_PAIR_MINB
+#define XDG_PAIR_MINB 4
+#endif
+
 // Sum of a row's block results (hi + lo) 2^k: each block scaled by 2^k and added in FP64 (four
 // FP64-pipe operations a block). A double-float sum relative to the row's first block, converted
 // to FP64 once per row, measured slower (more registers; the FP64 pipe is 8 % busy here).
@@ -104,7 +112,7 @@ template <int NP>
 __device__ __forceinline__ double row_dot_df(int64_t z0, int64_t z1, int r, const int32_t* __restrict__ col,
                                              const float2* __restrict__ val2, const int* __restrict__ ea,
                                              const float2* __restrict__ x2, const int* __restrict__ ex) {
-  constexpr int CH = Chunk<NP>::F64;
+  constexpr int CH = NP <= 10 ? XDG_CH_PAIR : 1;
   RowAcc acc;
   for (int64_t z = z0; z < z1; z += CH) {
     int32_t cc[CH];
@@ -132,12 +140,12 @@ __device__ __forceinline__ double row_dot_df(int64_t z0, int64_t z1, int r, cons
 // y = M x from the double-float operator and vector (rows spread as in k_spmv_dot) and
 // partial[blockIdx.x] = this CTA's part of x . y (x in FP64)
 template <int NP>
-__global__ void __launch_bounds__(kThreads) k_spmv_dot_df(int64_t nb, const int64_t* __restrict__ rp,
+__global__ void __launch_bounds__(kThreads, XDG_PAIR_MINB) k_spmv_dot_df(int64_t nb, const int64_t* __restrict__ rp,
                                                          const int32_t* __restrict__ col,
                                                          const float2* __restrict__ val2, const int* __restrict__ ea,
                                                          const float2* __restrict__ x2, const int* __restrict__ ex,
                                                          const double* __restrict__ x, double* __restrict__ y,
-                                                         double* __restrict__ partial) {
+                                                         double* __restrict__ partial, const uint8_t* __restrict__ act) {
   pdl_entry();
   constexpr int GPW = Grp<NP>::GPW;
   const int lane = threadIdx.x & 31;
@@ -147,6 +155,7 @@ __global__ void __launch_bounds__(kThreads) k_spmv_dot_df(int64_t nb, const int6
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = warp * GPW + g; i < nb; i += nw * GPW) {
+      if (act && !act[i]) continue;  // rows of finished problems of a batch
       const double acc = row_dot_df<NP>(__ldg(rp + i), __ldg(rp + i + 1), r, col, val2, ea, x2, ex);
       if (y) y[i * NP + r] = acc;
       if (partial) d = fma(x[i * NP + r], acc, d);
@@ -166,7 +175,7 @@ __device__ __forceinline__ double row_dot_df_sym(int64_t i, int r, const int64_t
                                                  const int32_t* __restrict__ ucol, const float2* __restrict__ uval2,
                                                  const int* __restrict__ uea, SymL L, const float2* __restrict__ x2,
                                                  const int* __restrict__ ex) {
-  constexpr int CH = Chunk<NP>::F64;
+  constexpr int CH = NP <= 10 ? XDG_CH_PAIR : 1;
   RowAcc acc;
   const int64_t l0 = __ldg(L.lrp + i), l1 = __ldg(L.lrp + i + 1);
   for (int64_t z = l0; z < l1; z += CH) {
@@ -215,13 +224,14 @@ __device__ __forceinline__ double row_dot_df_sym(int64_t i, int r, const int64_t
 }
 
 template <int NP>
-__global__ void __launch_bounds__(kThreads) k_spmv_dot_df_sym(int64_t nb, const int64_t* __restrict__ urp,
+__global__ void __launch_bounds__(kThreads, XDG_PAIR_MINB) k_spmv_dot_df_sym(int64_t nb, const int64_t* __restrict__ urp,
                                                              const int32_t* __restrict__ ucol,
                                                              const float2* __restrict__ uval2,
                                                              const int* __restrict__ uea, SymL L,
                                                              const float2* __restrict__ x2, const int* __restrict__ ex,
                                                              const double* __restrict__ x, double* __restrict__ y,
-                                                             double* __restrict__ partial) {
+                                                             double* __restrict__ partial,
+                                                             const uint8_t* __restrict__ act) {
   pdl_entry();
   constexpr int GPW = Grp<NP>::GPW;
   const int lane = threadIdx.x & 31;
@@ -231,6 +241,7 @@ __global__ void __launch_bounds__(kThreads) k_spmv_dot_df_sym(int64_t nb, const 
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = warp * GPW + g; i < nb; i += nw * GPW) {
+      if (act && !act[i]) continue;
       const double acc = row_dot_df_sym<NP>(i, r, urp, ucol, uval2, uea, L, x2, ex);
       if (y) y[i * NP + r] = acc;
       if (partial) d = fma(x[i * NP + r], acc, d);

@@ -445,7 +445,7 @@ class Batch:
     Vectors are the problems' level-1 vectors concatenated in list order (`offsets`)."""
 
     def __init__(self, problems, omega=0.0, lanczos_steps=12, nu=1, gamma=1, low_precision=0,
-                 w_levels=0, stream=None, split_rows=0, symmetric=0):
+                 w_levels=0, stream=None, split_rows=0, symmetric=0, outer_apply=0):
         L = load()
         torch = _torch()
         if stream is None:
@@ -455,7 +455,8 @@ class Batch:
         arr = (Problem * len(problems))()
         for i, p in enumerate(problems):
             arr[i] = _marshal(p.Np, p.nb, p.row_ptr, p.col, p.val, p.agg, p.R, keep)
-        opts = HierOpts(omega, lanczos_steps, nu, gamma, low_precision, w_levels, split_rows, 1, 1, symmetric)
+        opts = HierOpts(omega, lanczos_steps, nu, gamma, low_precision, w_levels, split_rows, 1, outer_apply,
+                        symmetric)
         h = C.c_void_p()
         self._h = None
         with _Ordered(self):

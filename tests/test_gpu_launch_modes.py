@@ -49,7 +49,7 @@ z = torch.empty_like(b)
 H.cycle(xdg.XDG_PREC_F32, b, z)
 out["cycle_f32"] = [digest(z), 0]
 probs = [xp.Problem(c) for c in xp.batch_configs(3, seed=7, N_range=(10, 16), ks=(2, 3), max_levels=4)]
-bt = xdg.Batch(probs, gamma=2, low_precision=1, split_rows=1)
+bt = xdg.Batch(probs, gamma=2, low_precision=1, split_rows=1, symmetric=2, outer_apply=2)
 bb = torch.from_numpy(np.concatenate([p.b.reshape(-1) for p in probs])).to(dev)
 xb = torch.zeros_like(bb)
 res = bt.solve(bb, xb, tol=1e-10, maxit=300, precision=xdg.XDG_PREC_F32)

@@ -126,3 +126,28 @@ def test_mixed_solve_with_pair_apply_reaches_oracle_solution(case):
         its.append(info["iterations"])
     assert abs(its[0] - its[1]) <= 1, its
     H.destroy()
+
+
+def test_batched_solve_with_pair_apply():
+    """A batch whose flexible CG applies M from FP32 pairs (rows of finished problems skipped)
+    reaches every problem's oracle solution, in the iterations of the FP64 outer apply (+-1)."""
+    probs = [xp.Problem(c) for c in xp.batch_configs(5, seed=21, N_range=(9, 18), ks=(2, 3, 4), max_levels=4)]
+    bb = _t(np.concatenate([p.b.reshape(-1) for p in probs]))
+    its = {}
+    for mode in (2, 1):
+        bt = xdg.Batch(probs, gamma=2, low_precision=1, outer_apply=mode)
+        x = torch.zeros_like(bb)
+        res = bt.solve(bb, x, tol=1e-10, maxit=300, precision=xdg.XDG_PREC_F32)
+        xs, off = _n(x), bt.offsets
+        for i, p in enumerate(probs):
+            assert res["problems"][i]["status"] == xdg.XDG_OK
+            if mode == 2:
+                O = oracle.Hierarchy(p, gamma=2)
+                xref, _, rr, _ = O.pcg(p.b, tol=1e-13, maxit=500)
+                O.close()
+                assert rr < 1e-12
+                err = np.linalg.norm(xs[off[i]:off[i + 1]] - xref.reshape(-1)) / np.linalg.norm(xref)
+                assert err < 1e-8, (i, err)
+        its[mode] = [r["iterations"] for r in res["problems"]]
+        bt.destroy()
+    assert all(abs(a - b) <= 1 for a, b in zip(its[2], its[1])), its

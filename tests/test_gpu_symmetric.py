@@ -109,7 +109,7 @@ def test_batched_solve_bitwise():
     bb = _t(np.concatenate([p.b.reshape(-1) for p in probs]))
     out = []
     for sym in (2, 1):
-        bt = xdg.Batch(probs, gamma=2, low_precision=1, split_rows=1, symmetric=sym)
+        bt = xdg.Batch(probs, gamma=2, low_precision=1, split_rows=1, symmetric=sym, outer_apply=2)
         x = torch.zeros_like(bb)
         res = bt.solve(bb, x, tol=1e-10, maxit=300, precision=xdg.XDG_PREC_F32)
         out.append((_n(x), [r["iterations"] for r in res["problems"]]))
