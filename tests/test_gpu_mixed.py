@@ -120,8 +120,9 @@ def test_fused_small_levels_match_launch_per_step(case, prec):
     b = _t(P.b.reshape(-1))
     out = []
     for mode in (1, 2):
+        # the other creation-time choices pinned too, so that only the small levels' launch differs
         H = xdg.Hierarchy.from_problem(P, gamma=gamma, w_levels=1, low_precision=3, split_rows=1,
-                                       fused_coarse=mode)
+                                       fused_coarse=mode, outer_apply=2, symmetric=2)
         fused = H.info()["fused_level"]
         if mode == 2 and P.n_levels >= 3 and P.nb[1] <= 16384:
             assert fused == 2, (name, fused)
