@@ -114,7 +114,8 @@ DOMINANT_HBM = "resid_rt_f32"
 DOMINANT_FP64 = "apply_f64"
 # DRAM bytes (read + write) of one launch at 64^3, from one ncu capture of the current kernels
 # (profiles/level1_kernels_dram_64cube.md), by kernel name
-NCU_TRAFFIC = {"k_spmv<10,0>": 1568570112}
+NCU_TRAFFIC = {"k_spmv_dot_df_sym<10>": 937077760, "k_resid_rt_lp_sym<10,float>": 583113216,
+               "k_smooth_lp_sym<10>": 579992576}
 # FP64 ALU peak from unit counts and clocks: 152 SMs x 2070 MHz x 4 FP64 flop per SM and clock
 # (2 FMA), the rate of GB300's nominal 1.25 TFLOP/s FP64
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12

@@ -249,7 +249,13 @@ int xdg_cycle(xdg_hier_t h, int prec, const double* b, double* x);
 
 /* Solve M^1 x = b (device vectors). x holds the initial guess on entry (resume from a
  * previous x to continue a solve). Returns XDG_OK when converged, XDG_ENOTCONV /
- * XDG_ETIMEOUT / XDG_EBREAKDOWN otherwise; info (optional) is filled in every case. */
+ * XDG_ETIMEOUT / XDG_EBREAKDOWN otherwise; info (optional) is filled in every case.
+ * With check_every == 1 and no time budget the whole iteration loop runs on the device (a
+ * CUDA graph whose conditional while node is set by the convergence check and bounded by
+ * maxit): one launch and one read-back per solve. Otherwise the host launches one recorded
+ * iteration graph per step and reads the residual norm every check_every steps. Both run the
+ * same kernels with the same arithmetic. The mixed-precision solves apply M with the FP32-pair
+ * product when xdg_hier_info.outer_pair is set. */
 int xdg_solve(xdg_hier_t h, const double* b, double* x, const xdg_solve_opts* o,
               xdg_solve_info* info);
 
@@ -274,8 +280,10 @@ int xdg_fma_peak(int prec, double* tflops);
  * precision prec; XDG_PREC_F64_PAIR: the pair product on level 1 from an already split
  * vector), 1 = block-Jacobi sweep from a nonzero guess (level < n_levels),
  * 2 = residual and restriction phase 1, R^T (b - M x) per fine block (level < n_levels).
- * The low-precision sweep and restriction read the FP32 operator (see xdg_cycle). Uses the
- * level's work vectors (zeroed first); synchronises. */
+ * The low-precision sweep and restriction read the FP32 operator (see xdg_cycle), on level 1
+ * from the symmetric storage when the cycle uses it (xdg_hier_info.symmetric, bit 1; the bytes
+ * then count the compact storage), as does the pair product (bit 2). Uses the level's work
+ * vectors (zeroed first); synchronises. */
 int xdg_kernel_time(xdg_hier_t h, int which, int level, int prec, int reps, double* ms,
                     double* bytes);
 

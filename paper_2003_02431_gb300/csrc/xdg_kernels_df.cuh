@@ -54,15 +54,42 @@ __device__ __forceinline__ float2 split_df(double v) {
 #define XDG_PAIR_MINB 4
 #endif
 
-// Sum of a row's block results (hi + lo) 2^k: each block scaled by 2^k and added in FP64 (four
-// FP64-pipe operations a block). A double-float sum relative to the row's first block, converted
-// to FP64 once per row, measured slower (more registers; the FP64 pipe is 8 % busy here).
+// x 2^k as a double, exactly, built from the float's bits (integer operations instead of an
+// FP64-pipe conversion and multiply); false for zero-exponent (subnormal), infinite or NaN x,
+// k outside the range pow2_d handles, or a result outside the normal range
+__device__ __forceinline__ bool f2d_scaled(float x, int k, double& out) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
+  if ((u & 0x7fffffffu) == 0u) {
+    out = __longlong_as_double((long long)sgn);
+    return true;
+  }
+  if (e == 0u || e == 0xffu || k < -1022 || k > 1023) return false;
+  const int E = (int)e - 127 + 1023 + k;
+  if (E < 1 || E > 2046) return false;
+  out = __longlong_as_double((long long)(sgn | ((unsigned long long)E << 52) |
+                                         ((unsigned long long)(u & 0x7fffffu) << 29)));
+  return true;
+}
+
+// Sum of a row's block results (hi + lo) 2^k in FP64. hi 2^k and lo 2^k are exact, so adding them
+// equals the fused multiply-add fma((double)hi, 2^k, acc) bit for bit; they are built with
+// integer operations (two FP64-pipe additions a block instead of two conversions and two FMAs:
+// the FP64 pipe was 61 % busy with the conversions), with the FMA form as the fallback. A
+// double-float sum relative to the row's first block, converted once per row, measured slower.
 struct RowAcc {
   double acc = 0.0;
   __device__ __forceinline__ void add(float hi, float lo, int k) {
-    const double sc = pow2_d(k);
-    acc = fma((double)hi, sc, acc);
-    acc = fma((double)lo, sc, acc);
+    double a, b;
+    if (f2d_scaled(hi, k, a) && f2d_scaled(lo, k, b)) {
+      acc = __dadd_rn(acc, a);
+      acc = __dadd_rn(acc, b);
+    } else {
+      const double sc = pow2_d(k);
+      acc = fma((double)hi, sc, acc);
+      acc = fma((double)lo, sc, acc);
+    }
   }
   __device__ __forceinline__ double result() const { return acc; }
 };
