@@ -73,6 +73,26 @@ __device__ __forceinline__ bool f2d_scaled(float x, int k, double& out) {
   return true;
 }
 
+// split_df(v 2^-k) with the scaling and the widening of hi done by integer operations where the
+// results are normal (bitwise the same pair; two FP64-pipe operations fewer per entry)
+__device__ __forceinline__ float2 split_scaled(double v, int k) {
+  const long long b = __double_as_longlong(v);
+  const int E = (int)((b >> 52) & 0x7ff);
+  double vs;
+  if (v == 0.0) {
+    vs = v;
+  } else if (E != 0 && E != 0x7ff && -k >= -1022 && -k <= 1023 && E - k >= 1 && E - k <= 2046) {
+    vs = __longlong_as_double((b & ~(0x7ffLL << 52)) | ((long long)(E - k) << 52));
+  } else {
+    vs = v * pow2_d(-k);
+  }
+  const float h = __double2float_rn(vs);
+  double hd;
+  if (!f2d_scaled(h, 0, hd)) hd = (double)h;
+  const float l = __double2float_rn(__dsub_rn(vs, hd));
+  return make_float2(h, l);
+}
+
 // Sum of a row's block results (hi + lo) 2^k in FP64. hi 2^k and lo 2^k are exact, so adding them
 // equals the fused multiply-add fma((double)hi, 2^k, acc) bit for bit; they are built with
 // integer operations (two FP64-pipe additions a block instead of two conversions and two FMAs:
@@ -341,7 +361,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_p_df(int64_t nb, const PcgScal
     const double v = first ? z[e] : fma(be, p[e], z[e]);
     p[e] = v;
     const int k = group_exp<NP>(v, mask);
-    p2[e] = split_df(v * pow2_d(-k));
+    p2[e] = split_scaled(v, k);
     if (r == 0) ex[i] = k;
   }
 }
@@ -362,7 +382,7 @@ __global__ void __launch_bounds__(kThreads) k_split_df(int64_t nb, const double*
     const int64_t e = i * NP + r;
     const double v = x[e];
     const int k = group_exp<NP>(v, mask);
-    x2[e] = split_df(v * pow2_d(-k));
+    x2[e] = split_scaled(v, k);
     if (r == 0) ex[i] = k;
   }
 }
