@@ -332,7 +332,9 @@ def reference_arm(args):
             per.append((time.perf_counter() - t) / 5)
     t_solve = statistics.mean(per) * iters
     value = P.dof / t_solve / 1e6
-    line = {"metric": METRIC, "value": value, "unit": "MDOF/s", "n_gpus": 0, "steps": args.steps,
+    # n_gpus: the launch's N (the driver pairs the arms by it); the oracle itself runs on host cores
+    line = {"metric": METRIC, "value": value, "unit": "MDOF/s", "n_gpus": args.gpus, "device": "host CPU cores",
+            "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "dof": P.dof, "tol": TOL, "iterations": iters,
