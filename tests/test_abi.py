@@ -86,3 +86,19 @@ def test_batch_validation_names_the_problem_without_gpu():
         rc, msg = _batch_rc(lst)
         assert rc == xdg.XDG_EINVAL, (idx, msg)
         assert ("problem %d" % idx) in msg and word in msg, msg
+
+
+def test_binding_argument_counts_match_prototypes():
+    """Every ctypes signature has as many arguments as the header's prototype."""
+    protos = {}
+    inc = os.path.join(ROOT, "include")
+    for fn in sorted(os.listdir(inc)):
+        if fn.endswith(".h"):
+            src = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, fn)).read(), flags=re.S)
+            for m in re.finditer(r"^\s*(?:const\s+)?\w+\s*\*?\s*(xdg_\w+)\s*\(([^)]*)\)\s*;", src, flags=re.M):
+                args = m.group(2).strip()
+                protos[m.group(1)] = 0 if args in ("", "void") else len(args.split(","))
+    sigs = {n: at for n, _, at in xdg.SIGNATURES}
+    assert set(protos) <= set(sigs)
+    bad = {n: (k, len(sigs[n])) for n, k in protos.items() if len(sigs[n]) != k}
+    assert not bad, bad
