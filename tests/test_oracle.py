@@ -189,3 +189,50 @@ def test_quantized_storage_rounding():
         expect = s.astype(np.float64)[:, None] * ratio.astype(np.float64)
         assert np.array_equal(q.reshape(200, -1), expect)
         assert np.all(q[3] == 0.0)
+
+
+def _blockdiag(A, Np):
+    D = np.zeros_like(A)
+    for i in range(A.shape[0] // Np):
+        D[i * Np:(i + 1) * Np, i * Np:(i + 1) * Np] = A[i * Np:(i + 1) * Np, i * Np:(i + 1) * Np]
+    return D
+
+
+@pytest.mark.parametrize("wlev", [0, 1, 2])
+def test_w_cycle_matches_dense_recursion(wlev):
+    """The W-cycle (gamma = 2) and its restriction to the wlev finest levels (V below), written
+    as the textbook recursion with dense matrices: pre-smoothing from zero, restriction, gamma
+    coarse steps z_c += B_c(r_c - M_c z_c) on levels l < wlev (one step below), prolongation,
+    post-smoothing; Galerkin coarse matrices; exact coarsest solve. Four levels."""
+    P = xp.Problem(xp.Config(D=2, N=16, k=2, c=(0.5, 0.5, 0), R=0.3, muA=1, muB=10, max_coarse_dof=20,
+                                max_levels=4))
+    assert P.n_levels == 4
+    H = oracle.Hierarchy(P, gamma=2)
+    if wlev:
+        oracle.set_w_levels(H, wlev)
+    Np, nl = P.Np, P.n_levels
+    A = [dense_from_bsr(P.row_ptr, P.col, P.val)]
+    Rd = []
+    for l in range(nl - 1):
+        Rd.append(_Rdense(P.agg[l], P.R[l], P.nb[l + 1]))
+        A.append(Rd[l].T @ A[l] @ Rd[l])
+    om = [H.level(l)["omega"] for l in range(nl - 1)]
+    wl = wlev if wlev else nl
+
+    def B(l, b):
+        if l == nl - 1:
+            return np.linalg.solve(A[l], b)
+        D = _blockdiag(A[l], Np)
+        x = om[l] * np.linalg.solve(D, b)
+        bc = Rd[l].T @ (b - A[l] @ x)
+        zc = B(l + 1, bc)
+        if l + 2 < nl and l < wl:
+            zc = zc + B(l + 1, bc - A[l + 1] @ zc)
+        x = x + Rd[l] @ zc
+        return x + om[l] * np.linalg.solve(D, b - A[l] @ x)
+
+    b = np.random.default_rng(21).standard_normal(P.dof)
+    ref = B(0, b)
+    got = H.vcycle(b)
+    assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref), wlev
+    H.close()
