@@ -4,14 +4,16 @@
 Workload (synthetic, generated in-process): 3D XDG Poisson problem on the unit cube, 64^3
 Cartesian cells, spherical interface (centre (0.5,0.5,0.5), radius 0.31), diffusivity 1 inside /
 1000 outside, SIP, DG degree k=2 (Np=10), agglomeration threshold 0.1, manufactured smooth
-solution: 266,232 blocks, 2,662,320 DOF, 1,849,256 non-zero 10x10 blocks, 5 levels.
+solution: 266,232 blocks, 2,662,320 DOF, 1,849,276 non-zero 10x10 blocks, 5 levels.
 
 A step is one complete solve from x = 0 to ||b - M x|| <= 1e-10 ||b|| (the parity tests show
 the solution then lies within 1e-8 relative L2 of the FP64 oracle's solution). The headline
-path is flexible CG in FP64 (operator apply, residuals, updates) preconditioned by an FP32
-W-cycle (block-Jacobi smoothing, fused residual-restriction, prolongation, FP64 coarsest
-solve); the plain FP64 path (CG with the FP64 W-cycle) is timed next to it. value = DOF
-solved per second of the headline path.
+path is flexible CG in FP64 (residuals, updates, inner products; the operator apply q = M p
+FP64-accurate from FP32 pairs when the creation-time autotuner keeps it) preconditioned by an
+FP32 W-cycle (block-Jacobi smoothing, fused residual-restriction, prolongation, FP64 coarsest
+solve; level 1 read from its symmetric storage when kept); the plain FP64 path (CG with the
+FP64 W-cycle and the FP64 apply) is timed next to it. value = DOF solved per second of the
+headline path.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl xdg|reference]
 """
