@@ -57,3 +57,29 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     monkeypatch.setattr(bench, "make_problem", lambda: called.append(1))
     bench.reference_arm(argparse.Namespace(steps=1, warmup=1))
     assert not called and capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_keeps_the_contract():
+    """bench.py --impl reference prints one JSON line with the benchmark's keys, the oracle's
+    cpu_baseline (its value the line's) and an e2e entry without host-device copies."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ)
+    env.pop("RANK", None)
+    p = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--size", "12",
+                        "--steps", "1", "--warmup", "1"], capture_output=True, text=True, timeout=600, env=env)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [ln for ln in p.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["higher_is_better"] is True and d["value"] > 0
+    assert d["config"]["workload"].startswith("xdg-poisson-3d-12^3")
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
