@@ -108,16 +108,42 @@ KERNEL_NAMES = {
     "apply_pair": ("k_spmv_dot_df<10>", "k_spmv_dot_df_sym<10>",
                    "level-1 FP64-accurate apply from FP32 pairs (the mixed solve's flexible CG)"),
 }
-# the largest kernel of the mixed solve's device time (launch list in
-# profiles/launch_list_mixed_solve_64cube.md), the largest kernel of the cycle, and the FP64
-# path's apply (ALU-bound)
+# the largest kernel of the mixed solve's device time (the launch list of the solve), the
+# largest kernel of the cycle, and the FP64 path's apply (ALU-bound)
 DOMINANT = "apply_pair"
 DOMINANT_HBM = "resid_rt_f32"
 DOMINANT_FP64 = "apply_f64"
-# DRAM bytes (read + write) of one launch at 64^3, from one ncu capture of the current kernels
-# (profiles/level1_kernels_dram_64cube.md), by kernel name
-NCU_TRAFFIC = {"k_spmv_dot_df_sym<10>": 937077760, "k_resid_rt_lp_sym<10,float>": 583113216,
-               "k_smooth_lp_sym<10>": 579992576}
+PARITY_BOUND = 1e-8   # the metric's tolerance: relative L2 distance to the oracle's solution
+
+
+def csrc_digest():
+    """sha256 (first 16 hex digits) of the CUDA sources, to tell whether a recorded ncu
+    measurement was taken on the kernels that run now."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2003_02431_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, size):
+    """DRAM bytes (read + write) per launch of `kernel` at `size`^3 from a committed ncu
+    summary line `traffic_per_launch kernel=<name> size=<N> bytes=<B> csrc_sha256=<digest>`,
+    only if the digest matches the current sources (else None: the counters are stale)."""
+    import glob
+    import re
+    digest = csrc_digest()
+    pat = re.compile(r"traffic_per_launch kernel=(\S+) size=(\d+) bytes=(\d+) csrc_sha256=([0-9a-f]+)")
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(path) as f:
+            for m in pat.finditer(f.read()):
+                if m.group(1) == kernel and int(m.group(2)) == size and m.group(4) == digest:
+                    return int(m.group(3))
+    return None
+
+
 # FP64 ALU peak from unit counts and clocks: 152 SMs x 2070 MHz x 4 FP64 flop per SM and clock
 # (2 FMA), the rate of GB300's nominal 1.25 TFLOP/s FP64
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
@@ -150,26 +176,51 @@ def oracle_hierarchy(P):
     return O
 
 
-def oracle_sample(P, iters_needed, budget_s=12.0):
-    """Time the oracle's PCG iterations on this problem (bounded sample) and extrapolate."""
+def oracle_solution(P, tol=1e-13):
+    """The oracle's FP64 solution of M x = b: PCG to a relative residual of `tol`."""
+    O = oracle_hierarchy(P)
+    x, it, rr, _ = O.pcg(P.b, tol=tol, maxit=1000)
+    O.close()
+    return x.reshape(-1), it, rr
+
+
+def rel_l2(x, ref):
+    return float(np.linalg.norm(np.asarray(x).reshape(-1) - ref) / np.linalg.norm(ref))
+
+
+def oracle_sample(P, iters_needed, budget_s=10.0):
+    """Time the oracle's PCG iterations on this problem (bounded samples) with all host cores
+    and with one thread, and extrapolate each to the full solve's iteration count."""
+    import oracle
     t = time.perf_counter()
     O = oracle_hierarchy(P)
     setup = time.perf_counter() - t
-    m, spent = 2, 0.0
-    while True:
-        t = time.perf_counter()
-        O.pcg(P.b, tol=0.0, maxit=m)
-        dt = time.perf_counter() - t
-        per = dt / m
-        spent += dt
-        if dt >= budget_s / 3 or spent >= budget_s:
-            break
-        m *= 2
-    return {"per_iteration_s": per, "sample_iterations": m, "setup_s": setup,
-            "est_solve_s": per * iters_needed, "cores": os.cpu_count()}
+    all_threads = oracle.set_threads(os.cpu_count() or 1)
+
+    def sample(budget):
+        m, spent = 1, 0.0
+        while True:
+            t = time.perf_counter()
+            O.pcg(P.b, tol=0.0, maxit=m)
+            dt = time.perf_counter() - t
+            spent += dt
+            if dt >= budget / 3 or spent >= budget:
+                return dt / m, m
+            m *= 2
+
+    per_all, m_all = sample(budget_s)
+    oracle.set_threads(1)
+    per_one, m_one = sample(budget_s)
+    oracle.set_threads(all_threads)
+    O.close()
+    return {"per_iteration_s": per_all, "sample_iterations": m_all, "setup_s": setup,
+            "est_solve_s": per_all * iters_needed, "cores": all_threads,
+            "single_thread": {"per_iteration_s": per_one, "sample_iterations": m_one,
+                              "est_solve_s": per_one * iters_needed}}
 
 
 BATCH_N = 256
+BATCH_PARITY_SAMPLES = 8
 BATCH_SEED = 20030244
 BATCH_WORKLOAD = ("256 independent 2D XDG Poisson problems: N~U{32..128}^2, k~U{2,3,4}, circle centre "
                   "U(0.3,0.7)^2, R~U(0.1,0.3), mu ratio 10^U(0,3), 6 aggregation levels, seed %d" % BATCH_SEED)
@@ -213,10 +264,18 @@ def batched_section(xdg, torch, dev, stream, steps, warmup):
             res.append(bt.solve(b, x, tol=TOL, maxit=1000, precision=prec))
         ev1.record(stream)
         torch.cuda.synchronize()
-        return ev0.elapsed_time(ev1) / steps, res[-1], sum(r["launches"] for r in res)
+        return ev0.elapsed_time(ev1) / steps, res[-1], sum(r["launches"] for r in res), x.cpu().numpy()
 
-    ms32, r32, launches = run(xdg.XDG_PREC_F32)
-    ms64, r64, _ = run(xdg.XDG_PREC_F64)
+    ms32, r32, launches, x32 = run(xdg.XDG_PREC_F32)
+    ms64, r64, _, x64 = run(xdg.XDG_PREC_F64)
+    # parity of sampled problems: the oracle's solution of each, against both timed solves
+    offs = np.concatenate([[0], np.cumsum([p.dof for p in probs])])
+    sample = sorted(np.random.default_rng(BATCH_SEED).choice(len(probs), BATCH_PARITY_SAMPLES, replace=False))
+    errs = {"mixed_f32": [], "plain_f64": []}
+    for i in sample:
+        ref = oracle_solution(probs[i])[0]
+        for key, xs in (("mixed_f32", x32), ("plain_f64", x64)):
+            errs[key].append(rel_l2(xs[offs[i]:offs[i + 1]], ref))
     its = [p["iterations"] for p in r32["problems"]]
     # end to end: host vectors in pinned memory, copies inside the call
     bp = torch.from_numpy(bh).pin_memory().numpy()
@@ -234,6 +293,8 @@ def batched_section(xdg, torch, dev, stream, steps, warmup):
         "plain_f64": {"solve_ms": ms64, "mdofs": n / ms64 / 1e3, "iterations_max": r64["iterations"],
                       "max_relres": r64["relres"]},
         "speedup_mixed_vs_f64": ms64 / ms32,
+        "parity": {"problems": [int(i) for i in sample], "bound": PARITY_BOUND,
+                   "max_rel_l2_vs_oracle": {k: max(v) for k, v in errs.items()}},
         "e2e": {"value": n / e2e_s / 1e6, "unit": "MDOF/s", "h2d_bytes_per_step": n * 8,
                 "d2h_bytes_per_step": n * 8},
         "kernel_nodes_per_solve": launches / steps,
@@ -305,6 +366,8 @@ def learned_section(xdg, torch, dev, stream, n_train=4):
         if tag == "plain":
             xplain = x0.clone()
     out["solution_diff_rel_l2"] = float(torch.linalg.norm(x0 - xplain) / torch.linalg.norm(xplain))
+    xref = oracle_solution(P)[0]
+    out["rel_l2_vs_oracle"] = {"plain": rel_l2(xplain.cpu().numpy(), xref), "learned": rel_l2(x0.cpu().numpy(), xref)}
     H.learned_enable(None)
     # the plain FP64 path on the same problem (CG with the FP64 cycle)
     x0.zero_()
@@ -399,6 +462,11 @@ def main():
 
     P = make_problem()
     n, Np, nb, nnzb = P.dof, P.Np, P.nb[0], int(P.row_ptr[-1])
+    # the oracle's solution of the same system (host cores, outside every timed region): every
+    # timed path's last solution is compared with it
+    t = time.perf_counter()
+    xref, it_ref, rr_ref = oracle_solution(P)
+    oracle_s = time.perf_counter() - t
     t = time.perf_counter()
     H = xdg.Hierarchy.from_problem(P, gamma=GAMMA, w_levels=W_LEVELS, low_precision=3, stream=stream,
                                    fused_coarse=args.fused_coarse, outer_apply=args.outer_apply,
@@ -440,15 +508,15 @@ def main():
         ms = ev0.elapsed_time(ev1)
         if dist:
             ms = max_over_ranks(ms, dist, dev)
-        return ms, launches, iters
+        return ms, launches, iters, rel_l2(x.cpu().numpy(), xref)
 
     # XDG_BENCH_PROFILE_RANGE=1 marks the headline timed region for `ncu --profile-from-start off`
     prof = os.environ.get("XDG_BENCH_PROFILE_RANGE") == "1"
     with ClockSampler(local) as clocks:
-        t_ms, launches, iters = timed_solves(xdg.XDG_PREC_F32, args.steps, prof=prof)
+        t_ms, launches, iters, err32 = timed_solves(xdg.XDG_PREC_F32, args.steps, prof=prof)
     value = job_throughput(world, n, args.steps, t_ms / 1e3)
-    t64_ms, _, iters64 = timed_solves(xdg.XDG_PREC_F64, args.steps)
-    tbf_ms, _, itersbf = timed_solves(xdg.XDG_PREC_BF16, args.steps)
+    t64_ms, _, iters64, err64 = timed_solves(xdg.XDG_PREC_F64, args.steps)
+    tbf_ms, _, itersbf, errbf = timed_solves(xdg.XDG_PREC_BF16, args.steps)
 
     def time_call(fn, reps=20):
         for _ in range(3):
@@ -517,9 +585,13 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         it64 = int(statistics.median(iters64))
         s = oracle_sample(P, it64)
+        one = s["single_thread"]
         cpu = {"value": n / s["est_solve_s"] / 1e6, "unit": "MDOF/s", "cores": s["cores"], "kind": "oracle",
                "sample": "%d FP64 PCG iterations of the same 64^3 problem (%.3f s each), extrapolated to the "
-                         "%d iterations of the FP64 solve" % (s["sample_iterations"], s["per_iteration_s"], it64)}
+                         "%d iterations of the FP64 solve" % (s["sample_iterations"], s["per_iteration_s"], it64),
+               "single_thread": {"value": n / one["est_solve_s"] / 1e6, "unit": "MDOF/s", "cores": 1,
+                                 "sample": "%d PCG iterations on one thread (%.3f s each), extrapolated the same way"
+                                           % (one["sample_iterations"], one["per_iteration_s"])}}
 
     if rank == 0:
         line = {
@@ -539,35 +611,41 @@ def main():
                        "fused_small_levels_from": hinfo["fused_level"],
                        "l2": "inputs larger than L2 (operator 1.49 GB FP64 + 0.74 GB FP32)"},
             "paths": {
-                "mixed_f32": {"solve_ms": t_ms / args.steps, "iterations": iters, "mdofs": value / world},
+                "mixed_f32": {"solve_ms": t_ms / args.steps, "iterations": iters, "mdofs": value / world,
+                              "rel_l2_vs_oracle": err32},
                 "plain_f64": {"solve_ms": t64_ms / args.steps, "iterations": iters64,
-                              "mdofs": n * args.steps / (t64_ms / 1e3) / 1e6},
+                              "mdofs": n * args.steps / (t64_ms / 1e3) / 1e6, "rel_l2_vs_oracle": err64},
                 "mixed_bf16_transfers": {"solve_ms": tbf_ms / args.steps, "iterations": itersbf,
-                                         "mdofs": n * args.steps / (tbf_ms / 1e3) / 1e6},
+                                         "mdofs": n * args.steps / (tbf_ms / 1e3) / 1e6, "rel_l2_vs_oracle": errbf},
                 "speedup_mixed_vs_f64": t64_ms / t_ms,
             },
+            "parity": {"rel_l2_vs_oracle": {"mixed_f32": err32, "plain_f64": err64, "mixed_bf16_transfers": errbf},
+                       "bound": PARITY_BOUND,
+                       "oracle": "FP64 PCG on the host cores to relative residual %.0e (%d iterations, %.1f s), "
+                                 "outside the timed regions; each path's last timed solution" % (
+                                     rr_ref if rr_ref > 0 else 1e-13, it_ref, oracle_s)},
             "vcycle_mdofs": {"f64": n / cyc_ms[0] / 1e3, "f32": n / cyc_ms[1] / 1e3, "bf16": n / cyc_ms[2] / 1e3},
             "vcycle_ms": cyc_ms,
             "setup_s": setup_s, "setup_ms_phases": hinfo["setup_ms"],
             "roofline": (
                 {"bound": "hbm", "kernel": dom["kernel"], "achieved": dom["achieved_gbs"], "peak": hbm,
                  "unit": "GB/s", "frac": dom["achieved_gbs"] / hbm, "peak_kind": hbm_kind, "bytes": dom["bytes"],
-                 "ms": dom["ms"], "traffic": NCU_TRAFFIC.get(dom["name"]) if SIZE == 64 else None}
+                 "ms": dom["ms"], "traffic": profiled_traffic(dom["name"], SIZE)}
                 if dom_key != DOMINANT_FP64 else
                 {"bound": "alu", "kernel": dom["kernel"], "achieved": ach64, "peak": FP64_PEAK_TFLOPS,
                  "unit": "TFLOP/s", "frac": ach64 / FP64_PEAK_TFLOPS, "flops": flops_apply, "bytes": dom["bytes"],
-                 "ms": dom["ms"], "traffic": NCU_TRAFFIC.get(dom["name"]) if SIZE == 64 else None,
+                 "ms": dom["ms"], "traffic": profiled_traffic(dom["name"], SIZE),
                  "peak_kind": "FP64 unit counts x clock (152 SMs x 2.07 GHz x 4 flop)"}),
             "roofline_fp64": {"bound": "alu", "kernel": d64["kernel"], "achieved": ach64, "peak": FP64_PEAK_TFLOPS,
                               "unit": "TFLOP/s", "frac": ach64 / FP64_PEAK_TFLOPS,
                               "peak_kind": "FP64 unit counts x clock (152 SMs x 2.07 GHz x 4 flop); the library's "
                                            "FMA probe reaches %.3f TFLOP/s of it" % fp64_peak,
                               "flops": flops_apply, "bytes": d64["bytes"], "ms": d64["ms"],
-                              "traffic": NCU_TRAFFIC.get(d64["name"]) if SIZE == 64 else None},
+                              "traffic": profiled_traffic(d64["name"], SIZE)},
             "roofline_hbm": {"bound": "hbm", "kernel": domh["kernel"], "achieved": domh["achieved_gbs"], "peak": hbm,
                              "unit": "GB/s", "frac": domh["achieved_gbs"] / hbm, "peak_kind": hbm_kind,
                              "bytes": domh["bytes"], "ms": domh["ms"],
-                             "traffic": NCU_TRAFFIC.get(domh["name"]) if SIZE == 64 else None},
+                             "traffic": profiled_traffic(domh["name"], SIZE)},
             "kernels_level1": kernels,
             "fp64_fma_probe_tflops": fp64_peak,
             "batched": batched,
@@ -580,6 +658,11 @@ def main():
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+    worst = max(err32, err64, errbf)
+    if worst > PARITY_BOUND:
+        print("bench: a timed solution is %.3e from the oracle's (bound %.0e)" % (worst, PARITY_BOUND),
+              file=sys.stderr, flush=True)
+        sys.exit(1)
 
 
 if __name__ == "__main__":

@@ -453,6 +453,13 @@ int xdg_learned_step(xdg_hier_t h, const double* r, double* z, int* n_kept);
  *   b, x                double[nb_fine*Np];  rc  double[nb_coarse*Np]
  *   stream              cudaStream_t the kernels are enqueued on (NULL: legacy stream)
  *
+ * The stream and every pointer must belong to the current CUDA device. The entry point cannot
+ * see the length of a device array, so the caller guarantees the layout: row_ptr[0] = 0,
+ * row_ptr non-decreasing, every col entry < nb_fine, child_ptr[0] = 0 and
+ * child_ptr[nb_coarse] = nb_fine, every child index < nb_fine, and every array at least as
+ * long as stated above (val: row_ptr[nb_fine]*Np*Np entries). A violation makes the kernels
+ * read or write out of bounds; only the sizes below are checked here.
+ *
  * Scratch: a fixed device array of XDG_NOALLOC_MAX_ENTRIES doubles (8 MiB) inside the
  * library, holding R_f^T (b_f - M_f x) for every fine block. Every GPU that loads the
  * library holds this array until the process exits. nb_fine*Np above

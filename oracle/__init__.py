@@ -179,6 +179,38 @@ class Hierarchy:
         self._L.or_coarse_solve(self._h, _p(r, _dp), _p(z, _dp))
         return z
 
+    def set_patches(self, l, patches, mode=1, lanczos_steps=12, omega=0.0):
+        """Additive Schwarz smoother (Algorithm Swz, exact patch solves) on level l (0-based):
+        patches = (ptr int64[n+1], blocks int32[ptr[n]]) or None for block Jacobi. mode 0 divides
+        the summed patch solutions by alpha (as printed), mode 1 scales by alpha^{-1/2} on both
+        sides (symmetric). Re-estimates the level's damping from the Schwarz preconditioner."""
+        L = self._L
+        if not hasattr(L, "_swz_set"):
+            L.or_hier_set_patches.restype = C.c_int
+            L.or_hier_set_patches.argtypes = [C.c_void_p, C.c_int, C.c_int64, _i64p, _i32p, C.c_int, C.c_int,
+                                              C.c_double]
+            L.or_schwarz.argtypes = [C.c_void_p, C.c_int, _dp, _dp]
+            L._swz_set = True
+        if patches is None:
+            rc = L.or_hier_set_patches(self._h, l, 0, None, None, mode, lanczos_steps, omega)
+        else:
+            ptr = np.ascontiguousarray(patches[0], np.int64)
+            blk = np.ascontiguousarray(patches[1], np.int32)
+            self._keep.append((ptr, blk))
+            rc = L.or_hier_set_patches(self._h, l, len(ptr) - 1, _p(ptr, _i64p), _p(blk, _i32p), mode,
+                                       lanczos_steps, omega)
+        if rc == -2:
+            raise RuntimeError("oracle Schwarz: a patch matrix is not positive definite")
+        if rc != 0:
+            raise ValueError("oracle Schwarz: invalid patches")
+
+    def schwarz(self, l, r):
+        """z = Swz(r) on level l (undamped; the patches of set_patches)."""
+        r = _f64(r).reshape(-1)
+        z = np.empty_like(r)
+        self._L.or_schwarz(self._h, l, _p(r, _dp), _p(z, _dp))
+        return z
+
     def pcg(self, b, x0=None, tol=1e-10, maxit=500):
         """Returns (x, iterations, true relative residual, history)."""
         b = _f64(b).reshape(-1)
@@ -213,6 +245,14 @@ def quantize_blocks(blocks, prec):
     sc = np.empty(nblk, dtype=np.float32)
     L.or_quantize_blocks(nblk, np2, prec, _p(a, _dp), _p(out, _dp), sc.ctypes.data_as(C.POINTER(C.c_float)))
     return out, sc
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's OpenMP loops (n >= 1); returns the number now in use."""
+    L = _load()
+    L.or_set_threads.restype = C.c_int
+    L.or_set_threads.argtypes = [C.c_int]
+    return int(L.or_set_threads(int(n)))
 
 
 def set_w_levels(h, wlev):

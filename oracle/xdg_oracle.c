@@ -29,10 +29,25 @@
  */
 #include <math.h>
 #include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
 #define OR_MAXL 24
+
+/* Threads of the OpenMP loops below (n >= 1); returns the number in use afterwards (1 when the
+ * library was built without OpenMP). Lets a caller time the oracle single-threaded. */
+int or_set_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 /* ---------------- operator apply ---------------- */
 
@@ -245,6 +260,14 @@ typedef struct {
   const int32_t* agg; /* to the next level */
   const double* R;
   double* w[4];      /* work vectors */
+  /* additive Schwarz smoother (Algorithm Swz); npatch = 0: block Jacobi */
+  int64_t npatch;
+  int64_t* pptr;     /* patch i = blocks pblk[pptr[i] .. pptr[i+1]-1] */
+  int32_t* pblk;
+  int64_t* poff;     /* offset of patch i's Cholesky factor in pchol */
+  double* pchol;     /* dense Cholesky factor of M restricted to each patch */
+  double* pscale;    /* per block: 1/alpha (mode 0) or 1/sqrt(alpha) (mode 1) */
+  int pmode;         /* 0: x ./ alpha after the sum; 1: alpha^{-1/2} on both sides */
 } or_level;
 
 typedef struct {
@@ -268,6 +291,55 @@ static void bj_apply(const or_level* L, int Np, const double* r, double* z) {
   const int64_t Np2 = (int64_t)Np * Np;
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < L->nb; ++i) chol_solve(Np, L->Dchol + i * Np2, r + i * Np, z + i * Np);
+}
+
+/* dense M_{PP} of the blocks blk[0..n-1] of a level (row-major, (n Np)^2) */
+static void gather_patch(const or_level* L, int Np, int64_t n, const int32_t* blk, double* A) {
+  const int64_t m = n * Np, Np2 = (int64_t)Np * Np;
+  memset(A, 0, sizeof(double) * m * m);
+  for (int64_t a = 0; a < n; ++a) {
+    const int64_t i = blk[a];
+    for (int64_t z = L->rp[i]; z < L->rp[i + 1]; ++z)
+      for (int64_t c = 0; c < n; ++c)
+        if (L->col[z] == blk[c])
+          for (int r = 0; r < Np; ++r)
+            for (int q = 0; q < Np; ++q) A[(a * Np + r) * m + c * Np + q] = L->val[z * Np2 + r * Np + q];
+  }
+}
+
+/* Additive Schwarz (Algorithm Swz) with exact block solves on the patches P_i (PMG with every
+ * mode in the low-order set is the direct solve of M_{P_i P_i}):
+ *   mode 0 (the algorithm as printed): z = (sum_i E_i M_ii^{-1} E_i^T r) ./ alpha,
+ *   mode 1 (symmetric): z = alpha^{-1/2} .* sum_i E_i M_ii^{-1} E_i^T (alpha^{-1/2} .* r),
+ * alpha = number of patches holding each block. The two agree when alpha is constant. */
+static void swz_apply(const or_level* L, int Np, const double* r, double* z) {
+  const int64_t n = L->nb * Np;
+  double* rs = (double*)malloc(sizeof(double) * n);
+  for (int64_t i = 0; i < n; ++i) {
+    z[i] = 0.0;
+    rs[i] = L->pmode ? L->pscale[i / Np] * r[i] : r[i];
+  }
+  for (int64_t p = 0; p < L->npatch; ++p) {
+    const int64_t nbp = L->pptr[p + 1] - L->pptr[p], m = nbp * Np;
+    const int32_t* blk = L->pblk + L->pptr[p];
+    double* rp = (double*)malloc(sizeof(double) * m);
+    double* xp = (double*)malloc(sizeof(double) * m);
+    for (int64_t a = 0; a < nbp; ++a)
+      for (int q = 0; q < Np; ++q) rp[a * Np + q] = rs[(int64_t)blk[a] * Np + q];
+    chol_solve(m, L->pchol + L->poff[p], rp, xp);
+    for (int64_t a = 0; a < nbp; ++a)
+      for (int q = 0; q < Np; ++q) z[(int64_t)blk[a] * Np + q] += xp[a * Np + q];
+    free(rp);
+    free(xp);
+  }
+  for (int64_t i = 0; i < n; ++i) z[i] *= L->pscale[i / Np];
+  free(rs);
+}
+
+/* the level's smoother preconditioner: block Jacobi or additive Schwarz */
+static void smoother_apply(const or_level* L, int Np, const double* r, double* z) {
+  if (L->npatch > 0) swz_apply(L, Np, r, z);
+  else bj_apply(L, Np, r, z);
 }
 
 /* Counter-based start vector for the Lanczos estimate (Knuth multiplicative hash):
@@ -366,6 +438,51 @@ static double lambda_max(or_level* L, int Np, int m) {
   return lm;
 }
 
+/* m-step Lanczos for the largest eigenvalue of S M with S the symmetric Schwarz preconditioner
+ * (S M is self-adjoint in the M inner product; one product with M and one application of S per
+ * step). Same start vector as the block-Jacobi estimate. */
+static double lambda_max_swz(or_level* L, int Np, int m) {
+  const int64_t n = L->nb * Np;
+  double* q = (double*)calloc(n, sizeof(double));
+  double* qp = (double*)calloc(n, sizeof(double));
+  double* u = (double*)malloc(sizeof(double) * n);
+  double* w = (double*)malloc(sizeof(double) * n);
+  double* v = (double*)malloc(sizeof(double) * n);
+  double al[64], be[64];
+  for (int64_t i = 0; i < n; ++i) q[i] = start_entry(i);
+  or_bsr_spmv(L->nb, Np, L->rp, L->col, L->val, q, u);
+  double nrm = sqrt(dot(n, q, u));
+  for (int64_t i = 0; i < n; ++i) {
+    q[i] /= nrm;
+    u[i] /= nrm;
+  }
+  double bprev = 0.0;
+  int steps = 0;
+  for (int j = 0; j < m; ++j) {
+    swz_apply(L, Np, u, w); /* w = S M q */
+    al[j] = dot(n, u, w);   /* <q, S M q>_M */
+    for (int64_t i = 0; i < n; ++i) w[i] -= al[j] * q[i] + bprev * qp[i];
+    or_bsr_spmv(L->nb, Np, L->rp, L->col, L->val, w, v);
+    steps = j + 1;
+    double bj = sqrt(dot(n, w, v));
+    be[j] = bj;
+    if (!(bj > 1e-300)) break;
+    for (int64_t i = 0; i < n; ++i) {
+      qp[i] = q[i];
+      q[i] = w[i] / bj;
+      u[i] = v[i] / bj;
+    }
+    bprev = bj;
+  }
+  double lm = tridiag_max(steps, al, be);
+  free(q);
+  free(qp);
+  free(u);
+  free(w);
+  free(v);
+  return lm;
+}
+
 /* Build the hierarchy: level-1 operator plus per-level (agg, R). All input arrays must stay
  * alive while the hierarchy exists. omega > 0 fixes the damping on every level; otherwise
  * omega_l = 4/(3 lambda_max(D^{-1} M^l)) from lanczos_steps Lanczos steps.
@@ -447,6 +564,11 @@ void or_hier_free(void* h) {
     }
     free(L->Dchol);
     for (int t = 0; t < 4; ++t) free(L->w[t]);
+    free(L->pptr);
+    free(L->pblk);
+    free(L->poff);
+    free(L->pchol);
+    free(L->pscale);
   }
   free(H->cchol);
   for (int t = 0; t < 5; ++t) free(H->pv[t]);
@@ -469,14 +591,15 @@ int or_hier_level(void* h, int l, int64_t* nb, int64_t* nnzb, double* omega, dou
   return 0;
 }
 
-/* one damped block-Jacobi step on level l: x += omega D^{-1} (b - M x) */
+/* one damped smoothing step on level l: x += omega S (b - M x), S = D^{-1} (block Jacobi) or
+ * the additive Schwarz preconditioner when the level has patches */
 void or_smooth(void* h, int l, const double* b, double* x) {
   or_hier* H = (or_hier*)h;
   or_level* L = &H->L[l];
   const int Np = H->Np;
   const int64_t n = L->nb * Np;
   or_residual(L->nb, Np, L->rp, L->col, L->val, b, x, L->w[2]);
-  bj_apply(L, Np, L->w[2], L->w[3]);
+  smoother_apply(L, Np, L->w[2], L->w[3]);
   for (int64_t i = 0; i < n; ++i) x[i] += L->omega * L->w[3][i];
 }
 
@@ -495,7 +618,7 @@ static void vcycle_rec(or_hier* H, int l, const double* b, double* x) {
     return;
   }
   /* pre-smoothing from x = 0 */
-  bj_apply(L, Np, b, x);
+  smoother_apply(L, Np, b, x);
   for (int64_t i = 0; i < n; ++i) x[i] *= L->omega;
   for (int s = 1; s < H->nu; ++s) or_smooth(H, l, b, x);
   /* restrict the residual */
@@ -608,3 +731,84 @@ void or_quantize_blocks(int64_t nblk, int np2, int prec, const double* in, doubl
 
 /* restrict the repeated coarse corrections to levels l < wlev (V-cycle below) */
 void or_hier_set_wlev(void* h, int wlev) { ((or_hier*)h)->wlev = wlev; }
+
+/* Additive Schwarz smoother on level l (Algorithm Swz, exact patch solves): patch i holds the
+ * blocks pblk[pptr[i] .. pptr[i+1]-1] (every block of the level in at least one patch). The
+ * dense matrices M_{P_i P_i} are factorised (Cholesky), alpha counted per block, and the damping
+ * re-estimated: omega = 4/(3 lambda_max(S M)) with S in its symmetric form, unless the
+ * hierarchy was built with a fixed omega. mode 0: x ./ alpha as printed; mode 1: alpha^{-1/2} on
+ * both sides (a symmetric smoother, as CG needs). npatch = 0 restores block Jacobi.
+ * Returns 0, -1 on invalid patches, -2 if a patch matrix is not positive definite. */
+int or_hier_set_patches(void* h, int l, int64_t npatch, const int64_t* pptr, const int32_t* pblk, int mode,
+                        int lanczos_steps, double omega_fixed) {
+  or_hier* H = (or_hier*)h;
+  if (l < 0 || l >= H->nlev - 1) return -1;
+  or_level* L = &H->L[l];
+  const int Np = H->Np;
+  free(L->pptr);
+  free(L->pblk);
+  free(L->poff);
+  free(L->pchol);
+  free(L->pscale);
+  L->pptr = NULL;
+  L->pblk = NULL;
+  L->poff = NULL;
+  L->pchol = NULL;
+  L->pscale = NULL;
+  L->npatch = 0;
+  if (npatch > 0) {
+    const int64_t tot = pptr[npatch];
+    int* cnt = (int*)calloc(L->nb, sizeof(int));
+    for (int64_t k = 0; k < tot; ++k) {
+      if (pblk[k] < 0 || pblk[k] >= L->nb) {
+        free(cnt);
+        return -1;
+      }
+      cnt[pblk[k]]++;
+    }
+    for (int64_t i = 0; i < L->nb; ++i)
+      if (cnt[i] == 0) {
+        free(cnt);
+        return -1;
+      }
+    L->pptr = (int64_t*)malloc(sizeof(int64_t) * (npatch + 1));
+    L->pblk = (int32_t*)malloc(sizeof(int32_t) * (tot > 0 ? tot : 1));
+    L->poff = (int64_t*)malloc(sizeof(int64_t) * (npatch + 1));
+    memcpy(L->pptr, pptr, sizeof(int64_t) * (npatch + 1));
+    memcpy(L->pblk, pblk, sizeof(int32_t) * tot);
+    L->poff[0] = 0;
+    for (int64_t p = 0; p < npatch; ++p) {
+      const int64_t m = (pptr[p + 1] - pptr[p]) * Np;
+      L->poff[p + 1] = L->poff[p] + m * m;
+    }
+    L->pchol = (double*)malloc(sizeof(double) * (L->poff[npatch] > 0 ? L->poff[npatch] : 1));
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic) reduction(| : bad)
+    for (int64_t p = 0; p < npatch; ++p) {
+      const int64_t nbp = pptr[p + 1] - pptr[p];
+      double* A = L->pchol + L->poff[p];
+      gather_patch(L, Np, nbp, pblk + pptr[p], A);
+      if (chol(nbp * Np, A)) bad |= 1;
+    }
+    L->pscale = (double*)malloc(sizeof(double) * L->nb);
+    for (int64_t i = 0; i < L->nb; ++i) L->pscale[i] = 1.0 / sqrt((double)cnt[i]);
+    free(cnt);
+    L->npatch = npatch;
+    L->pmode = 1;
+    if (bad) return -2;
+    L->lmax = lambda_max_swz(L, Np, lanczos_steps);
+    if (mode == 0)
+      for (int64_t i = 0; i < L->nb; ++i) L->pscale[i] *= L->pscale[i];
+    L->pmode = mode;
+  } else {
+    L->lmax = lambda_max(L, Np, lanczos_steps);
+  }
+  L->omega = omega_fixed > 0 ? omega_fixed : 4.0 / (3.0 * L->lmax);
+  return 0;
+}
+
+/* z = Swz(r) on level l with the patches of or_hier_set_patches (undamped) */
+void or_schwarz(void* h, int l, const double* r, double* z) {
+  or_hier* H = (or_hier*)h;
+  swz_apply(&H->L[l], H->Np, r, z);
+}

@@ -73,19 +73,25 @@ double ms_since(clk::time_point t0) {
 constexpr int kPartials = 4096;
 
 // One full wave: the grid-stride kernels get at most (resident CTAs per SM) x SMs CTAs, so that
-// no partial second wave of CTAs runs at the end of a launch (occupancy queried once per kernel).
+// no partial second wave of CTAs runs at the end of a launch (occupancy queried once per kernel
+// and device: the cap is kept per (kernel, device ordinal), so GPUs of different models in one
+// process each get their own).
 int wave_cap(const void* k) {
   static std::mutex mu;
-  static std::vector<std::pair<const void*, int>> cache;
-  std::lock_guard<std::mutex> lock(mu);
-  for (auto& e : cache)
-    if (e.first == k) return e.second;
+  struct Entry {
+    const void* k;
+    int dev, cap;
+  };
+  static std::vector<Entry> cache;
   int dev = 0, sms = 152, occ = 0;
   cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  for (auto& e : cache)
+    if (e.k == k && e.dev == dev) return e.cap;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kThreads, 0) != cudaSuccess || occ < 1) occ = 1;
   const int cap = occ * sms;
-  cache.emplace_back(k, cap);
+  cache.push_back(Entry{k, dev, cap});
   return cap;
 }
 inline int fit_grid(const void* k, int grid) { return std::max(1, std::min(grid, wave_cap(k))); }

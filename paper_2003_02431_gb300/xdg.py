@@ -592,23 +592,47 @@ class Mlp:
 
 def restrict_noalloc(Np, nb_fine, nb_coarse, row_ptr, col, val, R, child_ptr, child, b, x, rc, stream=None):
     """rc = R^T (b - M x) from caller-owned device tensors, with no allocation in the library
-    (see xdg_restrict_noalloc in include/xdg.h: fixed 8 MiB scratch, calls must not overlap).
-    row_ptr/child_ptr int64, col/child int32, the rest float64 CUDA tensors; x may be None."""
+    (xdg_restrict_noalloc: fixed 8 MiB scratch, calls must not overlap on one GPU).
+    row_ptr/child_ptr int64, col/child int32, the rest float64 CUDA tensors on the current
+    device; x may be None. The C entry point cannot see the length of a device array, so every
+    length is checked here, from tensor metadata and two scalar reads (row_ptr[nb_fine] and
+    child_ptr[nb_coarse]), before anything is enqueued: a short array would make the kernels
+    read or write past its end. Raises ValueError on a mismatch."""
     torch = _torch()
+    cur = torch.cuda.current_device()
     if stream is None:
         stream = torch.cuda.current_stream()
+    if stream.device.index != cur:
+        raise ValueError("the stream must belong to the current device (cuda:%d)" % cur)
+    Np, nb_fine, nb_coarse = int(Np), int(nb_fine), int(nb_coarse)
+    if nb_fine <= 0 or nb_coarse <= 0:
+        raise ValueError("nb_fine and nb_coarse must be positive")
 
-    def p(t, dt):
+    def p(t, dt, n, name):
         if t is None:
             return None
         if not (t.is_cuda and t.is_contiguous() and t.dtype == dt):
-            raise ValueError("expected a contiguous CUDA tensor of %s" % dt)
+            raise ValueError("%s: expected a contiguous CUDA tensor of %s" % (name, dt))
+        if t.device.index != cur:
+            raise ValueError("%s: on cuda:%d, not on the current device cuda:%d" % (name, t.device.index, cur))
+        if t.numel() < n:
+            raise ValueError("%s: %d entries, at least %d needed" % (name, t.numel(), n))
         return C.c_void_p(t.data_ptr())
 
     f64, i64, i32 = torch.float64, torch.int64, torch.int32
-    _check(load().xdg_restrict_noalloc(Np, nb_fine, nb_coarse, p(row_ptr, i64), p(col, i32), p(val, f64),
-                                       p(R, f64), p(child_ptr, i64), p(child, i32), p(b, f64), p(x, f64),
-                                       p(rc, f64), C.c_void_p(stream.cuda_stream)))
+    nf, nc = nb_fine * Np, nb_coarse * Np
+    args = [p(row_ptr, i64, nb_fine + 1, "row_ptr"), p(col, i32, 1, "col"), p(val, f64, 0, "val"),
+            p(R, f64, nf * Np, "R"), p(child_ptr, i64, nb_coarse + 1, "child_ptr"), p(child, i32, nb_fine, "child"),
+            p(b, f64, nf, "b"), p(x, f64, nf, "x"), p(rc, f64, nc, "rc")]
+    if None in args[:7] or args[8] is None:
+        raise ValueError("only x may be None")
+    nnzb = int(row_ptr[nb_fine].item())
+    if nnzb < 0 or nnzb > col.numel() or val.numel() < nnzb * Np * Np:
+        raise ValueError("row_ptr[nb_fine] = %d does not fit col (%d) and val (%d entries)"
+                         % (nnzb, col.numel(), val.numel()))
+    if int(child_ptr[nb_coarse].item()) != nb_fine:
+        raise ValueError("child_ptr[nb_coarse] must equal nb_fine (every fine block is one child)")
+    _check(load().xdg_restrict_noalloc(Np, nb_fine, nb_coarse, *args, C.c_void_p(stream.cuda_stream)))
 
 
 # C-name aliases

@@ -172,6 +172,21 @@ def test_mesh_independent_iterations_2d():
     assert max(its) <= 1.25 * min(its), its
 
 
+def test_mesh_independent_iterations_3d():
+    # sec. 4: the iteration counts of the multigrid solvers stay nearly independent of the mesh.
+    # The 3D workload (sphere R = 0.31, mu 1:1000, k = 2, W-cycle on the two finest levels) at
+    # N = 16, 24, 32: the counts move with how the sphere cuts each mesh (56, 48, 56), so the
+    # pin is a bounded spread and no growth from the coarsest to the finest mesh, not +-2.
+    its = []
+    for N in (16, 24, 32):
+        P = xp.Problem(xp.config_3d_64(N=N, max_coarse_dof=1000))
+        H = oracle.Hierarchy(P, gamma=2)
+        oracle.set_w_levels(H, 2)
+        its.append(H.pcg(P.b, tol=1e-10, maxit=400)[1])
+    assert max(its) <= 1.2 * min(its), its
+    assert its[-1] <= its[0] + 2, its
+
+
 def test_quantized_storage_rounding():
     # FP32 storage: entry/scale rounded to float; BF16: further rounded to bfloat16 with ties to
     # even -- checked against torch's float32 -> bfloat16 conversion

@@ -208,6 +208,38 @@ class Problem:
             "cut": np.ctypeslib.as_array(L.xp_level_cut(self._h, level), shape=(n,)).copy(),
         }
 
+    def schwarz_patches(self, level: int = 1, offset: int = 0, species: str = "both"):
+        """Patches of the additive Schwarz smoother on `level` from the background mesh: the
+        blocks whose representative cell lies in one group of 2 cells per direction, groups
+        shifted by `offset` cells (0 or 1; with 1 the boundary groups hold one cell in that
+        direction), both species together (species="both") or one patch per species
+        ("each"). Returns (ptr int64[n+1], blocks int32[ptr[n]]), blocks ascending in a patch,
+        patches ordered by group then species."""
+        meta = self.level_meta(level)
+        rep, spc = meta["rep"].astype(np.int64), meta["species"].astype(np.int64)
+        N, D = self.cfg.N, self.D
+        idx = [(rep // N ** d) % N for d in range(D)]
+        G = N // 2 + 1
+        key = np.zeros_like(rep)
+        for d in reversed(range(D)):
+            key = key * G + (idx[d] + offset) // 2
+        if species == "each":
+            key = key * 2 + spc
+        order = np.lexsort((np.arange(len(rep)), key))
+        k_sorted = key[order]
+        starts = np.flatnonzero(np.r_[True, k_sorted[1:] != k_sorted[:-1]])
+        ptr = np.r_[starts, len(order)].astype(np.int64)
+        return ptr, order.astype(np.int32)
+
+    def aggregate_patches(self, level: int = 1):
+        """Patches = the children of every block of the next level (the aggregates of the
+        aggregation sequence, one species each): (ptr, blocks) as in schwarz_patches."""
+        agg = np.asarray(self.agg[level - 1])
+        order = np.argsort(agg, kind="stable")
+        ptr = np.zeros(self.nb[level] + 1, dtype=np.int64)
+        np.add.at(ptr, agg + 1, 1)
+        return np.cumsum(ptr), order.astype(np.int32)
+
     @property
     def dof(self) -> int:
         return self.nb[0] * self.Np
