@@ -219,7 +219,13 @@ class Problem:
         rep, spc = meta["rep"].astype(np.int64), meta["species"].astype(np.int64)
         N, D = self.cfg.N, self.D
         idx = [(rep // N ** d) % N for d in range(D)]
-        G = N // 2 + 1
+        # cell coordinates on the level's Cartesian mesh: 2 cells per direction merge per
+        # level, an odd trailing cell joining the last group
+        n = N
+        for _ in range(level - 1):
+            idx = [np.minimum(c // 2, max(n // 2 - 1, 0)) for c in idx]
+            n = max(n // 2, 1)
+        G = n // 2 + 1
         key = np.zeros_like(rep)
         for d in reversed(range(D)):
             key = key * G + (idx[d] + offset) // 2
