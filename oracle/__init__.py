@@ -220,6 +220,38 @@ class Hierarchy:
         it = self._L.or_pcg(self._h, _p(b, _dp), _p(x, _dp), tol, maxit, C.byref(rr), _p(hist, _dp))
         return x, it, rr.value, hist[:it + 1]
 
+    def orthomg(self, b, x0=None, tol=1e-10, maxit=500, restart=30):
+        """Orthonormalisation multigrid (Algorithm OrthoMG with Algorithm ResMinimi) on the
+        finest level; the finest level's search space restarts after `restart` directions.
+        Returns (x, passes, true relative residual, residual history)."""
+        L = self._L
+        if not hasattr(L, "_omg_set"):
+            L.or_orthomg.restype = C.c_int
+            L.or_orthomg.argtypes = [C.c_void_p, _dp, _dp, C.c_double, C.c_int, C.c_int, _dp, _dp]
+            L._omg_set = True
+        b = _f64(b).reshape(-1)
+        x = np.zeros_like(b) if x0 is None else _f64(x0).reshape(-1).copy()
+        rr = C.c_double()
+        hist = np.zeros(maxit + 1)
+        it = L.or_orthomg(self._h, _p(b, _dp), _p(x, _dp), tol, maxit, restart, C.byref(rr), _p(hist, _dp))
+        return x, it, rr.value, hist[:it + 1]
+
+    def rm_steps(self, level, zs, b, x0):
+        """Algorithm ResMinimi applied k times on `level` with the raw directions zs (k, n) from
+        x0: returns (x, r, W (k, n), Z (k, n))."""
+        L = self._L
+        if not hasattr(L, "_rm_set"):
+            L.or_rm_steps.argtypes = [C.c_void_p, C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+            L._rm_set = True
+        zs = _f64(zs)
+        k, n = zs.shape
+        b, x0 = _f64(b).reshape(-1), _f64(x0).reshape(-1)
+        x, r = np.empty(n), np.empty(n)
+        W, Z = np.empty((k, n)), np.empty((k, n))
+        L.or_rm_steps(self._h, level, k, _p(zs, _dp), _p(b, _dp), _p(x0, _dp), _p(x, _dp), _p(r, _dp),
+                      _p(W, _dp), _p(Z, _dp))
+        return x, r, W, Z
+
     def close(self):
         if getattr(self, "_h", None):
             self._L.or_hier_free(self._h)
@@ -245,6 +277,13 @@ def quantize_blocks(blocks, prec):
     sc = np.empty(nblk, dtype=np.float32)
     L.or_quantize_blocks(nblk, np2, prec, _p(a, _dp), _p(out, _dp), sc.ctypes.data_as(C.POINTER(C.c_float)))
     return out, sc
+
+
+def set_orthomg_passes(passes: int) -> None:
+    """Passes of Algorithm OrthoMG on every coarse level (1 = one pass per visit, 2 = K-cycle)."""
+    L = _load()
+    L.or_set_orthomg_passes.argtypes = [C.c_int]
+    L.or_set_orthomg_passes(int(passes))
 
 
 def set_threads(n: int) -> int:

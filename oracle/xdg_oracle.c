@@ -812,3 +812,222 @@ void or_schwarz(void* h, int l, const double* r, double* z) {
   or_hier* H = (or_hier*)h;
   swz_apply(&H->L[l], H->Np, r, z);
 }
+
+/* ---------------- orthonormalisation multigrid (Algorithms ResMinimi and OrthoMG) ---------------- */
+
+/* Search space of a residual minimisation on one level: Z = (z_1..z_l), W = M Z with orthonormal
+ * columns, and the coefficients alpha_i = w_i . r_0. */
+typedef struct {
+  int64_t n;
+  int cap, l;
+  double *W, *Z, *alpha;
+} or_rm_space;
+
+static void rm_init(or_rm_space* S, int64_t n, int cap) {
+  S->n = n;
+  S->cap = cap;
+  S->l = 0;
+  S->W = (double*)malloc(sizeof(double) * n * cap);
+  S->Z = (double*)malloc(sizeof(double) * n * cap);
+  S->alpha = (double*)malloc(sizeof(double) * cap);
+}
+
+static void rm_free(or_rm_space* S) {
+  free(S->W);
+  free(S->Z);
+  free(S->alpha);
+}
+
+/* Algorithm ResMinimi: (x, r) = RM(x0, z, W, Z) on level `lev`. z is overwritten. The new
+ * direction w = M z is orthogonalised against the columns of W one after another (the loop of
+ * the algorithm: beta from the partly orthogonalised w), z follows with the same coefficients,
+ * both are normalised by gamma = 1/|w| and appended; alpha_{l+1} = w . r0; then
+ * x = x0 + Z alpha and r = r0 - W alpha. A direction that is numerically dependent on W
+ * (|w| <= 1e-14 |M z| after the loop; the algorithm leaves this case open) is appended as a
+ * zero column with alpha 0, which leaves x and r unchanged. */
+static void rm_step(or_hier* H, int lev, or_rm_space* S, const double* x0, const double* r0, double* z,
+                    double* x, double* r) {
+  or_level* L = &H->L[lev];
+  const int Np = H->Np;
+  const int64_t n = S->n;
+  if (S->l >= S->cap) return;
+  double* w = S->W + (int64_t)S->l * n;
+  or_bsr_spmv(L->nb, Np, L->rp, L->col, L->val, z, w);
+  const double w0 = sqrt(dot(n, w, w));
+  for (int i = 0; i < S->l; ++i) {
+    const double* wi = S->W + (int64_t)i * n;
+    const double* zi = S->Z + (int64_t)i * n;
+    const double beta = dot(n, wi, w);
+    for (int64_t k = 0; k < n; ++k) {
+      w[k] -= beta * wi[k];
+      z[k] -= beta * zi[k];
+    }
+  }
+  const double nw = sqrt(dot(n, w, w));
+  const double gamma = (nw > 1e-14 * w0) ? 1.0 / nw : 0.0;
+  double* zn = S->Z + (int64_t)S->l * n;
+  for (int64_t k = 0; k < n; ++k) {
+    w[k] *= gamma;
+    zn[k] = gamma * z[k];
+  }
+  S->alpha[S->l] = dot(n, w, r0);
+  S->l++;
+  for (int64_t k = 0; k < n; ++k) {
+    double xs = x0[k], rs = r0[k];
+    for (int i = 0; i < S->l; ++i) {
+      xs += S->Z[(int64_t)i * n + k] * S->alpha[i];
+      rs -= S->W[(int64_t)i * n + k] * S->alpha[i];
+    }
+    x[k] = xs;
+    r[k] = rs;
+  }
+}
+
+/* the smoother of Algorithm OrthoMG on a level: Swz (patches) or block Jacobi, undamped (the
+ * residual minimisation picks the step length) */
+static void omg_smoother(or_hier* H, int lev, const double* r, double* z) {
+  smoother_apply(&H->L[lev], H->Np, r, z);
+}
+
+static int g_omg_passes = 1; /* passes of Algorithm OrthoMG on every coarse level */
+
+/* Algorithm OrthoMG on a coarse level (x0 = 0, right-hand side b): `g_omg_passes` passes of
+ * pre-smoother, RM, restriction, MG on the next level, prolongation, RM, post-smoother, RM, one
+ * search space for all of them. On the coarsest level: the direct solve. x receives the result. */
+static void omg_level(or_hier* H, int lev, const double* b, double* x) {
+  const int Np = H->Np;
+  or_level* L = &H->L[lev];
+  const int64_t n = L->nb * Np;
+  if (lev == H->nlev - 1) {
+    chol_solve(H->nc, H->cchol, b, x);
+    return;
+  }
+  or_level* C = &H->L[lev + 1];
+  const int64_t nc = C->nb * Np;
+  or_rm_space S;
+  rm_init(&S, n, 3 * g_omg_passes);
+  double* x0 = (double*)calloc(n, sizeof(double));
+  double* r = (double*)malloc(sizeof(double) * n);
+  double* z = (double*)malloc(sizeof(double) * n);
+  double* rc = (double*)malloc(sizeof(double) * nc);
+  double* zc = (double*)malloc(sizeof(double) * nc);
+  memcpy(r, b, sizeof(double) * n); /* r0 = b - M 0 */
+  memset(x, 0, sizeof(double) * n);
+  for (int pass = 0; pass < g_omg_passes; ++pass) {
+    omg_smoother(H, lev, r, z);
+    rm_step(H, lev, &S, x0, b, z, x, r);
+    or_restrict(L->nb, C->nb, Np, L->agg, L->R, r, rc);
+    omg_level(H, lev + 1, rc, zc);
+    memset(z, 0, sizeof(double) * n);
+    or_prolong(L->nb, Np, L->agg, L->R, zc, z);
+    rm_step(H, lev, &S, x0, b, z, x, r);
+    omg_smoother(H, lev, r, z);
+    rm_step(H, lev, &S, x0, b, z, x, r);
+  }
+  rm_free(&S);
+  free(x0);
+  free(r);
+  free(z);
+  free(rc);
+  free(zc);
+}
+
+/* Algorithm OrthoMG on the finest level: x holds x0 on entry. Passes of (pre-smoother, RM,
+ * coarse correction by one OrthoMG pass per coarser level, RM, post-smoother, RM) while
+ * |r| > tol |b|, at most maxit passes. The search space of the finest level keeps every
+ * direction up to `restart` columns; then x0 := x, r0 := r and the space starts empty again.
+ * hist (optional, maxit+1 entries): |r|/|b| after each pass (hist[0]: initial).
+ * Returns the passes made; *relres = the final |b - M x| / |b| (recomputed). */
+int or_orthomg(void* h, const double* b, double* x, double tol, int maxit, int restart, double* relres,
+               double* hist) {
+  or_hier* H = (or_hier*)h;
+  const int Np = H->Np;
+  or_level* L = &H->L[0];
+  const int64_t n = L->nb * Np;
+  if (restart < 3) restart = 3;
+  restart -= restart % 3;
+  double* x0 = (double*)malloc(sizeof(double) * n);
+  double* r0 = (double*)malloc(sizeof(double) * n);
+  double* r = (double*)malloc(sizeof(double) * n);
+  double* z = (double*)malloc(sizeof(double) * n);
+  double bn = sqrt(dot(n, b, b));
+  if (bn == 0.0) bn = 1.0;
+  or_residual(L->nb, Np, L->rp, L->col, L->val, b, x, r0);
+  memcpy(x0, x, sizeof(double) * n);
+  memcpy(r, r0, sizeof(double) * n);
+  double rn = sqrt(dot(n, r, r));
+  if (hist) hist[0] = rn / bn;
+  int it = 0;
+  if (H->nlev == 1) { /* a single level: the direct solve */
+    double* e = (double*)malloc(sizeof(double) * n);
+    chol_solve(H->nc, H->cchol, r0, e);
+    for (int64_t k = 0; k < n; ++k) x[k] += e[k];
+    free(e);
+    it = 1;
+  } else {
+    or_level* C = &H->L[1];
+    const int64_t nc = C->nb * Np;
+    double* rc = (double*)malloc(sizeof(double) * nc);
+    double* zc = (double*)malloc(sizeof(double) * nc);
+    or_rm_space S;
+    rm_init(&S, n, restart);
+    while (rn / bn > tol && it < maxit) {
+      if (S.l + 3 > S.cap) { /* restart: the current iterate becomes x0 */
+        memcpy(x0, x, sizeof(double) * n);
+        memcpy(r0, r, sizeof(double) * n);
+        S.l = 0;
+      }
+      omg_smoother(H, 0, r, z);
+      rm_step(H, 0, &S, x0, r0, z, x, r);
+      or_restrict(L->nb, C->nb, Np, L->agg, L->R, r, rc);
+      omg_level(H, 1, rc, zc);
+      memset(z, 0, sizeof(double) * n);
+      or_prolong(L->nb, Np, L->agg, L->R, zc, z);
+      rm_step(H, 0, &S, x0, r0, z, x, r);
+      omg_smoother(H, 0, r, z);
+      rm_step(H, 0, &S, x0, r0, z, x, r);
+      rn = sqrt(dot(n, r, r));
+      ++it;
+      if (hist) hist[it] = rn / bn;
+    }
+    rm_free(&S);
+    free(rc);
+    free(zc);
+  }
+  or_residual(L->nb, Np, L->rp, L->col, L->val, b, x, r);
+  *relres = sqrt(dot(n, r, r)) / bn;
+  free(x0);
+  free(r0);
+  free(r);
+  free(z);
+  return it;
+}
+
+/* passes of Algorithm OrthoMG on each coarse level (1: one pass per visit; 2: a K-cycle) */
+void or_set_orthomg_passes(int passes) { g_omg_passes = passes < 1 ? 1 : passes; }
+
+/* Test access to Algorithm ResMinimi on level `lev`: k steps with the raw directions
+ * zin[j*n .. j*n+n-1] (j = 0..k-1) from x0 (r0 = b - M x0); outputs x, r and the final W, Z
+ * (k columns each, n x k column-major: column j at j*n). */
+void or_rm_steps(void* h, int lev, int k, const double* zin, const double* b, const double* x0, double* x,
+                 double* r, double* Wout, double* Zout) {
+  or_hier* H = (or_hier*)h;
+  or_level* L = &H->L[lev];
+  const int64_t n = L->nb * H->Np;
+  or_rm_space S;
+  rm_init(&S, n, k);
+  double* r0 = (double*)malloc(sizeof(double) * n);
+  double* z = (double*)malloc(sizeof(double) * n);
+  or_residual(L->nb, H->Np, L->rp, L->col, L->val, b, x0, r0);
+  memcpy(x, x0, sizeof(double) * n);
+  memcpy(r, r0, sizeof(double) * n);
+  for (int j = 0; j < k; ++j) {
+    memcpy(z, zin + (int64_t)j * n, sizeof(double) * n);
+    rm_step(H, lev, &S, x0, r0, z, x, r);
+  }
+  memcpy(Wout, S.W, sizeof(double) * n * k);
+  memcpy(Zout, S.Z, sizeof(double) * n * k);
+  rm_free(&S);
+  free(r0);
+  free(z);
+}
