@@ -252,6 +252,25 @@ class Hierarchy:
                       _p(W, _dp), _p(Z, _dp))
         return x, r, W, Z
 
+    def pmg(self, level, n_lo, b, blocks=None):
+        """Algorithm pMultigrid on `level` (0-based) with n_lo low-order modes per block, over the
+        given block subset (None: every block): x = PMG(b, k_lo, I)."""
+        L = self._L
+        if not hasattr(L, "_pmg_set"):
+            L.or_pmg.restype = C.c_int
+            L.or_pmg.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int64, _i32p, _dp, _dp]
+            L._pmg_set = True
+        b = _f64(b).reshape(-1)
+        x = np.empty_like(b)
+        if blocks is None:
+            rc = L.or_pmg(self._h, level, n_lo, -1, None, _p(b, _dp), _p(x, _dp))
+        else:
+            blk = np.ascontiguousarray(blocks, np.int32)
+            rc = L.or_pmg(self._h, level, n_lo, len(blk), _p(blk, _i32p), _p(b, _dp), _p(x, _dp))
+        if rc != 0:
+            raise RuntimeError("oracle PMG: a system is not positive definite")
+        return x
+
     def close(self):
         if getattr(self, "_h", None):
             self._L.or_hier_free(self._h)

@@ -1031,3 +1031,87 @@ void or_rm_steps(void* h, int lev, int k, const double* zin, const double* b, co
   free(r0);
   free(z);
 }
+
+/* ---------------- p-multigrid (Algorithm pMultigrid) ---------------- */
+
+/* PMG(b, k_lo, I) on level `lev`: the blocks I[0..nI-1] (ascending; nI < 0: every block), the
+ * first n_lo modes of each block form the low-order set (the modes are graded by degree, so
+ * they span the polynomials up to degree k_lo). Steps in the algorithm's order: x := 0; the
+ * low-order system M_lo = M[I_lo, I_lo] solved directly (dense Cholesky here) with b[I_lo] and
+ * added to x; r := b - M x; for every block j of I the high-order system M[I_hi,j, I_hi,j] solved
+ * directly with r[I_hi,j] (reading the printed b_hi,j as the residual r of the line before) and
+ * added to x. x has the level's length; entries outside I are zero. Returns 0, or -1 when a
+ * system is not positive definite. */
+int or_pmg(void* h, int lev, int n_lo, int64_t nI, const int32_t* I, const double* b, double* x) {
+  or_hier* H = (or_hier*)h;
+  or_level* L = &H->L[lev];
+  const int Np = H->Np;
+  const int64_t Np2 = (int64_t)Np * Np, n = L->nb * Np;
+  const int nhi = Np - n_lo;
+  int32_t* all = NULL;
+  if (nI < 0) {
+    nI = L->nb;
+    all = (int32_t*)malloc(sizeof(int32_t) * nI);
+    for (int64_t i = 0; i < nI; ++i) all[i] = (int32_t)i;
+    I = all;
+  }
+  /* position of every block in I (-1: not in I) */
+  int64_t* pos = (int64_t*)malloc(sizeof(int64_t) * L->nb);
+  for (int64_t i = 0; i < L->nb; ++i) pos[i] = -1;
+  for (int64_t a = 0; a < nI; ++a) pos[I[a]] = a;
+  for (int64_t k = 0; k < n; ++k) x[k] = 0.0;
+  int rc = 0;
+  /* low-order system */
+  const int64_t m = nI * n_lo;
+  double* A = (double*)calloc((size_t)m * m, sizeof(double));
+  double* bl = (double*)malloc(sizeof(double) * (m > 0 ? m : 1));
+  double* xl = (double*)malloc(sizeof(double) * (m > 0 ? m : 1));
+  for (int64_t a = 0; a < nI; ++a) {
+    const int64_t i = I[a];
+    for (int64_t z = L->rp[i]; z < L->rp[i + 1]; ++z) {
+      const int64_t c = pos[L->col[z]];
+      if (c < 0) continue;
+      for (int r = 0; r < n_lo; ++r)
+        for (int q = 0; q < n_lo; ++q) A[(a * n_lo + r) * m + c * n_lo + q] = L->val[z * Np2 + r * Np + q];
+    }
+    for (int r = 0; r < n_lo; ++r) bl[a * n_lo + r] = b[i * Np + r];
+  }
+  if (m > 0) {
+    if (chol(m, A)) rc = -1;
+    else chol_solve(m, A, bl, xl);
+  }
+  if (rc == 0)
+    for (int64_t a = 0; a < nI; ++a)
+      for (int r = 0; r < n_lo; ++r) x[(int64_t)I[a] * Np + r] += xl[a * n_lo + r];
+  /* residual and the cell-local high-order systems */
+  double* res = (double*)malloc(sizeof(double) * n);
+  or_residual(L->nb, Np, L->rp, L->col, L->val, b, x, res);
+  double* D = (double*)malloc(sizeof(double) * (nhi > 0 ? nhi * nhi : 1));
+  double* bh = (double*)malloc(sizeof(double) * (nhi > 0 ? nhi : 1));
+  double* xh = (double*)malloc(sizeof(double) * (nhi > 0 ? nhi : 1));
+  for (int64_t a = 0; rc == 0 && a < nI && nhi > 0; ++a) {
+    const int64_t j = I[a];
+    int64_t z = L->rp[j];
+    while (z < L->rp[j + 1] && L->col[z] != j) ++z;
+    for (int r = 0; r < nhi; ++r) {
+      for (int q = 0; q < nhi; ++q) D[r * nhi + q] = L->val[z * Np2 + (n_lo + r) * Np + n_lo + q];
+      bh[r] = res[j * Np + n_lo + r];
+    }
+    if (chol(nhi, D)) {
+      rc = -1;
+      break;
+    }
+    chol_solve(nhi, D, bh, xh);
+    for (int r = 0; r < nhi; ++r) x[j * Np + n_lo + r] += xh[r];
+  }
+  free(A);
+  free(bl);
+  free(xl);
+  free(res);
+  free(D);
+  free(bh);
+  free(xh);
+  free(pos);
+  free(all);
+  return rc;
+}
