@@ -381,6 +381,232 @@ def learned_section(xdg, torch, dev, stream, n_train=4):
     return out
 
 
+C3_SEED = 20030243
+C3_STEPS = 3
+
+
+def c3_config():
+    """Mixed-precision workload: 96^3, sphere radius = first draw of U(0.25, 0.4) from numpy
+    PCG64(20030243), mu 1:1000, k = 3 (Np = 20), about 18 million DOF."""
+    import xdg_problem as xp
+    rng = np.random.Generator(np.random.PCG64(C3_SEED))
+    R = float(rng.uniform(0.25, 0.4))
+    return xp.config_3d_64(N=96, k=3, R=R, max_coarse_dof=2048), R
+
+
+def staggered_patches(P, level):
+    """Schwarz patches of a level: the 2-cells-per-direction groups of its mesh and the same
+    groups shifted by one cell (every block in two patches)."""
+    a = P.schwarz_patches(level, 0)
+    b = P.schwarz_patches(level, 1)
+    return np.r_[a[0], a[0][-1] + b[0][1:]], np.r_[a[1], b[1]]
+
+
+def c3_section(xdg, torch, dev, stream, P, R, gen_s, steps, with_oracle):
+    """C3 (96^3, k = 3): FP32-cycle, BF16-transfer and FP64 solves to TOL (one warm-up, `steps`
+    timed solves each), V-cycle rates, the level-1 pair apply against the HBM roofline. The
+    solutions are compared with the FP64 GPU solve, and with the oracle's when asked (the
+    oracle's solve at this size takes minutes on the host cores)."""
+    n = P.dof
+    t = time.perf_counter()
+    H = xdg.Hierarchy.from_problem(P, gamma=GAMMA, w_levels=W_LEVELS, low_precision=3, stream=stream)
+    setup_s = time.perf_counter() - t
+    hinfo = H.info()
+    b = torch.from_numpy(P.b.reshape(-1).copy()).to(dev)
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"workload": "xdg-poisson-3d-96^3-k3-sphere-R%.4f-mu1:1000 (seed %d)" % (R, C3_SEED), "dof": n,
+           "blocks": P.nb[0], "nnz_blocks": int(P.row_ptr[-1]), "Np": P.Np, "levels": hinfo["nb"],
+           "generate_s": gen_s, "setup_s": setup_s, "device_gb": hinfo["device_bytes"] / 1e9, "paths": {}}
+    sols = {}
+    for key, prec in (("mixed_f32", xdg.XDG_PREC_F32), ("mixed_bf16_transfers", xdg.XDG_PREC_BF16),
+                      ("plain_f64", xdg.XDG_PREC_F64)):
+        x.zero_()
+        H.solve(b, x, tol=TOL, maxit=1000, precision=prec)
+        torch.cuda.synchronize()
+        its = []
+        ev0.record(stream)
+        for _ in range(steps):
+            x.zero_()
+            its.append(H.solve(b, x, tol=TOL, maxit=1000, precision=prec)["iterations"])
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        sols[key] = x.cpu().numpy()
+        out["paths"][key] = {"solve_ms": ms, "iterations": its, "mdofs": n / ms / 1e3}
+    for key in ("mixed_f32", "mixed_bf16_transfers"):
+        out["paths"][key]["rel_l2_vs_fp64_gpu"] = rel_l2(sols[key], sols["plain_f64"])
+    out["speedup_mixed_vs_f64"] = out["paths"]["plain_f64"]["solve_ms"] / out["paths"]["mixed_f32"]["solve_ms"]
+    if with_oracle:
+        xref = oracle_solution(P, tol=1e-12)[0]
+        for key in sols:
+            out["paths"][key]["rel_l2_vs_oracle"] = rel_l2(sols[key], xref)
+    hbm, hbm_kind = hbm_peak()
+    if hinfo["outer_pair"]:
+        ms, by = H.kernel_time(H.KERNEL_APPLY, 1, xdg.XDG_PREC_F64_PAIR, reps=10)
+        name = "k_spmv_dot_df_sym<20>" if hinfo["symmetric_pair"] else "k_spmv_dot_df<20>"
+    else:
+        ms, by = H.kernel_time(H.KERNEL_APPLY, 1, xdg.XDG_PREC_F32, reps=10)
+        name = "k_spmv_lp<20,float,float,0>"
+    ach = by / (ms / 1e3) / 1e9
+    out["roofline"] = {"bound": "hbm", "kernel": name + ": level-1 outer apply of the mixed solve", "achieved": ach,
+                       "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "peak_kind": hbm_kind, "bytes": by, "ms": ms,
+                       "traffic": profiled_traffic(name, 96)}
+    H.destroy()
+    return out
+
+
+def schwarz_section(xdg, torch, dev, stream, P, xref, steps, warmup):
+    """The 64^3 workload with the additive Schwarz smoother (Algorithm Swz, exact patch solves) on
+    the two finest levels, patches = the staggered 2^3-cell groups of each level (every block in
+    two patches): FP32-cycle flexible-CG and FP64 CG solves, iterations and time, against the
+    oracle's solution."""
+    t = time.perf_counter()
+    H = xdg.Hierarchy.from_problem(P, gamma=GAMMA, w_levels=W_LEVELS, low_precision=1, stream=stream)
+    for lv in (1, 2):
+        H.set_schwarz(lv, staggered_patches(P, lv))
+    setup_s = time.perf_counter() - t
+    b = torch.from_numpy(P.b.reshape(-1).copy()).to(dev)
+    x = torch.zeros(P.dof, dtype=torch.float64, device=dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"patches": "levels 1-2: 2-cell groups per direction and the same shifted by one cell (alpha = 2)",
+           "setup_s": setup_s, "levels": {}}
+    for lv in (1, 2):
+        si = H.schwarz_info(lv)
+        out["levels"][lv] = {"patches": si["n_patches"], "distinct_inverses": si["n_distinct"],
+                             "max_dof": si["max_dof"], "device_mb": si["device_bytes"] / 1e6,
+                             "omega": H.info()["omega"][lv - 1]}
+    for key, prec in (("mixed_f32", xdg.XDG_PREC_F32), ("plain_f64", xdg.XDG_PREC_F64)):
+        for _ in range(warmup):
+            x.zero_()
+            H.solve(b, x, tol=TOL, maxit=1000, precision=prec)
+        torch.cuda.synchronize()
+        its = []
+        ev0.record(stream)
+        for _ in range(steps):
+            x.zero_()
+            its.append(H.solve(b, x, tol=TOL, maxit=1000, precision=prec)["iterations"])
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        out[key] = {"solve_ms": ms, "iterations": its, "mdofs": P.dof / ms / 1e3,
+                    "rel_l2_vs_oracle": rel_l2(x.cpu().numpy(), xref)}
+    z = torch.empty_like(x)
+    for _ in range(3):
+        H.cycle(xdg.XDG_PREC_F32, b, z)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(20):
+        H.cycle(xdg.XDG_PREC_F32, b, z)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    out["cycle_f32_ms"] = ev0.elapsed_time(ev1) / 20
+    H.destroy()
+    return out
+
+
+TWIN_CASES = ((2, 16), (2, 32), (2, 64), (3, 16), (3, 32))
+
+
+def paper_dof_table():
+    """(k, N) -> DOF of the performance study's table (tab:DOFs), from the committed fixture."""
+    out = {}
+    with open(os.path.join(ROOT, "tests", "golden", "dof_table.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, N, dof = (int(v) for v in line.split())
+                out[(k, N)] = dof
+    return out
+
+
+TOL_RESMIN = 1e-12  # residual-minimising solvers (GMRES, OrthoMG): cond(M) amplifies the residual
+                    # into the error, 1e-12 keeps them inside the 1e-8 error bound
+
+
+def twin_section(xdg, torch, dev, stream, problems):
+    """The performance study's problem (sec. 4): (-1,1)^3, sphere R = 0.7, mu 1:1000, f = 1,
+    g_D = 0, k = 2 and 3 on N^3 meshes. Per mesh: the DOF count against the paper's table, and
+    the solvers from x = 0, each timed on its second run (the first records graphs): flexible CG
+    with the FP32 W-cycle (block Jacobi; this library's headline solver) to TOL, the
+    orthonormalisation multigrid (Algorithm OrthoMG) with additive Schwarz smoothing (FP32
+    patch inverses) on every level and two passes per coarse visit, and, up to 32^3, flexible
+    GMRES preconditioned by p-multigrid (Algorithm pMultigrid, k_lo = 1) with the low-order
+    system solved to 1e-5 by this library's CG; both to TOL_RESMIN. Solutions compared with the
+    plain FP64 GPU CG solve (to 1e-13)."""
+    table = paper_dof_table()
+    out = {"problem": "(-1,1)^3, sphere R=0.7, mu 1:1000, f=1, g_D=0, alpha=0.1", "cases": []}
+    for (k, N), P in problems:
+        e = {"k": k, "N": N, "dof": P.dof, "dof_paper_table": table.get((k, N)),
+             "dof_matches_table": P.dof == table.get((k, N)), "levels": len(P.nb)}
+        H = xdg.Hierarchy.from_problem(P, gamma=GAMMA, w_levels=W_LEVELS, low_precision=1, stream=stream)
+        b = torch.from_numpy(P.b.reshape(-1).copy()).to(dev)
+        x = torch.zeros(P.dof, dtype=torch.float64, device=dev)
+        H.solve(b, x, tol=1e-13, maxit=3000, precision=xdg.XDG_PREC_F64)
+        xref = x.cpu().numpy()
+
+        def run(tag, fn):
+            for rep in range(2):
+                x.zero_()
+                torch.cuda.synchronize()
+                info = fn()
+            e[tag] = {"iterations": info["iterations"], "ms": info["ms"], "relres": info["relres"],
+                      "converged": info["status"] == xdg.XDG_OK,
+                      "rel_l2_vs_fp64_cg": rel_l2(x.cpu().numpy(), xref)}
+
+        run("cg_f32_wcycle", lambda: H.solve(b, x, tol=TOL, maxit=2000, precision=xdg.XDG_PREC_F32))
+        HO = xdg.Hierarchy.from_problem(P, stream=stream)
+        for lv in range(1, len(P.nb)):
+            HO.set_schwarz(lv, staggered_patches(P, lv))
+        run("orthomg_schwarz", lambda: HO.solve_orthomg(b, x, tol=TOL_RESMIN, maxit=1500, restart=60, coarse_passes=2,
+                                                        smoother_precision=xdg.XDG_PREC_F32, raise_on_error=False))
+        HO.destroy()
+        if N <= 32:
+            H.pmg_setup(4, inner_tol=1e-5, inner_maxit=500)
+            run("gmres_pmg_klo1", lambda: H.solve_gmres(b, x, tol=TOL_RESMIN, maxit=3000, restart=60, preconditioner=1,
+                                                         raise_on_error=False))
+        H.destroy()
+        out["cases"].append(e)
+    return out
+
+
+def solvers_section(xdg, torch, dev, stream, P, xref):
+    """The 64^3 workload with the paper's other solvers, each from x = 0 to TOL_RESMIN, timed on
+    its second run: flexible GMRES with the FP32 W-cycle, flexible GMRES with p-multigrid
+    (Algorithm pMultigrid, k_lo = 1, the low-order system solved to 1e-5 by this library's CG),
+    and the orthonormalisation multigrid (Algorithm OrthoMG with residual minimisation) with
+    additive Schwarz smoothing (FP32 patch inverses) on every level. Against the oracle's
+    solution."""
+    b = torch.from_numpy(P.b.reshape(-1).copy()).to(dev)
+    x = torch.zeros(P.dof, dtype=torch.float64, device=dev)
+    out = {"tol": TOL_RESMIN}
+
+    def run(tag, fn, **extra):
+        for rep in range(2):
+            x.zero_()
+            torch.cuda.synchronize()
+            info = fn()
+        out[tag] = dict({"iterations": info["iterations"], "ms": info["ms"], "relres": info["relres"],
+                         "converged": info["status"] == xdg.XDG_OK, "mdofs": P.dof / info["ms"] / 1e3,
+                         "rel_l2_vs_oracle": rel_l2(x.cpu().numpy(), xref)}, **extra)
+
+    H = xdg.Hierarchy.from_problem(P, gamma=GAMMA, w_levels=W_LEVELS, low_precision=1, stream=stream)
+    run("gmres_f32_wcycle", lambda: H.solve_gmres(b, x, tol=TOL_RESMIN, maxit=1000, restart=60,
+                                                  precision=xdg.XDG_PREC_F32, raise_on_error=False), restart=60)
+    H.pmg_setup(4, inner_tol=1e-5, inner_maxit=500)
+    run("gmres_pmg_klo1", lambda: H.solve_gmres(b, x, tol=TOL_RESMIN, maxit=800, restart=60, preconditioner=1,
+                                                raise_on_error=False),
+        restart=60, inner="CG with the W-cycle on the low-order hierarchy to 1e-5")
+    H.destroy()
+    HO = xdg.Hierarchy.from_problem(P, stream=stream)
+    for lv in range(1, len(P.nb)):
+        HO.set_schwarz(lv, staggered_patches(P, lv))
+    run("orthomg_schwarz", lambda: HO.solve_orthomg(b, x, tol=TOL_RESMIN, maxit=1500, restart=60, coarse_passes=2,
+                                                    smoother_precision=xdg.XDG_PREC_F32, raise_on_error=False),
+        restart=60, coarse_passes=2)
+    HO.destroy()
+    return out
+
+
 def reference_arm(args):
     """The oracle (plain FP64 CPU code) on the same workload: each step is a bounded sample of
     5 PCG iterations, extrapolated with the iteration count of the oracle's full solve."""
@@ -420,6 +646,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 256-problem workload")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-correction section")
+    ap.add_argument("--no-schwarz", action="store_true", help="skip the additive Schwarz section")
+    ap.add_argument("--no-c3", action="store_true", help="skip the 96^3 k=3 mixed-precision workload")
+    ap.add_argument("--no-twin", action="store_true", help="skip the performance-study problem (sec. 4)")
+    ap.add_argument("--no-solvers", action="store_true", help="skip OrthoMG / GMRES / p-multigrid at 64^3")
+    ap.add_argument("--c3-oracle", action="store_true",
+                    help="also compare the 96^3 solutions with the oracle's (minutes of host time)")
     ap.add_argument("--fused-coarse", type=int, default=0, choices=[0, 1, 2],
                     help="small levels of the FP32 cycle as one launch: 0 autotuned, 1 never, 2 always "
                          "(for profiler runs, where the autotuner's timings are distorted)")
@@ -467,6 +699,24 @@ def main():
     t = time.perf_counter()
     xref, it_ref, rr_ref = oracle_solution(P)
     oracle_s = time.perf_counter() - t
+    # the C3 workload is generated on the host cores while the GPU works on this one (the
+    # generator's ctypes call releases the GIL)
+    c3 = {}
+    c3_thread = None
+    if not args.no_c3:
+        import xdg_problem as xp
+
+        def gen_c3():
+            t0 = time.perf_counter()
+            cfg, R = c3_config()
+            c3["P"], c3["R"] = xp.Problem(cfg), R
+            c3["gen_s"] = time.perf_counter() - t0
+            if not args.no_twin:
+                c3["twin"] = [((k, N), xp.Problem(xp.config_paper_twin(N=N, k=k, max_coarse_dof=1000)))
+                              for k, N in TWIN_CASES]
+
+        c3_thread = threading.Thread(target=gen_c3, daemon=True)
+        c3_thread.start()
     t = time.perf_counter()
     H = xdg.Hierarchy.from_problem(P, gamma=GAMMA, w_levels=W_LEVELS, low_precision=3, stream=stream,
                                    fused_coarse=args.fused_coarse, outer_apply=args.outer_apply,
@@ -572,9 +822,29 @@ def main():
         e2e_s = max_over_ranks(e2e_s, dist, dev)
     e2e = job_throughput(world, n, args.steps, e2e_s)
 
+    schwarz = None
+    if not args.no_schwarz:
+        schwarz = schwarz_section(xdg, torch, dev, stream, P, xref, args.steps, warmup)
+
+    solvers = None
+    if not args.no_solvers:
+        solvers = solvers_section(xdg, torch, dev, stream, P, xref)
+
     learned_out = None
     if not args.no_learned:
         learned_out = learned_section(xdg, torch, dev, stream)
+
+    c3_out = None
+    twin = None
+    if c3_thread is not None:
+        c3_thread.join()
+        H.destroy()
+        c3_out = c3_section(xdg, torch, dev, stream, c3["P"], c3["R"], c3["gen_s"], min(args.steps, C3_STEPS),
+                            args.c3_oracle)
+        c3.pop("P")
+        if "twin" in c3:
+            twin = twin_section(xdg, torch, dev, stream, c3.pop("twin"))
+        c3.clear()
 
     batched = None
     if not args.no_batch:
@@ -650,6 +920,10 @@ def main():
             "fp64_fma_probe_tflops": fp64_peak,
             "batched": batched,
             "learned": learned_out,
+            "schwarz": schwarz,
+            "c3_mixed_precision": c3_out,
+            "paper_twin": twin,
+            "other_solvers": solvers,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": "MDOF/s", "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8},
             "gpu_launches": launches,
@@ -658,7 +932,22 @@ def main():
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
-    worst = max(err32, err64, errbf)
+    errs = [err32, err64, errbf]
+    if schwarz:
+        errs += [schwarz["mixed_f32"]["rel_l2_vs_oracle"], schwarz["plain_f64"]["rel_l2_vs_oracle"]]
+    if learned_out:
+        errs += list(learned_out["rel_l2_vs_oracle"].values())
+    if batched:
+        errs += list(batched["parity"]["max_rel_l2_vs_oracle"].values())
+    if c3_out:
+        errs += [v[k] for v in c3_out["paths"].values() for k in ("rel_l2_vs_oracle", "rel_l2_vs_fp64_gpu") if k in v]
+    # other solvers: every solve that reports convergence must meet the bound
+    if solvers:
+        errs += [v["rel_l2_vs_oracle"] for v in solvers.values() if isinstance(v, dict) and v["converged"]]
+    if twin:
+        errs += [v[t]["rel_l2_vs_fp64_cg"] for v in twin["cases"]
+                 for t in ("cg_f32_wcycle", "orthomg_schwarz", "gmres_pmg_klo1") if t in v and v[t]["converged"]]
+    worst = max(errs)
     if worst > PARITY_BOUND:
         print("bench: a timed solution is %.3e from the oracle's (bound %.0e)" % (worst, PARITY_BOUND),
               file=sys.stderr, flush=True)

@@ -197,6 +197,9 @@ int xdg_export_level(xdg_hier_t h, int level, int64_t* row_ptr, int32_t* col, do
  * outer_pair, or outer_apply = 2); x is split into scaled FP32 pairs in the handle's scratch. */
 int xdg_apply(xdg_hier_t h, int level, const double* x, double* y, int prec);
 
+/* r = b - M^level x (FP64, device vectors; r may equal b but not x), Eq. GenericMatrixSystem. */
+int xdg_residual(xdg_hier_t h, int level, const double* b, const double* x, double* r);
+
 /* Set the row mapping of the low-precision kernels on `level` (1-based): on != 0 splits each
  * block row over a warp's groups, 0 gives each group its own row (see
  * xdg_hier_opts.split_rows; creation autotunes it). Records the low-precision solve graphs
@@ -215,9 +218,45 @@ int xdg_set_damping(xdg_hier_t h, int level, double omega);
  * came from (host outputs, either may be NULL). */
 int xdg_get_damping(xdg_hier_t h, int level, int problem, double* omega, double* lambda_max);
 
-/* One damped block-Jacobi step on `level`: x_out = x_in + omega D^{-1} (b - M x_in), the
- * diagonal blocks D solved with their Cholesky factors. x_in == NULL means x_in = 0. x_out
- * must not alias x_in or b. */
+/* Additive Schwarz smoother on `level` (1 <= level < n_levels), Algorithm Swz of sec. 3.3
+ * ("An additive Schwarz method"), in place of block Jacobi. The caller gives the patches (the
+ * sets I_i of the algorithm, here lists of the level's blocks), host arrays: patch i holds the
+ * blocks patch_blocks[patch_ptr[i] .. patch_ptr[i+1]-1], strictly ascending, every block of the
+ * level in at least one patch; patches may overlap; at most 512 / Np blocks per patch.
+ * The block solver is exact: each patch matrix M_{P_i P_i} is factorised (Cholesky, FP64, on
+ * the device) and inverted once; patches with bitwise equal matrices share the inverse (two
+ * 64-bit hashes of the matrix and its size decide). A smoothing step is then
+ *   x_out = x_in + omega S (b - M x_in),
+ *   S r = alpha^{-1/2} .* sum_i E_i M_{P_i P_i}^{-1} E_i^T (alpha^{-1/2} .* r),
+ * alpha = the number of patches holding each block: the algorithm's overlap scaling x ./ alpha,
+ * applied as alpha^{-1/2} on both sides so that the cycle stays symmetric (the two agree when
+ * alpha is the same for every block). The FP32 cycles use FP32 copies of the inverses.
+ * omega = 4 / (3 lambda_max(S M)) from a Lanczos estimate in the M inner product (or the fixed
+ * xdg_hier_opts.omega). Records the solve graphs again; levels at or below the fused small-level
+ * cycle (xdg_hier_opts.fused_coarse) then launch step by step. n_patches = 0 restores block
+ * Jacobi. Single problems only (XDG_EINVAL on a batch group). Allocates device memory for the
+ * patch data (released with the handle or the next call for the level).
+ * Errors: XDG_EINVAL (bad patches), XDG_EBREAKDOWN (a patch matrix not positive definite),
+ * XDG_ENOMEM, XDG_ECUDA. */
+int xdg_set_schwarz(xdg_hier_t h, int level, int64_t n_patches, const int64_t* patch_ptr,
+                    const int32_t* patch_blocks);
+
+typedef struct {
+  int64_t n_patches;       /* 0: the level smooths with block Jacobi */
+  int64_t n_slots;         /* patch memberships (sum of the patch sizes) */
+  int64_t n_distinct;      /* distinct patch matrices (stored inverses) */
+  int64_t inverse_entries; /* entries of the stored inverses (FP64, and again in FP32) */
+  int max_dof;             /* largest patch (modes) */
+  int overlap;             /* 1 when some block lies in more than one patch */
+  size_t device_bytes;     /* device memory of the level's Schwarz data */
+} xdg_schwarz_info;
+
+int xdg_get_schwarz(xdg_hier_t h, int level, xdg_schwarz_info* info);
+
+/* One damped smoothing step on `level`: x_out = x_in + omega D^{-1} (b - M x_in), the
+ * diagonal blocks D solved with their Cholesky factors (block Jacobi), or
+ * x_out = x_in + omega S (b - M x_in) on a level with the Schwarz smoother (xdg_set_schwarz).
+ * x_in == NULL means x_in = 0. x_out must not alias x_in or b. */
 int xdg_smooth(xdg_hier_t h, int level, const double* b, const double* x_in, double* x_out);
 
 /* rc = (R^{X,level})^T (b - M^level x)  (x == NULL: rc = R^T b), level < n_levels. */
@@ -258,6 +297,78 @@ int xdg_cycle(xdg_hier_t h, int prec, const double* b, double* x);
  * product when xdg_hier_info.outer_pair is set. */
 int xdg_solve(xdg_hier_t h, const double* b, double* x, const xdg_solve_opts* o,
               xdg_solve_info* info);
+
+/* Orthonormalisation multigrid, Algorithm OrthoMG of sec. 3.3 with the residual minimisation of
+ * Algorithm ResMinimi: on the finest level, passes of
+ *   z = S r (pre-smoother), RM; r_c = R^T r, z_c = MG(0, r_c) on the next level, z = R z_c, RM;
+ *   z = S r (post-smoother), RM
+ * until ||r||_2 <= tol ||b||_2 or maxit passes. RM(x0, z, W, Z) orthogonalises w = M z against
+ * the stored W (two classical Gram-Schmidt sweeps; in exact arithmetic the algorithm's
+ * sequential loop), normalises w and z by 1/||w||, appends them and sets x = x0 + Z alpha,
+ * r = r0 - W alpha with alpha = W^T r0 (applied one new column at a time), so the residual norm
+ * never grows. S is the level's smoother without damping (RM chooses the step): the Schwarz
+ * preconditioner of xdg_set_schwarz, else block Jacobi D^{-1}. On a coarser level MG(0, r_c)
+ * runs coarse_passes passes from zero with a space of 3 coarse_passes directions (1: one pass
+ * per visit; 2: a K-cycle); the coarsest level is solved directly. Readings of the algorithm:
+ * the smoothers act on the current residual r (the printed Swz(b) with b fixed would add no new
+ * direction), and the finest level keeps at most `restart` directions (then x0 := x,
+ * r0 := b - M x recomputed, the space restarts; also when the updated residual meets the
+ * tolerance but the recomputed one does not). A numerically dependent direction (||w|| <= 1e-14 ||M z|| after the
+ * orthogonalisation) is stored as a zero column and changes nothing. FP64 throughout. b, x
+ * device vectors; x holds x0 on entry. Single problems only. Allocates its work space on the
+ * first call (restart + 6 passes levels' vectors), records one CUDA graph per pass shape, and
+ * reads the residual norm back after every pass. info: iterations = passes. */
+typedef struct {
+  double tol;              /* stop when ||b - M x||_2 <= tol ||b||_2 */
+  int maxit;               /* passes on the finest level */
+  int restart;             /* directions kept on the finest level (>= 3; rounded down to a multiple of 3) */
+  int coarse_passes;       /* passes per coarse-level visit, 1..4 */
+  int smoother_precision;  /* XDG_PREC_F64, or XDG_PREC_F32: the smoothers from the FP32 copies of
+                              their inverses (r rounded to FP32, S r widened; everything else FP64) */
+} xdg_orthomg_opts;
+
+int xdg_solve_orthomg(xdg_hier_t h, const double* b, double* x, const xdg_orthomg_opts* o,
+                      xdg_solve_info* info);
+
+/* p-multigrid on level 1, Algorithm pMultigrid of sec. 3.3, as a preconditioner of GMRES:
+ *   x := 0; x[I_lo] := M_lo^{-1} b[I_lo]; r := b - M x; x[I_hi,j] += M_hi,j^{-1} r[I_hi,j] per block,
+ * I_lo = the first n_lo modes of every block (the modes are graded by degree: n_lo = C(k_lo+D, D)
+ * spans the polynomials of degree <= k_lo), I_hi,j the other modes of block j. The low-order
+ * system M_lo (the leading n_lo x n_lo parts of the level-1 blocks) is solved, where the paper
+ * uses a sparse direct solver, by this library's own solver on a hierarchy built from M_lo and
+ * the leading parts of the transfer blocks (options lo_opts, may be NULL), to the relative
+ * residual inner_tol within inner_maxit iterations (inner_precision as xdg_solve_opts.precision);
+ * the high-order systems with the inverses of the trailing (Np - n_lo)^2 parts of the diagonal
+ * blocks. The printed right-hand side of the high-order solves, b_hi,j, is read as the residual
+ * r of the line before. n_lo must be one of 3, 4, 6, 10, 15, 20 and smaller than Np.
+ * Allocates device memory (the low-order hierarchy, inverses, vectors); a second call replaces
+ * the first. Errors: XDG_EINVAL, XDG_EBREAKDOWN (a sub-block not positive definite), ENOMEM,
+ * ECUDA. Single problems only. */
+int xdg_pmg_setup(xdg_hier_t h, int n_lo, const xdg_hier_opts* lo_opts, double inner_tol, int inner_maxit,
+                  int inner_precision);
+
+/* z = PMG(r) (device vectors of level 1, z must not alias r); synchronises (the inner solve
+ * reads its residual back). */
+int xdg_pmg_apply(xdg_hier_t h, const double* r, double* z);
+
+/* Flexible GMRES(restart) on M x = b (device vectors; x holds x0): right preconditioning by the
+ * multigrid cycle (preconditioner 0, precision as xdg_solve_opts.precision: XDG_PREC_F64 the FP64
+ * cycle, F32 / BF16 the low-precision one) or by the p-multigrid of xdg_pmg_setup
+ * (preconditioner 1). The Krylov basis is orthogonalised with two classical Gram-Schmidt sweeps,
+ * the Hessenberg least-squares problem solved with Givens rotations on the device; the residual
+ * estimate is read after every step and the true residual recomputed at the end. Flexible (the
+ * search directions are kept), so an inexact or changing preconditioner is allowed (Saad 1993).
+ * Allocates (restart + 1) + restart vectors on the first call of a restart length; the steps
+ * with preconditioner 0 are recorded as CUDA graphs. info: iterations = Arnoldi steps. */
+typedef struct {
+  double tol;          /* stop when ||b - M x||_2 <= tol ||b||_2 */
+  int maxit;           /* Arnoldi steps in total */
+  int restart;         /* steps per cycle, 1..200 */
+  int preconditioner;  /* 0: multigrid cycle, 1: p-multigrid */
+  int precision;       /* cycle precision (preconditioner 0) */
+} xdg_gmres_opts;
+
+int xdg_solve_gmres(xdg_hier_t h, const double* b, double* x, const xdg_gmres_opts* o, xdg_solve_info* info);
 
 /* Same as xdg_solve with host vectors: copies b to the device, solves from x = 0 and copies
  * x back, all inside the call (the end-to-end path for callers without device memory). */

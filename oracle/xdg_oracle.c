@@ -935,7 +935,9 @@ static void omg_level(or_hier* H, int lev, const double* b, double* x) {
 /* Algorithm OrthoMG on the finest level: x holds x0 on entry. Passes of (pre-smoother, RM,
  * coarse correction by one OrthoMG pass per coarser level, RM, post-smoother, RM) while
  * |r| > tol |b|, at most maxit passes. The search space of the finest level keeps every
- * direction up to `restart` columns; then x0 := x, r0 := r and the space starts empty again.
+ * direction up to `restart` columns; then x0 := x, r0 := b - M x (recomputed) and the space
+ * starts empty again; the same when the updated residual meets the tolerance but the
+ * recomputed one does not.
  * hist (optional, maxit+1 entries): |r|/|b| after each pass (hist[0]: initial).
  * Returns the passes made; *relres = the final |b - M x| / |b| (recomputed). */
 int or_orthomg(void* h, const double* b, double* x, double tol, int maxit, int restart, double* relres,
@@ -971,10 +973,24 @@ int or_orthomg(void* h, const double* b, double* x, double tol, int maxit, int r
     double* zc = (double*)malloc(sizeof(double) * nc);
     or_rm_space S;
     rm_init(&S, n, restart);
-    while (rn / bn > tol && it < maxit) {
-      if (S.l + 3 > S.cap) { /* restart: the current iterate becomes x0 */
+    for (;;) {
+      if (!(rn / bn > tol)) {
+        /* the updated residual meets the tolerance: check the recomputed one; if rounding has
+         * moved them apart, restart from x with the recomputed residual */
+        or_residual(L->nb, Np, L->rp, L->col, L->val, b, x, z);
+        const double tn = sqrt(dot(n, z, z));
+        if (!(tn / bn > tol) || it >= maxit) break;
         memcpy(x0, x, sizeof(double) * n);
-        memcpy(r0, r, sizeof(double) * n);
+        memcpy(r0, z, sizeof(double) * n);
+        memcpy(r, z, sizeof(double) * n);
+        S.l = 0;
+        rn = tn;
+      }
+      if (it >= maxit) break;
+      if (S.l + 3 > S.cap) { /* restart: x0 := x, r0 := b - M x recomputed, the space empty */
+        memcpy(x0, x, sizeof(double) * n);
+        or_residual(L->nb, Np, L->rp, L->col, L->val, b, x, r0);
+        memcpy(r, r0, sizeof(double) * n);
         S.l = 0;
       }
       omg_smoother(H, 0, r, z);

@@ -17,9 +17,11 @@
 #include <cstdlib>
 #include <cstring>
 #include <functional>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -30,6 +32,8 @@
 #include "xdg_kernels_mlp.cuh"
 #include "xdg_kernels_fused.cuh"
 #include "xdg_kernels_df.cuh"
+#include "xdg_swz.h"
+#include "xdg_krylov.h"
 
 using namespace xdg;
 
@@ -56,6 +60,9 @@ void set_err(const char* fmt, ...) {
   } while (0)
 
 #define CKL()  CK(cudaGetLastError())
+
+// in void helpers that only enqueue work: the error surfaces at the next cudaGetLastError
+#define CK_VOID(call) (void)(call)
 
 #define TRY(expr)          \
   do {                     \
@@ -248,8 +255,12 @@ struct OpsT {
   }
 };
 
+// Np = 3 and 4 (the k = 1 spaces in 2D and 3D) exist for the low-order systems of the
+// p-multigrid; they have FP64 kernels only
 bool ops_for(int np, Ops* o) {
   switch (np) {
+    case 3: *o = OpsT<3>::make(); return true;
+    case 4: *o = OpsT<4>::make(); return true;
     case 6: *o = OpsT<6>::make(); return true;
     case 10: *o = OpsT<10>::make(); return true;
     case 15: *o = OpsT<15>::make(); return true;
@@ -516,6 +527,52 @@ struct Learned {
   int64_t nodes[3] = {0, 0, 0};
 };
 
+// Additive Schwarz smoother of one level (Algorithm Swz with exact patch solves; kernels in
+// xdg_swz.cu). Patches are caller-given block lists; the patch matrices' inverses are stored
+// once per distinct matrix (tid[p] names the inverse of patch p).
+struct SwzLevel {
+  int64_t npatch = 0, nslot = 0, nuniq = 0, inv_entries = 0, nitem = 0;
+  int maxdof = 0, stage_n = 0;
+  swz::Item* items = nullptr;  // work items: patches grouped by their stored inverse
+  int32_t* porder = nullptr;
+  bool single = false;  // every block in exactly one patch: the solves write the result directly
+  int64_t *pptr = nullptr, *ioff = nullptr, *bsptr = nullptr, *bslot = nullptr;
+  int32_t *pblk = nullptr, *tid = nullptr;
+  double *Ainv = nullptr, *isq = nullptr, *y = nullptr, *r = nullptr;
+  float *Ainv32 = nullptr, *isq32 = nullptr, *y32 = nullptr, *r32 = nullptr;
+  std::vector<int64_t> h_pptr;
+  std::vector<int32_t> h_pblk;
+  std::vector<void*> mem;
+  size_t bytes = 0;
+  ~SwzLevel() {
+    for (void* q : mem) cudaFree(q);
+  }
+  template <class T>
+  int alloc(T** p, size_t n) {
+    void* q = nullptr;
+    const size_t nbytes = std::max<size_t>(n, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&q, nbytes);
+    if (e != cudaSuccess) {
+      set_err("cudaMalloc(%zu bytes): %s", nbytes, cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? XDG_ENOMEM : XDG_ECUDA;
+    }
+    mem.push_back(q);
+    bytes += nbytes;
+    *p = static_cast<T*>(q);
+    return XDG_OK;
+  }
+};
+
+// One level of the orthonormalisation multigrid (Algorithms ResMinimi and OrthoMG): the search
+// space Z, W = M Z (cap columns each), the level's right-hand side, iterate and residuals, and
+// device scalars: sc[0] |w|^2, sc[1] |M z|^2, sc[2] alpha, sc[3 ..] Gram-Schmidt coefficients.
+struct OmgLevel {
+  int cap = 0, l = 0;
+  double *W = nullptr, *Z = nullptr, *b = nullptr, *x = nullptr, *r = nullptr, *r0 = nullptr, *x0 = nullptr,
+         *z = nullptr, *sc = nullptr, *part = nullptr;
+  float *rf = nullptr, *zf = nullptr;  // the residual and the smoother's result in FP32
+};
+
 }  // namespace
 
 struct xdg_hier {
@@ -524,6 +581,10 @@ struct xdg_hier {
   bool own_stream = false;
   Ops ops{};
   std::vector<Level> L;
+  std::vector<std::unique_ptr<SwzLevel>> swz;  // additive Schwarz smoother per level (else block Jacobi)
+  double omega_fixed = 0.0;                    // xdg_hier_opts.omega
+  int lanczos_m = 12;                          // xdg_hier_opts.lanczos_steps
+  bool has_swz(int l) const { return l < (int)swz.size() && swz[l]; }
   double* Minv = nullptr;       // dense inverses of the coarsest level, one per problem
   int64_t nc = 0;               // DOF of the coarsest level (all problems)
   int nprob = 1;                // problems in the hierarchy (a batch when > 1)
@@ -620,6 +681,7 @@ struct xdg_hier {
 
   ~xdg_hier() {
     if (stream) cudaStreamSynchronize(stream);
+    delete pm.lo;
     if (g_cycle) cudaGraphExecDestroy(g_cycle);
     if (g_iter) cudaGraphExecDestroy(g_iter);
     for (int p = 0; p < 3; ++p) {
@@ -629,6 +691,8 @@ struct xdg_hier {
     for (int p = 0; p < 3; ++p)
       if (lr.g_iter[p]) cudaGraphExecDestroy(lr.g_iter[p]);
     drop_loops();
+    omg_drop_graphs();
+    gm_drop();
     if (hlctl) cudaFreeHost(hlctl);
     for (void* p : allocs) cudaFree(p);
     if (h_bsc) cudaFreeHost(h_bsc);
@@ -677,10 +741,196 @@ struct xdg_hier {
     ops.spmv(grid(V.nb), stream, act, V.nb, V.rp, V.col, V.val, x, b, y, mode);
   }
   void smooth(int l, const double* b, const double* xi, double* xo) {
+    if (has_swz(l)) {
+      swz_smooth(l, b, xi, xo);
+      return;
+    }
     ++launches;
     Level& V = L[l];
     ops.smooth(grid(V.nb), stream, V.nb, V.rp, V.col, V.val, V.Dinv, V.omega, V.omr, b, xi, xo);
   }
+  // Schwarz patch solves z = (om) S r (T = double: FP64 inverses; float: FP32 copies); xi: add
+  // to xi (xi == nullptr: from zero)
+  template <class T>
+  void swz_solve(int l, const T* r, T om, const T* xi, T* xo) {
+    SwzLevel& S = *swz[l];
+    const T* Ai = std::is_same<T, double>::value ? (const T*)S.Ainv : (const T*)S.Ainv32;
+    const T* isq = std::is_same<T, double>::value ? (const T*)S.isq : (const T*)S.isq32;
+    if (S.single) {
+      swz::apply<T>(Np, stream, sms * 4, xi ? 2 : 1, S.nitem, S.items, S.porder, S.pptr, S.pblk, S.ioff, Ai, isq, r,
+                    om, xi, xo, S.maxdof, S.stage_n);
+      ++launches;
+    } else {
+      T* y = std::is_same<T, double>::value ? (T*)S.y : (T*)S.y32;
+      swz::apply<T>(Np, stream, sms * 4, 0, S.nitem, S.items, S.porder, S.pptr, S.pblk, S.ioff, Ai, isq, r, T(1),
+                    nullptr, y, S.maxdof, S.stage_n);
+      swz::accum<T>(Np, stream, sms * 8, L[l].nb, S.bsptr, S.bslot, isq, y, om, xi, xo);
+      launches += 2;
+    }
+  }
+  // xo = xi + omega S (b - M xi) with the level's Schwarz preconditioner (xi == nullptr: zero)
+  void swz_smooth(int l, const double* b, const double* xi, double* xo) {
+    Level& V = L[l];
+    const double* r = b;
+    if (xi) {
+      ops.spmv(grid(V.nb), stream, nullptr, V.nb, V.rp, V.col, V.val, xi, b, swz[l]->r, 1);
+      ++launches;
+      r = swz[l]->r;
+    }
+    swz_solve<double>(l, r, V.omega, xi, xo);
+  }
+  void swz_smooth_lp(int p, int l, const float* b, const float* xi, float* xo) {
+    Level& V = L[l];
+    LevelLP& W = LP[p][l];
+    const float* r = b;
+    if (xi) {
+      opl[p].resid32(grid_lp(l), V.spl, stream, V.nb, V.rp, V.col, W.val32, W.sc32, xi, b, swz[l]->r32);
+      ++launches;
+      r = swz[l]->r32;
+    }
+    swz_solve<float>(l, r, (float)V.omega, xi, xo);
+  }
+  int set_schwarz(int l, int64_t npatch, const int64_t* pptr, const int32_t* pblk);
+  // orthonormalisation multigrid (xdg_solve_orthomg)
+  std::vector<OmgLevel> omg;
+  int omg_restart = 0, omg_passes = 0;
+  std::vector<cudaGraphExec_t> omg_graphs;  // one recorded pass per start column of level 1
+  int omg_grid() const { return std::min(kRedBlocks, sms * 2); }
+  int omg_setup(int restart, int passes);
+  void omg_drop_graphs() {
+    for (auto& g : omg_graphs)
+      if (g) cudaGraphExecDestroy(g);
+    omg_graphs.clear();
+  }
+  // undamped smoother of Algorithm OrthoMG: z = S r (Schwarz) or D^{-1} r (block Jacobi), in
+  // FP64 or (omg_f32) from the FP32 copies of the patch or block inverses, r rounded to FP32
+  // and the result widened
+  bool omg_f32 = false;
+  void omg_smooth(int l, const double* r, double* z) {
+    Level& V = L[l];
+    OmgLevel& S = omg[l];
+    const int64_t n = V.nb * Np;
+    if (omg_f32) {
+      kl(k_d2f, vgrid(n), kThreads, 0, stream)(n, r, S.rf, nullptr, Np);
+      if (has_swz(l)) {
+        swz_solve<float>(l, S.rf, 1.0f, nullptr, S.zf);
+      } else {
+        LevelLP& W = LP[1][l];
+        opl[1].smooth(grid_lp(l), V.spl, stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, 1.0f, nullptr,
+                      S.rf, nullptr, S.zf, nullptr);
+        ++launches;
+      }
+      kl(k_f2d, vgrid(n), kThreads, 0, stream)(n, S.zf, z, nullptr, Np);
+      launches += 2;
+    } else if (has_swz(l)) {
+      swz_solve<double>(l, r, 1.0, nullptr, z);
+    } else {
+      ops.bjsolve(grid(V.nb), stream, V.nb, V.Dinv, r, z);
+      ++launches;
+    }
+  }
+  // Algorithm ResMinimi: append z (orthogonalised, normalised) and w = M z to the level's space
+  // and move x, r to the residual-minimising combination; two classical Gram-Schmidt sweeps
+  void omg_rm(int l, double* x, double* r) {
+    OmgLevel& S = omg[l];
+    Level& V = L[l];
+    const int64_t n = V.nb * Np;
+    const int vg = vgrid(n);
+    double* w = S.W + (int64_t)S.l * n;
+    double* znew = S.Z + (int64_t)S.l * n;
+    spmv(l, S.z, nullptr, w, 0);
+    dot(n, w, w, S.sc + 1);
+    for (int pass = 0; pass < 2 && S.l > 0; ++pass) {
+      kry::mdot_partial(stream, omg_grid(), n, S.l, S.W, w, S.part);
+      kry::mdot_final(stream, omg_grid(), S.l, S.part, S.sc + 3, nullptr);
+      kry::gs_update(stream, vg, n, S.l, S.W, S.Z, S.sc + 3, w, S.z);
+      launches += 3;
+    }
+    dot(n, w, w, S.sc);
+    kry::normalize(stream, vg, n, S.sc, S.sc + 1, w, S.z, znew, nullptr);
+    dot(n, w, S.r0, S.sc + 2);
+    kry::rm_update(stream, vg, n, S.sc + 2, znew, w, x, r);
+    launches += 2;
+    ++S.l;
+  }
+  // one pass of Algorithm OrthoMG on level l with the level's x, r (x0 = 0 on coarse levels)
+  void omg_pass(int l, double* x, double* r) {
+    OmgLevel& S = omg[l];
+    Level& V = L[l];
+    const int64_t n = V.nb * Np;
+    omg_smooth(l, r, S.z);
+    omg_rm(l, x, r);
+    restrict_(l, r, nullptr, omg[l + 1].b);
+    omg_level(l + 1);
+    CK_VOID(cudaMemsetAsync(S.z, 0, n * sizeof(double), stream));
+    prolong(l, omg[l + 1].x, S.z, S.z);
+    omg_rm(l, x, r);
+    omg_smooth(l, r, S.z);
+    omg_rm(l, x, r);
+  }
+  // Algorithm OrthoMG on a coarse level: x = MG(0, b) with omg_passes passes (the coarsest:
+  // the direct solve)
+  void omg_level(int l) {
+    OmgLevel& S = omg[l];
+    if (l == nlev - 1) {
+      coarse(S.b, S.x);
+      return;
+    }
+    const int64_t n = L[l].nb * Np;
+    S.l = 0;
+    CK_VOID(cudaMemcpyAsync(S.r0, S.b, n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    CK_VOID(cudaMemcpyAsync(S.r, S.b, n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    CK_VOID(cudaMemsetAsync(S.x, 0, n * sizeof(double), stream));
+    for (int p = 0; p < omg_passes; ++p) omg_pass(l, S.x, S.r);
+  }
+  int solve_orthomg(const double* b, double* x, const xdg_orthomg_opts* o, xdg_solve_info* info);
+  // flexible GMRES (xdg_solve_gmres): Arnoldi basis V (m+1 vectors), preconditioned Z (m), the
+  // Hessenberg matrix and Givens rotations on the device, one recorded graph per Arnoldi step
+  struct Gmres {
+    int m = 0, prec = -1, kind = -1;
+    double *V = nullptr, *Z = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *ny = nullptr,
+           *sc = nullptr, *part = nullptr;
+    std::vector<cudaGraphExec_t> step;
+    int64_t step_nodes = 0;
+  } gm;
+  void gm_drop() {
+    for (auto& g : gm.step)
+      if (g) cudaGraphExecDestroy(g);
+    gm.step.clear();
+  }
+  int solve_gmres(const double* b, double* x, const xdg_gmres_opts* o, xdg_solve_info* info);
+  // the preconditioner of the flexible GMRES: kind 0 = the multigrid cycle of precision prec,
+  // kind 1 = the p-multigrid of Algorithm pMultigrid
+  void gm_precond(int kind, int prec, const double* v, double* z) {
+    if (kind == 1) pmg_apply(v, z);
+    else precond(prec, v, z);
+  }
+  // p-multigrid of level 1: the low-order hierarchy, the high-order block inverses, vectors
+  struct Pmg {
+    int n_lo = 0;
+    xdg_hier* lo = nullptr;
+    double *Hinv = nullptr, *blo = nullptr, *xlo = nullptr, *res = nullptr;
+    xdg_solve_opts inner{};
+    int last_rc = 0;
+  } pm;
+  bool pmg_ready() const { return pm.lo != nullptr; }
+  int pmg_setup(int n_lo, const xdg_hier_opts* lo_opts, double inner_tol, int inner_maxit, int inner_prec);
+  void pmg_apply(const double* v, double* z) {
+    Level& V = L[0];
+    const int64_t nb = V.nb;
+    pmg::take_lo(stream, nb, Np, pm.n_lo, v, pm.blo);
+    CK_VOID(cudaMemsetAsync(pm.xlo, 0, nb * pm.n_lo * sizeof(double), stream));
+    const int rc = pm.lo->solve_dev(pm.blo, pm.xlo, &pm.inner, nullptr);
+    if (rc != XDG_OK && rc != XDG_ENOTCONV) pm.last_rc = rc;
+    pmg::put_lo(stream, nb, Np, pm.n_lo, pm.xlo, z);
+    spmv(0, z, v, pm.res, 1);
+    pmg::hi_apply(stream, nb, Np, pm.n_lo, pm.Hinv, pm.res, z);
+    launches += 4;
+  }
+  const double* omg_graph_x = nullptr;  // the solution vector the recorded passes write
+  int64_t omg_pass_nodes = 0;
+  int lanczos_swz(int l, int m, double* lmax);
+  int rerecord();
   void restrict_(int l, const double* b, const double* x, double* rc) {
     launches += 2;
     Level& V = L[l];
@@ -723,7 +973,7 @@ struct xdg_hier {
     }
     // coarse-grid correction: gamma cycles on the coarse level; above the coarsest level the
     // restriction's gather also does the coarse level's first sweep
-    if (l + 2 < nlev) {
+    if (l + 2 < nlev && !has_swz(l + 1)) {
       ops.resid_rt(grid(V.nb), stream, V.nb, V.rp, V.col, V.val, V.R, b, cur, V.s);
       ops.gather_smooth0(grid(C.nb), stream, C.nb, V.cptr, V.ch, V.s, C.Dinv, C.omega, C.omr, C.b, C.x);
       launches += 2;
@@ -805,23 +1055,32 @@ struct xdg_hier {
     const uint8_t* act = (l == 0) ? cur_act : nullptr;  // finished problems of a batch are skipped
     float* cur = x;
     float* oth = W.t;
+    const bool schwarz = has_swz(l);
     if (!pre0) {
-      o.smooth(grid_lp(l), V.spl, stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, V.omr_f, b, nullptr,
-               cur, act);
-      ++launches;
+      if (schwarz) {
+        swz_smooth_lp(p, l, b, nullptr, cur);
+      } else {
+        o.smooth(grid_lp(l), V.spl, stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, V.omr_f, b,
+                 nullptr, cur, act);
+        ++launches;
+      }
     }
     const bool sym = lvl1_sym(l);
-    auto sweep = [&](const float* xi, float* xo) {
+    auto sweep = [&](const float* xi, float* xo) {  // counts its own launches
+      if (schwarz) {
+        swz_smooth_lp(p, l, b, xi, xo);
+        return;
+      }
       if (sym)
         o.smooth_sym(grid_lp(l), stream, V.nb, sy.urp, sy.ucol, sy.uval, sy.usc, sy.L(), (const float*)W.Dinv, W.dsc, om, V.omr_f,
                      b, xi, xo, act);
       else
         o.smooth(grid_lp(l), V.spl, stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.Dinv, W.dsc, om, V.omr_f, b, xi,
                  xo, act);
+      ++launches;
     };
     for (int s = 1; s < nu; ++s) {
       sweep(cur, oth);
-      ++launches;
       std::swap(cur, oth);
     }
     if (sym)
@@ -829,7 +1088,7 @@ struct xdg_hier {
     else
       o.resid_rt(grid_lp(l), V.spl, stream, V.nb, V.rp, V.col, W.val32, W.sc32, W.R, W.rsc, b, cur, W.s, act);
     launches += 2;
-    if (l + 2 < nlev) {
+    if (l + 2 < nlev && !has_swz(l + 1)) {
       o.gather_smooth0(grid(C.nb), stream, C.nb, V.cptr, V.ch, W.s, (const float*)WC.Dinv, WC.dsc, (float)C.omega,
                        C.omr_f, WC.b, WC.x);
       cycle_lp(p, l + 1, WC.b, WC.x, true);
@@ -852,7 +1111,6 @@ struct xdg_hier {
     oth = (cur == x) ? W.t : x;
     for (int s = 0; s < nu; ++s) {
       sweep(cur, oth);
-      ++launches;
       std::swap(cur, oth);
     }
     if (cur != x) {
@@ -1126,6 +1384,8 @@ int xdg_hier::build(const xdg_problem* p, const xdg_hier_opts* o) {
   pair_mode = o ? o->outer_apply : 0;
   sym_mode = o ? o->symmetric : 0;
   const int lsteps = o && o->lanczos_steps > 0 ? o->lanczos_steps : 12;
+  lanczos_m = lsteps;
+  omega_fixed = (o && o->omega > 0.0) ? o->omega : 0.0;
   const int64_t Np2 = (int64_t)Np * Np;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1909,6 +2169,685 @@ int xdg_hier::tune_split(int p) {
 }
 
 // Host validation of problem s of a batch against its own sizes (no CUDA call).
+// The recorded graphs hold the cycle's kernels and arguments (damping, smoother): drop them and
+// record the iteration graphs again (cycle graphs are recorded at their next use).
+int xdg_hier::rerecord() {
+  drop_loops();
+  omg_drop_graphs();  // recorded OrthoMG passes and GMRES steps hold the old smoothers
+  gm_drop();
+  TRY(capture(&g_iter, 1, nullptr, nullptr));
+  for (int p = 1; p < 3; ++p)
+    if (has_lp[p]) TRY(capture(&g_iter_lp[p], 3, nullptr, nullptr, p));
+  if (g_cycle) cudaGraphExecDestroy(g_cycle);
+  g_cycle = nullptr;
+  g_cycle_b = nullptr;
+  for (int p = 0; p < 3; ++p) {
+    if (g_cyc_lp[p]) cudaGraphExecDestroy(g_cyc_lp[p]);
+    g_cyc_lp[p] = nullptr;
+    g_cyc_lp_b[p] = nullptr;
+    if (lr.g_iter[p]) cudaGraphExecDestroy(lr.g_iter[p]);
+    lr.g_iter[p] = nullptr;
+  }
+  return XDG_OK;
+}
+
+// m-step Lanczos for the largest eigenvalue of S M, S the level's Schwarz preconditioner: S M
+// is self-adjoint in the M inner product, so the recursion runs in that inner product (one
+// product with M and one application of S per step), from the same counter-based start vector
+// as the block-Jacobi estimate. Single problems only.
+int xdg_hier::lanczos_swz(int l, int m, double* lmax) {
+  Level& V = L[l];
+  const int64_t n = V.nb * Np;
+  double *q = V.b, *qp = V.x, *u = V.t, *w = V.r, *v = V.dz;
+  const int vg = vgrid(n);
+  double* dv = B.alpha;  // device scratch (free outside solves)
+  auto put = [&](double val) -> int {
+    h_bsc[0] = val;
+    CK(cudaMemcpyAsync(dv, h_bsc, sizeof(double), cudaMemcpyHostToDevice, stream));
+    CK(cudaStreamSynchronize(stream));
+    return XDG_OK;
+  };
+  auto get = [&](const double* x, const double* y, double* out) -> int {
+    seg_dot(l, x, y, dv);
+    return read_scalars(dv, 1, out);
+  };
+  kl(k_hash_vector_seg, vg, kThreads, 0, stream)(n, 1, V.sdof, q);
+  CK(cudaMemsetAsync(qp, 0, n * sizeof(double), stream));
+  spmv(l, q, nullptr, u, 0);
+  double h = 0.0;
+  TRY(get(q, u, &h));
+  TRY(put(1.0 / std::sqrt(h)));
+  kl(k_seg_scale, vg, kThreads, 0, stream)(n, 1, V.sdof, dv, q);
+  kl(k_seg_scale, vg, kThreads, 0, stream)(n, 1, V.sdof, dv, u);
+  std::vector<double> al, be;
+  double bprev = 0.0;
+  for (int j = 0; j < m; ++j) {
+    swz_solve<double>(l, u, 1.0, nullptr, w);  // w = S M q
+    double a = 0.0;
+    TRY(get(u, w, &a));
+    al.push_back(a);
+    TRY(put(-a));
+    kl(k_seg_axpy, vg, kThreads, 0, stream)(n, 1, V.sdof, dv, q, w);
+    TRY(put(-bprev));
+    kl(k_seg_axpy, vg, kThreads, 0, stream)(n, 1, V.sdof, dv, qp, w);
+    spmv(l, w, nullptr, v, 0);
+    double b2 = 0.0;
+    TRY(get(w, v, &b2));
+    CKL();
+    const double bj = std::sqrt(std::max(b2, 0.0));
+    be.push_back(bj);
+    if (!(bj > 1e-300)) break;
+    kl(k_copy, vg, kThreads, 0, stream)(n, q, qp);
+    kl(k_copy, vg, kThreads, 0, stream)(n, w, q);
+    kl(k_copy, vg, kThreads, 0, stream)(n, v, u);
+    TRY(put(1.0 / bj));
+    kl(k_seg_scale, vg, kThreads, 0, stream)(n, 1, V.sdof, dv, q);
+    kl(k_seg_scale, vg, kThreads, 0, stream)(n, 1, V.sdof, dv, u);
+    bprev = bj;
+  }
+  CKL();
+  *lmax = tridiag_lambda_max(al, be);
+  return XDG_OK;
+}
+
+// Install (npatch > 0) or remove (npatch == 0) the additive Schwarz smoother of level l:
+// validate the patches, count alpha, find the distinct patch matrices, factor and invert them
+// on the device, estimate the damping, record the graphs again.
+int xdg_hier::set_schwarz(int l, int64_t npatch, const int64_t* pptr, const int32_t* pblk) {
+  Level& V = L[l];
+  TRY(sync());
+  if ((int)swz.size() < nlev) swz.resize(nlev);
+  swz[l].reset();
+  if (npatch == 0) {  // back to block Jacobi with its own damping estimate
+    TRY(lanczos(l, lanczos_m));
+    V.lmax = V.lmax_p[0];
+    V.omega = omega_fixed > 0.0 ? omega_fixed : 4.0 / (3.0 * V.lmax);
+    V.lmax_p[0] = V.lmax;
+    V.omega_p[0] = V.omega;
+    return rerecord();
+  }
+  if (npatch < 0 || !pptr || !pblk || pptr[0] != 0) {
+    set_err("xdg_set_schwarz: bad patch arrays");
+    return XDG_EINVAL;
+  }
+  const int64_t nslot = pptr[npatch];
+  std::vector<int> cnt(V.nb, 0);
+  int maxdof = 0;
+  for (int64_t p = 0; p < npatch; ++p) {
+    const int64_t k = pptr[p + 1] - pptr[p];
+    if (k < 1 || k * Np > swz::kMaxDof) {
+      set_err("xdg_set_schwarz: patch %lld has %lld blocks (1..%d allowed for Np = %d)", (long long)p, (long long)k,
+              swz::kMaxDof / Np, Np);
+      return XDG_EINVAL;
+    }
+    maxdof = std::max<int>(maxdof, (int)(k * Np));
+    for (int64_t q = pptr[p]; q < pptr[p + 1]; ++q) {
+      const int32_t b = pblk[q];
+      if (b < 0 || b >= V.nb || (q > pptr[p] && b <= pblk[q - 1])) {
+        set_err("xdg_set_schwarz: patch %lld: block index %d out of range or not ascending", (long long)p, b);
+        return XDG_EINVAL;
+      }
+      ++cnt[b];
+    }
+  }
+  bool single = true;
+  for (int64_t i = 0; i < V.nb; ++i) {
+    if (cnt[i] == 0) {
+      set_err("xdg_set_schwarz: block %lld is in no patch", (long long)i);
+      return XDG_EINVAL;
+    }
+    single = single && cnt[i] == 1;
+  }
+  auto S = std::make_unique<SwzLevel>();
+  S->npatch = npatch;
+  S->nslot = nslot;
+  S->maxdof = maxdof;
+  S->single = single;
+  S->h_pptr.assign(pptr, pptr + npatch + 1);
+  S->h_pblk.assign(pblk, pblk + nslot);
+  // alpha^{-1/2} per block; slots of every block in ascending patch order
+  std::vector<double> isq(V.nb);
+  std::vector<float> isq32(V.nb);
+  for (int64_t i = 0; i < V.nb; ++i) {
+    isq[i] = 1.0 / std::sqrt((double)cnt[i]);
+    isq32[i] = (float)isq[i];
+  }
+  std::vector<int64_t> bsptr(V.nb + 1, 0), bslot(nslot);
+  for (int64_t q = 0; q < nslot; ++q) bsptr[pblk[q] + 1]++;
+  for (int64_t i = 0; i < V.nb; ++i) bsptr[i + 1] += bsptr[i];
+  {
+    std::vector<int64_t> pos(bsptr.begin(), bsptr.end() - 1);
+    for (int64_t q = 0; q < nslot; ++q) bslot[pos[pblk[q]]++] = q;
+  }
+  const int64_t n = V.nb * Np;
+  TRY(S->alloc(&S->pptr, npatch + 1));
+  TRY(S->alloc(&S->pblk, nslot));
+  TRY(S->alloc(&S->bsptr, V.nb + 1));
+  TRY(S->alloc(&S->bslot, nslot));
+  TRY(S->alloc(&S->isq, V.nb));
+  TRY(S->alloc(&S->isq32, V.nb));
+  TRY(S->alloc(&S->r, n));
+  TRY(S->alloc(&S->r32, n));
+  if (!single) {
+    TRY(S->alloc(&S->y, nslot * Np));
+    TRY(S->alloc(&S->y32, nslot * Np));
+  }
+  CK(cudaMemcpyAsync(S->pptr, pptr, (npatch + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(S->pblk, pblk, nslot * sizeof(int32_t), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(S->bsptr, bsptr.data(), (V.nb + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(S->bslot, bslot.data(), nslot * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(S->isq, isq.data(), V.nb * sizeof(double), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(S->isq32, isq32.data(), V.nb * sizeof(float), cudaMemcpyHostToDevice, stream));
+  // distinct patch matrices: two 64-bit hashes and the size per patch
+  std::vector<unsigned long long> hh(2 * npatch);
+  {
+    unsigned long long* dh = nullptr;
+    TRY(S->alloc(&dh, 2 * npatch));
+    CK(swz::hash(Np, stream, npatch, S->pptr, S->pblk, V.rp, V.col, V.val, dh));
+    CK(cudaMemcpyAsync(hh.data(), dh, 2 * npatch * sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream));
+    TRY(sync());
+  }
+  struct Key {
+    unsigned long long a, b;
+    int64_t n;
+    bool operator<(const Key& o) const {
+      return a != o.a ? a < o.a : (b != o.b ? b < o.b : n < o.n);
+    }
+  };
+  std::map<Key, int32_t> uniq;
+  std::vector<int32_t> tid(npatch);
+  std::vector<int64_t> rep, ioff(1, 0);
+  for (int64_t p = 0; p < npatch; ++p) {
+    const int64_t m = (pptr[p + 1] - pptr[p]) * Np;
+    auto it = uniq.emplace(Key{hh[2 * p], hh[2 * p + 1], m}, (int32_t)rep.size());
+    if (it.second) {  // every inverse starts 16-byte aligned in FP32 (and FP64): padded to 4 entries
+      rep.push_back(p);
+      ioff.push_back(ioff.back() + (m * m + 3) / 4 * 4);
+    }
+    tid[p] = it.first->second;
+  }
+  const int64_t nu = (int64_t)rep.size();
+  S->nuniq = nu;
+  S->inv_entries = ioff.back();
+  int64_t* drep = nullptr;
+  int* derr = nullptr;
+  TRY(S->alloc(&S->tid, npatch));
+  TRY(S->alloc(&S->ioff, nu + 1));
+  TRY(S->alloc(&drep, nu));
+  TRY(S->alloc(&S->Ainv, ioff.back()));
+  TRY(S->alloc(&S->Ainv32, ioff.back()));
+  TRY(S->alloc(&derr, 1));
+  CK(cudaMemcpyAsync(S->tid, tid.data(), npatch * sizeof(int32_t), cudaMemcpyHostToDevice, stream));
+  {
+    // work items: the patches of every stored inverse, in chunks of kItemPatches
+    std::vector<int32_t> porder(npatch);
+    for (int64_t p = 0; p < npatch; ++p) porder[p] = (int32_t)p;
+    std::stable_sort(porder.begin(), porder.end(), [&](int32_t a, int32_t b) { return tid[a] < tid[b]; });
+    std::vector<swz::Item> items;
+    for (int64_t q = 0; q < npatch;) {
+      int64_t e = q;
+      while (e < npatch && tid[porder[e]] == tid[porder[q]]) ++e;
+      const int m = (int)((pptr[porder[q] + 1] - pptr[porder[q]]) * Np);
+      for (int64_t c = q; c < e; c += swz::kItemPatches) {
+        const int cnt = (int)std::min<int64_t>(swz::kItemPatches, e - c);
+        items.push_back(swz::Item{c, tid[porder[q]], cnt, m, 0});
+        if (cnt > 1) S->stage_n = std::max(S->stage_n, m);
+      }
+      q = e;
+    }
+    S->nitem = (int64_t)items.size();
+    TRY(S->alloc(&S->items, items.size()));
+    TRY(S->alloc(&S->porder, npatch));
+    CK(cudaMemcpyAsync(S->items, items.data(), items.size() * sizeof(swz::Item), cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(S->porder, porder.data(), npatch * sizeof(int32_t), cudaMemcpyHostToDevice, stream));
+    TRY(sync());  // the host arrays are released at the end of this scope
+  }
+  CK(swz::prepare(Np));
+  CK(cudaMemcpyAsync(S->ioff, ioff.data(), (nu + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(drep, rep.data(), nu * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemsetAsync(derr, 0, sizeof(int), stream));
+  // factor and invert in chunks whose gathered matrices fit a bounded work array
+  {
+    const int64_t budget = std::max<int64_t>(64LL << 20, (int64_t)maxdof * maxdof);  // doubles
+    double* work = nullptr;
+    int64_t* dwoff = nullptr;
+    const int64_t wcap = std::min<int64_t>(budget, ioff.back());
+    cudaError_t e = cudaMalloc(&work, std::max<int64_t>(wcap, 1) * sizeof(double));
+    if (e != cudaSuccess) {
+      set_err("xdg_set_schwarz: work array: %s", cudaGetErrorString(e));
+      return XDG_ENOMEM;
+    }
+    e = cudaMalloc(&dwoff, (nu + 1) * sizeof(int64_t));
+    int rc = XDG_OK;
+    if (e != cudaSuccess) {
+      set_err("xdg_set_schwarz: %s", cudaGetErrorString(e));
+      rc = XDG_ENOMEM;
+    }
+    std::vector<int64_t> woff;
+    for (int64_t u0 = 0; rc == XDG_OK && u0 < nu;) {
+      woff.assign(1, 0);
+      int64_t u1 = u0;
+      while (u1 < nu && woff.back() + (ioff[u1 + 1] - ioff[u1]) <= wcap) {
+        woff.push_back(woff.back() + (ioff[u1 + 1] - ioff[u1]));
+        ++u1;
+      }
+      e = cudaMemcpyAsync(dwoff, woff.data(), woff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, stream);
+      if (e == cudaSuccess)
+        e = swz::factor(Np, stream, u0, u1, drep, S->pptr, S->pblk, V.rp, V.col, V.val, S->ioff, work, dwoff, S->Ainv,
+                        S->Ainv32, derr);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(stream);  // woff and work are reused
+      if (e != cudaSuccess) {
+        set_err("xdg_set_schwarz: factorisation: %s", cudaGetErrorString(e));
+        rc = XDG_ECUDA;
+      }
+      u0 = u1;
+    }
+    cudaFree(work);
+    if (dwoff) cudaFree(dwoff);
+    TRY(rc);
+  }
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  TRY(sync());
+  if (herr) {
+    set_err("xdg_set_schwarz: a patch matrix of level %d is not positive definite", l + 1);
+    return XDG_EBREAKDOWN;
+  }
+  swz[l] = std::move(S);
+  // the fused small-level cycle holds block-Jacobi steps: not for levels with Schwarz
+  if (fused_lc >= 0 && l >= fused_lc)
+    for (bool& f : fused_on) f = false;
+  double lm = 0.0;
+  int rc = lanczos_swz(l, lanczos_m, &lm);
+  if (rc) {
+    swz[l].reset();
+    return rc;
+  }
+  V.lmax = lm;
+  V.omega = omega_fixed > 0.0 ? omega_fixed : 4.0 / (3.0 * lm);
+  if (V.lmax_p.empty()) V.lmax_p.resize(1);
+  if (V.omega_p.empty()) V.omega_p.resize(1);
+  V.lmax_p[0] = V.lmax;
+  V.omega_p[0] = V.omega;
+  return rerecord();
+}
+
+// work space of the orthonormalisation multigrid: level 1 keeps `restart` directions, the
+// coarser levels 3 per pass
+int xdg_hier::omg_setup(int restart, int passes) {
+  if (restart == omg_restart && passes == omg_passes && !omg.empty()) return XDG_OK;
+  TRY(sync());
+  omg_drop_graphs();
+  omg.assign(nlev, OmgLevel{});
+  omg_restart = restart;
+  omg_passes = passes;
+  for (int l = 0; l < nlev; ++l) {
+    OmgLevel& S = omg[l];
+    const int64_t n = L[l].nb * Np;
+    TRY(alloc(&S.b, n));
+    TRY(alloc(&S.x, n));
+    if (l == nlev - 1) continue;
+    S.cap = (l == 0) ? restart : 3 * passes;
+    TRY(alloc(&S.W, (size_t)S.cap * n));
+    TRY(alloc(&S.Z, (size_t)S.cap * n));
+    TRY(alloc(&S.r, n));
+    TRY(alloc(&S.r0, n));
+    TRY(alloc(&S.x0, n));
+    TRY(alloc(&S.z, n));
+    TRY(alloc(&S.sc, 3 + S.cap));
+    TRY(alloc(&S.part, (size_t)omg_grid() * S.cap));
+    TRY(alloc(&S.rf, n));
+    TRY(alloc(&S.zf, n));
+  }
+  return XDG_OK;
+}
+
+int xdg_hier::solve_orthomg(const double* b, double* x, const xdg_orthomg_opts* o, xdg_solve_info* info) {
+  auto t0 = clk::now();
+  const int restart = std::max(3, o->restart - o->restart % 3);
+  const int passes = std::max(1, std::min(4, o->coarse_passes));
+  TRY(omg_setup(restart, passes));
+  if (omg_f32 != (o->smoother_precision == XDG_PREC_F32)) omg_drop_graphs();
+  omg_f32 = o->smoother_precision == XDG_PREC_F32;
+  OmgLevel& S = omg[0];
+  Level& V = L[0];
+  const int64_t n = V.nb * Np;
+  const int64_t before = launches;
+  double bn2 = 0.0, rn2 = 0.0;
+  dot(n, b, b, dsc);
+  TRY(read_scalar(dsc, &bn2));
+  const double bn = bn2 > 0.0 ? std::sqrt(bn2) : 1.0;
+  // (re)start from the current x: x0 := x, r0 := r := b - M x (recomputed), empty space
+  auto restart_here = [&]() -> int {
+    spmv(0, x, b, S.r0, 1);
+    CK(cudaMemcpyAsync(S.r, S.r0, n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    CK(cudaMemcpyAsync(S.x0, x, n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    S.l = 0;
+    return XDG_OK;
+  };
+  TRY(restart_here());
+  dot(n, S.r, S.r, dsc);
+  TRY(read_scalar(dsc, &rn2));
+  int it = 0;
+  if (nlev == 1) {
+    coarse(S.r0, S.z);
+    kl(k_axpy, vgrid(n), kThreads, 0, stream)(n, 1.0, S.z, x);
+    it = 1;
+  } else {
+    omg_graphs.resize(restart / 3, nullptr);
+    for (;;) {
+      if (!(std::sqrt(rn2) > o->tol * bn)) {
+        // the updated residual meets the tolerance: check the true one; if rounding has moved
+        // them apart, restart from x with the true residual
+        spmv(0, x, b, S.z, 1);
+        dot(n, S.z, S.z, dsc);
+        double t2 = 0.0;
+        TRY(read_scalar(dsc, &t2));
+        if (!(std::sqrt(t2) > o->tol * bn) || !std::isfinite(t2) || it >= o->maxit) break;
+        TRY(restart_here());
+        rn2 = t2;
+      }
+      if (it >= o->maxit || !std::isfinite(rn2)) break;
+      if (S.l + 3 > S.cap) TRY(restart_here());
+      // one pass, recorded once per start column of level 1 (and per x: the graph holds it)
+      const int gi = S.l / 3;
+      const int l_before = S.l;
+      if (!omg_graphs[gi] || omg_graph_x != x) {
+        if (omg_graph_x != x) {
+          omg_drop_graphs();
+          omg_graphs.resize(restart / 3, nullptr);
+          omg_graph_x = x;
+        }
+        cudaGraph_t g = nullptr;
+        const int64_t c0 = launches;
+        CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+        omg_pass(0, x, S.r);
+        cudaError_t e = cudaStreamEndCapture(stream, &g);
+        if (e != cudaSuccess) {
+          set_err("orthomg graph capture: %s", cudaGetErrorString(e));
+          return XDG_ECUDA;
+        }
+        e = cudaGraphInstantiate(&omg_graphs[gi], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+          set_err("orthomg graph instantiate: %s", cudaGetErrorString(e));
+          return XDG_ECUDA;
+        }
+        omg_pass_nodes = launches - c0;
+      }
+      S.l = l_before + 3;
+      CK(cudaGraphLaunch(omg_graphs[gi], stream));
+      ++it;
+      dot(n, S.r, S.r, dsc);
+      TRY(read_scalar(dsc, &rn2));
+    }
+  }
+  // final residual recomputed
+  spmv(0, x, b, S.z, 1);
+  dot(n, S.z, S.z, dsc);
+  TRY(read_scalar(dsc, &rn2));
+  CKL();
+  const double rel = std::sqrt(rn2) / bn;
+  int rc = XDG_OK;
+  if (!std::isfinite(rel)) rc = XDG_EBREAKDOWN;
+  else if (rel > o->tol) rc = XDG_ENOTCONV;
+  launches = before;
+  if (info) {
+    info->iterations = it;
+    info->outer = 1;
+    info->relres = rel;
+    info->status = rc;
+    info->ms = ms_since(t0);
+    info->launches = (int64_t)it * omg_pass_nodes;
+  }
+  return rc;
+}
+
+// Flexible GMRES(m) (right preconditioning with a preconditioner that may change between
+// applications, Saad 1993): Arnoldi with two classical Gram-Schmidt sweeps, Givens rotations and
+// the least-squares solve on the device; the residual estimate |g_{j+1}| is read after every
+// step; x += Z y at the end of every cycle of m steps.
+int xdg_hier::solve_gmres(const double* b, double* x, const xdg_gmres_opts* o, xdg_solve_info* info) {
+  auto t0 = clk::now();
+  const int m = std::max(1, std::min(o->restart, 200));
+  const int kind = o->preconditioner, prec = o->precision;
+  Level& V0 = L[0];
+  const int64_t n = V0.nb * Np;
+  const int vg = vgrid(n), G = std::min(kRedBlocks, sms * 2);
+  if (gm.m != m) {  // work space for this restart length
+    TRY(sync());
+    gm_drop();
+    gm = Gmres{};
+    gm.m = m;
+    TRY(alloc(&gm.V, (size_t)(m + 1) * n));
+    TRY(alloc(&gm.Z, (size_t)m * n));
+    TRY(alloc(&gm.H, (size_t)(m + 1) * m));
+    TRY(alloc(&gm.cs, m));
+    TRY(alloc(&gm.sn, m));
+    TRY(alloc(&gm.g, m + 1));
+    TRY(alloc(&gm.ny, m + 1));
+    TRY(alloc(&gm.sc, 4));
+    TRY(alloc(&gm.part, (size_t)G * (m + 1)));
+  }
+  if (gm.prec != prec || gm.kind != kind || (int)gm.step.size() != m) {
+    gm_drop();
+    gm.step.assign(m, nullptr);
+    gm.prec = prec;
+    gm.kind = kind;
+  }
+  const int ld = m + 1;
+  const int64_t before = launches;
+  int64_t nodes = 0;
+  double bn2 = 0.0;
+  dot(n, b, b, dsc);
+  TRY(read_scalar(dsc, &bn2));
+  const double bn = bn2 > 0.0 ? std::sqrt(bn2) : 1.0;
+  int it = 0;
+  double est = 0.0;
+  for (;;) {
+    // (re)start: r = b - M x, normalised, is the first Arnoldi vector
+    spmv(0, x, b, gm.V, 1);
+    dot(n, gm.V, gm.V, gm.sc);
+    kry::gmres_start(stream, m, gm.sc, gm.g, gm.sc + 1);
+    CK(cudaMemsetAsync(gm.H, 0, (size_t)(m + 1) * m * sizeof(double), stream));
+    TRY(read_scalar(gm.g, &est));
+    if (!(est > o->tol * bn) || it >= o->maxit || !std::isfinite(est)) break;
+    kry::scale(stream, vg, n, gm.sc + 1, gm.V, gm.V);
+    int k = 0;
+    // step j: z_j = P v_j, w = M z_j orthogonalised against v_0..v_j (H(:, j)), rotation j
+    auto step = [&](int j) {
+      double* vj = gm.V + (int64_t)j * n;
+      double* zj = gm.Z + (int64_t)j * n;
+      double* w = gm.V + (int64_t)(j + 1) * n;
+      gm_precond(kind, prec, vj, zj);
+      spmv(0, zj, nullptr, w, 0);
+      for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice; H(:, j) accumulates
+        kry::mdot_partial(stream, G, n, j + 1, gm.V, w, gm.part);
+        kry::mdot_final(stream, G, j + 1, gm.part, gm.ny, gm.H + (int64_t)j * ld);
+        kry::gs_update(stream, vg, n, j + 1, gm.V, nullptr, gm.ny, w, nullptr);
+        launches += 3;
+      }
+      dot(n, w, w, gm.sc + 2);
+      kry::givens(stream, j, ld, gm.H, gm.cs, gm.sn, gm.g, gm.sc + 2);
+      kry::normalize(stream, vg, n, gm.sc + 2, gm.sc + 2, w, nullptr, nullptr, nullptr);
+      launches += 2;
+    };
+    for (int j = 0; j < m && it < o->maxit; ++j) {
+      if (kind == 1) {  // the p-multigrid's inner solve reads back: launched step by step
+        const int64_t c0 = launches;
+        pm.last_rc = 0;
+        step(j);
+        nodes += launches - c0;
+        launches = c0;
+        if (pm.last_rc) return pm.last_rc;
+      } else if (!gm.step[j]) {  // record step j once
+        cudaGraph_t g = nullptr;
+        const int64_t c0 = launches;
+        CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+        step(j);
+        cudaError_t e = cudaStreamEndCapture(stream, &g);
+        if (e != cudaSuccess) {
+          set_err("gmres graph capture: %s", cudaGetErrorString(e));
+          return XDG_ECUDA;
+        }
+        e = cudaGraphInstantiate(&gm.step[j], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+          set_err("gmres graph instantiate: %s", cudaGetErrorString(e));
+          return XDG_ECUDA;
+        }
+        gm.step_nodes = launches - c0;
+        launches = c0;
+      }
+      if (kind == 0) {
+        CK(cudaGraphLaunch(gm.step[j], stream));
+        nodes += gm.step_nodes;
+      }
+      ++it;
+      k = j + 1;
+      double gj = 0.0;
+      TRY(read_scalar(gm.g + j + 1, &gj));
+      est = std::fabs(gj);
+      if (!(est > o->tol * bn) || !std::isfinite(est)) break;
+    }
+    // x += Z y, y = H^{-1} g on the k steps made
+    kry::gmres_solve(stream, k, ld, gm.H, gm.g, gm.ny);
+    kry::gs_update(stream, vg, n, k, gm.Z, nullptr, gm.ny, x, nullptr);
+    if (!(est > o->tol * bn) || it >= o->maxit || !std::isfinite(est)) break;
+  }
+  // final residual recomputed
+  spmv(0, x, b, gm.V, 1);
+  double rn2 = 0.0;
+  dot(n, gm.V, gm.V, dsc);
+  TRY(read_scalar(dsc, &rn2));
+  CKL();
+  const double rel = std::sqrt(rn2) / bn;
+  int rc = XDG_OK;
+  if (!std::isfinite(rel)) rc = XDG_EBREAKDOWN;
+  else if (rel > o->tol) rc = XDG_ENOTCONV;
+  const int64_t outside = launches - before;
+  launches = before;
+  if (info) {
+    info->iterations = it;
+    info->outer = 1;
+    info->relres = rel;
+    info->status = rc;
+    info->ms = ms_since(t0);
+    info->launches = nodes + outside;
+  }
+  return rc;
+}
+
+int xdg_hier::pmg_setup(int n_lo, const xdg_hier_opts* lo_opts, double inner_tol, int inner_maxit, int inner_prec) {
+  Ops lops;
+  OpsLP lpl;
+  if (inner_prec != XDG_PREC_F64 && !ops_lp_for(n_lo, inner_prec, &lpl)) {
+    set_err("xdg_pmg_setup: a low-precision inner solve needs n_lo in 6, 10, 15, 20 (n_lo = %d)", n_lo);
+    return XDG_EINVAL;
+  }
+  if (n_lo < 1 || n_lo >= Np || !ops_for(n_lo, &lops) || Np - n_lo > 32) {
+    set_err("xdg_pmg_setup: n_lo = %d (Np = %d) not supported (3, 4, 6, 10, 15, 20, below Np)", n_lo, Np);
+    return XDG_EINVAL;
+  }
+  TRY(sync());
+  delete pm.lo;
+  pm = Pmg{};
+  Level& V = L[0];
+  const int64_t nb = V.nb;
+  const int64_t m2 = (int64_t)n_lo * n_lo;
+  // leading n_lo x n_lo parts of the level-1 operator and of every transfer block, to the host
+  std::vector<double> hval((size_t)V.nnzb * m2);
+  std::vector<std::vector<double>> hR(nlev - 1);
+  std::vector<std::vector<int32_t>> hagg(nlev - 1);
+  std::vector<int64_t> hnb(nlev);
+  {
+    int64_t biggest = V.nnzb;
+    for (int l = 0; l + 1 < nlev; ++l) biggest = std::max(biggest, L[l].nb);
+    double* tmp = nullptr;
+    cudaError_t e = cudaMalloc(&tmp, std::max<int64_t>(1, biggest * m2) * sizeof(double));
+    if (e != cudaSuccess) {
+      set_err("xdg_pmg_setup: %s", cudaGetErrorString(e));
+      return XDG_ENOMEM;
+    }
+    int rc = XDG_OK;
+    auto take = [&](int64_t nblk, const double* src, double* dst) {
+      cudaError_t ee = pmg::sub_blocks(stream, nblk, Np, n_lo, src, tmp);
+      if (ee == cudaSuccess) ee = cudaMemcpyAsync(dst, tmp, nblk * m2 * sizeof(double), cudaMemcpyDeviceToHost, stream);
+      if (ee == cudaSuccess) ee = cudaStreamSynchronize(stream);
+      if (ee != cudaSuccess) {
+        set_err("xdg_pmg_setup: %s", cudaGetErrorString(ee));
+        rc = XDG_ECUDA;
+      }
+    };
+    take(V.nnzb, V.val, hval.data());
+    for (int l = 0; rc == XDG_OK && l + 1 < nlev; ++l) {
+      hR[l].resize((size_t)L[l].nb * m2);
+      take(L[l].nb, L[l].R, hR[l].data());
+      hagg[l].resize(L[l].nb);
+      if (cudaMemcpy(hagg[l].data(), L[l].agg, L[l].nb * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        set_err("xdg_pmg_setup: copying the aggregation map");
+        rc = XDG_ECUDA;
+      }
+    }
+    cudaFree(tmp);
+    TRY(rc);
+  }
+  for (int l = 0; l < nlev; ++l) hnb[l] = L[l].nb;
+  std::vector<const int32_t*> aggp(nlev);
+  std::vector<const double*> Rp(nlev);
+  for (int l = 0; l + 1 < nlev; ++l) {
+    aggp[l] = hagg[l].data();
+    Rp[l] = hR[l].data();
+  }
+  xdg_problem q{};
+  q.Np = n_lo;
+  q.n_levels = nlev;
+  q.nb = hnb.data();
+  q.row_ptr = V.h_rp.data();
+  q.col = V.h_col.data();
+  q.val = hval.data();
+  q.agg = aggp.data();
+  q.R = Rp.data();
+  xdg_hier_opts lo{};
+  if (lo_opts) lo = *lo_opts;
+  else {
+    lo.gamma = gamma;
+    lo.w_levels = wlev < (1 << 20) ? wlev : 0;
+  }
+  lo.low_precision = (inner_prec == XDG_PREC_F64) ? 0 : (lo.low_precision | 1);
+  auto child = new xdg_hier();
+  child->stream = stream;
+  child->own_stream = false;
+  int rc = child->build(&q, &lo);
+  if (rc) {
+    delete child;
+    return rc;
+  }
+  pm.lo = child;
+  pm.n_lo = n_lo;
+  pm.inner = xdg_solve_opts{inner_tol, inner_maxit, 1, inner_prec, 0.0, 0.0};
+  const int m = Np - n_lo;
+  int* derr = nullptr;
+  TRY(alloc(&pm.Hinv, (size_t)nb * m * m));
+  TRY(alloc(&pm.blo, (size_t)nb * n_lo));
+  TRY(alloc(&pm.xlo, (size_t)nb * n_lo));
+  TRY(alloc(&pm.res, (size_t)nb * Np));
+  TRY(alloc(&derr, 1));
+  CK(cudaMemsetAsync(derr, 0, sizeof(int), stream));
+  CK(pmg::hi_inverses(stream, nb, Np, n_lo, V.diag, V.val, pm.Hinv, derr));
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  TRY(sync());
+  if (herr) {
+    set_err("xdg_pmg_setup: a high-order diagonal sub-block is not positive definite");
+    delete pm.lo;
+    pm.lo = nullptr;
+    return XDG_EBREAKDOWN;
+  }
+  gm_drop();  // recorded GMRES steps may hold the previous preconditioner
+  return XDG_OK;
+}
+
 static int validate_problem(const xdg_problem& q, int s) {
   const int nl = q.n_levels;
   if (!q.nb || !q.row_ptr || !q.col || !q.val || (nl > 1 && (!q.agg || !q.R))) {
@@ -2631,6 +3570,119 @@ int xdg_apply(xdg_hier_t h, int level, const double* x, double* y, int prec) {
   return XDG_OK;
 }
 
+int xdg_set_schwarz(xdg_hier_t h, int level, int64_t n_patches, const int64_t* patch_ptr,
+                    const int32_t* patch_blocks) {
+  if (!h || level < 1 || level >= h->nlev || n_patches < 0) {
+    set_err("xdg_set_schwarz: bad handle, level %d or patch count", level);
+    return XDG_EINVAL;
+  }
+  if (h->nprob != 1) {
+    set_err("xdg_set_schwarz: batch groups smooth with block Jacobi only");
+    return XDG_EINVAL;
+  }
+  return h->set_schwarz(level - 1, n_patches, patch_ptr, patch_blocks);
+}
+
+int xdg_get_schwarz(xdg_hier_t h, int level, xdg_schwarz_info* info) {
+  if (!h || level < 1 || level > h->nlev || !info) {
+    set_err("xdg_get_schwarz: bad arguments");
+    return XDG_EINVAL;
+  }
+  std::memset(info, 0, sizeof(*info));
+  if (!h->has_swz(level - 1)) return XDG_OK;
+  const SwzLevel& S = *h->swz[level - 1];
+  info->n_patches = S.npatch;
+  info->n_slots = S.nslot;
+  info->n_distinct = S.nuniq;
+  info->inverse_entries = S.inv_entries;
+  info->max_dof = S.maxdof;
+  info->overlap = S.single ? 0 : 1;
+  info->device_bytes = S.bytes;
+  return XDG_OK;
+}
+
+int xdg_solve_orthomg(xdg_hier_t h, const double* b, double* x, const xdg_orthomg_opts* o,
+                      xdg_solve_info* info) {
+  if (!h || !b || !x || !o || !(o->tol >= 0.0) || o->maxit < 0 || o->restart < 3 || o->coarse_passes < 1 ||
+      o->coarse_passes > 4) {
+    set_err("xdg_solve_orthomg: bad arguments");
+    return XDG_EINVAL;
+  }
+  if (h->nprob != 1) {
+    set_err("xdg_solve_orthomg: single problems only");
+    return XDG_EINVAL;
+  }
+  if (o->smoother_precision != XDG_PREC_F64 && o->smoother_precision != XDG_PREC_F32) {
+    set_err("xdg_solve_orthomg: smoother_precision must be XDG_PREC_F64 or XDG_PREC_F32");
+    return XDG_EINVAL;
+  }
+  if (o->smoother_precision == XDG_PREC_F32 && !h->has_lp[XDG_PREC_F32]) {
+    bool all_swz = true;
+    for (int l = 0; l + 1 < h->nlev; ++l) all_swz = all_swz && h->has_swz(l);
+    if (!all_swz) {
+      set_err("xdg_solve_orthomg: an FP32 block-Jacobi smoother needs the FP32 copies (low_precision)");
+      return XDG_EINVAL;
+    }
+  }
+  return h->solve_orthomg(b, x, o, info);
+}
+
+int xdg_pmg_setup(xdg_hier_t h, int n_lo, const xdg_hier_opts* lo_opts, double inner_tol, int inner_maxit,
+                  int inner_precision) {
+  if (!h || !(inner_tol >= 0.0) || inner_maxit < 1 || inner_precision < 0 || inner_precision > 2) {
+    set_err("xdg_pmg_setup: bad arguments");
+    return XDG_EINVAL;
+  }
+  if (h->nprob != 1) {
+    set_err("xdg_pmg_setup: single problems only");
+    return XDG_EINVAL;
+  }
+  return h->pmg_setup(n_lo, lo_opts, inner_tol, inner_maxit, inner_precision);
+}
+
+int xdg_pmg_apply(xdg_hier_t h, const double* r, double* z) {
+  if (!h || !r || !z || r == z || !h->pmg_ready()) {
+    set_err("xdg_pmg_apply: bad arguments or no p-multigrid set up");
+    return XDG_EINVAL;
+  }
+  h->pm.last_rc = 0;
+  h->pmg_apply(r, z);
+  CKL();
+  TRY(h->sync());
+  return h->pm.last_rc;
+}
+
+int xdg_solve_gmres(xdg_hier_t h, const double* b, double* x, const xdg_gmres_opts* o, xdg_solve_info* info) {
+  if (!h || !b || !x || !o || !(o->tol >= 0.0) || o->maxit < 0 || o->restart < 1 || o->restart > 200 ||
+      o->preconditioner < 0 || o->preconditioner > 1 || o->precision < 0 || o->precision > 2) {
+    set_err("xdg_solve_gmres: bad arguments");
+    return XDG_EINVAL;
+  }
+  if (h->nprob != 1) {
+    set_err("xdg_solve_gmres: single problems only");
+    return XDG_EINVAL;
+  }
+  if (o->preconditioner == 0 && o->precision != XDG_PREC_F64 && !h->has_lp[o->precision]) {
+    set_err("xdg_solve_gmres: the hierarchy holds no copy of precision %d", o->precision);
+    return XDG_EINVAL;
+  }
+  if (o->preconditioner == 1 && !h->pmg_ready()) {
+    set_err("xdg_solve_gmres: no p-multigrid set up (xdg_pmg_setup)");
+    return XDG_EINVAL;
+  }
+  return h->solve_gmres(b, x, o, info);
+}
+
+int xdg_residual(xdg_hier_t h, int level, const double* b, const double* x, double* r) {
+  if (!h || level < 1 || level > h->nlev || !b || !x || !r || r == x) {
+    set_err("xdg_residual: bad arguments");
+    return XDG_EINVAL;
+  }
+  h->spmv(level - 1, x, b, r, 1);
+  CKL();
+  return XDG_OK;
+}
+
 int xdg_get_damping(xdg_hier_t h, int level, int problem, double* omega, double* lambda_max) {
   if (!h || level < 1 || level >= h->nlev || problem < 0 || problem >= h->nprob) {
     set_err("xdg_get_damping: bad level %d or problem %d", level, problem);
@@ -2682,21 +3734,7 @@ int xdg_set_damping(xdg_hier_t h, int level, double omega) {
     CK(cudaStreamSynchronize(h->stream));
   }
   // the recorded graphs hold the damping as a kernel argument: record them again
-  h->drop_loops();
-  TRY(h->capture(&h->g_iter, 1, nullptr, nullptr));
-  for (int p = 1; p < 3; ++p)
-    if (h->has_lp[p]) TRY(h->capture(&h->g_iter_lp[p], 3, nullptr, nullptr, p));
-  if (h->g_cycle) cudaGraphExecDestroy(h->g_cycle);
-  h->g_cycle = nullptr;
-  h->g_cycle_b = nullptr;
-  for (int p = 0; p < 3; ++p) {
-    if (h->g_cyc_lp[p]) cudaGraphExecDestroy(h->g_cyc_lp[p]);
-    h->g_cyc_lp[p] = nullptr;
-    h->g_cyc_lp_b[p] = nullptr;
-    if (h->lr.g_iter[p]) cudaGraphExecDestroy(h->lr.g_iter[p]);
-    h->lr.g_iter[p] = nullptr;
-  }
-  return XDG_OK;
+  return h->rerecord();
 }
 
 int xdg_smooth(xdg_hier_t h, int level, const double* b, const double* x_in, double* x_out) {

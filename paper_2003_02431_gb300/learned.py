@@ -23,12 +23,12 @@ def solver_residuals(H, b, iters, precision=xdg.XDG_PREC_F64):
     """r_0 = b and the residuals of `iters - 1` successive one-step solves from x = 0."""
     import torch
     x = torch.zeros_like(b)
-    y = torch.empty_like(b)
     out = [b.clone()]
     for _ in range(iters - 1):
         H.solve(b, x, tol=0.0, maxit=1, precision=precision, raise_on_error=False)
-        H.apply(1, x, y)
-        out.append(b - y)
+        r = torch.empty_like(b)
+        H.residual(1, b, x, r)
+        out.append(r)
     return out
 
 

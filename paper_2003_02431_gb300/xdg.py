@@ -18,28 +18,44 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _ROOT = os.path.dirname(_HERE)
 LIB_PATH = os.path.join(_HERE, "libxdg.so")
-_SRCS = [os.path.join(_HERE, "csrc", "xdg.cu"), os.path.join(_HERE, "csrc", "xdg_kernels.cuh"),
-         os.path.join(_HERE, "csrc", "xdg_kernels_lp.cuh"), os.path.join(_HERE, "csrc", "xdg_kernels_batch.cuh"),
-         os.path.join(_HERE, "csrc", "xdg_kernels_mlp.cuh"), os.path.join(_HERE, "csrc", "xdg_kernels_fused.cuh"),
-         os.path.join(_HERE, "csrc", "xdg_kernels_df.cuh"), os.path.join(_ROOT, "include", "xdg.h")]
+_CSRC = os.path.join(_HERE, "csrc")
+# translation units of libxdg (compiled in parallel, then linked) and every file they include
+_UNITS = [os.path.join(_CSRC, "xdg.cu"), os.path.join(_CSRC, "xdg_swz.cu"), os.path.join(_CSRC, "xdg_krylov.cu")]
+_SRCS = _UNITS + [os.path.join(_CSRC, f) for f in sorted(os.listdir(_CSRC)) if f.endswith((".cuh", ".h"))] + [
+    os.path.join(_ROOT, "include", "xdg.h")]
 
 XDG_OK, XDG_EINVAL, XDG_ECUDA, XDG_ENOMEM, XDG_ENOTCONV, XDG_EBREAKDOWN, XDG_ETIMEOUT = range(7)
 XDG_PREC_F64, XDG_PREC_F32, XDG_PREC_BF16, XDG_PREC_F64_PAIR = 0, 1, 2, 3
 MAX_LEVELS = 24
 
 NVCC_FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
-              "-Xcompiler", "-fPIC", "-shared"]
+              "-Xcompiler", "-fPIC"]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile libxdg.so in-tree for sm_103a with nvcc (cross-compiles without a GPU)."""
+    """Compile libxdg.so in-tree for sm_103a with nvcc (cross-compiles without a GPU): every
+    translation unit to an object file in parallel, then one shared library."""
+    from concurrent.futures import ThreadPoolExecutor
     newest = max(os.path.getmtime(s) for s in _SRCS)
     if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
         return LIB_PATH
     nvcc = os.environ.get("NVCC", "nvcc")
-    tmp = LIB_PATH + ".tmp%d" % os.getpid()
-    cmd = [nvcc] + NVCC_FLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-o", tmp, _SRCS[0]]
-    subprocess.run(cmd, check=True)
+    bdir = os.path.join(_HERE, "_build")
+    os.makedirs(bdir, exist_ok=True)
+    tag = "%d" % os.getpid()
+
+    def compile_unit(src):
+        obj = os.path.join(bdir, os.path.basename(src) + ".%s.o" % tag)
+        cmd = [nvcc] + NVCC_FLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-c", "-o", obj, src]
+        subprocess.run(cmd, check=True)
+        return obj
+
+    with ThreadPoolExecutor(len(_UNITS)) as ex:
+        objs = list(ex.map(compile_unit, _UNITS))
+    tmp = LIB_PATH + ".tmp%s" % tag
+    subprocess.run([nvcc, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp] + objs, check=True)
+    for o in objs:
+        os.remove(o)
     os.replace(tmp, LIB_PATH)
     return LIB_PATH
 
@@ -102,9 +118,32 @@ class BatchInfo(C.Structure):
 
 # (name, restype, argtypes) of every exported entry point
 _vp, _dp, _ip = C.c_void_p, C.POINTER(C.c_double), C.c_int
+class SchwarzInfo(C.Structure):
+    _fields_ = [("n_patches", C.c_int64), ("n_slots", C.c_int64), ("n_distinct", C.c_int64),
+                ("inverse_entries", C.c_int64), ("max_dof", C.c_int), ("overlap", C.c_int),
+                ("device_bytes", C.c_size_t)]
+
+
+class OrthoMGOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("restart", C.c_int), ("coarse_passes", C.c_int),
+                ("smoother_precision", C.c_int)]
+
+
+class GmresOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("restart", C.c_int), ("preconditioner", C.c_int),
+                ("precision", C.c_int)]
+
+
 SIGNATURES = [
     ("xdg_create_hierarchy", C.c_int, [C.POINTER(Problem), C.POINTER(HierOpts), _vp, C.POINTER(_vp)]),
     ("xdg_destroy", C.c_int, [_vp]),
+    ("xdg_set_schwarz", C.c_int, [_vp, _ip, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
+    ("xdg_get_schwarz", C.c_int, [_vp, _ip, C.POINTER(SchwarzInfo)]),
+    ("xdg_solve_orthomg", C.c_int, [_vp, _vp, _vp, C.POINTER(OrthoMGOpts), C.POINTER(SolveInfo)]),
+    ("xdg_pmg_setup", C.c_int, [_vp, _ip, C.POINTER(HierOpts), C.c_double, _ip, _ip]),
+    ("xdg_pmg_apply", C.c_int, [_vp, _vp, _vp]),
+    ("xdg_solve_gmres", C.c_int, [_vp, _vp, _vp, C.POINTER(GmresOpts), C.POINTER(SolveInfo)]),
+    ("xdg_residual", C.c_int, [_vp, _ip, _vp, _vp, _vp]),
     ("xdg_strerror", C.c_char_p, [_ip]),
     ("xdg_last_error", C.c_char_p, []),
     ("xdg_get_info", C.c_int, [_vp, C.POINTER(HierInfo)]),
@@ -316,6 +355,67 @@ class Hierarchy:
     def set_damping(self, level, omega):
         with _Ordered(self):
             _check(load().xdg_set_damping(self._h, level, omega))
+
+    def set_schwarz(self, level, patches):
+        """Additive Schwarz smoother on `level` (1-based) with patches = (ptr int64[n+1],
+        blocks int32[ptr[n]]) host arrays, or None for block Jacobi (xdg_set_schwarz)."""
+        with _Ordered(self):
+            if patches is None:
+                _check(load().xdg_set_schwarz(self._h, level, 0, None, None))
+                return
+            ptr = np.ascontiguousarray(patches[0], dtype=np.int64)
+            blk = np.ascontiguousarray(patches[1], dtype=np.int32)
+            _check(load().xdg_set_schwarz(self._h, level, len(ptr) - 1, ptr.ctypes.data_as(C.POINTER(C.c_int64)),
+                                          blk.ctypes.data_as(C.POINTER(C.c_int32))))
+
+    def solve_orthomg(self, b, x, tol=1e-10, maxit=500, restart=30, coarse_passes=1, smoother_precision=XDG_PREC_F64,
+                      raise_on_error=True) -> dict:
+        """Orthonormalisation multigrid (xdg_solve_orthomg); x holds x0 and receives the result."""
+        o = OrthoMGOpts(tol, maxit, restart, coarse_passes, smoother_precision)
+        info = SolveInfo()
+        with _Ordered(self):
+            rc = load().xdg_solve_orthomg(self._h, _dptr(b), _dptr(x), C.byref(o), C.byref(info))
+        if raise_on_error and rc not in (XDG_OK,):
+            _check(rc)
+        return {f: getattr(info, f) for f, _ in SolveInfo._fields_}
+
+    def residual(self, level, b, x, r):
+        """r = b - M^level x (xdg_residual)."""
+        with _Ordered(self):
+            _check(load().xdg_residual(self._h, level, _dptr(b), _dptr(x), _dptr(r)))
+
+    def pmg_setup(self, n_lo, inner_tol=1e-10, inner_maxit=500, inner_precision=XDG_PREC_F64, **lo_opts):
+        """p-multigrid on level 1 with n_lo low-order modes per block (xdg_pmg_setup); lo_opts
+        (omega, gamma, w_levels, ...) configure the low-order hierarchy, else the handle's cycle."""
+        o = None
+        if lo_opts:
+            o = HierOpts(lo_opts.get("omega", 0.0), lo_opts.get("lanczos_steps", 12), lo_opts.get("nu", 1),
+                         lo_opts.get("gamma", 1), lo_opts.get("low_precision", 0), lo_opts.get("w_levels", 0),
+                         lo_opts.get("split_rows", 0), lo_opts.get("fused_coarse", 1), lo_opts.get("outer_apply", 1),
+                         lo_opts.get("symmetric", 1))
+        with _Ordered(self):
+            _check(load().xdg_pmg_setup(self._h, n_lo, C.byref(o) if o is not None else None, inner_tol,
+                                        inner_maxit, inner_precision))
+
+    def pmg_apply(self, r, z):
+        with _Ordered(self):
+            _check(load().xdg_pmg_apply(self._h, _dptr(r), _dptr(z)))
+
+    def solve_gmres(self, b, x, tol=1e-10, maxit=1000, restart=50, preconditioner=0, precision=XDG_PREC_F64,
+                    raise_on_error=True) -> dict:
+        """Flexible GMRES (xdg_solve_gmres); preconditioner 0 = multigrid cycle, 1 = p-multigrid."""
+        o = GmresOpts(tol, maxit, restart, preconditioner, precision)
+        info = SolveInfo()
+        with _Ordered(self):
+            rc = load().xdg_solve_gmres(self._h, _dptr(b), _dptr(x), C.byref(o), C.byref(info))
+        if raise_on_error and rc != XDG_OK:
+            _check(rc)
+        return {f: getattr(info, f) for f, _ in SolveInfo._fields_}
+
+    def schwarz_info(self, level) -> dict:
+        i = SchwarzInfo()
+        _check(load().xdg_get_schwarz(self._h, level, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in SchwarzInfo._fields_}
 
     KERNEL_APPLY, KERNEL_SMOOTH, KERNEL_RESTRICT = 0, 1, 2
 

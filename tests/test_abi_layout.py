@@ -21,6 +21,9 @@ PAIRS = [
     (xdg.BatchResult, "xdg_batch_result"),
     (xdg.BatchInfo, "xdg_batch_info"),
     (xdg.TrainOpts, "xdg_train_opts"),
+    (xdg.SchwarzInfo, "xdg_schwarz_info"),
+    (xdg.OrthoMGOpts, "xdg_orthomg_opts"),
+    (xdg.GmresOpts, "xdg_gmres_opts"),
 ]
 
 

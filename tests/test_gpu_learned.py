@@ -189,8 +189,10 @@ def test_gain_on_held_out_problem(trained):
     """What the trained network gains: on a held-out radius it recovers more of the exact local
     solve's energy decrease than a block-Jacobi step on the same unit does (measured: -0.93 vs
     -0.83 at 16^3). In the solve the correction keeps the accuracy and the iteration count
-    (the exact pair solve itself saves only about 2 of 52 iterations here: the slow modes of
-    this multigrid are not local to the cut cells)."""
+    within 2 (measured here: 53 against 52; the exact pair solve itself saves only about 2 of 52
+    iterations: the slow modes of this multigrid are not local to the cut cells). Its wall time
+    is not asserted: the three extra kernels per iteration cost about as much as the iterations
+    saved (measured at 64^3: 61 instead of 65 iterations, 66.9 against 65.0 ms)."""
     net, *_ = trained
     P = xp.Problem(_cfg(16, 0.29))
     G = xdg.Hierarchy.from_problem(P, gamma=GAMMA, w_levels=WLEV, low_precision=1)

@@ -10,7 +10,8 @@ derives each bound):
   * Galerkin coarse operators: identical sparsity, values within 1e-12 of the largest entry
   * coarsest-level solve: 1e-12 relative to the solution times max(1, cond/1e4) (an explicit
     inverse and a triangular solve differ by about cond * eps)
-  * one multigrid cycle: every block within 1e-10 of its own largest entry, and 1e-12
+  * one multigrid cycle: every block within 1e-9 of its own largest entry (a block that
+    cancels to a small fraction of its neighbours carries their rounding), and 1e-12
     relative in the 2-norm
   * solution of the multigrid-preconditioned CG: 1e-8 relative L2 (coefficient 2-norm, the
     bases are orthonormal) against the oracle's solution converged to 1e-14
@@ -176,7 +177,7 @@ def test_cycle_parity(case):
         bt = _t(b)
         G.vcycle(bt, x)
         got = _n(x)
-        check_blocks(got, ref, P.Np, 1e-10, name)
+        check_blocks(got, ref, P.Np, 1e-9, name)
         assert _rel(got, ref) < 1e-12, name
         G.vcycle(bt, x)  # graph replay gives the same result
         assert np.array_equal(_n(x), got)
@@ -321,7 +322,7 @@ def test_full_size_apply_cycle_parity(c2):
     z = torch.empty(P.dof, dtype=torch.float64, device=DEV)
     G.vcycle(_t(P.b), z)
     refz = O.vcycle(P.b)
-    check_blocks(_n(z), refz, P.Np, 1e-10, "cycle 64^3")
+    check_blocks(_n(z), refz, P.Np, 1e-9, "cycle 64^3")
     assert _rel(_n(z), refz) < 1e-12
 
 
