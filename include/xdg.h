@@ -115,9 +115,11 @@ typedef struct {
                          1 = never split; 2 = split on every level */
   int fused_coarse;   /* low-precision cycle: the V-cycle of the small levels below the W levels
                          (from the first of them with at most 16384 blocks) as one persistent
-                         cooperative launch with grid barriers between its steps: 0 = if it
-                         measures faster at creation, 1 = never, 2 = always (single problems
-                         only; batches launch every step) */
+                         launch: a cooperative grid with grid barriers between its steps, or a
+                         single thread-block cluster of 16 (else 8) CTAs with hardware cluster
+                         barriers. 0 = the fastest of per-step, grid and cluster launches
+                         measured at creation, 1 = never, 2 = always the grid form, 3 = always
+                         the cluster form (single problems only; batches launch every step) */
   int outer_apply;    /* operator apply q = M p of the flexible CG around a low-precision cycle:
                          0 = the FP32-pair product (XDG_PREC_F64_PAIR) if it measures faster at
                          creation, 1 = FP64, 2 = FP32 pairs (the FP64 solve uses FP64) */
@@ -165,6 +167,8 @@ typedef struct {
   int outer_pair;         /* 1: the mixed-precision solves apply M with FP32 pairs */
   int symmetric;          /* bit 0: symmetric storage of level 1 exists; bit 1: the
                              low-precision cycle reads it; bit 2: the pair product reads it */
+  int fused_cluster;      /* > 0: the fused small levels run as one thread-block cluster of
+                             this many CTAs (0: grid form or not fused) */
 } xdg_hier_info;
 
 /* Build the hierarchy on the current CUDA device: validate every index on the host
@@ -196,6 +200,14 @@ int xdg_export_level(xdg_hier_t h, int level, int64_t* row_ptr, int32_t* col, do
  * XDG_PREC_F64_PAIR on level 1 of a hierarchy that holds the pair copy (xdg_get_info's
  * outer_pair, or outer_apply = 2); x is split into scaled FP32 pairs in the handle's scratch. */
 int xdg_apply(xdg_hier_t h, int level, const double* x, double* y, int prec);
+
+/* Test of the bounded waits (no counterpart in the paper): on != 0 makes every grid barrier of
+ * the fused small-level cycle (xdg_hier_opts.fused_coarse) wait for one CTA more than the
+ * launch has. Each barrier then gives up after its poll limit (about 0.3 s), sets the error
+ * word and lets the kernel finish; the solve returns XDG_ETIMEOUT ("a grid barrier timed out")
+ * and the context stays usable. on = 0 restores the normal barriers. XDG_EINVAL when the
+ * hierarchy runs no fused cycle. Synchronises. */
+int xdg_test_barrier_timeout(xdg_hier_t h, int on);
 
 /* r = b - M^level x (FP64, device vectors; r may equal b but not x), Eq. GenericMatrixSystem. */
 int xdg_residual(xdg_hier_t h, int level, const double* b, const double* x, double* r);

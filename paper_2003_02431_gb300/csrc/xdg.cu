@@ -290,6 +290,8 @@ struct OpsLP {
                          const float*, float, const float*, float*, float*);
   cudaError_t (*fused)(cudaStream_t, int grid, const FusedCycle*, int pre0);
   int (*fused_occupancy)();
+  cudaError_t (*fused_cluster)(cudaStream_t, int csize, const FusedCycle*, int pre0);
+  bool (*fused_cluster_ok)(int csize);
   // level 1 on the symmetric storage (sweep from a nonzero guess; residual-restriction)
   void (*smooth_sym)(int, cudaStream_t, int64_t, const int64_t*, const int32_t*, const float*, const float*, SymL,
                      const float*, const float*, float, const float*, const float*, const float*, float*,
@@ -378,12 +380,54 @@ struct OpsLPT {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_fused_vcycle<NP, TS>, F, pre0);
+    return cudaLaunchKernelEx(&cfg, k_fused_vcycle<NP, TS, false>, F, pre0);
   }
   static int fused_occupancy() {
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused_vcycle<NP, TS>, kThreads, 0) != cudaSuccess) occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused_vcycle<NP, TS, false>, kThreads, 0) != cudaSuccess)
+      occ = 0;
     return occ;
+  }
+  // the same cycle as one thread-block cluster of csize CTAs (csize <= 16)
+  static cudaError_t fused_cluster(cudaStream_t s, int csize, const FusedCycle* F, int pre0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)csize);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_fused_vcycle<NP, TS, true>, F, pre0);
+  }
+  // whether a cluster of csize CTAs of the cluster kernel can be resident
+  static bool fused_cluster_ok(int csize) {
+    if (csize > 8 &&
+        cudaFuncSetAttribute(k_fused_vcycle<NP, TS, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)csize);
+    cfg.blockDim = dim3(kThreads);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_fused_vcycle<NP, TS, true>, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return n >= 1;
   }
   static void smooth_sym(int grid, cudaStream_t s, int64_t nb, const int64_t* urp, const int32_t* ucol,
                          const float* uval, const float* usc, SymL Ls, const float* Dinv, const float* dsc, float om,
@@ -397,7 +441,7 @@ struct OpsLPT {
   }
   static OpsLP get() {
     return OpsLP{make, spmv_f, spmv_d, smooth, resid_rt, gather, prolong, resid32, gather_smooth0, fused,
-                 fused_occupancy, smooth_sym, resid_rt_sym, sizeof(TS)};
+                 fused_occupancy, fused_cluster, fused_cluster_ok, smooth_sym, resid_rt_sym, sizeof(TS)};
   }
 };
 
@@ -1035,7 +1079,12 @@ struct xdg_hier {
   // ---------------------------------------------------------------- low-precision cycle
   void cycle_lp(int p, int l, const float* b, float* x, bool pre0 = false) {
     const OpsLP& o = opl[p];
-    if (fused_on[p] && l == fused_lc && pre0 && b == LP[p][l].b && x == LP[p][l].x) {
+    if (fused_on[p] && l == fused_start[p] && pre0 && b == LP[p][l].b && x == LP[p][l].x && fused_csize[p] > 0) {
+      o.fused_cluster(stream, fused_csize[p], fdesc[p], 1);
+      ++launches;
+      return;
+    }
+    if (fused_on[p] && l == fused_start[p] && pre0 && b == LP[p][l].b && x == LP[p][l].x) {
       cudaMemsetAsync(fbar, 0, sizeof(unsigned), stream);
       o.fused(stream, fused_grid[p], fdesc[p], 1);
       ++launches;
@@ -1181,13 +1230,16 @@ struct xdg_hier {
   int split_mode = 0;  // xdg_hier_opts.split_rows
   // small levels of the low-precision cycle as one persistent launch (levels fused_lc..)
   int fused_mode = 0;  // xdg_hier_opts.fused_coarse
-  int fused_lc = -1;
+  int fused_lc = -1;                // the first level the fused cycle may start at
+  int fused_start[3] = {-1, -1, -1};  // the level it starts at, per precision (the descriptor's first)
   bool fused_on[3] = {false, false, false};
   int fused_grid[3] = {0, 0, 0};
+  int fused_csize[3] = {0, 0, 0};  // > 0: the fused cycle runs as one cluster of this many CTAs
   FusedCycle* fdesc[3] = {nullptr, nullptr, nullptr};
   unsigned* fbar = nullptr;
   int* ferr = nullptr;
-  int write_fused(int p);
+  unsigned fused_extra = 0;  // xdg_test_barrier_timeout
+  int write_fused(int p, int start = -1);
   int tune_fused(int p);
   int fused_error();
 
@@ -1820,8 +1872,15 @@ int xdg_hier::build_lp(int p) {
   }
   TRY(write_fused(p));
   if (fused_lc >= 0 && nprob == 1 && fused_mode != 1) {
-    if (fused_mode == 2) fused_on[p] = true;
-    else TRY(tune_fused(p));
+    if (fused_mode == 2) {
+      fused_on[p] = true;
+    } else if (fused_mode == 3) {
+      for (int cs : {16, 8})
+        if (fused_csize[p] == 0 && opl[p].fused_cluster_ok(cs)) fused_csize[p] = cs;
+      fused_on[p] = fused_csize[p] > 0;
+    } else {
+      TRY(tune_fused(p));
+    }
   }
   TRY(capture(&g_iter_lp[p], 3, nullptr, nullptr, p));
   return XDG_OK;
@@ -1839,11 +1898,14 @@ int xdg_hier::build_lp(int p) {
 // The fused small-level cycle of precision p: the first fused level is the first level below
 // the W-cycle levels (at least level 2) with at most 16384 blocks, if it lies above the
 // coarsest; the descriptor lists every fused level's arrays.
-int xdg_hier::write_fused(int p) {
+int xdg_hier::write_fused(int p, int start) {
   fused_lc = -1;
   const int lc = std::max(1, std::min(wlev, nlev));
   if (lc + 2 > nlev || L[lc].nb > 16384 || nlev - lc > kFusedMaxLevels) return XDG_OK;
   fused_lc = lc;
+  if (start < 0) start = fused_start[p] >= lc ? fused_start[p] : lc;
+  if (start + 2 > nlev) start = lc;
+  fused_start[p] = start;
   if (!fbar) {
     TRY(alloc(&fbar, 1));
     TRY(alloc(&ferr, 1));
@@ -1852,12 +1914,12 @@ int xdg_hier::write_fused(int p) {
   if (!fdesc[p]) TRY(alloc(&fdesc[p], 1));
   FusedCycle h;
   std::memset(&h, 0, sizeof(h));
-  h.n = nlev - lc;
+  h.n = nlev - start;
   h.nu = nu;
-  for (int l = lc; l < nlev; ++l) {
+  for (int l = start; l < nlev; ++l) {
     Level& V = L[l];
     LevelLP& W = LP[p][l];
-    FusedLevel& f = h.L[l - lc];
+    FusedLevel& f = h.L[l - start];
     f.nb = V.nb;
     f.rp = V.rp;
     f.col = V.col;
@@ -1884,6 +1946,7 @@ int xdg_hier::write_fused(int p) {
   h.nc = nc;
   h.bar = fbar;
   h.err = ferr;
+  h.extra = fused_extra;
   CK(cudaMemcpyAsync(fdesc[p], &h, sizeof(h), cudaMemcpyHostToDevice, stream));
   const int occ = opl[p].fused_occupancy();
   fused_grid[p] = std::max(1, std::min(occ, XDG_FUSED_CTAS_PER_SM)) * sms;
@@ -1892,7 +1955,9 @@ int xdg_hier::write_fused(int p) {
   return XDG_OK;
 }
 
-// time the low-precision cycle with the small levels fused and launched per step; keep the faster
+// time the low-precision cycle with the small levels launched per step, fused in one
+// cooperative grid, and fused in one thread-block cluster of 16 or 8 CTAs; keep the fastest
+// (a fused form only when >= 3 % faster than per step)
 int xdg_hier::tune_fused(int p) {
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
@@ -1900,10 +1965,27 @@ int xdg_hier::tune_fused(int p) {
   LevelLP& W = LP[p][0];
   const int64_t n = L[0].nb * Np;
   CK(cudaMemsetAsync(W.r, 0, n * sizeof(float), stream));
-  float ms[2] = {0.f, 0.f};
+  struct Cand {
+    bool on;
+    int csize, start;
+  };
+  // starts: the first level below the W levels, and (for a cluster, which has few SMs) the first
+  // level with at most 1024 blocks if that lies lower and above the coarsest
+  int lsmall = fused_lc;
+  while (lsmall + 2 < nlev && L[lsmall].nb > 1024) ++lsmall;
+  std::vector<Cand> cands = {{false, 0, fused_lc}, {true, 0, fused_lc}};
+  for (int cs : {16, 8}) {
+    if (!opl[p].fused_cluster_ok(cs)) continue;
+    cands.push_back({true, cs, fused_lc});
+    if (lsmall > fused_lc && L[lsmall].nb <= 1024) cands.push_back({true, cs, lsmall});
+    break;
+  }
+  std::vector<float> ms(cands.size(), 0.f);
   int rc = XDG_OK;
-  for (int v = 0; v < 2 && rc == XDG_OK; ++v) {
-    fused_on[p] = (v == 1);
+  for (size_t v = 0; v < cands.size() && rc == XDG_OK; ++v) {
+    fused_on[p] = cands[v].on;
+    fused_csize[p] = cands[v].csize;
+    if (cands[v].on) TRY(write_fused(p, cands[v].start));
     for (int k = 0; k < 2; ++k) cycle_lp(p, 0, W.r, W.dz);
     cudaEventRecord(e0, stream);
     for (int k = 0; k < 10; ++k) cycle_lp(p, 0, W.r, W.dz);
@@ -1913,13 +1995,19 @@ int xdg_hier::tune_fused(int p) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  fused_on[p] = false;
+  fused_csize[p] = 0;
   if (rc) {
-    fused_on[p] = false;
     set_err("fused-cycle tuning: %s", cudaGetErrorString(cudaGetLastError()));
     return rc;
   }
   TRY(fused_error());
-  fused_on[p] = ms[1] < 0.97f * ms[0];
+  size_t best = 0;
+  for (size_t v = 1; v < cands.size(); ++v)
+    if (ms[v] < 0.97f * ms[0] && ms[v] < ms[best]) best = v;
+  fused_on[p] = cands[best].on;
+  fused_csize[p] = cands[best].csize;
+  TRY(write_fused(p, cands[best].start));
   return XDG_OK;
 }
 
@@ -1932,7 +2020,7 @@ int xdg_hier::fused_error() {
   if (h) {
     cudaMemsetAsync(ferr, 0, sizeof(int), stream);
     set_err("fused small-level cycle: a grid barrier timed out");
-    return XDG_ECUDA;
+    return XDG_ETIMEOUT;
   }
   return XDG_OK;
 }
@@ -2455,8 +2543,8 @@ int xdg_hier::set_schwarz(int l, int64_t npatch, const int64_t* pptr, const int3
   }
   swz[l] = std::move(S);
   // the fused small-level cycle holds block-Jacobi steps: not for levels with Schwarz
-  if (fused_lc >= 0 && l >= fused_lc)
-    for (bool& f : fused_on) f = false;
+  for (int q = 1; q < 3; ++q)
+    if (fused_start[q] >= 0 && l >= fused_start[q]) fused_on[q] = false;
   double lm = 0.0;
   int rc = lanczos_swz(l, lanczos_m, &lm);
   if (rc) {
@@ -3506,7 +3594,8 @@ int xdg_get_info(xdg_hier_t h, xdg_hier_info* info) {
   for (int i = 0; i < 3; ++i) info->setup_ms[i] = h->setup_ms[i];
   for (int l = 0; l < h->nlev && l < 64; ++l)
     if (h->L[l].spl) info->split_mask |= (uint64_t)1 << l;
-  info->fused_level = (h->fused_on[1] || h->fused_on[2]) ? h->fused_lc + 1 : 0;
+  info->fused_level = h->fused_on[1] ? h->fused_start[1] + 1 : (h->fused_on[2] ? h->fused_start[2] + 1 : 0);
+  info->fused_cluster = h->fused_on[1] ? h->fused_csize[1] : (h->fused_on[2] ? h->fused_csize[2] : 0);
   info->outer_pair = h->pair_on ? 1 : 0;
   info->symmetric = (h->sym_built ? 1 : 0) | (h->sym_on && !h->L[0].spl ? 2 : 0) | (h->sym_pair ? 4 : 0);
   return XDG_OK;
@@ -3671,6 +3760,24 @@ int xdg_solve_gmres(xdg_hier_t h, const double* b, double* x, const xdg_gmres_op
     return XDG_EINVAL;
   }
   return h->solve_gmres(b, x, o, info);
+}
+
+int xdg_test_barrier_timeout(xdg_hier_t h, int on) {
+  if (!h) {
+    set_err("xdg_test_barrier_timeout: null handle");
+    return XDG_EINVAL;
+  }
+  bool any = false;
+  for (int p = 1; p < 3; ++p) any = any || (h->fused_on[p] && h->fused_csize[p] == 0);
+  if (!any) {
+    set_err("xdg_test_barrier_timeout: the hierarchy runs no fused small-level cycle with grid barriers");
+    return XDG_EINVAL;
+  }
+  TRY(h->sync());
+  h->fused_extra = on ? 1u : 0u;
+  for (int p = 1; p < 3; ++p)
+    if (h->fused_on[p]) TRY(h->write_fused(p));
+  return h->sync();
 }
 
 int xdg_residual(xdg_hier_t h, int level, const double* b, const double* x, double* r) {

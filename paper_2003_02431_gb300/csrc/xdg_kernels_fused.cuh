@@ -49,9 +49,11 @@ struct FusedCycle {
   int64_t nc;
   unsigned* bar;  // barrier counter (zero at launch)
   int* err;       // nonzero: a barrier gave up
+  unsigned extra; // 0; 1 makes every barrier wait for one CTA more than the grid has (a test of
+                  // the bounded wait: the barriers give up and report, nothing hangs)
 };
 
-__device__ __forceinline__ void fused_barrier(unsigned* bar, unsigned& phase, int* err) {
+__device__ __forceinline__ void fused_barrier(unsigned* bar, unsigned& phase, int* err, unsigned extra) {
   __syncthreads();
   ++phase;
   if (threadIdx.x == 0) {
@@ -59,7 +61,7 @@ __device__ __forceinline__ void fused_barrier(unsigned* bar, unsigned& phase, in
     if (*verr == 0) {
       __threadfence();
       atomicAdd(bar, 1u);
-      const unsigned target = phase * gridDim.x;
+      const unsigned target = phase * (gridDim.x + extra);
       volatile unsigned* vbar = bar;
       unsigned spins = 0;
       while (*vbar < target) {
@@ -76,6 +78,20 @@ __device__ __forceinline__ void fused_barrier(unsigned* bar, unsigned& phase, in
   __syncthreads();
 }
 
+// The same step separation for a launch that is one thread-block cluster: the hardware cluster
+// barrier (arrive with release, wait with acquire semantics at cluster scope) orders the
+// steps' global-memory writes before the next step's reads; those reads bypass L1 (.cg) as in
+// the grid-wide form. No polling, so nothing to bound.
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+template <bool CLUSTER>
+__device__ __forceinline__ void step_barrier(unsigned* bar, unsigned& phase, int* err, unsigned extra) {
+  if (CLUSTER) cluster_barrier();
+  else fused_barrier(bar, phase, err, extra);
+}
+
 template <int NP, bool ZERO>
 __device__ __forceinline__ void fused_smooth(const FusedLevel& V, int64_t warp, int64_t nw, const float* xi, float* xo) {
   if (V.spl)
@@ -86,8 +102,10 @@ __device__ __forceinline__ void fused_smooth(const FusedLevel& V, int64_t warp, 
                                            V.b, xi, xo, nullptr);
 }
 
-// pre0: the first sweep on the fused part's first level has been done (x holds it)
-template <int NP, class TS>
+// pre0: the first sweep on the fused part's first level has been done (x holds it).
+// CLUSTER: the launch is a single thread-block cluster (its CTAs separated by cluster
+// barriers); otherwise a cooperative grid (grid-wide barriers).
+template <int NP, class TS, bool CLUSTER>
 __global__ void __launch_bounds__(kThreads) k_fused_vcycle(const FusedCycle* __restrict__ F, int pre0) {
   pdl_entry();
   const int64_t warp = grid_warp(), nw = grid_warps();
@@ -105,11 +123,11 @@ __global__ void __launch_bounds__(kThreads) k_fused_vcycle(const FusedCycle* __r
     float* o = V.t;
     if (l == 0 && !pre0) {
       fused_smooth<NP, true>(V, warp, nw, nullptr, c);
-      fused_barrier(bar, phase, err);
+      step_barrier<CLUSTER>(bar, phase, err, F->extra);
     }
     for (int s = 1; s < nu; ++s) {
       fused_smooth<NP, false>(V, warp, nw, c, o);
-      fused_barrier(bar, phase, err);
+      step_barrier<CLUSTER>(bar, phase, err, F->extra);
       float* tmp = c;
       c = o;
       o = tmp;
@@ -121,19 +139,19 @@ __global__ void __launch_bounds__(kThreads) k_fused_vcycle(const FusedCycle* __r
     else
       resid_rt_lp_rows<NP, float, TS, true, false, true>(warp, nw, V.nb, V.rp, V.col, V.val, V.sc, (const TS*)V.R, V.rsc,
                                                    V.b, c, V.s, nullptr);
-    fused_barrier(bar, phase, err);
+    step_barrier<CLUSTER>(bar, phase, err, F->extra);
     if (l + 2 < n) {  // phase 2 and the coarse level's first sweep
       gather_smooth0_lp_rows<NP, true>(warp, nw, C.nb, V.cptr, V.ch, V.s, C.Dinv, C.dsc, C.omega, nullptr, C.b, C.x);
     } else {
       gather_lp_elems<NP, true>(tid, nt, C.nb, V.cptr, V.ch, V.s, C.b);
     }
-    fused_barrier(bar, phase, err);
+    step_barrier<CLUSTER>(bar, phase, err, F->extra);
   }
   // coarsest direct solve (FP64 inverse)
   {
     const FusedLevel& C = F->L[n - 1];
     gemv_seg_rows<float, true>(warp, nw, F->nc, F->nseg, F->doff, F->moff, F->Minv, C.b, C.x);
-    fused_barrier(bar, phase, err);
+    step_barrier<CLUSTER>(bar, phase, err, F->extra);
   }
   // up: prolongation, post-smoothing
   for (int l = n - 2; l >= 0; --l) {
@@ -143,19 +161,19 @@ __global__ void __launch_bounds__(kThreads) k_fused_vcycle(const FusedCycle* __r
     float* after = (nu % 2 == 0) ? x : V.t;
     float* c = cur[l];
     prolong_lp_rows<NP, TS, true>(warp, nw, V.nb, V.agg, (const TS*)V.R, V.rsc, C.x, c, after, nullptr);
-    fused_barrier(bar, phase, err);
+    step_barrier<CLUSTER>(bar, phase, err, F->extra);
     c = after;
     float* o = (c == x) ? V.t : x;
     for (int s = 0; s < nu; ++s) {
       fused_smooth<NP, false>(V, warp, nw, c, o);
-      fused_barrier(bar, phase, err);
+      step_barrier<CLUSTER>(bar, phase, err, F->extra);
       float* tmp = c;
       c = o;
       o = tmp;
     }
     if (c != x) {
       for (int64_t e = tid; e < V.nb * NP; e += nt) x[e] = __ldcg(c + e);
-      fused_barrier(bar, phase, err);
+      step_barrier<CLUSTER>(bar, phase, err, F->extra);
     }
   }
 }

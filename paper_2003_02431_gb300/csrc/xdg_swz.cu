@@ -193,63 +193,144 @@ constexpr int stage_max_n() {
   return sizeof(T) == 8 ? 78 : 110;
 }
 
-// y = A (isq .* r)_P for one patch (one warp), A column-major n x n (the symmetric inverse)
-template <int NP, class T, int OUT>
-__device__ __forceinline__ void patch_solve(const T* A, T* v, int64_t p0, int n, const int32_t* __restrict__ pblk,
-                                            const T* __restrict__ isq, const T* __restrict__ r, T om,
-                                            const T* __restrict__ xin, T* __restrict__ out) {
-  constexpr int RPL = kMaxDof / 32;  // rows per lane at most
+// y = A (isq .* r)_P for one patch (one warp), A column-major n x n (the symmetric inverse);
+// R = rows per lane = ceil(n / 32) as a compile-time constant (up to 8), so that the inner loop
+// issues only the loads and FMAs of real rows; larger patches take the loop with R = 16 rows
+// guarded at run time. np (modes per block) and the output form are run-time values: they
+// only enter the gather and the scatter.
+template <class T>
+__device__ __forceinline__ void patch_gather(T* v, int64_t p0, int n, int np, const int32_t* __restrict__ pblk,
+                                             const T* __restrict__ isq, const T* __restrict__ r) {
   const int lane = threadIdx.x & 31;
   for (int e = lane; e < n; e += 32) {
-    const int a = e / NP, q = e - a * NP;
+    const int a = e / np, q = e - a * np;
     const int32_t b = __ldg(pblk + p0 + a);
-    v[e] = ldg_t(isq + b) * r[(int64_t)b * NP + q];
+    v[e] = ldg_t(isq + b) * r[(int64_t)b * np + q];
   }
   __syncwarp();
-  const int rows = (n + 31) >> 5;
-  T acc[RPL];
+}
+
+template <class T>
+__device__ __forceinline__ void patch_store(int i, T acc, int64_t p0, int np, int out_mode,
+                                            const int32_t* __restrict__ pblk, const T* __restrict__ isq, T om,
+                                            const T* __restrict__ xin, T* __restrict__ out) {
+  const int a = i / np, q = i - a * np;
+  if (out_mode == 0) {
+    out[(p0 + a) * np + q] = acc;
+  } else {
+    const int32_t b = __ldg(pblk + p0 + a);
+    const int64_t o = (int64_t)b * np + q;
+    const T y = om * ldg_t(isq + b) * acc;
+    out[o] = (out_mode == 2) ? xin[o] + y : y;
+  }
+}
+
+template <class T, int R>
+__device__ __forceinline__ void patch_solve_r(const T* A, T* v, int64_t p0, int n, int np, int out_mode,
+                                              const int32_t* __restrict__ pblk, const T* __restrict__ isq,
+                                              const T* __restrict__ r, T om, const T* __restrict__ xin,
+                                              T* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  patch_gather(v, p0, n, np, pblk, isq, r);
+  // rows lane + 32k; a row beyond n reads row n - 1 (in bounds) and is not stored
+  int row[R];
 #pragma unroll
-  for (int k = 0; k < RPL; ++k) acc[k] = T(0);
+  for (int k = 0; k < R; ++k) row[k] = min(lane + 32 * k, n - 1);
+  T acc[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) acc[k] = T(0);
   int j = 0;
   for (; j + 2 <= n; j += 2) {  // two columns per step: more loads in flight
     const T v0 = v[j], v1 = v[j + 1];
     const T* A0 = A + (int64_t)j * n;
     const T* A1 = A0 + n;
 #pragma unroll
-    for (int k = 0; k < RPL; ++k) {
-      const int i = lane + 32 * k;
-      if (k < rows && i < n) {
-        const T a0 = A0[i], a1 = A1[i];
-        acc[k] = fma(a0, v0, acc[k]);
-        acc[k] = fma(a1, v1, acc[k]);
-      }
+    for (int k = 0; k < R; ++k) {
+      const T a0 = A0[row[k]], a1 = A1[row[k]];
+      acc[k] = fma(a0, v0, acc[k]);
+      acc[k] = fma(a1, v1, acc[k]);
     }
   }
   if (j < n) {
     const T v0 = v[j];
     const T* A0 = A + (int64_t)j * n;
 #pragma unroll
-    for (int k = 0; k < RPL; ++k) {
+    for (int k = 0; k < R; ++k) acc[k] = fma(A0[row[k]], v0, acc[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < R; ++k)
+    if (lane + 32 * k < n) patch_store(lane + 32 * k, acc[k], p0, np, out_mode, pblk, isq, om, xin, out);
+  __syncwarp();
+}
+
+// patches of more than 256 modes: rows guarded at run time
+template <class T>
+__device__ __forceinline__ void patch_solve_big(const T* A, T* v, int64_t p0, int n, int np, int out_mode,
+                                                const int32_t* __restrict__ pblk, const T* __restrict__ isq,
+                                                const T* __restrict__ r, T om, const T* __restrict__ xin,
+                                                T* __restrict__ out) {
+  constexpr int RB = kMaxDof / 32;
+  const int lane = threadIdx.x & 31;
+  patch_gather(v, p0, n, np, pblk, isq, r);
+  const int rows = (n + 31) >> 5;
+  T acc[RB];
+#pragma unroll
+  for (int k = 0; k < RB; ++k) acc[k] = T(0);
+  for (int j = 0; j < n; ++j) {
+    const T vj = v[j];
+    const T* Aj = A + (int64_t)j * n;
+#pragma unroll
+    for (int k = 0; k < RB; ++k) {
       const int i = lane + 32 * k;
-      if (k < rows && i < n) acc[k] = fma(A0[i], v0, acc[k]);
+      if (k < rows && i < n) acc[k] = fma(Aj[i], vj, acc[k]);
     }
   }
 #pragma unroll
-  for (int k = 0; k < RPL; ++k) {
-    const int i = lane + 32 * k;
-    if (k < rows && i < n) {
-      const int a = i / NP, q = i - a * NP;
-      if (OUT == 0) {
-        out[(p0 + a) * NP + q] = acc[k];
-      } else {
-        const int32_t b = __ldg(pblk + p0 + a);
-        const int64_t o = (int64_t)b * NP + q;
-        const T y = om * ldg_t(isq + b) * acc[k];
-        out[o] = (OUT == 2) ? xin[o] + y : y;
-      }
-    }
-  }
+  for (int k = 0; k < RB; ++k)
+    if (k < rows && lane + 32 * k < n) patch_store(lane + 32 * k, acc[k], p0, np, out_mode, pblk, isq, om, xin, out);
   __syncwarp();
+}
+
+template <class T>
+__device__ __forceinline__ void patch_solve(const T* A, T* v, int64_t p0, int n, int np, int out_mode,
+                                            const int32_t* __restrict__ pblk, const T* __restrict__ isq,
+                                            const T* __restrict__ r, T om, const T* __restrict__ xin,
+                                            T* __restrict__ out) {
+  switch ((n + 31) >> 5) {
+#define R_(K) \
+  case K: patch_solve_r<T, K>(A, v, p0, n, np, out_mode, pblk, isq, r, om, xin, out); break;
+    R_(1) R_(2) R_(3) R_(4) R_(5) R_(6) R_(7) R_(8)
+#undef R_
+    default: patch_solve_big<T>(A, v, p0, n, np, out_mode, pblk, isq, r, om, xin, out); break;
+  }
+}
+
+// one patch spread over the CTA: warp w adds the columns of its slice for rows lane + 32k,
+// partial sums into part[w * vstride + i]; R rows per lane (R = 16: rows guarded at run time)
+template <class T, int R>
+__device__ __forceinline__ void split_cols(const T* A, const T* vc, T* part, int vstride, int n) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int per = (n + kWarps - 1) / kWarps;
+  const int j0 = wid * per, j1 = min(n, j0 + per);
+  const int rows = (n + 31) >> 5;
+  int row[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) row[k] = min(lane + 32 * k, n - 1);
+  T acc[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) acc[k] = T(0);
+  for (int j = j0; j < j1; ++j) {
+    const T vj = vc[j];
+    const T* Aj = A + (int64_t)j * n;
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+      if (R <= 8 || k < rows) acc[k] = fma(Aj[row[k]], vj, acc[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    const int i = lane + 32 * k;
+    if ((R <= 8 || k < rows) && i < n) part[wid * vstride + i] = acc[k];
+  }
 }
 
 // 16-byte asynchronous global -> shared copies (LDGSTS), completed by wait_group
@@ -277,7 +358,7 @@ __device__ __forceinline__ void stage_async(T* buf, const T* Ag, int n) {
 // (asynchronous copies). An item of several patches (a shared inverse) gives each warp its own
 // patches; an item of one patch (a distinct inverse) spreads the patch's rows over the CTA.
 // Inverses larger than the staging buffer are read from global memory.
-template <int NP, class T, int OUT>
+template <class T>
 __global__ void __launch_bounds__(kWarps * 32) k_swz_apply(int64_t nitem, const Item* __restrict__ items,
                                                           const int32_t* __restrict__ porder,
                                                           const int64_t* __restrict__ pptr,
@@ -285,7 +366,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_swz_apply(int64_t nitem, const 
                                                           const int64_t* __restrict__ ioff,
                                                           const T* __restrict__ Ainv, const T* __restrict__ isq,
                                                           const T* __restrict__ r, T om, const T* __restrict__ xin,
-                                                          T* __restrict__ out, int vstride, int stage_n) {
+                                                          T* __restrict__ out, int vstride, int stage_n, int np,
+                                                          int out_mode) {
   pdl_entry();
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int sbuf = ((stage_n * stage_n + 3) / 4) * 4;  // elements per staging buffer (16-byte multiple)
@@ -315,56 +397,31 @@ __global__ void __launch_bounds__(kWarps * 32) k_swz_apply(int64_t nitem, const 
     if (I.count > 1) {
       for (int q = wid; q < I.count; q += kWarps) {
         const int64_t p0 = __ldg(pptr + __ldg(porder + I.start + q));
-        patch_solve<NP, T, OUT>(A, v, p0, I.n, pblk, isq, r, om, xin, out);
+        patch_solve<T>(A, v, p0, I.n, np, out_mode, pblk, isq, r, om, xin, out);
       }
     } else {
       const int n = I.n;
       const int64_t p0 = __ldg(pptr + __ldg(porder + I.start));
       for (int e = threadIdx.x; e < n; e += blockDim.x) {
-        const int a = e / NP, q = e - a * NP;
+        const int a = e / np, q = e - a * np;
         const int32_t b = __ldg(pblk + p0 + a);
-        vc[e] = ldg_t(isq + b) * r[(int64_t)b * NP + q];
+        vc[e] = ldg_t(isq + b) * r[(int64_t)b * np + q];
       }
       __syncthreads();
       // the columns split over the warps (short dependent chains), partial sums per warp in
       // the warps' vector space, added in warp order
-      {
-        constexpr int RPL = kMaxDof / 32;
-        const int lane = threadIdx.x & 31;
-        const int rows = (n + 31) >> 5;
-        const int per = (n + kWarps - 1) / kWarps;
-        const int j0 = wid * per, j1 = min(n, j0 + per);
-        T acc[RPL];
-#pragma unroll
-        for (int k = 0; k < RPL; ++k) acc[k] = T(0);
-        for (int j = j0; j < j1; ++j) {
-          const T vj = vc[j];
-          const T* Aj = A + (int64_t)j * n;
-#pragma unroll
-          for (int k = 0; k < RPL; ++k) {
-            const int i = lane + 32 * k;
-            if (k < rows && i < n) acc[k] = fma(Aj[i], vj, acc[k]);
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < RPL; ++k) {
-          const int i = lane + 32 * k;
-          if (k < rows && i < n) vall[wid * vstride + i] = acc[k];
-        }
+      switch ((n + 31) >> 5) {
+#define R_(K) \
+  case K: split_cols<T, K>(A, vc, vall, vstride, n); break;
+        R_(1) R_(2) R_(3) R_(4) R_(5) R_(6) R_(7) R_(8)
+#undef R_
+        default: split_cols<T, kMaxDof / 32>(A, vc, vall, vstride, n); break;
       }
       __syncthreads();
       for (int i = threadIdx.x; i < n; i += blockDim.x) {
         T acc = T(0);
         for (int w = 0; w < kWarps; ++w) acc += vall[w * vstride + i];
-        const int a = i / NP, q = i - a * NP;
-        if (OUT == 0) {
-          out[(p0 + a) * NP + q] = acc;
-        } else {
-          const int32_t b = __ldg(pblk + p0 + a);
-          const int64_t o = (int64_t)b * NP + q;
-          const T y = om * ldg_t(isq + b) * acc;
-          out[o] = (OUT == 2) ? xin[o] + y : y;
-        }
+        patch_store(i, acc, p0, np, out_mode, pblk, isq, om, xin, out);
       }
     }
     __syncthreads();  // the buffer is refilled two items later
@@ -425,19 +482,15 @@ cudaError_t factor_t(cudaStream_t s, int64_t u0, int64_t u1, const int64_t* rep,
   return cudaGetLastError();
 }
 
-template <int NP, class T>
+template <class T>
 cudaError_t prepare_t() {
-  cudaError_t e = cudaSuccess;
-  const int sm = (int)kSmemOptIn;
-  for (auto k : {k_swz_apply<NP, T, 0>, k_swz_apply<NP, T, 1>, k_swz_apply<NP, T, 2>})
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  return e;
+  return cudaFuncSetAttribute(k_swz_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemOptIn);
 }
 
-template <int NP, class T>
-cudaError_t apply_t(cudaStream_t s, int grid, int out_mode, int64_t nitem, const Item* items, const int32_t* porder,
-                    const int64_t* pptr, const int32_t* pblk, const int64_t* ioff, const T* Ainv, const T* isq,
-                    const T* r, T om, const T* xin, T* out, int maxdof, int stage_n) {
+template <class T>
+cudaError_t apply_t(int np, cudaStream_t s, int grid, int out_mode, int64_t nitem, const Item* items,
+                    const int32_t* porder, const int64_t* pptr, const int32_t* pblk, const int64_t* ioff,
+                    const T* Ainv, const T* isq, const T* r, T om, const T* xin, T* out, int maxdof, int stage_n) {
   cudaLaunchAttribute at[1];
   const int g = (int)std::max<int64_t>(1, std::min<int64_t>(grid, nitem));
   cudaLaunchConfig_t cfg = pdl_cfg(dim3(g), dim3(kWarps * 32), s, at);
@@ -448,14 +501,8 @@ cudaError_t apply_t(cudaStream_t s, int grid, int out_mode, int64_t nitem, const
   };
   while (stage_n > 0 && smem(stage_n) > kSmemOptIn) --stage_n;
   cfg.dynamicSmemBytes = smem(stage_n);
-  if (out_mode == 0)
-    return cudaLaunchKernelEx(&cfg, k_swz_apply<NP, T, 0>, nitem, items, porder, pptr, pblk, ioff, Ainv, isq, r, om,
-                              xin, out, maxdof, stage_n);
-  if (out_mode == 1)
-    return cudaLaunchKernelEx(&cfg, k_swz_apply<NP, T, 1>, nitem, items, porder, pptr, pblk, ioff, Ainv, isq, r, om,
-                              xin, out, maxdof, stage_n);
-  return cudaLaunchKernelEx(&cfg, k_swz_apply<NP, T, 2>, nitem, items, porder, pptr, pblk, ioff, Ainv, isq, r, om,
-                            xin, out, maxdof, stage_n);
+  return cudaLaunchKernelEx(&cfg, k_swz_apply<T>, nitem, items, porder, pptr, pblk, ioff, Ainv, isq, r, om, xin, out,
+                            maxdof, stage_n, np, out_mode);
 }
 
 template <int NP, class T>
@@ -497,31 +544,18 @@ cudaError_t factor(int np, cudaStream_t s, int64_t u0, int64_t u1, const int64_t
 }
 
 cudaError_t prepare(int np) {
-  switch (np) {
-#define C_(N) \
-  case N: {                                   \
-    cudaError_t e = prepare_t<N, double>();   \
-    return e == cudaSuccess ? prepare_t<N, float>() : e; \
-  }
-    XDG_SWZ_NP(C_)
-#undef C_
-    default: return cudaErrorInvalidValue;
-  }
+  if (np < 1 || np > 32) return cudaErrorInvalidValue;
+  cudaError_t e = prepare_t<double>();
+  return e == cudaSuccess ? prepare_t<float>() : e;
 }
 
 template <class T>
 cudaError_t apply(int np, cudaStream_t s, int grid, int out_mode, int64_t nitem, const Item* items,
                   const int32_t* porder, const int64_t* pptr, const int32_t* pblk, const int64_t* ioff,
                   const T* Ainv, const T* isq, const T* r, T om, const T* xin, T* out, int maxdof, int stage_n) {
-  switch (np) {
-#define C_(N) \
-  case N:       \
-    return apply_t<N, T>(s, grid, out_mode, nitem, items, porder, pptr, pblk, ioff, Ainv, isq, r, om, xin, out, maxdof, \
-                         stage_n);
-    XDG_SWZ_NP(C_)
-#undef C_
-    default: return cudaErrorInvalidValue;
-  }
+  if (np < 1 || np > 32) return cudaErrorInvalidValue;
+  return apply_t<T>(np, s, grid, out_mode, nitem, items, porder, pptr, pblk, ioff, Ainv, isq, r, om, xin, out, maxdof,
+                    stage_n);
 }
 
 template <class T>

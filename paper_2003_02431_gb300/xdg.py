@@ -98,7 +98,8 @@ class HierInfo(C.Structure):
                 ("nnzb", C.c_int64 * MAX_LEVELS), ("omega", C.c_double * MAX_LEVELS),
                 ("lambda_max", C.c_double * MAX_LEVELS), ("coarse_n", C.c_int64),
                 ("device_bytes", C.c_size_t), ("setup_ms", C.c_double * 3), ("split_mask", C.c_uint64),
-                ("fused_level", C.c_int), ("outer_pair", C.c_int), ("symmetric", C.c_int)]
+                ("fused_level", C.c_int), ("outer_pair", C.c_int), ("symmetric", C.c_int),
+                ("fused_cluster", C.c_int)]
 
 
 class TrainOpts(C.Structure):
@@ -144,6 +145,7 @@ SIGNATURES = [
     ("xdg_pmg_apply", C.c_int, [_vp, _vp, _vp]),
     ("xdg_solve_gmres", C.c_int, [_vp, _vp, _vp, C.POINTER(GmresOpts), C.POINTER(SolveInfo)]),
     ("xdg_residual", C.c_int, [_vp, _ip, _vp, _vp, _vp]),
+    ("xdg_test_barrier_timeout", C.c_int, [_vp, _ip]),
     ("xdg_strerror", C.c_char_p, [_ip]),
     ("xdg_last_error", C.c_char_p, []),
     ("xdg_get_info", C.c_int, [_vp, C.POINTER(HierInfo)]),
@@ -324,7 +326,8 @@ class Hierarchy:
                 "coarse_n": i.coarse_n, "device_bytes": i.device_bytes, "setup_ms": list(i.setup_ms),
                 "split": [bool((i.split_mask >> l) & 1) for l in range(nl)], "fused_level": i.fused_level,
                 "outer_pair": bool(i.outer_pair), "symmetric_built": bool(i.symmetric & 1),
-                "symmetric_cycle": bool(i.symmetric & 2), "symmetric_pair": bool(i.symmetric & 4)}
+                "symmetric_cycle": bool(i.symmetric & 2), "symmetric_pair": bool(i.symmetric & 4),
+                "fused_cluster": i.fused_cluster}
 
     def export_level(self, level: int):
         _torch().cuda.synchronize(self.stream.device)
@@ -378,6 +381,11 @@ class Hierarchy:
         if raise_on_error and rc not in (XDG_OK,):
             _check(rc)
         return {f: getattr(info, f) for f, _ in SolveInfo._fields_}
+
+    def test_barrier_timeout(self, on):
+        """Make the fused cycle's grid barriers give up (xdg_test_barrier_timeout)."""
+        with _Ordered(self):
+            _check(load().xdg_test_barrier_timeout(self._h, 1 if on else 0))
 
     def residual(self, level, b, x, r):
         """r = b - M^level x (xdg_residual)."""

@@ -113,19 +113,21 @@ def test_split_row_mapping_agrees(case):
 
 @pytest.mark.parametrize("prec", [xdg.XDG_PREC_F32, xdg.XDG_PREC_BF16])
 def test_fused_small_levels_match_launch_per_step(case, prec):
-    """The small levels' V-cycle as one persistent launch runs the same per-row arithmetic as the
-    launch-per-step cycle: identical results, bit for bit (same row mapping on both sides)."""
+    """The small levels' V-cycle as one persistent launch (a cooperative grid, mode 2, or one
+    thread-block cluster, mode 3) runs the same per-row arithmetic as the launch-per-step cycle:
+    identical results, bit for bit (same row mapping on every side)."""
     name, P, O, G = case
     gamma = CASES[name][1]
     b = _t(P.b.reshape(-1))
     out = []
-    for mode in (1, 2):
+    for mode in (1, 2, 3):
         # the other creation-time choices pinned too, so that only the small levels' launch differs
         H = xdg.Hierarchy.from_problem(P, gamma=gamma, w_levels=1, low_precision=3, split_rows=1,
                                        fused_coarse=mode, outer_apply=2, symmetric=2)
         fused = H.info()["fused_level"]
-        if mode == 2 and P.n_levels >= 3 and P.nb[1] <= 16384:
+        if mode >= 2 and P.n_levels >= 3 and P.nb[1] <= 16384:
             assert fused == 2, (name, fused)
+            assert (H.info()["fused_cluster"] > 0) == (mode == 3)
         x = torch.empty(P.dof, dtype=torch.float64, device=DEV)
         H.cycle(prec, b, x)
         xs = torch.zeros_like(x)
@@ -133,8 +135,9 @@ def test_fused_small_levels_match_launch_per_step(case, prec):
         out.append((_n(x), _n(xs), res["iterations"], fused))
         H.destroy()
     assert out[0][3] == 0
-    assert np.array_equal(out[0][0], out[1][0]), name
-    assert np.array_equal(out[0][1], out[1][1]) and out[0][2] == out[1][2], name
+    for k in (1, 2):
+        assert np.array_equal(out[0][0], out[k][0]), (name, k)
+        assert np.array_equal(out[0][1], out[k][1]) and out[0][2] == out[k][2], (name, k)
 
 
 @pytest.mark.parametrize("prec", [xdg.XDG_PREC_F32, xdg.XDG_PREC_BF16])
