@@ -128,19 +128,22 @@ def csrc_digest():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel, size):
-    """DRAM bytes (read + write) per launch of `kernel` at `size`^3 from a committed ncu
-    summary line `traffic_per_launch kernel=<name> size=<N> bytes=<B> csrc_sha256=<digest>`,
-    only if the digest matches the current sources (else None: the counters are stale)."""
+def profiled_traffic(kernel, alg_bytes):
+    """DRAM bytes (read + write) per launch of `kernel`, from a committed ncu summary line
+    `traffic_per_launch kernel=<name> size=<N> bytes=<B> alg_bytes=<A> csrc_sha256=<digest>`
+    whose digest matches the current sources (else None: the counters are stale). A capture on a
+    smaller mesh (the capture-size rule) is scaled to this launch by the algorithmic bytes:
+    B * alg_bytes / A (the kernel streams its storage once, so its traffic grows with it)."""
     import glob
     import re
     digest = csrc_digest()
-    pat = re.compile(r"traffic_per_launch kernel=(\S+) size=(\d+) bytes=(\d+) csrc_sha256=([0-9a-f]+)")
+    pat = re.compile(r"traffic_per_launch kernel=(\S+) size=(\d+) bytes=(\d+) alg_bytes=(\d+) "
+                     r"csrc_sha256=([0-9a-f]+)")
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         with open(path) as f:
             for m in pat.finditer(f.read()):
-                if m.group(1) == kernel and int(m.group(2)) == size and m.group(4) == digest:
-                    return int(m.group(3))
+                if m.group(1) == kernel and m.group(5) == digest:
+                    return int(round(int(m.group(3)) * float(alg_bytes) / int(m.group(4))))
     return None
 
 
@@ -451,7 +454,7 @@ def c3_section(xdg, torch, dev, stream, P, R, gen_s, steps, with_oracle):
     ach = by / (ms / 1e3) / 1e9
     out["roofline"] = {"bound": "hbm", "kernel": name + ": level-1 outer apply of the mixed solve", "achieved": ach,
                        "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "peak_kind": hbm_kind, "bytes": by, "ms": ms,
-                       "traffic": profiled_traffic(name, 96)}
+                       "traffic": profiled_traffic(name, by)}
     H.destroy()
     return out
 
@@ -900,22 +903,22 @@ def main():
             "roofline": (
                 {"bound": "hbm", "kernel": dom["kernel"], "achieved": dom["achieved_gbs"], "peak": hbm,
                  "unit": "GB/s", "frac": dom["achieved_gbs"] / hbm, "peak_kind": hbm_kind, "bytes": dom["bytes"],
-                 "ms": dom["ms"], "traffic": profiled_traffic(dom["name"], SIZE)}
+                 "ms": dom["ms"], "traffic": profiled_traffic(dom["name"], dom["bytes"])}
                 if dom_key != DOMINANT_FP64 else
                 {"bound": "alu", "kernel": dom["kernel"], "achieved": ach64, "peak": FP64_PEAK_TFLOPS,
                  "unit": "TFLOP/s", "frac": ach64 / FP64_PEAK_TFLOPS, "flops": flops_apply, "bytes": dom["bytes"],
-                 "ms": dom["ms"], "traffic": profiled_traffic(dom["name"], SIZE),
+                 "ms": dom["ms"], "traffic": profiled_traffic(dom["name"], dom["bytes"]),
                  "peak_kind": "FP64 unit counts x clock (152 SMs x 2.07 GHz x 4 flop)"}),
             "roofline_fp64": {"bound": "alu", "kernel": d64["kernel"], "achieved": ach64, "peak": FP64_PEAK_TFLOPS,
                               "unit": "TFLOP/s", "frac": ach64 / FP64_PEAK_TFLOPS,
                               "peak_kind": "FP64 unit counts x clock (152 SMs x 2.07 GHz x 4 flop); the library's "
                                            "FMA probe reaches %.3f TFLOP/s of it" % fp64_peak,
                               "flops": flops_apply, "bytes": d64["bytes"], "ms": d64["ms"],
-                              "traffic": profiled_traffic(d64["name"], SIZE)},
+                              "traffic": profiled_traffic(d64["name"], d64["bytes"])},
             "roofline_hbm": {"bound": "hbm", "kernel": domh["kernel"], "achieved": domh["achieved_gbs"], "peak": hbm,
                              "unit": "GB/s", "frac": domh["achieved_gbs"] / hbm, "peak_kind": hbm_kind,
                              "bytes": domh["bytes"], "ms": domh["ms"],
-                             "traffic": profiled_traffic(domh["name"], SIZE)},
+                             "traffic": profiled_traffic(domh["name"], domh["bytes"])},
             "kernels_level1": kernels,
             "fp64_fma_probe_tflops": fp64_peak,
             "batched": batched,
