@@ -508,7 +508,10 @@ def schwarz_section(xdg, torch, dev, stream, P, xref, steps, warmup):
     return out
 
 
-TWIN_CASES = ((2, 16), (2, 32), (2, 64), (3, 16), (3, 32))
+TWIN_CASES = ((2, 16), (2, 32), (2, 64), (3, 16), (3, 32), (5, 8), (5, 16), (5, 24))
+# p-multigrid low orders per k (sec. 4 uses k_lo = 1 and 3) -> low-order modes in 3D
+PMG_KLO = {2: (1,), 3: (1,), 5: (1, 3)}
+N_LO_3D = {1: 4, 2: 10, 3: 20}
 
 
 def paper_dof_table():
@@ -528,20 +531,23 @@ TOL_RESMIN = 1e-12  # residual-minimising solvers (GMRES, OrthoMG): cond(M) ampl
 
 def twin_section(xdg, torch, dev, stream, problems):
     """The performance study's problem (sec. 4): (-1,1)^3, sphere R = 0.7, mu 1:1000, f = 1,
-    g_D = 0, k = 2 and 3 on N^3 meshes. Per mesh: the DOF count against the paper's table, and
+    g_D = 0, k = 2, 3 and 5 on N^3 meshes. Per mesh: the DOF count against the paper's table, and
     the solvers from x = 0, each timed on its second run (the first records graphs): flexible CG
-    with the FP32 W-cycle (block Jacobi; this library's headline solver) to TOL, the
-    orthonormalisation multigrid (Algorithm OrthoMG) with additive Schwarz smoothing (FP32
-    patch inverses) on every level and two passes per coarse visit, and, up to 32^3, flexible
-    GMRES preconditioned by p-multigrid (Algorithm pMultigrid, k_lo = 1) with the low-order
+    with the FP32 W-cycle (block Jacobi; this library's headline solver) to TOL -- for k = 5
+    (Np = 56, FP64 kernels only) CG with the FP64 W-cycle --, the orthonormalisation multigrid
+    (Algorithm OrthoMG) with additive Schwarz smoothing (FP32 patch inverses) on every level and
+    two passes per coarse visit (Np <= 32), and, up to 32^3, flexible GMRES preconditioned by
+    p-multigrid (Algorithm pMultigrid; k_lo = 1, and k_lo = 3 for k = 5) with the low-order
     system solved to 1e-5 by this library's CG; both to TOL_RESMIN. Solutions compared with the
     plain FP64 GPU CG solve (to 1e-13)."""
     table = paper_dof_table()
     out = {"problem": "(-1,1)^3, sphere R=0.7, mu 1:1000, f=1, g_D=0, alpha=0.1", "cases": []}
     for (k, N), P in problems:
-        e = {"k": k, "N": N, "dof": P.dof, "dof_paper_table": table.get((k, N)),
+        lp = P.Np <= 32
+        e = {"k": k, "N": N, "Np": P.Np, "dof": P.dof, "dof_paper_table": table.get((k, N)),
              "dof_matches_table": P.dof == table.get((k, N)), "levels": len(P.nb)}
-        H = xdg.Hierarchy.from_problem(P, gamma=GAMMA, w_levels=W_LEVELS, low_precision=1, stream=stream)
+        H = xdg.Hierarchy.from_problem(P, gamma=GAMMA, w_levels=W_LEVELS, low_precision=1 if lp else 0,
+                                       stream=stream)
         b = torch.from_numpy(P.b.reshape(-1).copy()).to(dev)
         x = torch.zeros(P.dof, dtype=torch.float64, device=dev)
         H.solve(b, x, tol=1e-13, maxit=3000, precision=xdg.XDG_PREC_F64)
@@ -556,17 +562,22 @@ def twin_section(xdg, torch, dev, stream, problems):
                       "converged": info["status"] == xdg.XDG_OK,
                       "rel_l2_vs_fp64_cg": rel_l2(x.cpu().numpy(), xref)}
 
-        run("cg_f32_wcycle", lambda: H.solve(b, x, tol=TOL, maxit=2000, precision=xdg.XDG_PREC_F32))
-        HO = xdg.Hierarchy.from_problem(P, stream=stream)
-        for lv in range(1, len(P.nb)):
-            HO.set_schwarz(lv, staggered_patches(P, lv))
-        run("orthomg_schwarz", lambda: HO.solve_orthomg(b, x, tol=TOL_RESMIN, maxit=1500, restart=60, coarse_passes=2,
-                                                        smoother_precision=xdg.XDG_PREC_F32, raise_on_error=False))
-        HO.destroy()
+        if lp:
+            run("cg_f32_wcycle", lambda: H.solve(b, x, tol=TOL, maxit=2000, precision=xdg.XDG_PREC_F32))
+            HO = xdg.Hierarchy.from_problem(P, stream=stream)
+            for lv in range(1, len(P.nb)):
+                HO.set_schwarz(lv, staggered_patches(P, lv))
+            run("orthomg_schwarz", lambda: HO.solve_orthomg(b, x, tol=TOL_RESMIN, maxit=1500, restart=60,
+                                                            coarse_passes=2, smoother_precision=xdg.XDG_PREC_F32,
+                                                            raise_on_error=False))
+            HO.destroy()
+        else:
+            run("cg_f64_wcycle", lambda: H.solve(b, x, tol=TOL, maxit=2000, precision=xdg.XDG_PREC_F64))
         if N <= 32:
-            H.pmg_setup(4, inner_tol=1e-5, inner_maxit=500)
-            run("gmres_pmg_klo1", lambda: H.solve_gmres(b, x, tol=TOL_RESMIN, maxit=3000, restart=60, preconditioner=1,
-                                                         raise_on_error=False))
+            for klo in PMG_KLO[k]:
+                H.pmg_setup(N_LO_3D[klo], inner_tol=1e-5, inner_maxit=500)
+                run("gmres_pmg_klo%d" % klo, lambda: H.solve_gmres(b, x, tol=TOL_RESMIN, maxit=3000, restart=60,
+                                                                    preconditioner=1, raise_on_error=False))
         H.destroy()
         out["cases"].append(e)
     return out
@@ -949,7 +960,8 @@ def main():
         errs += [v["rel_l2_vs_oracle"] for v in solvers.values() if isinstance(v, dict) and v["converged"]]
     if twin:
         errs += [v[t]["rel_l2_vs_fp64_cg"] for v in twin["cases"]
-                 for t in ("cg_f32_wcycle", "orthomg_schwarz", "gmres_pmg_klo1") if t in v and v[t]["converged"]]
+                 for t in ("cg_f32_wcycle", "cg_f64_wcycle", "orthomg_schwarz", "gmres_pmg_klo1", "gmres_pmg_klo3")
+                 if t in v and v[t]["converged"]]
     worst = max(errs)
     if worst > PARITY_BOUND:
         print("bench: a timed solution is %.3e from the oracle's (bound %.0e)" % (worst, PARITY_BOUND),

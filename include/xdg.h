@@ -76,7 +76,10 @@ typedef struct xdg_hier* xdg_hier_t;
 
 /* The linear system and its aggregation hierarchy, as host arrays (caller-owned; the library
  * deep-copies them to the device in xdg_create_hierarchy and keeps no reference).
- *   Np          block size (modes per block), 1 <= Np <= 32
+ *   Np          block size (modes per block): 3, 4, 6, 10, 15, 20 (k = 1..3 in 2D and 3D, k = 4
+ *               in 2D), with every kernel; 35 or 56 (k = 4, 5 in 3D), FP64 only: low_precision
+ *               must be 0 (no FP32 / BF16 cycle, no pair apply, no symmetric storage), and neither
+ *               the additive Schwarz smoother nor the learned correction exists for them
  *   n_levels    number of aggregation levels (>= 1); level 1 is the finest
  *   nb[l]       number of blocks on level l+1, l = 0..n_levels-1
  *   row_ptr     int64[nb[0]+1], BSR row pointer of M^1 (row_ptr[0] = 0, non-decreasing)
@@ -246,8 +249,9 @@ int xdg_get_damping(xdg_hier_t h, int level, int problem, double* omega, double*
  * omega = 4 / (3 lambda_max(S M)) from a Lanczos estimate in the M inner product (or the fixed
  * xdg_hier_opts.omega). Records the solve graphs again; levels at or below the fused small-level
  * cycle (xdg_hier_opts.fused_coarse) then launch step by step. n_patches = 0 restores block
- * Jacobi. Single problems only (XDG_EINVAL on a batch group). Allocates device memory for the
- * patch data (released with the handle or the next call for the level).
+ * Jacobi. Single problems with Np <= 32 only (XDG_EINVAL on a batch group or a wider block).
+ * Allocates device memory for the patch data (released with the handle or the next call for
+ * the level).
  * Errors: XDG_EINVAL (bad patches), XDG_EBREAKDOWN (a patch matrix not positive definite),
  * XDG_ENOMEM, XDG_ECUDA. */
 int xdg_set_schwarz(xdg_hier_t h, int level, int64_t n_patches, const int64_t* patch_ptr,
@@ -352,7 +356,8 @@ int xdg_solve_orthomg(xdg_hier_t h, const double* b, double* x, const xdg_orthom
  * residual inner_tol within inner_maxit iterations (inner_precision as xdg_solve_opts.precision);
  * the high-order systems with the inverses of the trailing (Np - n_lo)^2 parts of the diagonal
  * blocks. The printed right-hand side of the high-order solves, b_hi,j, is read as the residual
- * r of the line before. n_lo must be one of 3, 4, 6, 10, 15, 20 and smaller than Np.
+ * r of the line before. n_lo must be one of 3, 4, 6, 10, 15, 20, 35, smaller than Np, with at
+ * most 64 high-order modes (Np - n_lo <= 64).
  * Allocates device memory (the low-order hierarchy, inverses, vectors); a second call replaces
  * the first. Errors: XDG_EINVAL, XDG_EBREAKDOWN (a sub-block not positive definite), ENOMEM,
  * ECUDA. Single problems only. */
@@ -566,7 +571,7 @@ int xdg_learned_step(xdg_hier_t h, const double* r, double* z, int* n_kept);
  * cudaMalloc, cudaFree or allocating library call).
  *
  *   rc = R^T (b - M x) for one level (x == NULL: rc = R^T b), with
- *   Np                  block size (6, 10, 15 or 20)
+ *   Np                  block size (3, 4, 6, 10, 15, 20, 35 or 56)
  *   nb_fine, nb_coarse  blocks on the fine and the coarse level
  *   row_ptr, col, val   fine-level BSR operator (layout as in xdg_problem)
  *   R                   double[nb_fine*Np*Np] transfer blocks

@@ -34,6 +34,7 @@
 #include "xdg_kernels_df.cuh"
 #include "xdg_swz.h"
 #include "xdg_krylov.h"
+#include "xdg_big.h"
 
 using namespace xdg;
 
@@ -255,10 +256,36 @@ struct OpsT {
   }
 };
 
+static_assert(kPartials == big::kMaxPartials, "partial-sum buffers of the apply-and-dot kernels");
+
+// Np = 35 and 56 (the k = 4 and 5 spaces in 3D): the warp-per-row kernels of xdg_big.cu, FP64
+// only (no low-precision cycle, no pair or symmetric storage)
+bool ops_big(int np, Ops* o) {
+  big::Table t;
+  if (!big::table_for(np, &t)) return false;
+  *o = Ops{};
+  o->np = np;
+  o->spmv = t.spmv;
+  o->smooth = t.smooth;
+  o->bjsolve = t.bjsolve;
+  o->diagmul = t.diagmul;
+  o->resid_rt = t.resid_rt;
+  o->gather = t.gather;
+  o->gather_smooth0 = t.gather_smooth0;
+  o->prolong = t.prolong;
+  o->galerkin = t.galerkin;
+  o->diag_inv = t.diag_inv;
+  o->spmv_dot = t.spmv_dot;
+  o->gpw = 1;
+  return true;
+}
+
 // Np = 3 and 4 (the k = 1 spaces in 2D and 3D) exist for the low-order systems of the
 // p-multigrid; they have FP64 kernels only
 bool ops_for(int np, Ops* o) {
   switch (np) {
+    case 35:
+    case 56: return ops_big(np, o);
     case 3: *o = OpsT<3>::make(); return true;
     case 4: *o = OpsT<4>::make(); return true;
     case 6: *o = OpsT<6>::make(); return true;
@@ -1425,7 +1452,7 @@ int xdg_hier::build(const xdg_problem* p, const xdg_hier_opts* o) {
     return XDG_EINVAL;
   }
   if (!ops_for(Np, &ops)) {
-    set_err("block size Np = %d not supported (6, 10, 15, 20)", Np);
+    set_err("block size Np = %d not supported (3, 4, 6, 10, 15, 20, 35, 56)", Np);
     return XDG_EINVAL;
   }
   nu = o && o->nu > 0 ? o->nu : 1;
@@ -2833,8 +2860,9 @@ int xdg_hier::pmg_setup(int n_lo, const xdg_hier_opts* lo_opts, double inner_tol
     set_err("xdg_pmg_setup: a low-precision inner solve needs n_lo in 6, 10, 15, 20 (n_lo = %d)", n_lo);
     return XDG_EINVAL;
   }
-  if (n_lo < 1 || n_lo >= Np || !ops_for(n_lo, &lops) || Np - n_lo > 32) {
-    set_err("xdg_pmg_setup: n_lo = %d (Np = %d) not supported (3, 4, 6, 10, 15, 20, below Np)", n_lo, Np);
+  if (n_lo < 1 || n_lo >= Np || !ops_for(n_lo, &lops) || Np - n_lo > 64) {
+    set_err("xdg_pmg_setup: n_lo = %d (Np = %d) not supported (3, 4, 6, 10, 15, 20, 35, below Np and at most 64 "
+            "below it)", n_lo, Np);
     return XDG_EINVAL;
   }
   TRY(sync());
@@ -3669,6 +3697,10 @@ int xdg_set_schwarz(xdg_hier_t h, int level, int64_t n_patches, const int64_t* p
     set_err("xdg_set_schwarz: batch groups smooth with block Jacobi only");
     return XDG_EINVAL;
   }
+  if (h->Np > 32) {
+    set_err("xdg_set_schwarz: Np = %d: the patch solves exist for Np <= 32", h->Np);
+    return XDG_EINVAL;
+  }
   return h->set_schwarz(level - 1, n_patches, patch_ptr, patch_blocks);
 }
 
@@ -4430,7 +4462,7 @@ extern "C" int xdg_restrict_noalloc(int Np, int64_t nb_fine, int64_t nb_coarse, 
                                     const double* x, double* rc, void* stream) {
   Ops ops;
   if (!ops_for(Np, &ops)) {
-    set_err("xdg_restrict_noalloc: block size Np = %d not supported (6, 10, 15, 20)", Np);
+    set_err("xdg_restrict_noalloc: block size Np = %d not supported (3, 4, 6, 10, 15, 20, 35, 56)", Np);
     return XDG_EINVAL;
   }
   if (nb_fine <= 0 || nb_coarse <= 0 || !row_ptr || !col || !val || !R || !child_ptr || !child || !b || !rc) {

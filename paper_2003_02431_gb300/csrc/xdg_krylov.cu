@@ -245,12 +245,15 @@ __global__ void k_put_lo(int64_t nb, int np, int n_lo, const double* __restrict_
   }
 }
 
+// largest trailing (high-order) sub-block: k = 5 in 3D (56 modes) above k_lo = 1 (4 modes)
+constexpr int kHiMax = 64;
+
 // one CTA of 32 threads per block: the trailing sub-block in shared memory, Cholesky by one
-// thread (m <= 31), inverse columns by the threads
+// thread (m <= kHiMax), inverse columns by the threads
 __global__ void k_hi_inv(int64_t nb, int np, int n_lo, const int64_t* __restrict__ diag,
                          const double* __restrict__ val, double* __restrict__ Hinv, int* __restrict__ err) {
   pdl_entry();
-  __shared__ double A[32 * 32];
+  __shared__ double A[kHiMax * kHiMax];
   __shared__ int bad;
   const int m = np - n_lo;
   for (int64_t i = blockIdx.x; i < nb; i += gridDim.x) {
@@ -279,7 +282,7 @@ __global__ void k_hi_inv(int64_t nb, int np, int n_lo, const int64_t* __restrict
     __syncthreads();
     double* X = Hinv + i * m * m;
     for (int j = threadIdx.x; j < m; j += blockDim.x) {  // column j: L y = e_j, L^T x = y
-      double y[32];
+      double y[kHiMax];
       for (int r = 0; r < m; ++r) {
         double t = (r == j) ? 1.0 : 0.0;
         for (int p = 0; p < r; ++p) t -= A[r * m + p] * y[p];
@@ -339,7 +342,7 @@ cudaError_t put_lo(cudaStream_t s, int64_t nb, int np, int n_lo, const double* l
 }
 cudaError_t hi_inverses(cudaStream_t s, int64_t nb, int np, int n_lo, const int64_t* diag, const double* val,
                         double* Hinv, int* err) {
-  if (np - n_lo < 1 || np - n_lo > 32) return cudaErrorInvalidValue;
+  if (np - n_lo < 1 || np - n_lo > kHiMax) return cudaErrorInvalidValue;
   return launch_n(k_hi_inv, nb * 32, 32, s, nb, np, n_lo, diag, val, Hinv, err);
 }
 cudaError_t hi_apply(cudaStream_t s, int64_t nb, int np, int n_lo, const double* Hinv, const double* res, double* z) {

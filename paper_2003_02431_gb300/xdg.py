@@ -20,7 +20,8 @@ _ROOT = os.path.dirname(_HERE)
 LIB_PATH = os.path.join(_HERE, "libxdg.so")
 _CSRC = os.path.join(_HERE, "csrc")
 # translation units of libxdg (compiled in parallel, then linked) and every file they include
-_UNITS = [os.path.join(_CSRC, "xdg.cu"), os.path.join(_CSRC, "xdg_swz.cu"), os.path.join(_CSRC, "xdg_krylov.cu")]
+_UNITS = [os.path.join(_CSRC, "xdg.cu"), os.path.join(_CSRC, "xdg_swz.cu"), os.path.join(_CSRC, "xdg_krylov.cu"),
+          os.path.join(_CSRC, "xdg_big.cu")]
 _SRCS = _UNITS + [os.path.join(_CSRC, f) for f in sorted(os.listdir(_CSRC)) if f.endswith((".cuh", ".h"))] + [
     os.path.join(_ROOT, "include", "xdg.h")]
 

@@ -13,6 +13,9 @@ derives each bound):
   * one multigrid cycle: every block within 1e-9 of its own largest entry (a block that
     cancels to a small fraction of its neighbours carries their rounding), and 1e-12
     relative in the 2-norm
+  * the 2-norm checks of the smoothing step and the cycle (1e-12) scale with Np / 20 above
+    Np = 20: they contain explicit block inverses compared with Cholesky substitutions, whose
+    difference grows with the block size (gamma_Np); the entry-wise bounds are not scaled
   * solution of the multigrid-preconditioned CG: 1e-8 relative L2 (coefficient 2-norm, the
     bases are orthonormal) against the oracle's solution converged to 1e-14
 """
@@ -41,6 +44,9 @@ CASES = {
     "3d_k3": (xp.Config(D=3, N=7, k=3, c=(0.48, 0.51, 0.5), R=0.3, muA=1, muB=1000, max_coarse_dof=200), 1),
     # W-cycle on the finest level only, V-cycle below
     "3d_k2_w1": (xp.Config(D=3, N=12, k=2, c=(0.47, 0.52, 0.5), R=0.3, muA=1, muB=1000, max_coarse_dof=100), 2, 1),
+    # blocks wider than a warp (Np = 35, 56): the warp-per-row kernels
+    "3d_k4": (xp.Config(D=3, N=7, k=4, c=(0.48, 0.51, 0.5), R=0.3, muA=1, muB=1000, max_coarse_dof=600), 2),
+    "3d_k5": (xp.Config(D=3, N=6, k=5, c=(0.48, 0.51, 0.5), R=0.3, muA=1, muB=1000, max_coarse_dof=600), 1),
 }
 
 
@@ -55,6 +61,11 @@ def _n(t):
 
 def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _norm_tol(Np):
+    """2-norm tolerance of the steps with block inverses (smoothing, cycle)."""
+    return 1e-12 * max(1.0, Np / 20.0)
 
 
 @pytest.fixture(scope="module", params=sorted(CASES))
@@ -116,12 +127,12 @@ def test_smoother_parity(case):
         out = torch.empty(n, dtype=torch.float64, device=DEV)
         G.smooth(l + 1, _t(b), _t(x), out)
         check(_n(out), ref, bound(lv["omega"], b, x), (name, l))
-        assert _rel(_n(out), ref) < 1e-12, (name, l)
+        assert _rel(_n(out), ref) < _norm_tol(P.Np), (name, l)
         # from a zero initial guess
         ref0 = O.smooth(l, b, np.zeros(n))
         G.smooth(l + 1, _t(b), None, out)
         check(_n(out), ref0, bound(lv["omega"], b, np.zeros(n)), (name, l, "x=0"))
-        assert _rel(_n(out), ref0) < 1e-12
+        assert _rel(_n(out), ref0) < _norm_tol(P.Np)
 
 
 def test_transfer_parity(case):
@@ -178,7 +189,7 @@ def test_cycle_parity(case):
         G.vcycle(bt, x)
         got = _n(x)
         check_blocks(got, ref, P.Np, 1e-9, name)
-        assert _rel(got, ref) < 1e-12, name
+        assert _rel(got, ref) < _norm_tol(P.Np), name
         G.vcycle(bt, x)  # graph replay gives the same result
         assert np.array_equal(_n(x), got)
 
