@@ -15,7 +15,9 @@ derives each bound):
     relative in the 2-norm
   * the 2-norm checks of the smoothing step and the cycle (1e-12) scale with Np / 20 above
     Np = 20: they contain explicit block inverses compared with Cholesky substitutions, whose
-    difference grows with the block size (gamma_Np); the entry-wise bounds are not scaled
+    difference grows with the block size (gamma_Np); the entry-wise bounds are not scaled. The
+    cycle's check also carries the coarsest solve's allowance, max(1, cond/1e4) (an explicit
+    inverse against a triangular solve, as in the coarsest-solve check)
   * solution of the multigrid-preconditioned CG: 1e-8 relative L2 (coefficient 2-norm, the
     bases are orthonormal) against the oracle's solution converged to 1e-14
 """
@@ -181,6 +183,9 @@ def test_cycle_parity(case):
     name, P, O, G = case
     for l in range(P.n_levels - 1):
         G.set_damping(l + 1, O.level(l)["omega"])
+    lc = O.level(P.n_levels - 1)
+    cond = np.linalg.cond(dense_from_bsr(lc["row_ptr"], lc["col"], lc["val"]))
+    tol = _norm_tol(P.Np) * max(1.0, cond / 1e4)
     rng = np.random.default_rng(5)
     for b in (P.b.reshape(-1), rng.standard_normal(P.dof)):
         ref = O.vcycle(b)
@@ -189,7 +194,7 @@ def test_cycle_parity(case):
         G.vcycle(bt, x)
         got = _n(x)
         check_blocks(got, ref, P.Np, 1e-9, name)
-        assert _rel(got, ref) < _norm_tol(P.Np), name
+        assert _rel(got, ref) < tol, (name, cond)
         G.vcycle(bt, x)  # graph replay gives the same result
         assert np.array_equal(_n(x), got)
 
