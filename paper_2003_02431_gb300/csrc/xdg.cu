@@ -502,9 +502,12 @@ struct OpsUT {
                      double* Hi, int* e) {
     kl(k_unit_factor<NP>, U, 32, 0, s)(U, z, v, Li, Hm, M, Hi, e);
   }
-  static void resid_rows(int g, cudaStream_t s, int64_t nr, const int32_t* rows, const int64_t* rp,
+  // one row per warp (k_resid_rows_split): the grid argument is ignored
+  static void resid_rows(int, cudaStream_t s, int64_t nr, const int32_t* rows, const int64_t* rp,
                          const int32_t* col, const double* val, const double* x, const double* b, double* y) {
-    kl(k_resid_rows<NP>, g, kThreads, 0, s)(nr, rows, rp, col, val, x, b, y);
+    const int64_t ctas = (nr + kThreads / 32 - 1) / (kThreads / 32);
+    kl(k_resid_rows_split<NP>, fit_grid((const void*)&k_resid_rows_split<NP>, (int)std::min<int64_t>(ctas, 1 << 20)),
+       kThreads, 0, s)(nr, rows, rp, col, val, x, b, y);
   }
   static void samples(cudaStream_t s, int U, int ng, const int32_t* pr, const float* geo, const double* r,
                       const double* Li, const double* Hi, float* X, float* R, float* C) {
@@ -512,9 +515,11 @@ struct OpsUT {
   }
   static void apply(cudaStream_t s, int U, MlpDims d, int ng, const int32_t* pr, const float* geo, const double* r,
                     const __nv_bfloat16* W, const double* Li, const float* Hm, double* dl, int* kp, double* E) {
-    // BF16 weights (<= 30.2 KB for n_in <= 64, n_out <= 40) and 32 units x 2 x 65 floats
-    const size_t sm = (size_t)((d.total * 2 + 15) / 16) * 16 + 32 * 2 * kActStride * sizeof(float);
-    kl(k_unit_apply<NP>, (U + 31) / 32, 128, sm, s)(U, d, ng, pr, geo, r, W, Li, Hm, dl, kp, E);
+    // BF16 weights (<= 30.2 KB for n_in <= 64, n_out <= 40) and kUnitsPerCta units x 2 x 65 floats
+    const size_t sm =
+        (size_t)((d.total * 2 + 15) / 16) * 16 + (size_t)kUnitsPerCta * 2 * kActStride * sizeof(float);
+    kl(k_unit_apply<NP>, (U + kUnitsPerCta - 1) / kUnitsPerCta, kUnitWarps * 32, sm, s)(U, d, ng, pr, geo, r, W, Li,
+                                                                                         Hm, dl, kp, E);
   }
   static void gather(cudaStream_t s, int nt, const int32_t* tb, const int64_t* tp, const int32_t* tl,
                      const double* dl, double th, double* z) {
@@ -1228,7 +1233,7 @@ struct xdg_hier {
     const int64_t n = L[0].nb * Np;
     const bool pair = use_pair(p);
     apply_alpha(pair);
-    if (p == XDG_PREC_F64 || lr.on) {  // FP64 cycle or learned correction: generic tail
+    if (p == XDG_PREC_F64) {  // FP64 cycle: generic tail
       kl(k_pcg_xr, kRedBlocks, kThreads, 0, stream)(n, S, s_p, s_q, s_x, s_r, partial, nullptr);
       kl(k_sum_final, 1, kThreads, 0, stream)(kRedBlocks, partial, &S->rr);
       launches += 2;
@@ -1237,6 +1242,16 @@ struct xdg_hier {
       dot(n, s_z, s_q, &S->zq);
       kl(k_fcg_beta, 1, 1, 0, stream)(S);
       ++launches;
+    } else if (lr.on) {  // low-precision cycle, widened, plus the learned correction
+      LevelLP& W = LP[p][0];
+      kl(k_pcg_xr, kRedBlocks, kThreads, 0, stream)(n, S, s_p, s_q, s_x, s_r, partial, W.b);
+      kl(k_sum_final, 1, kThreads, 0, stream)(kRedBlocks, partial, &S->rr);
+      cycle_lp(p, 0, W.b, W.x);
+      kl(k_f2d, vgrid(n), kThreads, 0, stream)(n, W.x, s_z, cur_act, Np);
+      learned_apply(s_r, s_z);
+      kl(k_fcg_dots, kRedBlocks, kThreads, 0, stream)(n, s_r, s_q, s_z, partial);
+      kl(k_fcg_beta_final, 1, kThreads, 0, stream)(kRedBlocks, partial, S);
+      launches += 5;
     } else {
       LevelLP& W = LP[p][0];
       kl(k_pcg_xr, kRedBlocks, kThreads, 0, stream)(n, S, s_p, s_q, s_x, s_r, partial, W.b);

@@ -630,6 +630,26 @@ __global__ void __launch_bounds__(kThreads) k_fcg_tail(int64_t n, const float* _
   }
 }
 
+// the same partial sums of r . z and z . q for an FP64 z (the cycle's output after the learned
+// correction was added to it)
+__global__ void __launch_bounds__(kThreads) k_fcg_dots(int64_t n, const double* __restrict__ r,
+                                                      const double* __restrict__ q, const double* __restrict__ z,
+                                                      double* __restrict__ partial) {
+  pdl_entry();
+  double a = 0.0, c = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double zi = z[i];
+    a = fma(r[i], zi, a);
+    c = fma(zi, q[i], c);
+  }
+  a = block_sum(a);
+  c = block_sum(c);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = a;
+    partial[2 * blockIdx.x + 1] = c;
+  }
+}
+
 // rz, zq from the partial sums, then the flexible-CG beta = -zq / pq
 __global__ void __launch_bounds__(kThreads) k_fcg_beta_final(int np, const double* __restrict__ partial, PcgScal* S) {
   pdl_entry();

@@ -423,23 +423,51 @@ __global__ void __launch_bounds__(32) k_unit_factor(int U, const int64_t* __rest
   if (!ok && lane == 0) atomicOr(err, 1);
 }
 
-// y[i] = b[i] - (M x)[i] for the listed block rows i = rows[t]
+// y[i] = b[i] - (M x)[i] for the listed block rows i = rows[t], one row per warp: group g of
+// the warp takes the row's blocks z0 + g, z0 + g + GPW, ... (two at a time, so their loads
+// overlap) and the groups' partial sums are added in group order (fixed). The units' rows are
+// scattered over the mesh and few; with one row per group each warp waited on one long chain of
+// dependent loads (27.7 us for the 13k rows of the 64^3 units).
 template <int NP>
-__global__ void __launch_bounds__(kThreads) k_resid_rows(int64_t nr, const int32_t* __restrict__ rows,
-                                                        const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                                        const double* __restrict__ val, const double* __restrict__ x,
-                                                        const double* __restrict__ b, double* __restrict__ y) {
+__global__ void __launch_bounds__(kThreads) k_resid_rows_split(int64_t nr, const int32_t* __restrict__ rows,
+                                                              const int64_t* __restrict__ rp,
+                                                              const int32_t* __restrict__ col,
+                                                              const double* __restrict__ val,
+                                                              const double* __restrict__ x,
+                                                              const double* __restrict__ b, double* __restrict__ y) {
   pdl_entry();
   constexpr int GPW = Grp<NP>::GPW;
   const int lane = threadIdx.x & 31;
-  const int g = lane / NP, r = lane - g * NP;
-  if (g >= GPW) return;
+  const int g = lane / NP, r = lane - g * NP;  // idle lanes (g == GPW) keep r < NP
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t t = warp * GPW + g; t < nr; t += nw * GPW) {
+  for (int64_t t = warp; t < nr; t += nw) {
     const int64_t i = rows[t];
-    const double acc = row_dot<NP>(__ldg(rp + i), __ldg(rp + i + 1), r, col, val, x);
-    y[i * NP + r] = b[i * NP + r] - acc;
+    const int64_t z0 = __ldg(rp + i), z1 = __ldg(rp + i + 1);
+    double acc = 0.0;
+    if (g < GPW) {
+      for (int64_t z = z0 + g; z < z1; z += 2 * GPW) {
+        const int64_t z2 = z + GPW;
+        const int32_t c0 = __ldg(col + z), c1 = z2 < z1 ? __ldg(col + z2) : -1;
+        double a0[NP], x0[NP], a1[NP], x1[NP];
+        ldrow<NP>(val + z * (NP * NP) + r * NP, a0);
+        ldrow<NP>(x + (int64_t)c0 * NP, x0);
+        if (c1 >= 0) {
+          ldrow<NP>(val + z2 * (NP * NP) + r * NP, a1);
+          ldrow<NP>(x + (int64_t)c1 * NP, x1);
+        }
+#pragma unroll
+        for (int c = 0; c < NP; ++c) acc = fma(a0[c], x0[c], acc);
+        if (c1 >= 0) {
+#pragma unroll
+          for (int c = 0; c < NP; ++c) acc = fma(a1[c], x1[c], acc);
+        }
+      }
+    }
+    double tot = 0.0;
+#pragma unroll
+    for (int gg = 0; gg < GPW; ++gg) tot += __shfl_sync(0xffffffffu, acc, gg * NP + r);
+    if (g == 0) y[i * NP + r] = b[i * NP + r] - tot;
   }
 }
 
@@ -529,22 +557,28 @@ __global__ void __launch_bounds__(256) k_unit_samples(int U, int n_geo, const in
 // energy: E = s^2 (y^T H y - 2 y^T rhat) = delta^T M_uu delta - 2 delta^T r_u < 0 (FP64).
 // delta[u][0..m) = kept correction (zeros otherwise), keep[u], E[u].
 //
-// Mapping: four lanes per unit (eight units per warp); in every layer lane q of a unit computes
-// outputs q*16 .. q*16+15 with sixteen independent accumulators, reading the layer input from
-// the unit's row of a padded shared-memory buffer (stride 65: the eight units of a warp fall in
-// different banks) and the weights from shared memory. Sums over the four lanes use shuffles in
-// a fixed order.
-constexpr int kUnitLanes = 4;
+// Mapping: sixteen lanes per unit (two units per warp, sixteen per CTA of eight warps); in every
+// layer lane q of a unit computes outputs 4q .. 4q+3 with four independent accumulators, reading
+// the layer input from the unit's row of a padded shared-memory buffer (one broadcast per unit)
+// and the weights from shared memory (the sixteen lanes read 128 consecutive bytes). Sums over
+// a unit's lanes use shuffles in a fixed order. (Four lanes per unit left about four warps per
+// SM at 64^3, 5k units, and a 42 us launch.)
+constexpr int kUnitLanes = 16;
+constexpr int kUnitsPerWarp = 32 / kUnitLanes;
+constexpr int kUnitWarps = 8;
+constexpr int kUnitsPerCta = kUnitsPerWarp * kUnitWarps;
+constexpr int kOutPerLane = kHid / kUnitLanes;
 constexpr int kActStride = 65;
 
-__device__ __forceinline__ double quad_sum(double v) {
-  v += __shfl_xor_sync(0xffffffffu, v, 1);
-  v += __shfl_xor_sync(0xffffffffu, v, 2);
+// sum over the kUnitLanes lanes of a unit (aligned groups of the warp)
+__device__ __forceinline__ double unit_sum(double v) {
+#pragma unroll
+  for (int o = 1; o < kUnitLanes; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
 template <int NP>
-__global__ void __launch_bounds__(128) k_unit_apply(int U, MlpDims d, int n_geo, const int32_t* __restrict__ pairs,
+__global__ void __launch_bounds__(kUnitWarps * 32) k_unit_apply(int U, MlpDims d, int n_geo, const int32_t* __restrict__ pairs,
                                                    const float* __restrict__ geom, const double* __restrict__ r,
                                                    const __nv_bfloat16* __restrict__ P,
                                                    const double* __restrict__ Linv, const float* __restrict__ Hf,
@@ -559,11 +593,11 @@ __global__ void __launch_bounds__(128) k_unit_apply(int U, MlpDims d, int n_geo,
   float* act = reinterpret_cast<float*>(smem_raw + wbytes);
   stage_params(sp, P, d.total);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int uu = lane >> 2, q = lane & 3;
-  const int slot = w * 8 + uu;
+  const int uu = lane / kUnitLanes, q = lane % kUnitLanes;
+  const int slot = w * kUnitsPerWarp + uu;
   float* A0 = act + slot * 2 * kActStride;
   float* A1 = A0 + kActStride;
-  const int u = blockIdx.x * 32 + slot;
+  const int u = blockIdx.x * kUnitsPerCta + slot;
   const bool valid = u < U;
   // residual of the unit in block-Jacobi coordinates: entries e = q + 4 t
   double rt[T];
@@ -578,12 +612,22 @@ __global__ void __launch_bounds__(128) k_unit_apply(int U, MlpDims d, int n_geo,
       const int h = e / NP, i = e - h * NP;
       const double* xr = X + h * NP * NP + i * NP;
       const double* rv = r + (int64_t)blk[h] * NP;
-      for (int k = 0; k <= i; ++k) acc = fma(xr[k], rv[k], acc);
+      // the triangular row unrolled to NP (predicated): all loads issue before the first FMA
+      double xk[NP], rk[NP];
+#pragma unroll
+      for (int k = 0; k < NP; ++k)
+        if (k <= i) {
+          xk[k] = __ldg(xr + k);
+          rk[k] = __ldg(rv + k);
+        }
+#pragma unroll
+      for (int k = 0; k < NP; ++k)
+        if (k <= i) acc = fma(xk[k], rk[k], acc);
     }
     rt[t] = acc;
     ss = fma(acc, acc, ss);
   }
-  ss = quad_sum(ss);
+  ss = unit_sum(ss);
   const double s = sqrt(ss);
   const double inv = s > 0.0 ? 1.0 / s : 0.0;
   // network input
@@ -594,7 +638,7 @@ __global__ void __launch_bounds__(128) k_unit_apply(int U, MlpDims d, int n_geo,
     if (e < m) A0[n_geo + e] = (float)(rt[t] * inv);
   }
   __syncwarp();
-  // three hidden layers (GELU), 16 outputs per lane
+  // three hidden layers (GELU), kOutPerLane outputs per lane
   const int nin[3] = {d.n_in, kHid, kHid};
   const int ow[3] = {d.oW1, d.oW2, d.oW3};
   const int ob[3] = {d.ob1, d.ob2, d.ob3};
@@ -602,17 +646,17 @@ __global__ void __launch_bounds__(128) k_unit_apply(int U, MlpDims d, int n_geo,
   float* out = A1;
 #pragma unroll
   for (int layer = 0; layer < 3; ++layer) {
-    float acc[16];
+    float acc[kOutPerLane];
 #pragma unroll
-    for (int jj = 0; jj < 16; ++jj) acc[jj] = wload(sp + ob[layer], q * 16 + jj);
-    const __nv_bfloat16* Wl = sp + ow[layer] + q * 16;
+    for (int jj = 0; jj < kOutPerLane; ++jj) acc[jj] = wload(sp + ob[layer], q * kOutPerLane + jj);
+    const __nv_bfloat16* Wl = sp + ow[layer] + q * kOutPerLane;
     for (int i = 0; i < nin[layer]; ++i) {
       const float xi = in[i];
 #pragma unroll
-      for (int jj = 0; jj < 16; ++jj) acc[jj] = fmaf(wload(Wl, i * kHid + jj), xi, acc[jj]);
+      for (int jj = 0; jj < kOutPerLane; ++jj) acc[jj] = fmaf(wload(Wl, i * kHid + jj), xi, acc[jj]);
     }
 #pragma unroll
-    for (int jj = 0; jj < 16; ++jj) out[q * 16 + jj] = gelu_f(acc[jj]);
+    for (int jj = 0; jj < kOutPerLane; ++jj) out[q * kOutPerLane + jj] = gelu_f(acc[jj]);
     __syncwarp();
     float* tmp = in;
     in = out;
@@ -658,7 +702,7 @@ __global__ void __launch_bounds__(128) k_unit_apply(int U, MlpDims d, int n_geo,
       part += y[t] * ((double)hy - 2.0 * rt[t] * inv);
     }
   }
-  const double en = quad_sum(part) * ss;
+  const double en = unit_sum(part) * ss;
   const bool kp = valid && (en < 0.0) && (s > 0.0);
   // delta = s X^T y per half: delta_e = s sum_{j >= i} X_h[j][i] y_{h NP + j}
 #pragma unroll
@@ -666,8 +710,14 @@ __global__ void __launch_bounds__(128) k_unit_apply(int U, MlpDims d, int n_geo,
     const int e = q + kUnitLanes * t;
     if (valid && e < m) {
       const int h = e / NP, i = e - h * NP;
+      double xj[NP];
+#pragma unroll
+      for (int j = 0; j < NP; ++j)
+        if (j >= i) xj[j] = __ldg(X + h * NP * NP + j * NP + i);
       double acc = 0.0;
-      for (int j = i; j < NP; ++j) acc = fma(X[h * NP * NP + j * NP + i], (double)out[h * NP + j], acc);
+#pragma unroll
+      for (int j = 0; j < NP; ++j)
+        if (j >= i) acc = fma(xj[j], (double)out[h * NP + j], acc);
       delta[(int64_t)u * m + e] = kp ? s * acc : 0.0;
     }
   }
