@@ -515,9 +515,10 @@ struct OpsUT {
   }
   static void apply(cudaStream_t s, int U, MlpDims d, int ng, const int32_t* pr, const float* geo, const double* r,
                     const __nv_bfloat16* W, const double* Li, const float* Hm, double* dl, int* kp, double* E) {
-    // BF16 weights (<= 30.2 KB for n_in <= 64, n_out <= 40) and kUnitsPerCta units x 2 x 65 floats
-    const size_t sm =
-        (size_t)((d.total * 2 + 15) / 16) * 16 + (size_t)kUnitsPerCta * 2 * kActStride * sizeof(float);
+    // BF16 weights (<= 30.2 KB for n_in <= 64, n_out <= 40), the BF16 activation parts and
+    // kUnitsPerCta units x 2 x 65 floats (up to 52.4 KB: above 48 KB the kernel's limit is raised)
+    const size_t sm = (size_t)((d.total * 2 + 15) / 16) * 16 + kUnitTriBytes + kUnitActBytes;
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_unit_apply<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     kl(k_unit_apply<NP>, (U + kUnitsPerCta - 1) / kUnitsPerCta, kUnitWarps * 32, sm, s)(U, d, ng, pr, geo, r, W, Li,
                                                                                          Hm, dl, kp, E);
   }

@@ -557,18 +557,101 @@ __global__ void __launch_bounds__(256) k_unit_samples(int U, int n_geo, const in
 // energy: E = s^2 (y^T H y - 2 y^T rhat) = delta^T M_uu delta - 2 delta^T r_u < 0 (FP64).
 // delta[u][0..m) = kept correction (zeros otherwise), keep[u], E[u].
 //
-// Mapping: sixteen lanes per unit (two units per warp, sixteen per CTA of eight warps); in every
-// layer lane q of a unit computes outputs 4q .. 4q+3 with four independent accumulators, reading
-// the layer input from the unit's row of a padded shared-memory buffer (one broadcast per unit)
-// and the weights from shared memory (the sixteen lanes read 128 consecutive bytes). Sums over
-// a unit's lanes use shuffles in a fixed order. (Four lanes per unit left about four warps per
-// SM at 64^3, 5k units, and a 42 us launch.)
+// Mapping: sixteen lanes per unit (two units per warp, sixteen per CTA of eight warps) for the
+// per-unit work (residual transform, energy, correction; sums over a unit's lanes by shuffles in
+// a fixed order). The three hidden layers are dense products of the CTA's 16 x K activations
+// with the K x 64 weights and run on the tensor cores (mma_layer below); the output layer
+// (2 Np outputs) runs on the unit's lanes from an FP32 copy of the last hidden layer.
 constexpr int kUnitLanes = 16;
 constexpr int kUnitsPerWarp = 32 / kUnitLanes;
 constexpr int kUnitWarps = 8;
-constexpr int kUnitsPerCta = kUnitsPerWarp * kUnitWarps;
-constexpr int kOutPerLane = kHid / kUnitLanes;
+constexpr int kUnitsPerCta = kUnitsPerWarp * kUnitWarps;  // = 16, the rows of one MMA tile
+static_assert(kUnitsPerCta == 16 && kUnitWarps * 8 == kHid, "one 16-row tile, eight columns per warp");
 constexpr int kActStride = 65;
+constexpr int kTriStride = 72;  // BF16 activation rows: 36 words, so a fragment's rows hit distinct banks
+// shared memory of k_unit_apply after the parameters: two activation buffers of three BF16
+// parts, then the FP32 rows (last hidden layer, outputs)
+constexpr size_t kUnitTriBytes = 2 * 3 * kUnitsPerCta * kTriStride * sizeof(__nv_bfloat16);
+constexpr size_t kUnitActBytes = (size_t)kUnitsPerCta * 2 * kActStride * sizeof(float);
+
+// v = hi + mid + lo + O(2^-24 |v|), each part a BF16 number (the split of an FP32 operand into
+// low-precision terms, Markidis et al. 2018: with BF16 weights every partial product is exact in
+// FP32, so the three products reproduce the FP32 product to the FP32 rounding level)
+__device__ __forceinline__ void split_bf16x3(float v, __nv_bfloat16& hi, __nv_bfloat16& mid, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(v);
+  const float r1 = v - __bfloat162float(hi);
+  mid = __float2bfloat16_rn(r1);
+  lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo_half, __nv_bfloat16 hi_half) {
+  return (uint32_t)__bfloat16_as_ushort(lo_half) | ((uint32_t)__bfloat16_as_ushort(hi_half) << 16);
+}
+
+// d += a b for one 16 x 8 x 16 tile: BF16 operands, FP32 accumulators. Fragments (PTX ISA,
+// mma.m16n8k16 with .bf16): with g = lane / 4 and t = lane % 4, a holds rows g and g + 8 at
+// columns 2t, 2t+1 (a[0], a[1]) and 2t+8, 2t+9 (a[2], a[3]); b holds rows 2t, 2t+1 and 2t+8,
+// 2t+9 of column g; d holds rows g, g + 8 at columns 2t, 2t+1.
+__device__ __forceinline__ void mma_16816_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// One hidden layer for the CTA's 16 units on the tensor cores: out = GELU(in W + bias), 64
+// outputs; warp w computes columns 8w .. 8w+7 for all 16 rows. in: three BF16 parts
+// tin[p][row][k] (k < K, K a multiple of 16; entries past the layer's n_in are zero), W: BF16
+// rows of 64 (rows >= kmax read as zero). The partial products of the lo, mid and hi parts go
+// into one FP32 accumulator started at the bias. The result goes either to tout (three BF16
+// parts, the next layer's input) or, FP32, to fout[row * 2 kActStride + col].
+template <bool TRI_OUT>
+__device__ __forceinline__ void mma_layer(const __nv_bfloat16* tin, int K, int kmax, const __nv_bfloat16* W,
+                                          const __nv_bfloat16* bias, __nv_bfloat16* tout, float* fout) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int n0 = 8 * w, c0 = n0 + 2 * t;
+  constexpr int PS = kUnitsPerCta * kTriStride;  // elements per part
+  float d[4];
+  d[0] = d[2] = __bfloat162float(bias[c0]);
+  d[1] = d[3] = __bfloat162float(bias[c0 + 1]);
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    uint32_t b[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int k = k0 + 2 * t + 8 * j;
+      const __nv_bfloat16 w0 = k < kmax ? W[k * kHid + n0 + g] : zero;
+      const __nv_bfloat16 w1 = k + 1 < kmax ? W[(k + 1) * kHid + n0 + g] : zero;
+      b[j] = pack_bf16x2(w0, w1);
+    }
+#pragma unroll
+    for (int p = 2; p >= 0; --p) {  // lo, mid, hi
+      const __nv_bfloat16* A = tin + p * PS;
+      uint32_t a[4];
+      a[0] = *reinterpret_cast<const uint32_t*>(A + g * kTriStride + k0 + 2 * t);
+      a[1] = *reinterpret_cast<const uint32_t*>(A + (g + 8) * kTriStride + k0 + 2 * t);
+      a[2] = *reinterpret_cast<const uint32_t*>(A + g * kTriStride + k0 + 2 * t + 8);
+      a[3] = *reinterpret_cast<const uint32_t*>(A + (g + 8) * kTriStride + k0 + 2 * t + 8);
+      mma_16816_bf16(d, a, b);
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int row = g + 8 * (e >> 1), col = c0 + (e & 1);
+    const float v = gelu_f(d[e]);
+    if constexpr (TRI_OUT) {
+      __nv_bfloat16 h, mdl, l;
+      split_bf16x3(v, h, mdl, l);
+      tout[row * kTriStride + col] = h;
+      tout[PS + row * kTriStride + col] = mdl;
+      tout[2 * PS + row * kTriStride + col] = l;
+    } else {
+      fout[row * 2 * kActStride + col] = v;
+    }
+  }
+}
 
 // sum over the kUnitLanes lanes of a unit (aligned groups of the warp)
 __device__ __forceinline__ double unit_sum(double v) {
@@ -590,7 +673,8 @@ __global__ void __launch_bounds__(kUnitWarps * 32) k_unit_apply(int U, MlpDims d
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __nv_bfloat16* sp = reinterpret_cast<__nv_bfloat16*>(smem_raw);
   const int wbytes = ((d.total * 2 + 15) / 16) * 16;
-  float* act = reinterpret_cast<float*>(smem_raw + wbytes);
+  __nv_bfloat16* tri = reinterpret_cast<__nv_bfloat16*>(smem_raw + wbytes);
+  float* act = reinterpret_cast<float*>(smem_raw + wbytes + kUnitTriBytes);
   stage_params(sp, P, d.total);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int uu = lane / kUnitLanes, q = lane % kUnitLanes;
@@ -630,38 +714,33 @@ __global__ void __launch_bounds__(kUnitWarps * 32) k_unit_apply(int U, MlpDims d
   ss = unit_sum(ss);
   const double s = sqrt(ss);
   const double inv = s > 0.0 ? 1.0 / s : 0.0;
-  // network input
-  for (int e = q; e < n_geo; e += kUnitLanes) A0[e] = valid ? geom[(int64_t)u * n_geo + e] : 0.f;
-#pragma unroll
-  for (int t = 0; t < T; ++t) {
-    const int e = q + kUnitLanes * t;
-    if (e < m) A0[n_geo + e] = (float)(rt[t] * inv);
+  // network input: the unit's row of the first activation buffer, three BF16 parts, zero from
+  // n_in up to K1 (the first layer's K, a multiple of 16)
+  constexpr int PS = kUnitsPerCta * kTriStride;
+  const int K1 = (d.n_in + 15) & ~15;  // d.n_in = n_geo + m
+  __nv_bfloat16* trow = tri + slot * kTriStride;
+  for (int e = q; e < K1; e += kUnitLanes) {  // geometry features, then zeros past n_in
+    if (e >= n_geo && e < d.n_in) continue;
+    const float v = (e < n_geo && valid) ? geom[(int64_t)u * n_geo + e] : 0.f;
+    split_bf16x3(v, trow[e], trow[PS + e], trow[2 * PS + e]);
   }
-  __syncwarp();
-  // three hidden layers (GELU), kOutPerLane outputs per lane
-  const int nin[3] = {d.n_in, kHid, kHid};
-  const int ow[3] = {d.oW1, d.oW2, d.oW3};
-  const int ob[3] = {d.ob1, d.ob2, d.ob3};
-  float* in = A0;
+#pragma unroll
+  for (int t = 0; t < T; ++t) {  // rhat entry q + kUnitLanes t, held by this lane
+    const int k = q + kUnitLanes * t;
+    if (k < m) split_bf16x3((float)(rt[t] * inv), trow[n_geo + k], trow[PS + n_geo + k], trow[2 * PS + n_geo + k]);
+  }
+  __syncthreads();
+  // three hidden layers (GELU) on the tensor cores, the last one into FP32 rows A0
+  __nv_bfloat16* tri0 = tri;
+  __nv_bfloat16* tri1 = tri + 3 * PS;
+  mma_layer<true>(tri0, K1, d.n_in, sp + d.oW1, sp + d.ob1, tri1, nullptr);
+  __syncthreads();
+  mma_layer<true>(tri1, kHid, kHid, sp + d.oW2, sp + d.ob2, tri0, nullptr);
+  __syncthreads();
+  mma_layer<false>(tri0, kHid, kHid, sp + d.oW3, sp + d.ob3, nullptr, act);
+  __syncthreads();
+  const float* in = A0;
   float* out = A1;
-#pragma unroll
-  for (int layer = 0; layer < 3; ++layer) {
-    float acc[kOutPerLane];
-#pragma unroll
-    for (int jj = 0; jj < kOutPerLane; ++jj) acc[jj] = wload(sp + ob[layer], q * kOutPerLane + jj);
-    const __nv_bfloat16* Wl = sp + ow[layer] + q * kOutPerLane;
-    for (int i = 0; i < nin[layer]; ++i) {
-      const float xi = in[i];
-#pragma unroll
-      for (int jj = 0; jj < kOutPerLane; ++jj) acc[jj] = fmaf(wload(Wl, i * kHid + jj), xi, acc[jj]);
-    }
-#pragma unroll
-    for (int jj = 0; jj < kOutPerLane; ++jj) out[q * kOutPerLane + jj] = gelu_f(acc[jj]);
-    __syncwarp();
-    float* tmp = in;
-    in = out;
-    out = tmp;
-  }
   // output layer: y_e, e = q + 4 t
   double y[T];
 #pragma unroll
