@@ -412,9 +412,10 @@ def staggered_patches(P, level):
     return np.r_[a[0], a[0][-1] + b[0][1:]], np.r_[a[1], b[1]]
 
 
-def c3_section(xdg, torch, dev, stream, P, R, gen_s, steps, with_oracle):
+def c3_section(xdg, torch, dev, stream, P, R, gen_s, steps, with_oracle, with_schwarz=True):
     """C3 (96^3, k = 3): FP32-cycle, BF16-transfer and FP64 solves to TOL (one warm-up, `steps`
-    timed solves each), V-cycle rates, the level-1 pair apply against the HBM roofline. The
+    timed solves each), the FP32-cycle solve with the additive Schwarz smoother on levels 1-2
+    (timed on its second run), the level-1 pair apply against the HBM roofline. The
     solutions are compared with the FP64 GPU solve, and with the oracle's when asked (the
     oracle's solve at this size takes minutes on the host cores)."""
     n = P.dof
@@ -447,6 +448,24 @@ def c3_section(xdg, torch, dev, stream, P, R, gen_s, steps, with_oracle):
     for key in ("mixed_f32", "mixed_bf16_transfers"):
         out["paths"][key]["rel_l2_vs_fp64_gpu"] = rel_l2(sols[key], sols["plain_f64"])
     out["speedup_mixed_vs_f64"] = out["paths"]["plain_f64"]["solve_ms"] / out["paths"]["mixed_f32"]["solve_ms"]
+    if with_schwarz:
+        # the additive Schwarz smoother (staggered 2^3-cell patches, alpha = 2) on levels 1-2
+        # instead of block Jacobi, the same FP32-cycle flexible CG
+        t = time.perf_counter()
+        for lv in (1, 2):
+            H.set_schwarz(lv, staggered_patches(P, lv))
+        swz_setup = time.perf_counter() - t
+        x.zero_()
+        H.solve(b, x, tol=TOL, maxit=1000, precision=xdg.XDG_PREC_F32)
+        torch.cuda.synchronize()
+        x.zero_()
+        info = H.solve(b, x, tol=TOL, maxit=1000, precision=xdg.XDG_PREC_F32)
+        sols["schwarz_mixed_f32"] = x.cpu().numpy()
+        out["paths"]["schwarz_mixed_f32"] = {
+            "solve_ms": info["ms"], "iterations": [info["iterations"]], "mdofs": n / info["ms"] / 1e3,
+            "setup_s": swz_setup, "rel_l2_vs_fp64_gpu": rel_l2(sols["schwarz_mixed_f32"], sols["plain_f64"]),
+            "levels": {lv: {k: H.schwarz_info(lv)[k] for k in ("n_patches", "n_distinct", "max_dof")} for lv in (1, 2)},
+            "device_gb": H.info()["device_bytes"] / 1e9}
     if with_oracle:
         xref = oracle_solution(P, tol=1e-12)[0]
         for key in sols:
@@ -884,7 +903,7 @@ def main():
         section_s["c3_generation_wait"] = round(time.perf_counter() - t0, 1)
         H.destroy()
         c3_out = timed("c3", c3_section, xdg, torch, dev, stream, c3["P"], c3["R"], c3["gen_s"],
-                       min(args.steps, C3_STEPS), args.c3_oracle)
+                       min(args.steps, C3_STEPS), args.c3_oracle, not args.no_schwarz)
         c3.pop("P")
         if "twin" in c3:
             twin = timed("paper_twin", twin_section, xdg, torch, dev, stream, c3.pop("twin"))
