@@ -574,32 +574,6 @@ constexpr int kTriStride = 72;  // BF16 activation rows: 36 words, so a fragment
 constexpr size_t kUnitTriBytes = 2 * 3 * kUnitsPerCta * kTriStride * sizeof(__nv_bfloat16);
 constexpr size_t kUnitActBytes = (size_t)kUnitsPerCta * 2 * kActStride * sizeof(float);
 
-// v = hi + mid + lo + O(2^-24 |v|), each part a BF16 number (the split of an FP32 operand into
-// low-precision terms, Markidis et al. 2018: with BF16 weights every partial product is exact in
-// FP32, so the three products reproduce the FP32 product to the FP32 rounding level)
-__device__ __forceinline__ void split_bf16x3(float v, __nv_bfloat16& hi, __nv_bfloat16& mid, __nv_bfloat16& lo) {
-  hi = __float2bfloat16_rn(v);
-  const float r1 = v - __bfloat162float(hi);
-  mid = __float2bfloat16_rn(r1);
-  lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
-}
-
-__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo_half, __nv_bfloat16 hi_half) {
-  return (uint32_t)__bfloat16_as_ushort(lo_half) | ((uint32_t)__bfloat16_as_ushort(hi_half) << 16);
-}
-
-// d += a b for one 16 x 8 x 16 tile: BF16 operands, FP32 accumulators. Fragments (PTX ISA,
-// mma.m16n8k16 with .bf16): with g = lane / 4 and t = lane % 4, a holds rows g and g + 8 at
-// columns 2t, 2t+1 (a[0], a[1]) and 2t+8, 2t+9 (a[2], a[3]); b holds rows 2t, 2t+1 and 2t+8,
-// 2t+9 of column g; d holds rows g, g + 8 at columns 2t, 2t+1.
-__device__ __forceinline__ void mma_16816_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
 // One hidden layer for the CTA's 16 units on the tensor cores: out = GELU(in W + bias), 64
 // outputs; warp w computes columns 8w .. 8w+7 for all 16 rows. in: three BF16 parts
 // tin[p][row][k] (k < K, K a multiple of 16; entries past the layer's n_in are zero), W: BF16
