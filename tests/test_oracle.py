@@ -24,6 +24,18 @@ def prob3d():
                                 max_coarse_dof=80))
 
 
+@pytest.fixture(scope="module")
+def prob3d_k5():
+    """k = 5 in 3D (Np = 56, the paper's highest degree): the block size of the wide-block GPU
+    kernels, three levels on 4^3 cells."""
+    return xp.Problem(xp.Config(D=3, N=4, k=5, c=(0.47, 0.52, 0.55), R=0.3, muA=1, muB=1000,
+                                max_coarse_dof=300))
+
+
+def _prob(which, prob2d, prob3d, prob3d_k5):
+    return {"2d": prob2d, "3d": prob3d, "3d_k5": prob3d_k5}[which]
+
+
 def _Rdense(agg, R, nbc):
     nbf, Np = R.shape[0], R.shape[-1]
     Rd = np.zeros((nbf * Np, nbc * Np))
@@ -52,9 +64,9 @@ def test_spmv_random_bsr():
     assert np.allclose(y, dense_from_bsr(rp, col, val) @ x, rtol=0, atol=1e-12)
 
 
-@pytest.mark.parametrize("which", ["2d", "3d"])
-def test_transfers_match_dense(which, prob2d, prob3d):
-    P = prob2d if which == "2d" else prob3d
+@pytest.mark.parametrize("which", ["2d", "3d", "3d_k5"])
+def test_transfers_match_dense(which, prob2d, prob3d, prob3d_k5):
+    P = _prob(which, prob2d, prob3d, prob3d_k5)
     rng = np.random.default_rng(3)
     for l in range(P.n_levels - 1):
         Rd = _Rdense(P.agg[l], P.R[l], P.nb[l + 1])
@@ -65,9 +77,9 @@ def test_transfers_match_dense(which, prob2d, prob3d):
         assert np.allclose(oracle.prolong_add(P.agg[l], P.R[l], zc, x).reshape(-1), x + Rd @ zc, atol=1e-12)
 
 
-@pytest.mark.parametrize("which", ["2d", "3d"])
-def test_galerkin_matches_dense_and_direct_assembly(which, prob2d, prob3d):
-    P = prob2d if which == "2d" else prob3d
+@pytest.mark.parametrize("which", ["2d", "3d", "3d_k5"])
+def test_galerkin_matches_dense_and_direct_assembly(which, prob2d, prob3d, prob3d_k5):
+    P = _prob(which, prob2d, prob3d, prob3d_k5)
     rp, cl, vl = P.row_ptr, P.col, P.val
     for l in range(P.n_levels - 1):
         rpc, clc, vlc = oracle.galerkin(rp, cl, vl, P.agg[l], P.R[l], P.nb[l + 1])
@@ -76,10 +88,13 @@ def test_galerkin_matches_dense_and_direct_assembly(which, prob2d, prob3d):
         Ac = dense_from_bsr(rpc, clc, vlc)
         scale = np.abs(Ac).max()
         assert np.abs(Ac - Rd.T @ A @ Rd).max() <= 1e-12 * scale
-        # Galerkin consistency: a_sip assembled directly in the coarse basis
+        # Galerkin consistency: a_sip assembled directly in the coarse basis. The two agree to
+        # the accuracy of the orthonormal bases, built by Cholesky of Gram matrices of Legendre
+        # products in graded order: ~1e-12 up to k = 3; at k = 5 the Gram matrices of small cut
+        # parts are far worse conditioned (4.7e-8 measured), hence 1e-7 there.
         rpd, cld, vld, bd = P.assemble_level(l + 2)
         assert np.array_equal(rpd, rpc) and np.array_equal(cld, clc)
-        assert np.abs(vld - vlc).max() <= 1e-11 * scale
+        assert np.abs(vld - vlc).max() <= (1e-11 if P.Np <= 20 else 1e-7) * scale
         rp, cl, vl = rpc, clc, vlc
 
 
@@ -112,6 +127,29 @@ def test_smoother_matches_dense(prob2d):
     lm = H.level(0)["lmax"]
     assert lm <= lam * (1 + 1e-10) and lm >= 0.95 * lam
     assert abs(om - 4.0 / (3.0 * lm)) < 1e-15
+
+
+def test_k5_smoother_spmv_and_solve_match_dense(prob3d_k5):
+    """Np = 56: the operator apply, one damped block-Jacobi step and the PCG solution against
+    dense numpy / LAPACK."""
+    P = prob3d_k5
+    A = dense_from_bsr(P.row_ptr, P.col, P.val)
+    rng = np.random.default_rng(13)
+    x = rng.standard_normal(P.dof)
+    y = oracle.bsr_spmv(P.row_ptr, P.col, P.val, x).reshape(-1)
+    assert np.abs(y - A @ x).max() <= 1e-12 * np.abs(A).max() * np.abs(x).max() * 10
+    H = oracle.Hierarchy(P)
+    Np = P.Np
+    Dm = np.zeros_like(A)
+    for i in range(P.nb[0]):
+        Dm[i * Np:(i + 1) * Np, i * Np:(i + 1) * Np] = A[i * Np:(i + 1) * Np, i * Np:(i + 1) * Np]
+    b = rng.standard_normal(P.dof)
+    om = H.level(0)["omega"]
+    ref = x + om * np.linalg.solve(Dm, b - A @ x)
+    assert np.abs(H.smooth(0, b, x) - ref).max() <= 1e-10 * np.abs(ref).max()
+    sol, it, rr, _ = H.pcg(P.b, tol=1e-13, maxit=600)
+    dense = np.linalg.solve(A, P.b.reshape(-1))
+    assert rr <= 1e-13 and np.linalg.norm(sol - dense) <= 1e-8 * np.linalg.norm(dense), it
 
 
 @pytest.mark.parametrize("gamma", [1, 2])
