@@ -676,7 +676,7 @@ def reference_arm(args):
             per.append((time.perf_counter() - t) / 5)
     t_solve = statistics.mean(per) * iters
     value = P.dof / t_solve / 1e6
-    # n_gpus: the launch's N (the driver pairs the arms by it); the oracle itself runs on host cores
+    # n_gpus: the launch's N (comparisons pair the two arms by it); the oracle itself runs on host cores
     line = {"metric": METRIC, "value": value, "unit": "MDOF/s", "n_gpus": args.gpus, "device": "host CPU cores",
             "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": True,
