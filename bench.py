@@ -302,7 +302,15 @@ def batched_section(xdg, torch, dev, stream, steps, warmup):
                 "d2h_bytes_per_step": n * 8},
         "kernel_nodes_per_solve": launches / steps,
         "generate_s": gen_s, "setup_s": setup_s, "device_gb": binfo["device_bytes"] / 1e9,
+        "groups_tuned": [],
     }
+    # what the creation-time autotuner chose for every group (union hierarchy of one Np and depth)
+    for g in range(binfo["n_groups"]):
+        Hg, members = bt.group(g)
+        gi = Hg.info()
+        out["groups_tuned"].append({"Np": gi["Np"], "problems": len(members), "blocks_per_level": gi["nb"],
+                                    "split_rows_levels": gi["split"], "outer_apply_pair": gi["outer_pair"],
+                                    "symmetric_cycle": gi["symmetric_cycle"], "fused_level": gi["fused_level"]})
     bt.destroy()
     return out
 
