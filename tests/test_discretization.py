@@ -85,6 +85,16 @@ def test_dof_table_blocks_for_all_degrees():
 
 
 # ------------------------------------------------------------------ operator properties
+@pytest.mark.parametrize("k", [4, 5])
+def test_symmetric_positive_definite_high_degree_3d(k):
+    """The 3D k = 4 and k = 5 operators (Np = 35, 56; the blocks of the wide-block GPU
+    kernels) are exactly symmetric and positive definite (one cut configuration each)."""
+    P = xp.Problem(xp.Config(D=3, N=3, k=k, c=(0.5, 0.47, 0.52), R=0.3, muA=1, muB=1000, max_levels=1))
+    A = dense_from_bsr(P.row_ptr, P.col, P.val)
+    assert np.array_equal(A, A.T)
+    assert np.linalg.eigvalsh(A)[0] > 0
+
+
 @pytest.mark.parametrize("D,N,k", [(2, 6, 2), (2, 6, 3), (2, 5, 4), (3, 3, 2), (3, 3, 3)])
 def test_symmetric_positive_definite(D, N, k):
     rng = np.random.default_rng(D * 100 + N * 10 + k)
