@@ -279,10 +279,26 @@ typedef struct {
   double* pv[5]; /* PCG vectors */
 } or_hier;
 
+/* a . b as contiguous chunks, one per thread, whose sums are added in thread order: a fixed
+   order at a given thread count, so that a result repeats from run to run (an OpenMP reduction
+   combines its partial sums in an unspecified order) */
+#define OR_MAX_CHUNKS 512
 static double dot(int64_t n, const double* a, const double* b) {
+  double part[OR_MAX_CHUNKS];
+  int nchunk = 1;
+#ifdef _OPENMP
+  nchunk = omp_get_max_threads();
+  if (nchunk > OR_MAX_CHUNKS) nchunk = OR_MAX_CHUNKS;
+#endif
+#pragma omp parallel for schedule(static, 1) num_threads(nchunk)
+  for (int c = 0; c < nchunk; ++c) {
+    const int64_t i0 = n * c / nchunk, i1 = n * (c + 1) / nchunk;
+    double s = 0.0;
+    for (int64_t i = i0; i < i1; ++i) s += a[i] * b[i];
+    part[c] = s;
+  }
   double s = 0.0;
-#pragma omp parallel for reduction(+ : s) schedule(static)
-  for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+  for (int c = 0; c < nchunk; ++c) s += part[c];
   return s;
 }
 
