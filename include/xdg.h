@@ -448,7 +448,8 @@ typedef struct {
 
 /* Build the hierarchies of n problems (layout of each as in xdg_problem; host arrays, deep
  * copied). Every index is validated against the problem's own sizes (EINVAL names the
- * problem). Supported: Np in {6, 10, 15, 20}, at most 4096 DOF on each problem's coarsest
+ * problem). Supported: Np in {6, 10, 15, 20} (another Np: XDG_EINVAL, naming the problem, before
+ * any CUDA call), at most 4096 DOF on each problem's coarsest
  * level, at most 65535 problems per group. opts apply to every problem (omega <= 0 gives each
  * problem its own Lanczos-based damping per level). stream: as in xdg_create_hierarchy (all
  * work of the batch is ordered on it). */

@@ -3999,7 +3999,14 @@ int xdg_create_batch(int n, const xdg_problem* probs, const xdg_hier_opts* o, vo
   }
   *out = nullptr;
   auto t0 = clk::now();
-  for (int i = 0; i < n; ++i) TRY(validate_problem(probs[i], i));  // host only, before any CUDA call
+  for (int i = 0; i < n; ++i) {  // host only, before any CUDA call
+    const int np = probs[i].Np;
+    if (np != 6 && np != 10 && np != 15 && np != 20) {
+      set_err("problem %d: Np = %d: batches take Np 6, 10, 15 or 20", i, np);
+      return XDG_EINVAL;
+    }
+    TRY(validate_problem(probs[i], i));
+  }
   std::unique_ptr<xdg_batch> bt(new xdg_batch());
   bt->n = n;
   bt->stream = static_cast<cudaStream_t>(stream);

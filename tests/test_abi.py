@@ -88,6 +88,17 @@ def test_batch_validation_names_the_problem_without_gpu():
         assert ("problem %d" % idx) in msg and word in msg, msg
 
 
+def test_batch_rejects_unsupported_block_sizes_without_gpu():
+    """Batches take the block sizes of the low-precision cycle (6, 10, 15, 20): another Np is
+    refused on the host, naming the problem, before any CUDA call."""
+    import xdg_problem as xp
+    ok = xp.Problem(xp.batch_configs(1, seed=5, N_range=(8, 8), ks=(2,), max_levels=3)[0])
+    wide = xp.Problem(xp.Config(D=3, N=2, k=5, c=(0.5, 0.5, 0.5), R=0.3, max_levels=1))
+    assert wide.Np == 56
+    rc, msg = _batch_rc([ok, wide])
+    assert rc == xdg.XDG_EINVAL and "problem 1" in msg and "Np = 56" in msg, msg
+
+
 def test_binding_argument_counts_match_prototypes():
     """Every ctypes signature has as many arguments as the header's prototype."""
     protos = {}
