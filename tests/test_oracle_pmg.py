@@ -50,6 +50,23 @@ def test_pmg_matches_dense_restatement(prob, n_lo):
     assert np.all(got.reshape(-1, P.Np)[out] == 0.0)
 
 
+@pytest.fixture(scope="module")
+def prob_k5():
+    return xp.Problem(xp.Config(D=3, N=3, k=5, c=(0.5, 0.47, 0.52), R=0.3, muA=1, muB=1000, max_levels=2))
+
+
+@pytest.mark.parametrize("n_lo", [4, 20])
+def test_pmg_k5_matches_dense_restatement(prob_k5, n_lo):
+    """3D k = 5 (Np = 56) with the paper's low orders k_lo = 1 and 3 (n_lo = 4, 20): the
+    reference of the GPU's wide-block p-multigrid tests."""
+    P = prob_k5
+    H = oracle.Hierarchy(P)
+    A = dense_from_bsr(P.row_ptr, P.col, P.val)
+    b = np.random.default_rng(3).standard_normal(P.dof)
+    ref = _dense_pmg(A, P.Np, n_lo, b, range(P.nb[0]))
+    assert np.linalg.norm(H.pmg(0, n_lo, b) - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
 def test_pmg_special_cases(prob):
     P = prob
     H = oracle.Hierarchy(P)
