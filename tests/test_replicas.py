@@ -83,3 +83,6 @@ def test_reference_arm_line_keeps_the_contract():
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
     e = d["e2e"]
     assert e["value"] == d["value"] and e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+    # ms_per_step is the measured step (the sample); value extrapolates it to the full solve
+    assert d["extrapolated_solve_ms"] >= d["ms_per_step"] > 0
+    assert abs(d["value"] - d["config"]["dof"] / d["extrapolated_solve_ms"] / 1e3) <= 1e-9 * d["value"]
